@@ -1,0 +1,140 @@
+"""Closed forms written straight from the paper's statement of the problem,
+used to pin the oracle to something other than itself.
+
+* ``laplacian_dense``: the cell-centred Neumann Laplacian as a Kronecker sum
+  of 1-D second differences (textbook construction, mirror ghost cells).
+* ``operator_dense``: the damped semi-implicit system of Sec. 2.1, written
+  row block by row block from its component expansion (three scalar
+  equations, each holding the cross-product terms and the alpha-terms), then
+  divided by dt.  Unknown order [m1; m2; m3] (component-major).
+* ``dct_solve``: exact solution for a spatially constant unit m~ by the
+  DCT-II diagonalisation of the Neumann Laplacian.
+* ``manufactured``: an exact smooth unit field and the forcing that makes it
+  solve the damped LL equation, for the time-convergence pin.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft as sfft
+
+
+def second_difference_1d(n: int, h: float) -> np.ndarray:
+    """1-D cell-centred second difference with homogeneous Neumann ends."""
+    t = np.zeros((n, n))
+    for i in range(n):
+        if i > 0:
+            t[i, i - 1] += 1.0
+            t[i, i] -= 1.0
+        if i < n - 1:
+            t[i, i + 1] += 1.0
+            t[i, i] -= 1.0
+    return t / (h * h)
+
+
+def laplacian_dense(nx: int, ny: int, nz: int, h: float) -> np.ndarray:
+    ix, iy, iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    tx, ty, tz = (second_difference_1d(n, h) for n in (nx, ny, nz))
+    return (np.kron(iz, np.kron(iy, tx)) + np.kron(iz, np.kron(ty, ix))
+            + np.kron(tz, np.kron(iy, ix)))
+
+
+def operator_dense(nx, ny, nz, h, alpha, dt, m) -> np.ndarray:
+    """Dense system matrix from the component form of the damped scheme.
+
+    Row 1 (Sec. 2.1): m1 + dt(m2 D m3 - m3 D m2)
+                      + alpha dt[-(m2^2+m3^2) D m1 + m1 m2 D m2 + m1 m3 D m3]
+    and rows 2, 3 as printed, all divided by dt (right-hand side m^n/dt).
+    """
+    n = nx * ny * nz
+    m = np.asarray(m, np.float64).reshape(3, n)
+    m1, m2, m3 = m
+    L = laplacian_dense(nx, ny, nz, h)
+    I = np.eye(n)
+
+    def d(v):
+        return np.diag(v) @ L
+
+    a = alpha
+    blocks = [
+        [I / dt + d(-a * (m2 ** 2 + m3 ** 2)), d(-m3 + a * m1 * m2), d(m2 + a * m1 * m3)],
+        [d(m3 + a * m1 * m2), I / dt + d(-a * (m1 ** 2 + m3 ** 2)), d(-m1 + a * m2 * m3)],
+        [d(-m2 + a * m1 * m3), d(m1 + a * m2 * m3), I / dt + d(-a * (m1 ** 2 + m2 ** 2))],
+    ]
+    return np.block(blocks)
+
+
+def _frame(mdir):
+    """Right-handed orthonormal frame (e1, e2, m) with e1 x e2 = m."""
+    m = np.asarray(mdir, np.float64)
+    m = m / np.linalg.norm(m)
+    t = np.array([1.0, 0.0, 0.0]) if abs(m[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = t - m * (m @ t)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(m, e1)
+    return e1, e2, m
+
+
+def dct_solve(nx, ny, nz, h, alpha, dt, mdir, b) -> np.ndarray:
+    """Exact solution of A x = b for the constant unit field m~ = mdir.
+
+    In the frame (e1, e2, m): C(m) maps e1 -> e2 - alpha e1 and
+    e2 -> -e1 - alpha e2 and kills m, so w = x.e1 + i x.e2 obeys
+    w/dt + (i - alpha) Delta_h w = b.e1 + i b.e2 and x.m = dt b.m.
+    Delta_h is diagonal in the orthonormal DCT-II basis with eigenvalues
+    -(4/h^2) sum_d sin^2(pi k_d / (2 n_d)).
+    """
+    e1, e2, m = _frame(mdir)
+    b = np.asarray(b, np.float64).reshape(3, nz, ny, nx)
+    be1 = np.tensordot(e1, b, axes=(0, 0))
+    be2 = np.tensordot(e2, b, axes=(0, 0))
+    bm = np.tensordot(m, b, axes=(0, 0))
+    kz, ky, kx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lam = -(4.0 / h ** 2) * (np.sin(np.pi * kx / (2 * nx)) ** 2 + np.sin(np.pi * ky / (2 * ny)) ** 2
+                             + np.sin(np.pi * kz / (2 * nz)) ** 2)
+    denom = 1.0 / dt + (1j - alpha) * lam
+    beta_hat = sfft.dctn(be1, type=2, norm="ortho") + 1j * sfft.dctn(be2, type=2, norm="ortho")
+    w_hat = beta_hat / denom
+    wr = sfft.idctn(w_hat.real, type=2, norm="ortho")
+    wi = sfft.idctn(w_hat.imag, type=2, norm="ortho")
+    a3 = dt * bm
+    x = (e1[:, None, None, None] * wr + e2[:, None, None, None] * wi
+         + m[:, None, None, None] * a3)
+    return x.reshape(-1)
+
+
+class Manufactured:
+    """m_e = (sin th cos phi, sin th sin phi, cos th), th = pi/4,
+    phi = t + cos(pi x) cos(pi y) on the unit square (zero normal derivative
+    on the boundary).  forcing(t) = d_t m_e + m_e x Delta m_e
+    + alpha m_e x (m_e x Delta m_e), so that m_e solves
+    d_t m = -m x Delta m - alpha m x (m x Delta m) + f."""
+
+    def __init__(self, n: int, alpha: float):
+        self.n, self.alpha = n, alpha
+        s = (np.arange(n) + 0.5) / n
+        self.Y, self.X = np.meshgrid(s, s, indexing="ij")
+        self.th = np.pi / 4
+
+    def phi(self, t):
+        return t + np.cos(np.pi * self.X) * np.cos(np.pi * self.Y)
+
+    def m(self, t):
+        p = self.phi(t)
+        s, c = np.sin(self.th), np.cos(self.th)
+        return np.stack([s * np.cos(p), s * np.sin(p), c + 0 * p])[:, None]
+
+    def forcing(self, t):
+        X, Y = self.X, self.Y
+        p = self.phi(t)
+        s = np.sin(self.th)
+        grad2 = np.pi ** 2 * (np.sin(np.pi * X) ** 2 * np.cos(np.pi * Y) ** 2
+                              + np.cos(np.pi * X) ** 2 * np.sin(np.pi * Y) ** 2)
+        lap = -2 * np.pi ** 2 * np.cos(np.pi * X) * np.cos(np.pi * Y)
+        dcos = -np.sin(p) * lap - np.cos(p) * grad2
+        dsin = np.cos(p) * lap - np.sin(p) * grad2
+        me = self.m(t)[:, 0]
+        lm = np.stack([s * dcos, s * dsin, 0 * p])
+        dt_m = np.stack([-s * np.sin(p), s * np.cos(p), 0 * p])
+        c1 = np.cross(me, lm, axis=0)
+        c2 = np.cross(me, c1, axis=0)
+        return (dt_m + c1 + self.alpha * c2)[:, None]

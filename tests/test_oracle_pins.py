@@ -1,0 +1,426 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: the
+paper's component form (Sec. 2.1), textbook Neumann Laplacians, the DCT
+closed form for a constant field, dense direct solves, the Galerkin
+identity (Eq. galerkin / Eq. Ac_direct) by an independent sparse product,
+the GCR identity r_m = b - A u_m (Sec. 3.1.2), first-order convergence in
+time on a manufactured solution, and an independent restatement of the
+aggregation rule.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from paper_2608_09102_b300 import inputs
+from tests import aggregation_bruteforce as bf
+from tests import reference_forms as rf
+
+
+def _rand_m(n, seed, unit=False):
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal((3, n))
+    if unit:
+        m /= np.linalg.norm(m, axis=0)
+    return m.reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# operator (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("grid", [(3, 3, 3), (4, 3, 1), (5, 1, 1), (2, 3, 2)])
+def test_operator_matches_component_form(grid):
+    nx, ny, nz = grid
+    n = nx * ny * nz
+    h, alpha, dt = 0.37, 0.3, 0.011
+    m = _rand_m(n, 1)  # deliberately not unit length
+    H = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(coarsest_cells=10 ** 6))
+    A = H.matrix(0).toarray()
+    ref = rf.operator_dense(nx, ny, nz, h, alpha, dt, m)
+    np.testing.assert_allclose(A, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_constant_vectors_see_only_the_mass_term():
+    """Delta_h c = 0 under Neumann conditions, so A c = c/dt for any m~."""
+    grid = (6, 5, 4)
+    n = 120
+    H = oracle.Hierarchy(grid, 0.1, 0.05, 1e-3, _rand_m(n, 2, unit=True), oracle.Params())
+    c = np.repeat(np.array([0.3, -1.2, 2.0]), n)
+    np.testing.assert_allclose(H.apply(c), c / 1e-3, rtol=1e-12)
+
+
+def test_pointwise_orthogonality_of_the_solution():
+    """m_k^T C(m_k) = 0, so m_k.(A x)_k = m_k.x_k/dt: with b = m/dt the
+    solution satisfies m_k.x_k - 1 = -dt m_k.r_k in every cell."""
+    grid = (24, 24, 1)
+    n = 576
+    h, alpha, dt = 1 / 24, 0.1, 2e-3
+    m = inputs.smooth_field(24, 24, 1, seed=3).reshape(-1)
+    H = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-9))
+    b = m / dt
+    x, st, it, rr = H.solve(b, np.zeros_like(b))
+    assert st == oracle.OK and rr < 1e-9
+    r = b - H.apply(x)
+    mx = (m.reshape(3, n) * x.reshape(3, n)).sum(0)
+    mr = (m.reshape(3, n) * r.reshape(3, n)).sum(0)
+    np.testing.assert_allclose(mx - 1.0, -dt * mr, rtol=0, atol=1e-12)
+    assert np.all(np.linalg.norm(x.reshape(3, n), axis=0) >= 1.0 - 1e-7)
+
+
+# --------------------------------------------------------------------------
+# whole solve against exact solutions
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("grid,mdir,alpha", [((32, 32, 1), (0, 0, 1), 0.1),
+                                             ((12, 10, 8), (0.3, -0.4, 0.8), 0.02),
+                                             ((40, 1, 1), (1, 2, 2), 1.0)])
+def test_solve_matches_dct_closed_form(grid, mdir, alpha):
+    nx, ny, nz = grid
+    n = nx * ny * nz
+    h, dt = 1.0 / nx, 4.0 / nx ** 2
+    m = inputs.constant_field(nx, ny, nz, mdir).reshape(-1)
+    b = inputs.rhs_field(nx, ny, nz, seed=5).reshape(-1)
+    H = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-13, coarsest_cells=8))
+    x, st, it, rr = H.solve(b)
+    assert st == oracle.OK
+    xe = rf.dct_solve(nx, ny, nz, h, alpha, dt, mdir, b)
+    assert np.linalg.norm(x - xe) <= 1e-10 * np.linalg.norm(xe)
+
+
+@pytest.mark.parametrize("grid,alpha,seed", [((4, 4, 2), 0.3, 0), ((6, 5, 1), 0.02, 1), ((7, 1, 1), 1.0, 2)])
+def test_solve_matches_dense_direct(grid, alpha, seed):
+    nx, ny, nz = grid
+    n = nx * ny * nz
+    h, dt = 1.0 / nx, 2.0 / nx ** 2
+    m = _rand_m(n, seed, unit=True)
+    b = np.random.default_rng(seed + 7).standard_normal(3 * n)
+    H = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-14, coarsest_cells=2))
+    assert H.nlevels >= 2
+    x, st, it, rr = H.solve(b)
+    xe = np.linalg.solve(rf.operator_dense(nx, ny, nz, h, alpha, dt, m), b)
+    assert np.linalg.norm(x - xe) <= 1e-10 * np.linalg.norm(xe)
+
+
+def test_constant_field_is_a_fixed_point():
+    """For constant m~ = m^n the system returns x = m^n exactly (Sec. 4's
+    trivial initial state): 0 iterations from the guess m^n."""
+    nx = ny = 16
+    m = inputs.trivial_state(nx, ny, 1).reshape(-1)
+    dt = 1e-3
+    H = oracle.Hierarchy((nx, ny, 1), 1 / nx, 0.01, dt, m, oracle.Params(rtol=1e-10))
+    x, st, it, rr = H.solve(m / dt, m)
+    assert st == oracle.OK and it == 0 and rr < 1e-14
+    x0, st0, it0, rr0 = H.solve(m / dt)
+    assert st0 == oracle.OK and it0 <= 3
+    np.testing.assert_allclose(x0, m, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Galerkin (Eq. galerkin, Eq. Ac_direct) and aggregation (Eq. Pagg)
+# --------------------------------------------------------------------------
+
+def _boolean_p(agg, nc):
+    n = agg.size
+    p = sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, nc))
+    return sp.kron(sp.eye(3), p).tocsr()  # component-major at both levels
+
+
+@pytest.mark.parametrize("grid", [(12, 10, 1), (6, 6, 5)])
+def test_galerkin_equals_independent_product(grid):
+    nx, ny, nz = grid
+    n = nx * ny * nz
+    m = _rand_m(n, 4, unit=True)
+    H = oracle.Hierarchy(grid, 0.2, 0.07, 1e-2, m, oracle.Params(coarsest_cells=4))
+    assert H.nlevels >= 3
+    for l in range(H.nlevels - 1):
+        A = H.matrix(l)
+        P = _boolean_p(H.agg(l), H.cells(l + 1))
+        Ac = (P.T @ A @ P).toarray()
+        got = H.matrix(l + 1).toarray()
+        np.testing.assert_allclose(got, Ac, rtol=0, atol=1e-12 * np.abs(Ac).max())
+
+
+def test_galerkin_entrywise_double_sum_on_tiny_grid():
+    """(A_c)_ij = sum_{k in G_i} sum_{l in G_j} a_kl, evaluated by brute force."""
+    grid = (4, 4, 1)
+    n = 16
+    m = _rand_m(n, 9)
+    H = oracle.Hierarchy(grid, 0.5, 0.2, 0.1, m, oracle.Params(coarsest_cells=2))
+    A = rf.operator_dense(4, 4, 1, 0.5, 0.2, 0.1, m)
+    agg = H.agg(0)
+    nc = H.cells(1)
+    ref = np.zeros((3 * nc, 3 * nc))
+    for c in range(3):
+        for k in range(n):
+            for c2 in range(3):
+                for l in range(n):
+                    ref[c * nc + agg[k], c2 * nc + agg[l]] += A[c * n + k, c2 * n + l]
+    np.testing.assert_allclose(H.matrix(1).toarray(), ref, atol=1e-12 * np.abs(ref).max())
+
+
+def test_galerkin_preserves_constants():
+    """A_l (1 (x) c) = |G_I| c/dt: constants see only the mass term on every
+    level, |G_I| the number of grid cells in the composite aggregate."""
+    grid = (10, 9, 7)
+    n = 630
+    dt = 3e-3
+    H = oracle.Hierarchy(grid, 0.1, 0.3, dt, _rand_m(n, 11, unit=True), oracle.Params(coarsest_cells=4))
+    comp = np.arange(n)
+    for l in range(H.nlevels):
+        nl = H.cells(l)
+        size = np.bincount(comp, minlength=nl).astype(float)
+        c = np.array([1.5, -0.5, 0.25])
+        v = np.repeat(c, nl)
+        np.testing.assert_allclose(H.apply(v, l), np.kron(c, size) / dt, rtol=1e-10)
+        if l < H.nlevels - 1:
+            comp = H.agg(l)[comp]
+
+
+@pytest.mark.parametrize("grid", [(64, 64, 1), (16, 16, 16), (200, 1, 1)])
+def test_aggregates_partition_and_coarsen_by_about_four(grid):
+    nx, ny, nz = grid
+    n = nx * ny * nz
+    H = oracle.Hierarchy(grid, 1 / nx, 0.1, 1e-3, inputs.smooth_field(nx, ny, nz).reshape(-1),
+                         oracle.Params(coarsest_cells=64))
+    for l in range(H.nlevels - 1):
+        agg = H.agg(l)
+        nl, nc = H.cells(l), H.cells(l + 1)
+        assert agg.min() == 0 and agg.max() == nc - 1
+        sizes = np.bincount(agg, minlength=nc)
+        assert sizes.min() >= 1
+        # numbering = rank of the smallest member
+        first = np.full(nc, nl)
+        np.minimum.at(first, agg, np.arange(nl))
+        assert np.all(np.diff(first) > 0)
+        if l == 0:
+            assert 2.5 < nl / nc <= 4.6, (l, nl, nc)
+
+
+def _grid_adj(nx, ny, nz):
+    H = oracle.Hierarchy((nx, ny, nz), 1.0, 0.1, 1.0, inputs.constant_field(nx, ny, nz).reshape(-1),
+                         oracle.Params(coarsest_cells=10 ** 6))
+    return H.graph(0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 12345])
+def test_aggregation_equals_independent_restatement(seed):
+    rng = np.random.default_rng(seed)
+    graphs = [_grid_adj(9, 7, 1), _grid_adj(4, 4, 4)]
+    # a random symmetric weighted graph
+    n = 60
+    W = np.zeros((n, n), np.int32)
+    for _ in range(180):
+        i, j = rng.integers(0, n, 2)
+        if i != j:
+            W[i, j] = W[j, i] = rng.integers(1, 9)
+    S = sp.csr_matrix(W)
+    S.sort_indices()
+    graphs.append((S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.int32)))
+    # and a coarse level of a real hierarchy (weights > 1)
+    H = oracle.Hierarchy((12, 12, 6), 0.1, 0.1, 1e-3, inputs.smooth_field(12, 12, 6).reshape(-1),
+                         oracle.Params(coarsest_cells=8, seed=seed))
+    graphs.append(H.graph(1))
+    for rp, ci, w in graphs:
+        adj = bf.to_adj(rp, ci, w)
+        got, nc = oracle.aggregate_graph(rp, ci, w, seed=seed)
+        ref, nref = bf.aggregate(adj, seed=seed)
+        assert nc == nref
+        assert got.tolist() == ref
+        g1, n1 = oracle.matching_pass(rp, ci, w, seed=seed)
+        r1, m1 = bf.matching_pass(adj, seed=seed)
+        assert n1 == m1 and g1.tolist() == r1
+        col, _ = oracle.colour_graph(rp, ci, seed=seed)
+        assert col.tolist() == bf.colour(adj, seed=seed)
+
+
+def test_round_cap_is_respected():
+    rp, ci, w = _grid_adj(16, 16, 1)
+    adj = bf.to_adj(rp, ci, w)
+    for R in (1, 2, 3):
+        got, nc = oracle.matching_pass(rp, ci, w, rounds=R)
+        ref, nref = bf.matching_pass(adj, rounds=R)
+        assert got.tolist() == ref
+    one, n_one = oracle.matching_pass(rp, ci, w, rounds=1)
+    full, n_full = oracle.matching_pass(rp, ci, w, rounds=32)
+    assert n_full < n_one
+
+
+def test_hash_functions_match_restatement():
+    for a, b, s in [(0, 1, 0), (7, 12345, 3), (2 ** 20, 2 ** 30 + 5, 0xDEADBEEF)]:
+        assert oracle.edge_hash(a, b, s) == bf.edge_hash(a, b, s)
+        assert oracle.vertex_hash(a, s) == bf.vertex_hash(a, s)
+    assert bf.fmix32(0) == 0
+
+
+def test_colourings_are_proper():
+    grid = (20, 20, 1)
+    H = oracle.Hierarchy(grid, 0.05, 0.1, 1e-3, inputs.smooth_field(20, 20, 1).reshape(-1),
+                         oracle.Params(coarsest_cells=4))
+    c0 = H.colours(0).reshape(20, 20)
+    yy, xx = np.mgrid[0:20, 0:20]
+    assert np.array_equal(c0, (xx + yy) % 2)
+    for l in range(H.nlevels):
+        rp, ci, _ = H.graph(l)
+        col = H.colours(l)
+        for i in range(H.cells(l)):
+            for p in range(rp[i], rp[i + 1]):
+                assert col[i] != col[ci[p]]
+
+
+# --------------------------------------------------------------------------
+# smoother, coarse solve, V-cycle
+# --------------------------------------------------------------------------
+
+def test_gauss_seidel_fixed_point_and_convergence():
+    grid = (8, 6, 1)
+    n = 48
+    m = _rand_m(n, 13, unit=True)
+    H = oracle.Hierarchy(grid, 1.0, 0.5, 0.05, m, oracle.Params(coarsest_cells=2))
+    A = rf.operator_dense(8, 6, 1, 1.0, 0.5, 0.05, m)
+    b = np.random.default_rng(3).standard_normal(3 * n)
+    xe = np.linalg.solve(A, b)
+    for fwd in (True, False):
+        np.testing.assert_allclose(H.smooth(b, xe, fwd), xe, rtol=0, atol=1e-12 * np.abs(xe).max())
+    x = np.zeros(3 * n)
+    for _ in range(60):
+        x = H.smooth(b, x, True)
+    assert np.linalg.norm(x - xe) < 1e-8 * np.linalg.norm(xe)
+
+
+def test_gauss_seidel_on_coarse_level_converges():
+    grid = (10, 10, 1)
+    H = oracle.Hierarchy(grid, 0.1, 0.3, 1e-2, _rand_m(100, 14, unit=True), oracle.Params(coarsest_cells=4))
+    A1 = H.matrix(1).toarray()
+    b = np.random.default_rng(5).standard_normal(A1.shape[0])
+    xe = np.linalg.solve(A1, b)
+    np.testing.assert_allclose(H.smooth(b, xe, True, l=1), xe, atol=1e-11 * np.abs(xe).max())
+    x = np.zeros_like(b)
+    for _ in range(200):
+        x = H.smooth(b, x, True, l=1)
+    assert np.linalg.norm(x - xe) < 1e-6 * np.linalg.norm(xe)
+
+
+def test_coarsest_lu_is_exact():
+    H = oracle.Hierarchy((16, 16, 1), 1 / 16, 0.1, 1e-3, inputs.smooth_field(16, 16, 1).reshape(-1),
+                         oracle.Params(coarsest_cells=40))
+    L = H.nlevels - 1
+    Ac = H.matrix(L).toarray()
+    b = np.random.default_rng(1).standard_normal(Ac.shape[0])
+    np.testing.assert_allclose(H.coarse_solve(b), np.linalg.solve(Ac, b), rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(H.vcycle(b, l=L), np.linalg.solve(Ac, b), rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("grid,mdir,alpha", [((16, 16, 1), None, 0.1), ((8, 8, 1), (0, 0, 1), 0.02),
+                                             ((6, 6, 6), (0.6, 0, 0.8), 0.1)])
+def test_vcycle_contracts(grid, mdir, alpha):
+    """Spectral radius of the V-cycle error propagation I - B A below one
+    (constant fields, and a vortex resolved by the grid)."""
+    nx, ny, nz = grid
+    n = nx * ny * nz
+    m = (inputs.vortex(nx, ny, nz) if mdir is None else inputs.constant_field(nx, ny, nz, mdir)).reshape(-1)
+    H = oracle.Hierarchy(grid, 1 / nx, alpha, 8.0 / nx ** 2, m, oracle.Params(coarsest_cells=4))
+    assert H.nlevels >= 3
+    A = H.matrix(0).toarray()
+    B = np.column_stack([H.vcycle(e) for e in np.eye(3 * n)])
+    rho = np.abs(np.linalg.eigvals(np.eye(3 * n) - B @ A)).max()
+    assert rho < 0.9
+
+
+# --------------------------------------------------------------------------
+# GCR (Algorithm 1)
+# --------------------------------------------------------------------------
+
+def test_gcr_recurrence_equals_true_residual():
+    """r_m = b - A u_m (Sec. 3.1.2): stop after j iterations (no restart) and
+    compare the recurrence residual with the true residual."""
+    grid = (20, 20, 1)
+    m = inputs.smooth_field(20, 20, 1, seed=2).reshape(-1)
+    b = inputs.rhs_field(20, 20, 1, seed=2).reshape(-1)
+    for j in (1, 3, 7):
+        H = oracle.Hierarchy(grid, 0.05, 0.1, 1e-2, m, oracle.Params(maxit=j, restart=j, rtol=1e-30))
+        x, st, it, rr, hist = H.solve(b, history=True)
+        assert it == j and st == oracle.NOT_CONVERGED
+        assert abs(hist[-1] - rr) <= 1e-9 * rr
+
+
+def test_gcr_with_exact_preconditioner_takes_one_iteration():
+    grid = (5, 4, 3)
+    n = 60
+    m = _rand_m(n, 21, unit=True)
+    b = np.random.default_rng(2).standard_normal(3 * n)
+    H = oracle.Hierarchy(grid, 0.3, 0.05, 0.02, m, oracle.Params(prec=2, rtol=1e-12))
+    x, st, it, rr = H.solve(b)
+    assert st == oracle.OK and it == 1 and rr < 1e-12
+
+
+def test_unpreconditioned_gcr_reaches_dense_solution():
+    grid = (6, 6, 1)
+    m = _rand_m(36, 22, unit=True)
+    b = np.random.default_rng(3).standard_normal(108)
+    H = oracle.Hierarchy(grid, 1 / 6, 0.1, 0.05, m, oracle.Params(prec=1, rtol=1e-13, restart=200))
+    x, st, it, rr = H.solve(b)
+    xe = np.linalg.solve(rf.operator_dense(6, 6, 1, 1 / 6, 0.1, 0.05, m), b)
+    assert st == oracle.OK and np.linalg.norm(x - xe) < 1e-10 * np.linalg.norm(xe)
+
+
+def test_zero_rhs_and_breakdown_free_statuses():
+    H = oracle.Hierarchy((8, 8, 1), 1 / 8, 0.1, 1e-2, inputs.smooth_field(8, 8, 1).reshape(-1), oracle.Params())
+    x, st, it, rr = H.solve(np.zeros(192), np.ones(192))
+    assert st == oracle.OK and it == 0 and np.all(x == 0)
+    bad = np.full(192, np.nan)
+    _, st2, _, _ = H.solve(bad)
+    assert st2 == oracle.BREAKDOWN
+
+
+# --------------------------------------------------------------------------
+# iteration counts and time stepping (Sec. 4)
+# --------------------------------------------------------------------------
+
+def test_iteration_counts_stay_bounded_under_refinement():
+    """Mesh-independent convergence (the paper's claim for the aggregation
+    solver), qualitatively: fixed dt/h^2, growing grids."""
+    its = []
+    for n in (32, 64, 128):
+        m = inputs.vortex(n, n, 1, seed=0).reshape(-1)
+        dt = 8.19 / n ** 2
+        H = oracle.Hierarchy((n, n, 1), 1 / n, 0.02, dt, m, oracle.Params(rtol=1e-8))
+        _, st, it, _ = H.solve(m / dt, m)
+        assert st == oracle.OK
+        its.append(it)
+    assert its[-1] <= its[0] + 10, its
+
+
+def test_projection_leaves_iteration_counts_unchanged():
+    """The paper observes that the projection m <- m/|m| does not change
+    the iteration numbers."""
+    n = 24
+    m0 = inputs.smooth_field(n, n, 1, seed=4).reshape(-1)
+    p = oracle.Params(rtol=1e-10)
+    m1, it1, _, s1 = oracle.step(m0, 4, (n, n, 1), 1 / n, 0.01, 1e-3, p, project=True)
+    m2, it2, _, s2 = oracle.step(m0, 4, (n, n, 1), 1 / n, 0.01, 1e-3, p, project=False)
+    assert s1 == s2 == oracle.OK
+    assert np.all(np.abs(it1 - it2) <= 2), (it1, it2)
+    assert np.allclose(np.linalg.norm(m1.reshape(3, -1), axis=0), 1.0, atol=1e-14)
+
+
+def test_first_order_convergence_in_time():
+    """BDF1 with first-order extrapolation of m~: the error of a manufactured
+    solution halves with dt (h fixed and fine)."""
+    n, alpha, T = 48, 0.1, 0.2
+    ms = rf.Manufactured(n, alpha)
+    errs = []
+    for nsteps in (10, 20, 40):
+        dt = T / nsteps
+        m = ms.m(0.0).reshape(-1)
+        for s in range(nsteps):
+            H = oracle.Hierarchy((n, n, 1), 1 / n, alpha, dt, m, oracle.Params(rtol=1e-12))
+            b = m / dt + ms.forcing((s + 1) * dt).reshape(-1)
+            m, st, it, rr = H.solve(b, m)
+            assert st == oracle.OK
+        errs.append(np.abs(m - ms.m(T).reshape(-1)).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.7 < r1 < 2.3 and 1.7 < r2 < 2.3, errs
