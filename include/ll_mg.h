@@ -1,0 +1,162 @@
+/*
+ * ll_mg.h -- C ABI of the B300 (sm_103a) aggregation-multigrid solver for the
+ * semi-implicit BDF1 Landau-Lifshitz system.
+ *
+ * The problem (Sec. 2.1, Sec. 2.2 of the paper): one time step of the damped
+ * scheme with first-order extrapolation m~ = m^n solves
+ *
+ *     (I + dt m~ x Delta_h + alpha dt m~ x (m~ x Delta_h)) m^{n+1} = m^n,
+ *
+ * one 3x3 block per cell coupled through the discrete Laplacian.  The library
+ * solves it divided by dt:  (A x)_k = x_k/dt + C(m~_k) (Delta_h x)_k with
+ * C(m) = [m]_x + alpha (m m^T - |m|^2 I), right-hand side m^n/dt (the relative
+ * residual is the same for both scalings).  Delta_h is the cell-centred
+ * 7-point (3-D), 5-point (2-D) or 3-point (1-D) Laplacian with spacing h and
+ * homogeneous Neumann boundaries (missing neighbours are left out).
+ *
+ * Solver (Sec. 3): aggregation algebraic multigrid -- two passes of pairwise
+ * matching per level, Boolean prolongation (Eq. Pagg), Galerkin coarse
+ * operators A_c = P^T A P (Eq. galerkin), block Gauss-Seidel smoothing, dense
+ * LU at the coarsest level -- as a V-cycle preconditioner of GCR
+ * (Algorithm 1), everything in hand-written CUDA kernels on one GPU.
+ *
+ * Layout of every field argument: structure of arrays, component-major,
+ * float64, 3*N values: m1 of all cells, then m2, then m3; within a component
+ * the cell (x, y, z) sits at x + nx*(y + ny*z).  N = nx*ny*nz.
+ *
+ * Ownership: the caller owns every field buffer; the library never keeps a
+ * pointer to one after a call returns.  The hierarchy (aggregates, coarse
+ * operators, workspaces) is owned by the library and freed by
+ * ll_mg_destroy.  Unless stated otherwise, pointers are DEVICE pointers on
+ * the current CUDA device, and all work is enqueued on `cuda_stream` (a
+ * cudaStream_t, NULL for the legacy default stream); calls return after the
+ * work they launched has completed.
+ *
+ * Errors: a return value of 0 (LL_OK) means success.  Positive values are
+ * numerical outcomes with the outputs written (best iterate, true residual).
+ * Negative values mean failure with the outputs untouched.
+ */
+#ifndef LL_MG_H
+#define LL_MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define LL_OK 0
+#define LL_NOT_CONVERGED 1    /* maxit reached; x = last iterate */
+#define LL_BREAKDOWN 2        /* non-finite residual or gamma_jj = 0 in GCR */
+#define LL_EINVAL (-1)        /* bad argument (null pointer, dt <= 0, ...) */
+#define LL_ECUDA (-2)         /* a CUDA runtime call failed */
+#define LL_ENOMEM (-3)        /* device allocation failed */
+#define LL_SINGULAR_COARSE (-4) /* zero pivot in the coarsest LU */
+#define LL_ELIMIT (-5)        /* a structural limit was exceeded (see below) */
+
+/* ---- precision of the V-cycle preconditioner ----------------------------- */
+#define LL_FP64 0        /* everything in float64 */
+#define LL_MIXED_FP32 1  /* V-cycle vectors and operators in float32, GCR float64 */
+
+typedef struct ll_grid {
+  int nx, ny, nz; /* cells per direction; ny = nz = 1 for 1-D, nz = 1 for 2-D */
+} ll_grid;
+
+/* Solver parameters.  Fill with ll_mg_default_params(). */
+typedef struct ll_mg_params {
+  double rtol;         /* stop when ||b - A x||_2 < rtol ||b||_2      (1e-8) */
+  int maxit;           /* GCR iterations in total, over restarts      (1000) */
+  int restart;         /* GCR restart length, 1..64                   (20)   */
+  int nu_pre;          /* forward block-GS sweeps before restriction  (1)    */
+  int nu_post;         /* backward block-GS sweeps after prolongation (1)    */
+  int coarsest_cells;  /* stop coarsening at or below this many cells (64)   */
+  int max_levels;      /* at most this many levels, 1..32             (20)   */
+  int rounds;          /* handshake rounds per matching pass          (32)   */
+  unsigned int seed;   /* tie-break hash seed of matching, colouring  (0)    */
+  int precision;       /* LL_FP64 or LL_MIXED_FP32                    (LL_FP64) */
+} ll_mg_params;
+
+typedef struct ll_mg_hierarchy ll_mg_hierarchy; /* opaque, library-owned */
+
+/* Fill *p with the defaults listed above. */
+void ll_mg_default_params(ll_mg_params* p);
+
+/* Build the hierarchy for one time step (Sec. 3.1.1: aggregation, Galerkin
+ * coarse operators; Sec. 3: smoother and coarsest factorisation).
+ *   m_tilde  device, SoA 3*N float64: the frozen field m~ = m^n (any length;
+ *            the operator uses |m~|^2 as written).  Read during the call only.
+ *   alpha >= 0, dt > 0, h > 0; grid with nx >= 1, ny >= 1, nz >= 1, N >= 2.
+ *   p        parameters (NULL: defaults).
+ *   out      receives the new hierarchy.
+ * Aggregates depend on the grid only (integer graph weights), so they are
+ * computed here once; ll_mg_update reuses them.
+ * Errors: LL_EINVAL, LL_ENOMEM, LL_ECUDA, LL_SINGULAR_COARSE, LL_ELIMIT (a
+ * coarse graph needs more than 128 colours, or N >= 2^30). */
+int ll_mg_setup(const double* m_tilde, double alpha, double dt, double h, ll_grid grid,
+                const ll_mg_params* p, void* cuda_stream, ll_mg_hierarchy** out);
+
+/* Recompute the numeric part (operators, smoother blocks, coarsest LU) for
+ * a new m~, alpha, dt on the same grid (the system changes every step,
+ * Sec. 2.2).  Errors as ll_mg_setup. */
+int ll_mg_update(ll_mg_hierarchy* H, const double* m_tilde, double alpha, double dt);
+
+/* Solve A x = rhs by V-cycle-preconditioned GCR (Algorithm 1, restarted).
+ *   rhs        device, SoA 3*N float64 (read only).
+ *   x          device, SoA 3*N float64: initial guess in, solution out.
+ *   rtol       relative tolerance on the true residual (<= 0: the
+ *              hierarchy's parameter).
+ *   iterations host, optional: preconditioner applications, summed over
+ *              restarts.
+ *   rel_residual host, optional: ||rhs - A x||_2 / ||rhs||_2 of the returned
+ *              x, recomputed in float64 from the true residual.
+ * Returns LL_OK, LL_NOT_CONVERGED or LL_BREAKDOWN (x written), or an error. */
+int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, int* iterations,
+                double* rel_residual);
+
+/* n_steps time steps of the semi-implicit scheme with projection (Sec. 4):
+ * per step m~ = m, rhs = m/dt, solve from the guess m, then m <- x/|x| per
+ * cell.  Aggregates are computed once; each step redoes the numeric setup.
+ *   m               device SoA 3*N float64, in/out (cells must be nonzero).
+ *   iters_per_step  host, optional, n_steps ints.
+ *   relres_per_step host, optional, n_steps doubles.
+ * Returns the worst status over the steps (errors stop early). */
+int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid grid,
+            const ll_mg_params* p, void* cuda_stream, int* iters_per_step, double* relres_per_step);
+
+/* Release the hierarchy and all its device memory (NULL is ignored). */
+void ll_mg_destroy(ll_mg_hierarchy* H);
+
+/* Human-readable text of a status code (static storage). */
+const char* ll_status_string(int status);
+
+/* ---- introspection (for tests and benchmarks) ------------------------------ */
+
+/* Number of levels (level 0 = the grid). */
+int ll_mg_levels(const ll_mg_hierarchy* H);
+/* Cells on level l, or -1. */
+int ll_mg_level_cells(const ll_mg_hierarchy* H, int l);
+/* Copy the aggregate map of level l (cells of l -> cells of l+1, natural
+ * cell order on level 0) to the HOST buffer agg (ll_mg_level_cells(l) ints). */
+int ll_mg_level_aggregates(const ll_mg_hierarchy* H, int l, int* agg);
+/* Copy the colour of each cell of level l to the HOST buffer colour. */
+int ll_mg_level_colours(const ll_mg_hierarchy* H, int l, int* colour);
+/* Number of 3x3 blocks of the operator of level l >= 1 (BSR), or -1. */
+int ll_mg_level_blocks(const ll_mg_hierarchy* H, int l);
+/* Copy the BSR operator of level l >= 1 to HOST buffers: rowptr (n+1),
+ * col (nnzb), val (9*nnzb, each block row-major, component (r, c) at
+ * 3r + c, cell-major unknowns).  Values are float64 whatever the storage. */
+int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col, double* val);
+
+/* y = A_0 x on level 0 (device SoA buffers), float64. */
+int ll_mg_apply(ll_mg_hierarchy* H, const double* x, double* y);
+/* One V-cycle z = B r from level 0 (device SoA buffers), in the
+ * hierarchy's precision. */
+int ll_mg_vcycle(ll_mg_hierarchy* H, const double* r, double* z);
+/* One block Gauss-Seidel sweep on level l: x <- GS(b, x), forward (colours
+ * ascending) if forward != 0 else backward.  Device buffers; on level 0 SoA
+ * 3*N, on coarse levels cell-major 3*n_l.  float64 hierarchies only. */
+int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forward);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LL_MG_H */

@@ -122,6 +122,8 @@ def _load():
         "orc_matching_pass": (i, [i, _ip, _ip, _ip, i, u32, i, _ip]),
         "orc_colour_graph": (i, [i, _ip, _ip, u32, _ip]),
         "orc_edge_hash": (u32, [u32, u32, u32]),
+        "orc_operator_apply": (None, [i, i, i, d, d, d, _dp, _dp, _dp]),
+        "orc_grid_aggregates": (i, [i, i, i, i, u32, _ip]),
         "orc_vertex_hash": (u32, [u32, u32]),
     }
     for name, (res, args) in sig.items():
@@ -289,6 +291,23 @@ def colour_graph(rowptr, col, seed: int = 0):
     c = np.zeros(max(n, 1), np.int32)
     nc = _load().orc_colour_graph(n, rowptr, col, seed & 0xFFFFFFFF, c)
     return c[:n], nc
+
+
+def operator_apply(grid, h, alpha, dt, m, x):
+    """y = A x for the operator alone (assembled CSR, no hierarchy)."""
+    nx, ny, nz = _grid3(grid)
+    n = nx * ny * nz
+    y = np.zeros(3 * n)
+    _load().orc_operator_apply(nx, ny, nz, float(h), float(alpha), float(dt), _soa(m, n), _soa(x, n), y)
+    return y
+
+
+def grid_aggregates(grid, rounds: int = 32, seed: int = 0):
+    """Level-0 aggregates of the grid graph (natural cell order)."""
+    nx, ny, nz = _grid3(grid)
+    agg = np.zeros(nx * ny * nz, np.int32)
+    nc = _load().orc_grid_aggregates(nx, ny, nz, rounds, seed & 0xFFFFFFFF, agg)
+    return agg, nc
 
 
 def edge_hash(a: int, b: int, seed: int = 0) -> int:

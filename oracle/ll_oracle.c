@@ -1039,6 +1039,23 @@ void orc_coarse_solve(const orc_hier *H, double *x) {
   lu_solve(3 * H->lev[H->nlev - 1].n, H->lu, H->piv, x);
 }
 
+/* y = A x for the operator of Sec. 2.1 alone (no hierarchy): assembles the
+ * CSR matrix and multiplies; used for residual checks at full size. */
+void orc_operator_apply(int nx, int ny, int nz, double h, double alpha, double dt, const double *m,
+                        const double *x, double *y) {
+  csr_t A = assemble_operator(nx, ny, nz, h, alpha, dt, m);
+  csr_matvec(&A, x, y);
+  csr_free(&A);
+}
+
+/* Aggregates of the grid graph alone (level 0 -> 1), for full-size checks. */
+int orc_grid_aggregates(int nx, int ny, int nz, int rounds, uint32_t seed, int *agg) {
+  graph_t g = grid_graph(nx, ny, nz);
+  int nc = aggregate_level(&g, rounds, seed, agg);
+  graph_free(&g);
+  return nc;
+}
+
 /* Aggregation of an arbitrary weighted graph (for tests of the rule). */
 int orc_aggregate_graph(int n, const int *rowptr, const int *col, const int *w, int rounds, uint32_t seed,
                         int *agg) {

@@ -1,0 +1,267 @@
+"""B300-native aggregation-multigrid solver for the semi-implicit BDF1
+Landau-Lifshitz system (Python binding of the C ABI in ``include/ll_mg.h``).
+
+The binding only marshals arguments: every step of the solve runs in the
+hand-written sm_103a kernels of ``_lib/libllmg.so``.  PyTorch provides the
+device memory and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or no CUDA device is present the calls raise.
+
+Fields are float64 tensors holding 3*N values in component-major order (m1 of
+all cells, then m2, then m3; cell (x, y, z) at x + nx*(y + ny*z)), e.g. of
+shape (3, nz, ny, nx).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libllmg.so")
+
+LL_OK, LL_NOT_CONVERGED, LL_BREAKDOWN = 0, 1, 2
+LL_EINVAL, LL_ECUDA, LL_ENOMEM, LL_SINGULAR_COARSE, LL_ELIMIT = -1, -2, -3, -4, -5
+LL_FP64, LL_MIXED_FP32 = 0, 1
+
+# every symbol declared in include/ll_mg.h
+EXPORTS = (
+    "ll_mg_default_params", "ll_mg_setup", "ll_mg_update", "ll_mg_solve", "ll_step", "ll_mg_destroy",
+    "ll_status_string", "ll_mg_levels", "ll_mg_level_cells", "ll_mg_level_aggregates",
+    "ll_mg_level_colours", "ll_mg_level_blocks", "ll_mg_level_operator", "ll_mg_apply", "ll_mg_vcycle",
+    "ll_mg_smooth",
+)
+
+
+class LLError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (status %d)" % (what, status_string(status), status))
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
+        ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("coarsest_cells", ctypes.c_int),
+        ("max_levels", ctypes.c_int), ("rounds", ctypes.c_int), ("seed", ctypes.c_uint),
+        ("precision", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Params:
+    """Mirror of ``ll_mg_params`` with the library's defaults."""
+
+    rtol: float = 1e-8
+    maxit: int = 1000
+    restart: int = 20
+    nu_pre: int = 1
+    nu_post: int = 1
+    coarsest_cells: int = 64
+    max_levels: int = 20
+    rounds: int = 32
+    seed: int = 0
+    precision: int = LL_FP64
+
+    def _c(self) -> _Params:
+        return _Params(self.rtol, self.maxit, self.restart, self.nu_pre, self.nu_post, self.coarsest_cells,
+                       self.max_levels, self.rounds, self.seed & 0xFFFFFFFF, self.precision)
+
+
+_lib = None
+
+
+def load_library():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("the sm_103a library %s is missing; build it with "
+                           "paper_2608_09102_b300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    P = ctypes.POINTER(_Params)
+    sig = {
+        "ll_mg_default_params": (None, [P]),
+        "ll_mg_setup": (i, [vp, d, d, d, _Grid, P, vp, ctypes.POINTER(vp)]),
+        "ll_mg_update": (i, [vp, vp, d, d]),
+        "ll_mg_solve": (i, [vp, vp, vp, d, ip, dp]),
+        "ll_step": (i, [vp, i, d, d, d, _Grid, P, vp, ip, dp]),
+        "ll_mg_destroy": (None, [vp]),
+        "ll_status_string": (ctypes.c_char_p, [i]),
+        "ll_mg_levels": (i, [vp]),
+        "ll_mg_level_cells": (i, [vp, i]),
+        "ll_mg_level_aggregates": (i, [vp, i, vp]),
+        "ll_mg_level_colours": (i, [vp, i, vp]),
+        "ll_mg_level_blocks": (i, [vp, i]),
+        "ll_mg_level_operator": (i, [vp, i, vp, vp, vp]),
+        "ll_mg_apply": (i, [vp, vp, vp]),
+        "ll_mg_vcycle": (i, [vp, vp, vp]),
+        "ll_mg_smooth": (i, [vp, i, vp, vp, i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().ll_status_string(int(status)).decode()
+
+
+def default_params() -> Params:
+    c = _Params()
+    load_library().ll_mg_default_params(ctypes.byref(c))
+    return Params(c.rtol, c.maxit, c.restart, c.nu_pre, c.nu_post, c.coarsest_cells, c.max_levels, c.rounds,
+                  c.seed, c.precision)
+
+
+def _grid(grid) -> _Grid:
+    g = [int(v) for v in grid] + [1] * (3 - len(grid))
+    return _Grid(*g)
+
+
+def _field(t, n, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError("%s must be a float64 CUDA tensor" % name)
+    if not t.is_contiguous() or t.numel() != 3 * n:
+        raise ValueError("%s must be contiguous with 3*N = %d values" % (name, 3 * n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(st, what, ok=(LL_OK, LL_NOT_CONVERGED, LL_BREAKDOWN)):
+    if st not in ok:
+        raise LLError(st, what)
+    return st
+
+
+class Hierarchy:
+    """Library-owned multigrid hierarchy for one grid (``ll_mg_setup``)."""
+
+    def __init__(self, m_tilde, alpha, dt, h, grid, params: Params | None = None):
+        lib = load_library()
+        g = _grid(grid)
+        self.grid = (g.nx, g.ny, g.nz)
+        nx, ny, nz = self.grid
+        self.n = nx * ny * nz
+        self.params = params or Params()
+        self._h = ctypes.c_void_p()
+        self._cp = self.params._c()
+        st = lib.ll_mg_setup(_field(m_tilde, self.n, "m_tilde"), float(alpha), float(dt), float(h), _grid(grid),
+                             ctypes.byref(self._cp), _stream(), ctypes.byref(self._h))
+        _check(st, "ll_mg_setup", ok=(LL_OK,))
+
+    def close(self):
+        if self._h:
+            load_library().ll_mg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, m_tilde, alpha, dt):
+        st = load_library().ll_mg_update(self._h, _field(m_tilde, self.n, "m_tilde"), float(alpha), float(dt))
+        _check(st, "ll_mg_update", ok=(LL_OK,))
+
+    def solve(self, rhs, x, rtol: float = 0.0):
+        """Solve in place (x: initial guess in, solution out); returns
+        (status, iterations, true relative residual)."""
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load_library().ll_mg_solve(self._h, _field(rhs, self.n, "rhs"), _field(x, self.n, "x"), float(rtol),
+                                        ctypes.byref(it), ctypes.byref(rr))
+        _check(st, "ll_mg_solve")
+        return st, it.value, rr.value
+
+    # -- introspection ---------------------------------------------------
+    @property
+    def levels(self) -> int:
+        return load_library().ll_mg_levels(self._h)
+
+    def level_cells(self, l: int) -> int:
+        return load_library().ll_mg_level_cells(self._h, l)
+
+    def aggregates(self, l: int):
+        import numpy as np
+
+        out = np.zeros(self.level_cells(l), np.int32)
+        _check(load_library().ll_mg_level_aggregates(self._h, l, out.ctypes.data), "ll_mg_level_aggregates")
+        return out
+
+    def colours(self, l: int):
+        import numpy as np
+
+        out = np.zeros(self.level_cells(l), np.int32)
+        _check(load_library().ll_mg_level_colours(self._h, l, out.ctypes.data), "ll_mg_level_colours")
+        return out
+
+    def operator(self, l: int):
+        """BSR operator of level l >= 1 as (rowptr, col, val[nnzb, 3, 3])."""
+        import numpy as np
+
+        lib = load_library()
+        n = self.level_cells(l)
+        nb = lib.ll_mg_level_blocks(self._h, l)
+        rp = np.zeros(n + 1, np.int32)
+        ci = np.zeros(nb, np.int32)
+        va = np.zeros(9 * nb, np.float64)
+        _check(lib.ll_mg_level_operator(self._h, l, rp.ctypes.data, ci.ctypes.data, va.ctypes.data),
+               "ll_mg_level_operator")
+        return rp, ci, va.reshape(nb, 3, 3)
+
+    def apply(self, x, y):
+        _check(load_library().ll_mg_apply(self._h, _field(x, self.n, "x"), _field(y, self.n, "y")), "ll_mg_apply",
+               ok=(LL_OK,))
+
+    def vcycle(self, r, z):
+        _check(load_library().ll_mg_vcycle(self._h, _field(r, self.n, "r"), _field(z, self.n, "z")),
+               "ll_mg_vcycle", ok=(LL_OK,))
+
+    def smooth(self, l: int, b, x, forward: bool = True):
+        n = self.n if l == 0 else self.level_cells(l)
+        st = load_library().ll_mg_smooth(self._h, l, _field(b, n, "b"), _field(x, n, "x"), 1 if forward else 0)
+        _check(st, "ll_mg_smooth", ok=(LL_OK,))
+
+
+def step(m, n_steps: int, alpha, dt, h, grid, params: Params | None = None):
+    """n_steps semi-implicit steps with projection (``ll_step``), in place.
+
+    ``m`` may be a CUDA tensor, or a CPU tensor (then it is copied to the
+    device through pinned memory and back).  Returns (status, iterations per
+    step, relative residual per step)."""
+    import torch
+
+    lib = load_library()
+    params = params or Params()
+    g = _grid(grid)
+    n = g.nx * g.ny * g.nz
+    dev = m
+    if not m.is_cuda:
+        dev = m.pin_memory().to("cuda", non_blocking=True) if not m.is_pinned() else m.to("cuda", non_blocking=True)
+    its = (ctypes.c_int * max(1, n_steps))()
+    rrs = (ctypes.c_double * max(1, n_steps))()
+    cp = params._c()
+    st = lib.ll_step(_field(dev, n, "m"), int(n_steps), float(alpha), float(dt), float(h), g, ctypes.byref(cp),
+                     _stream(), its, rrs)
+    _check(st, "ll_step")
+    if dev is not m:
+        m.copy_(dev, non_blocking=False)
+    return st, list(its[:n_steps]), list(rrs[:n_steps])

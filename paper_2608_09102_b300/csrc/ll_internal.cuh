@@ -1,0 +1,96 @@
+// Internal declarations of the sm_103a solver library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ll_mg.h"
+
+namespace llmg {
+
+// ---------------------------------------------------------------------------
+// error handling: every CUDA call is checked; failures unwind as a status
+// ---------------------------------------------------------------------------
+struct Status {
+  int code;
+};
+#define LL_CU(call)                                                   \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) throw ::llmg::Status{e_ == cudaErrorMemoryAllocation ? LL_ENOMEM : LL_ECUDA}; \
+  } while (0)
+#define LL_LAUNCHED() LL_CU(cudaGetLastError())
+
+constexpr int kBlock = 256;
+constexpr int kRedBlocks = 592;   // 4 x 148 SMs: fixed grid of reduction kernels
+constexpr int kMaxRestart = 64;
+constexpr int kMaxColours = 128;
+constexpr int kMaxLevels = 32;
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+// Device allocation owned by the hierarchy (freed in the destructor).
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    LL_CU(cudaMalloc((void**)&p, count * sizeof(T)));
+    n = count;
+  }
+  void zero(cudaStream_t s) { LL_CU(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
+  operator T*() const { return p; }
+};
+
+// ---------------------------------------------------------------------------
+// integer mixing: the MurmurHash3 32-bit finaliser (a published function)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+// tie-break key of the undirected edge {lo, hi}
+__host__ __device__ __forceinline__ uint32_t pair_key(uint32_t lo, uint32_t hi, uint32_t seed) {
+  return mix32((lo * 2654435761u) ^ hi ^ seed);
+}
+// colouring priority of node v
+__host__ __device__ __forceinline__ uint32_t node_key(uint32_t v, uint32_t seed) {
+  return mix32((v * 2654435761u) ^ seed ^ 0x5bd1e995u);
+}
+
+// ---------------------------------------------------------------------------
+// graphs and levels
+// ---------------------------------------------------------------------------
+struct DevGraph {  // CSR, no self loops, integer weights
+  int n = 0;
+  int nnz = 0;
+  DBuf<int> rowptr, col, w;
+};
+
+// Red-black ("checkerboard") storage of grid fields: colour c = (x+y+z)&1,
+// slot = c*Nh + (z*ny + y)*nxh + (x>>1), nxh = ceil(nx/2), Nh = nxh*ny*nz.
+// Slots past the end of a row (odd nx) are padding and stay zero.
+struct GridGeom {
+  int nx, ny, nz, nxh;
+  long nh;  // slots per colour
+  long n;   // real cells
+};
+
+}  // namespace llmg

@@ -1,0 +1,765 @@
+// Device kernels of the numeric setup, the V-cycle and the GCR iteration.
+// Included by ll_solver.cu only.
+#pragma once
+
+#include <math.h>
+
+#include "ll_internal.cuh"
+
+namespace llmg {
+
+// ---------------------------------------------------------------------------
+// red-black slot geometry of level 0
+// ---------------------------------------------------------------------------
+struct SlotPos {
+  int x, y, z;
+  long row;
+  bool real;
+};
+__device__ __forceinline__ SlotPos slot_pos(const GridGeom& g, int c, long r) {
+  SlotPos p;
+  int i = (int)(r % g.nxh);
+  p.row = r / g.nxh;
+  p.y = (int)(p.row % g.ny);
+  p.z = (int)(p.row / g.ny);
+  p.x = 2 * i + ((c + p.y + p.z) & 1);
+  p.real = p.x < g.nx;
+  return p;
+}
+
+// slots of the face neighbours (all of the other colour); returns the count
+__device__ __forceinline__ int slot_neighbours(const GridGeom& g, int c, const SlotPos& p, long* s) {
+  long base = (long)(1 - c) * g.nh;
+  long row = p.row * g.nxh;
+  int d = 0;
+  if (p.z > 0) s[d++] = base + row - (long)g.ny * g.nxh + (p.x >> 1);
+  if (p.y > 0) s[d++] = base + row - g.nxh + (p.x >> 1);
+  if (p.x > 0) s[d++] = base + row + ((p.x - 1) >> 1);
+  if (p.x < g.nx - 1) s[d++] = base + row + ((p.x + 1) >> 1);
+  if (p.y < g.ny - 1) s[d++] = base + row + g.nxh + (p.x >> 1);
+  if (p.z < g.nz - 1) s[d++] = base + row + (long)g.ny * g.nxh + (p.x >> 1);
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 helpers (row-major blocks)
+// ---------------------------------------------------------------------------
+// inverse by the adjugate; returns false for a zero or non-finite determinant
+__host__ __device__ __forceinline__ bool inv3(const double* a, double* o) {
+  double c00 = a[4] * a[8] - a[5] * a[7];
+  double c01 = a[5] * a[6] - a[3] * a[8];
+  double c02 = a[3] * a[7] - a[4] * a[6];
+  double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(det != 0.0) || !isfinite(det)) return false;
+  double id = 1.0 / det;
+  o[0] = c00 * id;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  o[3] = c01 * id;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  o[6] = c02 * id;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) {
+  return __ldg(p);
+}
+
+// ---------------------------------------------------------------------------
+// numeric setup, level 0: per slot C(m~)/h^2 and the inverse of the diagonal
+// block I/dt - deg C(m~)/h^2.  C(m) = [m]_x + alpha (m m^T - |m|^2 I)  (the
+// component form of the damped scheme, Sec. 2.1).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, double dt, double ih2,
+                        double* __restrict__ chat64, T* __restrict__ chat, T* __restrict__ dinv,
+                        int* __restrict__ bad) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  double C[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, Di[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (p.real) {
+    long k = p.x + (long)g.nx * (p.y + (long)g.ny * p.z);
+    double m1 = m[k], m2 = m[g.n + k], m3 = m[2 * g.n + k];
+    double s = m1 * m1 + m2 * m2 + m3 * m3;
+    C[0] = alpha * (m1 * m1 - s);
+    C[1] = -m3 + alpha * m1 * m2;
+    C[2] = m2 + alpha * m1 * m3;
+    C[3] = m3 + alpha * m2 * m1;
+    C[4] = alpha * (m2 * m2 - s);
+    C[5] = -m1 + alpha * m2 * m3;
+    C[6] = -m2 + alpha * m3 * m1;
+    C[7] = m1 + alpha * m3 * m2;
+    C[8] = alpha * (m3 * m3 - s);
+    int deg = (p.x > 0) + (p.x < g.nx - 1) + (p.y > 0) + (p.y < g.ny - 1) + (p.z > 0) + (p.z < g.nz - 1);
+    double D[9];
+    for (int e = 0; e < 9; ++e) {
+      C[e] *= ih2;
+      D[e] = -deg * C[e];
+    }
+    D[0] += 1.0 / dt;
+    D[4] += 1.0 / dt;
+    D[8] += 1.0 / dt;
+    if (!inv3(D, Di)) atomicExch(bad, 1);
+  }
+  for (int e = 0; e < 9; ++e) {
+    if (chat64) chat64[e * n2 + sl] = C[e];
+    if (chat) chat[e * n2 + sl] = (T)C[e];
+    dinv[e * n2 + sl] = (T)Di[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// numeric Galerkin products (Eq. galerkin), accumulated in float64
+// ---------------------------------------------------------------------------
+// level 1: A_1(I,J) = delta_IJ |G_I|/dt I + sum_{k in G_I} w_kJ Chat_k
+__global__ void k_galerkin_l1(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const int* __restrict__ sptr, const int* __restrict__ sidx, const int* __restrict__ sw,
+                              const int* __restrict__ mptr, long n2, const double* __restrict__ chat64, double inv_dt,
+                              double* __restrict__ val, double* __restrict__ dinv64, int* __restrict__ bad) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) {
+    double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
+      long k = sidx[q];
+      double w = (double)sw[q];
+      for (int e = 0; e < 9; ++e) a[e] += w * chat64[e * n2 + k];
+    }
+    if (col[p] == I) {
+      double sz = (double)(mptr[I + 1] - mptr[I]) * inv_dt;
+      a[0] += sz;
+      a[4] += sz;
+      a[8] += sz;
+      double o[9];
+      if (!inv3(a, o)) atomicExch(bad, 1);
+      for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
+    }
+    for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
+  }
+}
+
+// levels >= 2: sum of the fine blocks of each coarse slot
+__global__ void k_galerkin_bsr(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                               const int* __restrict__ sptr, const int* __restrict__ sidx,
+                               const double* __restrict__ fval, double* __restrict__ val, double* __restrict__ dinv64,
+                               int* __restrict__ bad) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) {
+    double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
+      const double* f = fval + 9 * (long)sidx[q];
+      for (int e = 0; e < 9; ++e) a[e] += f[e];
+    }
+    if (col[p] == I) {
+      double o[9];
+      if (!inv3(a, o)) atomicExch(bad, 1);
+      for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
+    }
+    for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
+  }
+}
+
+template <typename T>
+__global__ void k_cast(long n, const double* __restrict__ in, T* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: dense LU with partial pivoting (one CTA), unknown 3I + c
+// ---------------------------------------------------------------------------
+__global__ void k_dense_from_bsr(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                 const double* __restrict__ val, double* __restrict__ a) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int N = 3 * n;
+  for (int r = 0; r < 3; ++r)
+    for (int j = 0; j < N; ++j) a[(long)(3 * I + r) * N + j] = 0.0;
+  for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) {
+    int J = col[p];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) a[(long)(3 * I + r) * N + 3 * J + c] = val[9 * (long)p + 3 * r + c];
+  }
+}
+
+// In place: a = L\U (unit L), perm[i] = original row now in position i.
+__global__ void k_lu_factor(int N, double* __restrict__ a, int* __restrict__ perm, int* __restrict__ status) {
+  __shared__ double sval[1024];
+  __shared__ int sidx[1024];
+  __shared__ int piv;
+  int t = threadIdx.x, nt = blockDim.x;
+  for (int i = t; i < N; i += nt) perm[i] = i;
+  if (t == 0) *status = 0;
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    // pivot search: largest |a_ik|, ties to the lowest row
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + t; i < N; i += nt) {
+      double v = fabs(a[(long)i * N + k]);
+      if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    sval[t] = bv;
+    sidx[t] = bi;
+    __syncthreads();
+    for (int o = nt / 2; o > 0; o >>= 1) {
+      if (t < o) {
+        double v2 = sval[t + o];
+        int i2 = sidx[t + o];
+        if (v2 > sval[t] || (v2 == sval[t] && i2 < sidx[t])) {
+          sval[t] = v2;
+          sidx[t] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (t == 0) {
+      piv = sidx[0];
+      if (!(sval[0] > 0.0)) *status = 1;
+    }
+    __syncthreads();
+    int p = piv;
+    if (p != k && p < N) {
+      for (int j = t; j < N; j += nt) {
+        double x = a[(long)k * N + j];
+        a[(long)k * N + j] = a[(long)p * N + j];
+        a[(long)p * N + j] = x;
+      }
+      if (t == 0) {
+        int x = perm[k];
+        perm[k] = perm[p];
+        perm[p] = x;
+      }
+    }
+    __syncthreads();
+    double akk = a[(long)k * N + k];
+    for (int i = k + 1 + t; i < N; i += nt) a[(long)i * N + k] /= akk;
+    __syncthreads();
+    int m = N - k - 1;
+    for (long e = t; e < (long)m * m; e += nt) {
+      int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      a[(long)i * N + j] -= a[(long)i * N + k] * a[(long)k * N + j];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_lu_solve(int N, const double* __restrict__ a, const int* __restrict__ perm,
+                           const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ double y[];
+  int t = threadIdx.x, nt = blockDim.x;
+  for (int i = t; i < N; i += nt) y[i] = (double)b[perm[i]];
+  __syncthreads();
+  for (int j = 0; j < N; ++j) {  // forward, unit lower
+    double yj = y[j];
+    for (int i = j + 1 + t; i < N; i += nt) y[i] -= a[(long)i * N + j] * yj;
+    __syncthreads();
+  }
+  for (int j = N - 1; j >= 0; --j) {  // backward
+    if (t == 0) y[j] /= a[(long)j * N + j];
+    __syncthreads();
+    double yj = y[j];
+    for (int i = t; i < j; i += nt) y[i] -= a[(long)i * N + j] * yj;
+    __syncthreads();
+  }
+  for (int i = t; i < N; i += nt) x[i] = (T)y[i];
+}
+
+// ---------------------------------------------------------------------------
+// level-0 V-cycle kernels (red-black slots, matrix free)
+// ---------------------------------------------------------------------------
+// Block Gauss-Seidel update of the cells of colour c:
+//   x_k = Dinv_k (b_k - Chat_k S_k),  S_k = sum of the neighbours' x.
+// mode 0: neighbours are zero (first half-sweep from x = 0);
+// mode 1: plain update;
+// mode 2: neighbours are read as x_l + e[agg(l)] (prolongation of the coarse
+//         correction folded into the first half-sweep after it).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k0_smooth(GridGeom g, int c, const double* __restrict__ b, T* __restrict__ x,
+                                                 const T* __restrict__ chat, const T* __restrict__ dinv,
+                                                 const int* __restrict__ agg, const T* __restrict__ e) {
+  long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= g.nh) return;
+  long n2 = 2 * g.nh;
+  long sl = (long)c * g.nh + r;
+  SlotPos p = slot_pos(g, c, r);
+  if (!p.real) return;
+  T v0 = (T)b[sl], v1 = (T)b[n2 + sl], v2 = (T)b[2 * n2 + sl];
+  if (MODE != 0) {
+    long nb[6];
+    int d = slot_neighbours(g, c, p, nb);
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int q = 0; q < d; ++q) {
+      long l = nb[q];
+      s0 += x[l];
+      s1 += x[n2 + l];
+      s2 += x[2 * n2 + l];
+      if (MODE == 2) {
+        long a = 3L * agg[l];
+        s0 += e[a];
+        s1 += e[a + 1];
+        s2 += e[a + 2];
+      }
+    }
+    const T* C = chat + sl;
+    T c0 = ld(C), c1 = ld(C + n2), c2 = ld(C + 2 * n2), c3 = ld(C + 3 * n2), c4 = ld(C + 4 * n2),
+      c5 = ld(C + 5 * n2), c6 = ld(C + 6 * n2), c7 = ld(C + 7 * n2), c8 = ld(C + 8 * n2);
+    v0 -= c0 * s0 + c1 * s1 + c2 * s2;
+    v1 -= c3 * s0 + c4 * s1 + c5 * s2;
+    v2 -= c6 * s0 + c7 * s1 + c8 * s2;
+  }
+  const T* D = dinv + sl;
+  T d0 = ld(D), d1 = ld(D + n2), d2 = ld(D + 2 * n2), d3 = ld(D + 3 * n2), d4 = ld(D + 4 * n2),
+    d5 = ld(D + 5 * n2), d6 = ld(D + 6 * n2), d7 = ld(D + 7 * n2), d8 = ld(D + 8 * n2);
+  x[sl] = d0 * v0 + d1 * v1 + d2 * v2;
+  x[n2 + sl] = d3 * v0 + d4 * v1 + d5 * v2;
+  x[2 * n2 + sl] = d6 * v0 + d7 * v1 + d8 * v2;
+}
+
+// operator at one slot: y = x/dt + Chat (S - deg x), S = sum of neighbours
+template <typename T, typename TX>
+__device__ __forceinline__ void slot_apply(const GridGeom& g, int c, long sl, const SlotPos& p, const TX* x,
+                                           const T* chat, T inv_dt, T* y) {
+  long n2 = 2 * g.nh;
+  long nb[6];
+  int d = slot_neighbours(g, c, p, nb);
+  T x0 = (T)x[sl], x1 = (T)x[n2 + sl], x2 = (T)x[2 * n2 + sl];
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int q = 0; q < d; ++q) {
+    long l = nb[q];
+    s0 += (T)x[l];
+    s1 += (T)x[n2 + l];
+    s2 += (T)x[2 * n2 + l];
+  }
+  T fd = (T)d;
+  s0 -= fd * x0;
+  s1 -= fd * x1;
+  s2 -= fd * x2;
+  const T* C = chat + sl;
+  y[0] = x0 * inv_dt + ld(C) * s0 + ld(C + n2) * s1 + ld(C + 2 * n2) * s2;
+  y[1] = x1 * inv_dt + ld(C + 3 * n2) * s0 + ld(C + 4 * n2) * s1 + ld(C + 5 * n2) * s2;
+  y[2] = x2 * inv_dt + ld(C + 6 * n2) * s0 + ld(C + 7 * n2) * s1 + ld(C + 8 * n2) * s2;
+}
+
+// residual of one slot: r = b - A x
+template <typename T, typename TX>
+__device__ __forceinline__ void slot_residual(const GridGeom& g, int c, long sl, const SlotPos& p, const double* b,
+                                              const TX* x, const T* chat, T inv_dt, T* r) {
+  long n2 = 2 * g.nh;
+  T y[3];
+  slot_apply<T, TX>(g, c, sl, p, x, chat, inv_dt, y);
+  r[0] = (T)b[sl] - y[0];
+  r[1] = (T)b[n2 + sl] - y[1];
+  r[2] = (T)b[2 * n2 + sl] - y[2];
+}
+
+// Residual and restriction (P^T) in one pass: bc_I = sum over the members k
+// of aggregate I of (b - A x)_k.  After a forward half-sweep of colour 1 the
+// colour-1 residuals vanish, so only the colour-0 members are listed.
+template <typename T>
+__global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* __restrict__ x,
+                            const T* __restrict__ chat, T inv_dt, int nc, const int* __restrict__ mptr,
+                            const int* __restrict__ mem, T* __restrict__ bc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  T a0 = 0, a1 = 0, a2 = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+    long sl = mem[q];
+    int c = (int)(sl / g.nh);
+    SlotPos p = slot_pos(g, c, sl % g.nh);
+    T r[3];
+    slot_residual<T, T>(g, c, sl, p, b, x, chat, inv_dt, r);
+    a0 += r[0];
+    a1 += r[1];
+    a2 += r[2];
+  }
+  bc[3L * I] = a0;
+  bc[3L * I + 1] = a1;
+  bc[3L * I + 2] = a2;
+}
+
+// restriction of b itself (no pre-smoothing: x = 0)
+template <typename T>
+__global__ void k0_restrict_b(GridGeom g, const double* __restrict__ b, int nc, const int* __restrict__ mptr,
+                              const int* __restrict__ mem, T* __restrict__ bc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  long n2 = 2 * g.nh;
+  T a0 = 0, a1 = 0, a2 = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+    long sl = mem[q];
+    a0 += (T)b[sl];
+    a1 += (T)b[n2 + sl];
+    a2 += (T)b[2 * n2 + sl];
+  }
+  bc[3L * I] = a0;
+  bc[3L * I + 1] = a1;
+  bc[3L * I + 2] = a2;
+}
+
+// x_k += e[agg(k)] on all real slots (used when no post-smoothing follows)
+template <typename T>
+__global__ void k0_prolong(GridGeom g, const int* __restrict__ agg, const T* __restrict__ e, T* __restrict__ x) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int a = agg[sl];
+  if (a < 0) return;
+  x[sl] += e[3L * a];
+  x[n2 + sl] += e[3L * a + 1];
+  x[2 * n2 + sl] += e[3L * a + 2];
+}
+
+template <typename T>
+__global__ void k_zero(long n, T* __restrict__ p) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (T)0;
+}
+
+// ---------------------------------------------------------------------------
+// coarse levels: 3x3 BSR, cell-major vectors; a group of G lanes per row
+// ---------------------------------------------------------------------------
+template <int G, typename T>
+__device__ __forceinline__ void group_sum3(T& a, T& b, T& c) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+}
+
+// x_I = Dinv_I (b_I - sum_{J != I} A_IJ x_J) for the rows of one colour class
+template <typename T, int G>
+__global__ void kb_smooth(int nrows, const int* __restrict__ rows, const int* __restrict__ rowptr,
+                          const int* __restrict__ col, const T* __restrict__ val, const T* __restrict__ dinv,
+                          const T* __restrict__ b, T* __restrict__ x) {
+  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long q = gt / G;
+  int lane = threadIdx.x % G;
+  bool active = q < nrows;
+  int I = active ? rows[q] : 0;
+  T a0 = 0, a1 = 0, a2 = 0;
+  if (active) {
+    for (int p = rowptr[I] + lane; p < rowptr[I + 1]; p += G) {
+      int J = col[p];
+      if (J == I) continue;
+      const T* A = val + 9L * p;
+      T x0 = x[3L * J], x1 = x[3L * J + 1], x2 = x[3L * J + 2];
+      a0 += A[0] * x0 + A[1] * x1 + A[2] * x2;
+      a1 += A[3] * x0 + A[4] * x1 + A[5] * x2;
+      a2 += A[6] * x0 + A[7] * x1 + A[8] * x2;
+    }
+  }
+  group_sum3<G>(a0, a1, a2);
+  if (active && lane == 0) {
+    T v0 = b[3L * I] - a0, v1 = b[3L * I + 1] - a1, v2 = b[3L * I + 2] - a2;
+    const T* D = dinv + 9L * I;
+    x[3L * I] = D[0] * v0 + D[1] * v1 + D[2] * v2;
+    x[3L * I + 1] = D[3] * v0 + D[4] * v1 + D[5] * v2;
+    x[3L * I + 2] = D[6] * v0 + D[7] * v1 + D[8] * v2;
+  }
+}
+
+// r = b - A x
+template <typename T, int G>
+__global__ void kb_residual(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const T* __restrict__ val, const T* __restrict__ b, const T* __restrict__ x,
+                            T* __restrict__ r) {
+  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long I = gt / G;
+  int lane = threadIdx.x % G;
+  bool active = I < n;
+  T a0 = 0, a1 = 0, a2 = 0;
+  if (active) {
+    for (int p = rowptr[I] + lane; p < rowptr[I + 1]; p += G) {
+      int J = col[p];
+      const T* A = val + 9L * p;
+      T x0 = x[3L * J], x1 = x[3L * J + 1], x2 = x[3L * J + 2];
+      a0 += A[0] * x0 + A[1] * x1 + A[2] * x2;
+      a1 += A[3] * x0 + A[4] * x1 + A[5] * x2;
+      a2 += A[6] * x0 + A[7] * x1 + A[8] * x2;
+    }
+  }
+  group_sum3<G>(a0, a1, a2);
+  if (active && lane == 0) {
+    r[3 * I] = b[3 * I] - a0;
+    r[3 * I + 1] = b[3 * I + 1] - a1;
+    r[3 * I + 2] = b[3 * I + 2] - a2;
+  }
+}
+
+// bc_I = sum of r over the members of aggregate I
+template <typename T>
+__global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __restrict__ mem,
+                            const T* __restrict__ r, T* __restrict__ bc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  T a0 = 0, a1 = 0, a2 = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+    long k = mem[q];
+    a0 += r[3 * k];
+    a1 += r[3 * k + 1];
+    a2 += r[3 * k + 2];
+  }
+  bc[3L * I] = a0;
+  bc[3L * I + 1] = a1;
+  bc[3L * I + 2] = a2;
+}
+
+template <typename T>
+__global__ void kb_prolong(int n, const int* __restrict__ agg, const T* __restrict__ e, T* __restrict__ x) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  long a = 3L * agg[I];
+  x[3L * I] += e[a];
+  x[3L * I + 1] += e[a + 1];
+  x[3L * I + 2] += e[a + 2];
+}
+
+// ---------------------------------------------------------------------------
+// float64 outer operator and GCR vector kernels (red-black layout)
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double* v, double* partial, int nvals) {
+  __shared__ double sh[NV][kBlock / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double a = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < nvals && threadIdx.x < NV) {
+    double a = 0;
+    for (int w = 0; w < kBlock / 32; ++w) a += sh[threadIdx.x][w];
+    partial[(long)threadIdx.x * kRedBlocks + blockIdx.x] = a;
+  }
+}
+
+// out[q] = sum of partial[q][0..kRedBlocks), fixed order
+__global__ void k_finish(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[kBlock];
+  int q = blockIdx.x;
+  double a = 0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kBlock) a += partial[(long)q * kRedBlocks + i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kBlock / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[q] = sh[0];
+}
+
+// y = A x (float64); pads stay zero.  TX = storage type of x.
+template <typename TX>
+__global__ void __launch_bounds__(256) kg_apply(GridGeom g, const TX* __restrict__ x, const double* __restrict__ chat,
+                                                double inv_dt, double* __restrict__ y) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  if (!p.real) {
+    y[sl] = 0;
+    y[n2 + sl] = 0;
+    y[2 * n2 + sl] = 0;
+    return;
+  }
+  double v[3];
+  slot_apply<double, TX>(g, c, sl, p, x, chat, inv_dt, v);
+  y[sl] = v[0];
+  y[n2 + sl] = v[1];
+  y[2 * n2 + sl] = v[2];
+}
+
+// r = b - A x, partial sums of |r|^2 and |b|^2
+__global__ void __launch_bounds__(256) kg_residual(GridGeom g, const double* __restrict__ b,
+                                                   const double* __restrict__ x, const double* __restrict__ chat,
+                                                   double inv_dt, double* __restrict__ r, double* __restrict__ partial) {
+  long n2 = 2 * g.nh;
+  double acc[2] = {0, 0};
+  for (long sl = blockIdx.x * (long)blockDim.x + threadIdx.x; sl < n2; sl += (long)gridDim.x * blockDim.x) {
+    int c = (int)(sl / g.nh);
+    SlotPos p = slot_pos(g, c, sl % g.nh);
+    if (!p.real) {
+      r[sl] = 0;
+      r[n2 + sl] = 0;
+      r[2 * n2 + sl] = 0;
+      continue;
+    }
+    double v[3];
+    slot_residual<double, double>(g, c, sl, p, b, x, chat, inv_dt, v);
+    r[sl] = v[0];
+    r[n2 + sl] = v[1];
+    r[2 * n2 + sl] = v[2];
+    acc[0] += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    acc[1] += b[sl] * b[sl] + b[n2 + sl] * b[n2 + sl] + b[2 * n2 + sl] * b[2 * n2 + sl];
+  }
+  block_reduce_store<2>(acc, partial, 2);
+}
+
+// partial dots d_i = C_i . v for i in [i0, i0 + cnt), cnt <= NV
+template <int NV>
+__global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restrict__ C, int i0, int cnt,
+                                                   const double* __restrict__ v, double* __restrict__ partial) {
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    double vt = v[t];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q < cnt) acc[q] += C[(long)(i0 + q) * n + t] * vt;
+  }
+  block_reduce_store<NV>(acc, partial, cnt);
+}
+
+// v -= sum_{i<j} coef[i] C_i  (coef on the device)
+__global__ void __launch_bounds__(256) kg_multiaxpy(long n, double* __restrict__ v, const double* __restrict__ C,
+                                                    int j, const double* __restrict__ coef) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double a = v[t];
+  for (int i = 0; i < j; ++i) a -= coef[i] * C[(long)i * n + t];
+  v[t] = a;
+}
+
+// partial sums of |c|^2 and c.r
+__global__ void __launch_bounds__(256) kg_dot2(long n, const double* __restrict__ c, const double* __restrict__ r,
+                                               double* __restrict__ partial) {
+  double acc[2] = {0, 0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    double ct = c[t];
+    acc[0] += ct * ct;
+    acc[1] += ct * r[t];
+  }
+  block_reduce_store<2>(acc, partial, 2);
+}
+
+// r -= coef * c, partial |r|^2
+__global__ void __launch_bounds__(256) kg_rupdate(long n, double* __restrict__ r, const double* __restrict__ c,
+                                                  const double* __restrict__ coef, double* __restrict__ partial) {
+  double f = *coef;
+  double acc[1] = {0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    double v = r[t] - f * c[t];
+    r[t] = v;
+    acc[0] += v * v;
+  }
+  block_reduce_store<1>(acc, partial, 1);
+}
+
+// x += sum_k y_k Z_k
+template <typename TZ>
+__global__ void __launch_bounds__(256) kg_xupdate(long n, double* __restrict__ x, const TZ* __restrict__ Z, int m,
+                                                  const double* __restrict__ y) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double a = x[t];
+  for (int k = 0; k < m; ++k) a += y[k] * (double)Z[(long)k * n + t];
+  x[t] = a;
+}
+
+// natural SoA <-> red-black slots (pads of the output are zeroed)
+template <typename TI, typename TO>
+__global__ void k_to_rb(GridGeom g, const int* __restrict__ nat_of_slot, const TI* __restrict__ in,
+                        TO* __restrict__ out) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int k = nat_of_slot[sl];
+  for (int c = 0; c < 3; ++c) out[c * n2 + sl] = k < 0 ? (TO)0 : (TO)in[c * g.n + k];
+}
+template <typename TI, typename TO>
+__global__ void k_from_rb(GridGeom g, const int* __restrict__ nat_of_slot, const TI* __restrict__ in,
+                          TO* __restrict__ out) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int k = nat_of_slot[sl];
+  if (k < 0) return;
+  for (int c = 0; c < 3; ++c) out[c * g.n + k] = (TO)in[c * n2 + sl];
+}
+
+// ---------------------------------------------------------------------------
+// GCR scalars (device resident, one thread)
+// ---------------------------------------------------------------------------
+struct GcrScal {
+  double rn2, bn2, cc, cr;         // reduction results (read by the host)
+  double gjj, rcoef, pad0, pad1;   // gamma_jj, alpha_j s_j
+  double d[kMaxRestart];           // dots of the current vector with C'_i
+  double coef[kMaxRestart];        // projection coefficients of the update
+  double gam[kMaxRestart * kMaxRestart];  // Gamma, row-major
+  double alpha[kMaxRestart], s[kMaxRestart], y[kMaxRestart];
+};
+
+// Gram-Schmidt coefficients from the dots d_i = C'_i . c (C'_i unnormalised,
+// c_i = s_i C'_i): gamma_i = s_i d_i is added to Gamma_ij and the update
+// c -= gamma_i c_i uses coef_i = gamma_i s_i.
+__global__ void k_gs_coef(GcrScal* S, int j, int first) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < j; ++i) {
+    double gm = S->s[i] * S->d[i];
+    S->gam[i * kMaxRestart + j] = first ? gm : S->gam[i * kMaxRestart + j] + gm;
+    S->coef[i] = gm * S->s[i];
+  }
+}
+// gamma_jj = |c|, s_j = 1/gamma_jj, alpha_j = c_j . r = s_j (c . r)
+__global__ void k_norm_coef(GcrScal* S, int j) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double g = sqrt(S->cc);
+  S->gjj = g;
+  S->gam[j * kMaxRestart + j] = g;
+  double s = 1.0 / g;
+  S->s[j] = s;
+  S->alpha[j] = s * S->cr;
+  S->rcoef = S->alpha[j] * s;
+}
+// y = Gamma^{-1} alpha (upper triangular)
+__global__ void k_backsub(GcrScal* S, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = m - 1; i >= 0; --i) {
+    double a = S->alpha[i];
+    for (int k = i + 1; k < m; ++k) a -= S->gam[i * kMaxRestart + k] * S->y[k];
+    S->y[i] = a / S->gam[i * kMaxRestart + i];
+  }
+}
+
+// m <- x / |x| per cell (the projection step), natural SoA
+__global__ void k_renormalise(long n, const double* __restrict__ x, double* __restrict__ m, int* __restrict__ bad) {
+  long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double a = x[k], b = x[n + k], c = x[2 * n + k];
+  double s = sqrt(a * a + b * b + c * c);
+  if (!(s > 0.0) || !isfinite(s)) {
+    atomicExch(bad, 1);
+    return;
+  }
+  m[k] = a / s;
+  m[n + k] = b / s;
+  m[2 * n + k] = c / s;
+}
+
+// rhs = m / dt
+__global__ void k_scale(long n, const double* __restrict__ m, double inv_dt, double* __restrict__ b) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = m[i] * inv_dt;
+}
+
+}  // namespace llmg

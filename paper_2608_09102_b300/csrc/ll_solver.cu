@@ -1,0 +1,802 @@
+// Hierarchy, numeric setup, V-cycle, GCR and the C ABI of the sm_103a
+// aggregation-multigrid solver (see include/ll_mg.h for the contract).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ll_internal.cuh"
+#include "ll_kernels.cuh"
+#include "ll_setup.cuh"
+
+namespace llmg {
+
+struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
+  int n = 0, nnzb = 0, ncol = 0;
+  DevGraph graph;                   // integer weight graph
+  DBuf<int> rowptr, col, diag;      // BSR pattern
+  DBuf<int> colour, cptr, crow;     // colouring and its classes
+  std::vector<int> h_cptr;
+  DBuf<int> sptr, sidx, sw;         // Galerkin slot map from the finer level
+  DBuf<int> mptr, mem;              // members in the finer level (level 1: red-black slots)
+  DBuf<int> mptr0, mem0;            // level 1: colour-0 members only
+  DBuf<int> agg;                    // this level -> next level
+  DBuf<double> val64, dinv64;
+  DBuf<float> val32, dinv32;
+  DBuf<double> x64, b64, r64;
+  DBuf<float> x32, b32, r32;
+  template <typename T> T* val();
+  template <typename T> T* dinv();
+  template <typename T> T* x();
+  template <typename T> T* b();
+  template <typename T> T* r();
+};
+template <> double* CLevel::val<double>() { return val64; }
+template <> float* CLevel::val<float>() { return val32; }
+template <> double* CLevel::dinv<double>() { return dinv64; }
+template <> float* CLevel::dinv<float>() { return dinv32; }
+template <> double* CLevel::x<double>() { return x64; }
+template <> float* CLevel::x<float>() { return x32; }
+template <> double* CLevel::b<double>() { return b64; }
+template <> float* CLevel::b<float>() { return b32; }
+template <> double* CLevel::r<double>() { return r64; }
+template <> float* CLevel::r<float>() { return r32; }
+
+}  // namespace llmg
+
+using namespace llmg;
+
+struct ll_mg_hierarchy {
+  ll_mg_params prm;
+  cudaStream_t s = nullptr;
+  GridGeom g;
+  double alpha = 0, dt = 1, h = 1;
+  int nlev = 1;
+  long n2 = 0, n3 = 0;
+  // level 0
+  DevGraph graph0;
+  DBuf<int> agg_nat0, agg0, nat_of_slot;
+  DBuf<double> chat64, dinv64;
+  DBuf<float> chat32, dinv32;
+  CLevel lev[kMaxLevels];
+  // coarsest dense LU
+  int ncoarse3 = 0;
+  DBuf<double> lu;
+  DBuf<int> perm, lu_status, flag;
+  // GCR workspace (red-black layout, 3*n2 doubles per vector)
+  DBuf<double> Z64, C, r, xw, bw, partial;
+  DBuf<float> Z32;
+  DBuf<GcrScal> scal;
+  double* h_head = nullptr;  // pinned copy of the first scalars
+  // time-step workspace (natural layout)
+  DBuf<double> stepb, stepx;
+  ~ll_mg_hierarchy() {
+    if (h_head) cudaFreeHost(h_head);
+  }
+  template <typename T> T* chat();
+  template <typename T> T* dinv0();
+  template <typename T> T* Z();
+};
+template <> double* ll_mg_hierarchy::chat<double>() { return chat64; }
+template <> float* ll_mg_hierarchy::chat<float>() { return chat32; }
+template <> double* ll_mg_hierarchy::dinv0<double>() { return dinv64; }
+template <> float* ll_mg_hierarchy::dinv0<float>() { return dinv32; }
+template <> double* ll_mg_hierarchy::Z<double>() { return Z64; }
+template <> float* ll_mg_hierarchy::Z<float>() { return Z32; }
+
+namespace {
+
+constexpr int kLanes = 4;  // lanes per block row in the BSR kernels
+constexpr int kDotChunk = 8;
+constexpr int kMaxCoarsestCells = 2048;
+
+void check_flag(ll_mg_hierarchy* H, int code) {
+  int v = 0;
+  LL_CU(cudaMemcpyAsync(&v, H->flag.p, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+  LL_CU(cudaStreamSynchronize(H->s));
+  if (v) throw Status{code};
+}
+
+// ---------------------------------------------------------------------------
+// symbolic setup (once per grid): aggregation, patterns, colours, slot maps
+// ---------------------------------------------------------------------------
+void symbolic(ll_mg_hierarchy* H) {
+  cudaStream_t s = H->s;
+  const GridGeom& g = H->g;
+  const ll_mg_params& p = H->prm;
+  build_grid_graph(g.nx, g.ny, g.nz, H->graph0, s);
+  H->nlev = 1;
+  const DevGraph* cur = &H->graph0;
+  int ncur = (int)g.n;
+  while (ncur > p.coarsest_cells && H->nlev < p.max_levels) {
+    int l = H->nlev - 1;
+    DBuf<int>& agg = l == 0 ? H->agg_nat0 : H->lev[l].agg;
+    agg.alloc(ncur);
+    int nc = aggregate_level(*cur, p.rounds, p.seed, agg, s);
+    if (3L * nc > 2L * ncur) {  // coarsening ratio below 1.5: stop here
+      agg.release();
+      break;
+    }
+    CLevel& C = H->lev[l + 1];
+    C.n = nc;
+    build_members(ncur, agg, nc, C.mptr, C.mem, s);
+    contract_graph(*cur, agg, nc, C.mptr, C.mem, C.graph, s);
+    bsr_pattern(C.graph, C.rowptr, C.col, C.diag, C.nnzb, s);
+    C.colour.alloc(nc);
+    C.ncol = colour_graph(C.graph, p.seed, C.colour, s);
+    if (C.ncol < 0) throw Status{LL_ELIMIT};
+    colour_classes(nc, C.colour, C.ncol, C.cptr, C.crow, C.h_cptr, s);
+    if (l == 0) {
+      slot_map_level1(g, H->agg_nat0, C.graph, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, C.sw, s);
+    } else {
+      CLevel& F = H->lev[l];
+      slot_map_bsr(F.n, F.rowptr, F.col, F.agg, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, s);
+    }
+    H->nlev++;
+    cur = &C.graph;
+    ncur = nc;
+  }
+  H->nat_of_slot.alloc(H->n2);
+  if (H->nlev > 1) {
+    H->agg0.alloc(H->n2);
+    rb_maps(g, H->agg_nat0, H->agg0, H->nat_of_slot, s);
+    CLevel& L1 = H->lev[1];
+    build_members((int)H->n2, H->agg0, L1.n, L1.mptr, L1.mem, s);  // red-black slots now
+    members_colour0(L1.n, L1.mptr, L1.mem, g.nh, L1.mptr0, L1.mem0, s);
+  } else {
+    rb_maps(g, nullptr, nullptr, H->nat_of_slot, s);
+  }
+  int ncoarse = H->nlev == 1 ? (int)g.n : H->lev[H->nlev - 1].n;
+  if (ncoarse > kMaxCoarsestCells) throw Status{LL_ELIMIT};
+  LL_CU(cudaStreamSynchronize(s));
+}
+
+void allocate(ll_mg_hierarchy* H) {
+  bool mixed = H->prm.precision == LL_MIXED_FP32;
+  long n2 = H->n2;
+  H->chat64.alloc(9 * n2);
+  if (mixed) {
+    H->chat32.alloc(9 * n2);
+    H->dinv32.alloc(9 * n2);
+  } else {
+    H->dinv64.alloc(9 * n2);
+  }
+  for (int l = 1; l < H->nlev; ++l) {
+    CLevel& C = H->lev[l];
+    C.val64.alloc(9L * C.nnzb);
+    C.dinv64.alloc(9L * C.n);
+    if (mixed) {
+      C.val32.alloc(9L * C.nnzb);
+      C.dinv32.alloc(9L * C.n);
+      C.x32.alloc(3L * C.n);
+      C.b32.alloc(3L * C.n);
+      C.r32.alloc(3L * C.n);
+    } else {
+      C.x64.alloc(3L * C.n);
+      C.b64.alloc(3L * C.n);
+      C.r64.alloc(3L * C.n);
+    }
+  }
+  int nc = H->nlev == 1 ? (int)H->g.n : H->lev[H->nlev - 1].n;
+  H->ncoarse3 = 3 * nc;
+  H->lu.alloc((size_t)H->ncoarse3 * H->ncoarse3);
+  H->perm.alloc(H->ncoarse3);
+  H->lu_status.alloc(1);
+  H->flag.alloc(1);
+  int m = H->prm.restart;
+  long n3 = H->n3;
+  if (mixed) H->Z32.alloc((size_t)m * n3);
+  else H->Z64.alloc((size_t)m * n3);
+  H->C.alloc((size_t)m * n3);
+  H->r.alloc(n3);
+  H->xw.alloc(n3);
+  H->bw.alloc(n3);
+  H->partial.alloc((size_t)(kMaxRestart + 2) * kRedBlocks);
+  H->scal.alloc(1);
+  H->scal.zero(H->s);
+  LL_CU(cudaMallocHost((void**)&H->h_head, 8 * sizeof(double)));
+  H->stepb.alloc(3 * H->g.n);
+  H->stepx.alloc(3 * H->g.n);
+}
+
+// dense level-0 operator (single-level hierarchies), unknown 3k + c, k natural
+__global__ void k_dense_from_l0(GridGeom g, const double* __restrict__ chat64, double inv_dt,
+                                double* __restrict__ a) {
+  long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (k >= g.n) return;
+  long N = 3 * g.n;
+  int x = (int)(k % g.nx);
+  long t = k / g.nx;
+  int y = (int)(t % g.ny), z = (int)(t / g.ny);
+  int c = (x + y + z) & 1;
+  long sl = c * g.nh + ((long)z * g.ny + y) * g.nxh + (x >> 1);
+  long n2 = 2 * g.nh;
+  double C[9];
+  for (int e = 0; e < 9; ++e) C[e] = chat64[e * n2 + sl];
+  for (int r = 0; r < 3; ++r)
+    for (long j = 0; j < N; ++j) a[(3 * k + r) * N + j] = 0.0;
+  long nb[6];
+  int d = 0;
+  if (z > 0) nb[d++] = k - (long)g.nx * g.ny;
+  if (y > 0) nb[d++] = k - g.nx;
+  if (x > 0) nb[d++] = k - 1;
+  if (x < g.nx - 1) nb[d++] = k + 1;
+  if (y < g.ny - 1) nb[d++] = k + g.nx;
+  if (z < g.nz - 1) nb[d++] = k + (long)g.nx * g.ny;
+  for (int r = 0; r < 3; ++r)
+    for (int cc = 0; cc < 3; ++cc) {
+      a[(3 * k + r) * N + 3 * k + cc] = -d * C[3 * r + cc] + (r == cc ? inv_dt : 0.0);
+      for (int q = 0; q < d; ++q) a[(3 * k + r) * N + 3 * nb[q] + cc] = C[3 * r + cc];
+    }
+}
+
+// red-black SoA <-> cell-major natural vector (single-level hierarchies)
+template <typename TI, typename TO>
+__global__ void k_rb_to_cellmajor(GridGeom g, const int* __restrict__ nat, const TI* __restrict__ in,
+                                  TO* __restrict__ out) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2 || nat[sl] < 0) return;
+  long k = nat[sl];
+  for (int c = 0; c < 3; ++c) out[3 * k + c] = (TO)in[c * n2 + sl];
+}
+template <typename TI, typename TO>
+__global__ void k_cellmajor_to_rb(GridGeom g, const int* __restrict__ nat, const TI* __restrict__ in,
+                                  TO* __restrict__ out) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  long k = nat[sl];
+  for (int c = 0; c < 3; ++c) out[c * n2 + sl] = k < 0 ? (TO)0 : (TO)in[3 * k + c];
+}
+
+// ---------------------------------------------------------------------------
+// numeric setup (every time step)
+// ---------------------------------------------------------------------------
+void numeric(ll_mg_hierarchy* H, const double* m) {
+  cudaStream_t s = H->s;
+  const GridGeom& g = H->g;
+  bool mixed = H->prm.precision == LL_MIXED_FP32;
+  H->flag.zero(s);
+  double ih2 = 1.0 / (H->h * H->h), inv_dt = 1.0 / H->dt;
+  int nb = cdiv(H->n2, kBlock);
+  if (mixed)
+    k0_coef<float><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, H->chat32, H->dinv32, H->flag);
+  else
+    k0_coef<double><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, nullptr, H->dinv64, H->flag);
+  LL_LAUNCHED();
+  for (int l = 1; l < H->nlev; ++l) {
+    CLevel& C = H->lev[l];
+    if (l == 1)
+      k_galerkin_l1<<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.rowptr, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
+                                                   H->chat64, inv_dt, C.val64, C.dinv64, H->flag);
+    else
+      k_galerkin_bsr<<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.rowptr, C.col, C.sptr, C.sidx, H->lev[l - 1].val64,
+                                                    C.val64, C.dinv64, H->flag);
+    LL_LAUNCHED();
+    if (mixed) {
+      k_cast<float><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val32);
+      LL_LAUNCHED();
+      k_cast<float><<<cdiv(9L * C.n, kBlock), kBlock, 0, s>>>(9L * C.n, C.dinv64, C.dinv32);
+      LL_LAUNCHED();
+    }
+  }
+  check_flag(H, LL_SINGULAR_COARSE);
+  // coarsest dense LU
+  int N = H->ncoarse3;
+  if (H->nlev == 1) {
+    k_dense_from_l0<<<cdiv(g.n, 64), 64, 0, s>>>(g, H->chat64, inv_dt, H->lu);
+  } else {
+    CLevel& C = H->lev[H->nlev - 1];
+    k_dense_from_bsr<<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val64, H->lu);
+  }
+  LL_LAUNCHED();
+  k_lu_factor<<<1, 1024, 0, s>>>(N, H->lu, H->perm, H->lu_status);
+  LL_LAUNCHED();
+  int st = 0;
+  LL_CU(cudaMemcpyAsync(&st, H->lu_status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LL_CU(cudaStreamSynchronize(s));
+  if (st) throw Status{LL_SINGULAR_COARSE};
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle (Sec. 3): pre-smoothing, residual, restriction, coarse correction,
+// prolongation, post-smoothing; x = 0 initially on every level
+// ---------------------------------------------------------------------------
+template <typename T>
+void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
+  int N = H->ncoarse3;
+  k_lu_solve<T><<<1, 256, N * sizeof(double), H->s>>>(N, H->lu, H->perm, b, x);
+  LL_LAUNCHED();
+}
+
+template <typename T>
+void smooth_level(ll_mg_hierarchy* H, int l, bool forward) {
+  CLevel& L = H->lev[l];
+  for (int t = 0; t < L.ncol; ++t) {
+    int c = forward ? t : L.ncol - 1 - t;
+    int a = L.h_cptr[c], cnt = L.h_cptr[c + 1] - a;
+    if (cnt == 0) continue;
+    kb_smooth<T, kLanes><<<cdiv((long)cnt * kLanes, kBlock), kBlock, 0, H->s>>>(
+        cnt, L.crow.p + a, L.rowptr, L.col, L.val<T>(), L.dinv<T>(), L.b<T>(), L.x<T>());
+    LL_LAUNCHED();
+  }
+}
+
+template <typename T>
+void vcycle_coarse(ll_mg_hierarchy* H, int l) {
+  CLevel& L = H->lev[l];
+  cudaStream_t s = H->s;
+  if (l == H->nlev - 1) {
+    coarse_solve<T>(H, L.b<T>(), L.x<T>());
+    return;
+  }
+  CLevel& N = H->lev[l + 1];
+  k_zero<T><<<cdiv(3L * L.n, kBlock), kBlock, 0, s>>>(3L * L.n, L.x<T>());
+  LL_LAUNCHED();
+  for (int sweep = 0; sweep < H->prm.nu_pre; ++sweep) smooth_level<T>(H, l, true);
+  kb_residual<T, kLanes><<<cdiv((long)L.n * kLanes, kBlock), kBlock, 0, s>>>(L.n, L.rowptr, L.col, L.val<T>(),
+                                                                              L.b<T>(), L.x<T>(), L.r<T>());
+  LL_LAUNCHED();
+  kb_restrict<T><<<cdiv(N.n, kBlock), kBlock, 0, s>>>(N.n, N.mptr, N.mem, L.r<T>(), N.b<T>());
+  LL_LAUNCHED();
+  vcycle_coarse<T>(H, l + 1);
+  kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
+  LL_LAUNCHED();
+  for (int sweep = 0; sweep < H->prm.nu_post; ++sweep) smooth_level<T>(H, l, false);
+}
+
+// z = V-cycle(r) on level 0; r float64 red-black, z red-black in T
+template <typename T>
+void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
+  cudaStream_t s = H->s;
+  const GridGeom& g = H->g;
+  if (H->nlev == 1) {  // the whole problem is the coarsest level
+    DBuf<T> tb, tx;
+    tb.alloc(H->ncoarse3);
+    tx.alloc(H->ncoarse3);
+    k_rb_to_cellmajor<double, T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->nat_of_slot, r, tb);
+    LL_LAUNCHED();
+    coarse_solve<T>(H, tb, tx);
+    k_cellmajor_to_rb<T, T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->nat_of_slot, tx, z);
+    LL_LAUNCHED();
+    LL_CU(cudaStreamSynchronize(s));
+    return;
+  }
+  CLevel& L1 = H->lev[1];
+  const T* chat = H->chat<T>();
+  const T* dinv = H->dinv0<T>();
+  T inv_dt = (T)(1.0 / H->dt);
+  int nb = cdiv(g.nh, kBlock);
+  if (H->prm.nu_pre >= 1) {
+    k0_smooth<T, 0><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+    LL_LAUNCHED();
+    k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+    LL_LAUNCHED();
+    for (int sweep = 1; sweep < H->prm.nu_pre; ++sweep) {
+      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+      LL_LAUNCHED();
+      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+      LL_LAUNCHED();
+    }
+    k0_restrict<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
+                                                          L1.b<T>());
+  } else {
+    k_zero<T><<<cdiv(H->n3, kBlock), kBlock, 0, s>>>(H->n3, z);
+    LL_LAUNCHED();
+    k0_restrict_b<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, L1.n, L1.mptr, L1.mem, L1.b<T>());
+  }
+  LL_LAUNCHED();
+  vcycle_coarse<T>(H, 1);
+  if (H->prm.nu_post >= 1) {
+    k0_smooth<T, 2><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, H->agg0, L1.x<T>());
+    LL_LAUNCHED();
+    k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+    LL_LAUNCHED();
+    for (int sweep = 1; sweep < H->prm.nu_post; ++sweep) {
+      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+      LL_LAUNCHED();
+      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+      LL_LAUNCHED();
+    }
+  } else {
+    k0_prolong<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->agg0, L1.x<T>(), z);
+    LL_LAUNCHED();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GCR (Algorithm 1) with classical Gram-Schmidt applied twice
+// ---------------------------------------------------------------------------
+void read_head(ll_mg_hierarchy* H) {
+  LL_CU(cudaMemcpyAsync(H->h_head, H->scal.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+  LL_CU(cudaStreamSynchronize(H->s));
+}
+
+void finish(ll_mg_hierarchy* H, int nvals, double* out) {
+  k_finish<<<nvals, kBlock, 0, H->s>>>(H->partial, out);
+  LL_LAUNCHED();
+}
+
+void true_residual(ll_mg_hierarchy* H) {
+  kg_residual<<<kRedBlocks, kBlock, 0, H->s>>>(H->g, H->bw, H->xw, H->chat64, 1.0 / H->dt, H->r, H->partial);
+  LL_LAUNCHED();
+  finish(H, 2, &H->scal.p->rn2);
+  read_head(H);
+}
+
+template <typename T>
+int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int* iters, double* relres) {
+  cudaStream_t s = H->s;
+  const GridGeom& g = H->g;
+  long n3 = H->n3;
+  int nbs = cdiv(H->n2, kBlock), nbv = cdiv(n3, kBlock);
+  k_to_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, b_nat, H->bw);
+  LL_LAUNCHED();
+  k_to_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, x_nat, H->xw);
+  LL_LAUNCHED();
+  GcrScal* S = H->scal.p;
+  int total = 0, status = LL_NOT_CONVERGED;
+  double bnorm = 0;
+  for (;;) {
+    true_residual(H);
+    double rn2 = H->h_head[0];
+    bnorm = sqrt(H->h_head[1]);
+    if (bnorm == 0.0) {
+      k_zero<double><<<nbv, kBlock, 0, s>>>(n3, H->xw);
+      LL_LAUNCHED();
+      status = LL_OK;
+      break;
+    }
+    if (!isfinite(rn2)) {
+      status = LL_BREAKDOWN;
+      break;
+    }
+    if (sqrt(rn2) < rtol * bnorm) {
+      status = LL_OK;
+      break;
+    }
+    if (total >= H->prm.maxit) break;
+    int m = std::min(H->prm.restart, H->prm.maxit - total);
+    int jdone = 0;
+    bool broke = false;
+    for (int j = 0; j < m; ++j) {
+      T* zj = H->Z<T>() + (size_t)j * n3;
+      double* cj = H->C.p + (size_t)j * n3;
+      vcycle<T>(H, H->r, zj);                                                       // step 1
+      kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);        // step 2
+      LL_LAUNCHED();
+      for (int pass = 0; pass < 2 && j > 0; ++pass) {                                // step 3
+        for (int i0 = 0; i0 < j; i0 += kDotChunk) {
+          int cnt = std::min(kDotChunk, j - i0);
+          kg_multidot<kDotChunk><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
+          LL_LAUNCHED();
+          finish(H, cnt, S->d + i0);
+        }
+        k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0);
+        LL_LAUNCHED();
+        kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef);
+        LL_LAUNCHED();
+      }
+      kg_dot2<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->r, H->partial);             // step 4
+      LL_LAUNCHED();
+      finish(H, 2, &S->cc);
+      k_norm_coef<<<1, 1, 0, s>>>(S, j);
+      LL_LAUNCHED();
+      kg_rupdate<<<kRedBlocks, kBlock, 0, s>>>(n3, H->r, cj, &S->rcoef, H->partial); // step 5
+      LL_LAUNCHED();
+      finish(H, 1, &S->rn2);
+      ++total;
+      read_head(H);
+      double gjj = H->h_head[4];
+      if (!(gjj > 0.0) || !isfinite(gjj)) {
+        broke = true;
+        break;
+      }
+      jdone = j + 1;
+      double rj = sqrt(H->h_head[0]);
+      if (!isfinite(rj)) {
+        broke = true;
+        break;
+      }
+      if (rj < rtol * bnorm) break;                                                  // step 6
+    }
+    if (jdone > 0) {
+      k_backsub<<<1, 1, 0, s>>>(S, jdone);
+      LL_LAUNCHED();
+      kg_xupdate<T><<<nbv, kBlock, 0, s>>>(n3, H->xw, H->Z<T>(), jdone, S->y);
+      LL_LAUNCHED();
+    }
+    if (broke) {
+      status = LL_BREAKDOWN;
+      break;
+    }
+  }
+  true_residual(H);
+  if (iters) *iters = total;
+  if (relres) *relres = bnorm > 0 ? sqrt(H->h_head[0]) / bnorm : 0.0;
+  k_from_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, H->xw, x_nat);
+  LL_LAUNCHED();
+  LL_CU(cudaStreamSynchronize(s));
+  return status;
+}
+
+int solve(ll_mg_hierarchy* H, const double* b, double* x, double rtol, int* it, double* rr) {
+  if (rtol <= 0) rtol = H->prm.rtol;
+  if (H->prm.precision == LL_MIXED_FP32) return gcr<float>(H, b, x, rtol, it, rr);
+  return gcr<double>(H, b, x, rtol, it, rr);
+}
+
+bool valid_params(const ll_mg_params& p) {
+  return p.rtol >= 0 && p.maxit >= 0 && p.restart >= 1 && p.restart <= kMaxRestart && p.nu_pre >= 0 &&
+         p.nu_pre <= 16 && p.nu_post >= 0 && p.nu_post <= 16 && p.coarsest_cells >= 1 && p.max_levels >= 1 &&
+         p.max_levels <= kMaxLevels && p.rounds >= 1 && (p.precision == LL_FP64 || p.precision == LL_MIXED_FP32);
+}
+
+int create(const double* m, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p, void* stream,
+           ll_mg_hierarchy** out) {
+  ll_mg_hierarchy* H = nullptr;
+  try {
+    H = new ll_mg_hierarchy();
+    ll_mg_default_params(&H->prm);
+    if (p) H->prm = *p;
+    H->s = (cudaStream_t)stream;
+    H->alpha = alpha;
+    H->dt = dt;
+    H->h = h;
+    GridGeom& g = H->g;
+    g.nx = grid.nx;
+    g.ny = grid.ny;
+    g.nz = grid.nz;
+    g.nxh = (grid.nx + 1) / 2;
+    g.nh = (long)g.nxh * grid.ny * grid.nz;
+    g.n = (long)grid.nx * grid.ny * grid.nz;
+    H->n2 = 2 * g.nh;
+    H->n3 = 3 * H->n2;
+    symbolic(H);
+    allocate(H);
+    numeric(H, m);
+    *out = H;
+    return LL_OK;
+  } catch (Status st) {
+    delete H;
+    return st.code;
+  } catch (std::bad_alloc&) {
+    delete H;
+    return LL_ENOMEM;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void ll_mg_default_params(ll_mg_params* p) {
+  if (!p) return;
+  p->rtol = 1e-8;
+  p->maxit = 1000;
+  p->restart = 20;
+  p->nu_pre = 1;
+  p->nu_post = 1;
+  p->coarsest_cells = 64;
+  p->max_levels = 20;
+  p->rounds = 32;
+  p->seed = 0;
+  p->precision = LL_FP64;
+}
+
+static bool valid_problem(double alpha, double dt, double h, ll_grid grid) {
+  if (!(dt > 0) || !(h > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(h) || !isfinite(alpha)) return false;
+  if (grid.nx < 1 || grid.ny < 1 || grid.nz < 1) return false;
+  long n = (long)grid.nx * grid.ny * grid.nz;
+  return n >= 2 && n < (1L << 29);
+}
+
+int ll_mg_setup(const double* m_tilde, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p,
+                void* cuda_stream, ll_mg_hierarchy** out) {
+  if (!m_tilde || !out || !valid_problem(alpha, dt, h, grid)) return LL_EINVAL;
+  if (p && !valid_params(*p)) return LL_EINVAL;
+  return create(m_tilde, alpha, dt, h, grid, p, cuda_stream, out);
+}
+
+int ll_mg_update(ll_mg_hierarchy* H, const double* m_tilde, double alpha, double dt) {
+  if (!H || !m_tilde || !(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha)) return LL_EINVAL;
+  try {
+    H->alpha = alpha;
+    H->dt = dt;
+    numeric(H, m_tilde);
+    return LL_OK;
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, int* iterations,
+                double* rel_residual) {
+  if (!H || !rhs || !x) return LL_EINVAL;
+  try {
+    return solve(H, rhs, x, rtol, iterations, rel_residual);
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p,
+            void* cuda_stream, int* iters_per_step, double* relres_per_step) {
+  if (!m || n_steps < 0 || !valid_problem(alpha, dt, h, grid)) return LL_EINVAL;
+  if (p && !valid_params(*p)) return LL_EINVAL;
+  if (n_steps == 0) return LL_OK;
+  ll_mg_hierarchy* H = nullptr;
+  int st = create(m, alpha, dt, h, grid, p, cuda_stream, &H);
+  if (st != LL_OK) return st;
+  int worst = LL_OK;
+  try {
+    long n3 = 3 * H->g.n;
+    for (int k = 0; k < n_steps; ++k) {
+      if (k > 0) numeric(H, m);
+      k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
+      LL_LAUNCHED();
+      LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+      int it = 0;
+      double rr = 0;
+      int s2 = solve(H, H->stepb, H->stepx, H->prm.rtol, &it, &rr);
+      if (iters_per_step) iters_per_step[k] = it;
+      if (relres_per_step) relres_per_step[k] = rr;
+      worst = std::max(worst, s2);
+      H->flag.zero(H->s);
+      k_renormalise<<<cdiv(H->g.n, kBlock), kBlock, 0, H->s>>>(H->g.n, H->stepx, m, H->flag);
+      LL_LAUNCHED();
+      check_flag(H, LL_BREAKDOWN);
+    }
+  } catch (Status e) {
+    worst = e.code;
+  }
+  delete H;
+  return worst;
+}
+
+void ll_mg_destroy(ll_mg_hierarchy* H) {
+  if (H) {
+    cudaStreamSynchronize(H->s);
+    delete H;
+  }
+}
+
+const char* ll_status_string(int status) {
+  switch (status) {
+    case LL_OK: return "converged";
+    case LL_NOT_CONVERGED: return "not converged within maxit";
+    case LL_BREAKDOWN: return "breakdown (non-finite residual or zero GCR norm)";
+    case LL_EINVAL: return "invalid argument";
+    case LL_ECUDA: return "CUDA runtime error";
+    case LL_ENOMEM: return "out of device memory";
+    case LL_SINGULAR_COARSE: return "singular block or coarsest matrix";
+    case LL_ELIMIT: return "structural limit exceeded";
+    default: return "unknown status";
+  }
+}
+
+int ll_mg_levels(const ll_mg_hierarchy* H) { return H ? H->nlev : -1; }
+
+int ll_mg_level_cells(const ll_mg_hierarchy* H, int l) {
+  if (!H || l < 0 || l >= H->nlev) return -1;
+  return l == 0 ? (int)H->g.n : H->lev[l].n;
+}
+
+int ll_mg_level_aggregates(const ll_mg_hierarchy* H, int l, int* agg) {
+  if (!H || !agg || l < 0 || l >= H->nlev - 1) return LL_EINVAL;
+  const int* src = l == 0 ? H->agg_nat0.p : H->lev[l].agg.p;
+  int n = ll_mg_level_cells(H, l);
+  if (cudaMemcpy(agg, src, n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LL_ECUDA;
+  return LL_OK;
+}
+
+int ll_mg_level_colours(const ll_mg_hierarchy* H, int l, int* colour) {
+  if (!H || !colour || l < 0 || l >= H->nlev) return LL_EINVAL;
+  if (l == 0) {
+    const GridGeom& g = H->g;
+    for (long k = 0; k < g.n; ++k) {
+      long x = k % g.nx, t = k / g.nx, y = t % g.ny, z = t / g.ny;
+      colour[k] = (int)((x + y + z) & 1);
+    }
+    return LL_OK;
+  }
+  if (cudaMemcpy(colour, H->lev[l].colour.p, H->lev[l].n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LL_ECUDA;
+  return LL_OK;
+}
+
+int ll_mg_level_blocks(const ll_mg_hierarchy* H, int l) {
+  if (!H || l < 1 || l >= H->nlev) return -1;
+  return H->lev[l].nnzb;
+}
+
+int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col, double* val) {
+  if (!H || l < 1 || l >= H->nlev || !rowptr || !col || !val) return LL_EINVAL;
+  const CLevel& C = H->lev[l];
+  if (cudaMemcpy(rowptr, C.rowptr.p, (C.n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(col, C.col.p, C.nnzb * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(val, C.val64.p, 9L * C.nnzb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LL_ECUDA;
+  return LL_OK;
+}
+
+int ll_mg_apply(ll_mg_hierarchy* H, const double* x, double* y) {
+  if (!H || !x || !y) return LL_EINVAL;
+  try {
+    const GridGeom& g = H->g;
+    int nbs = cdiv(H->n2, kBlock);
+    k_to_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, x, H->xw);
+    LL_LAUNCHED();
+    kg_apply<double><<<nbs, kBlock, 0, H->s>>>(g, H->xw, H->chat64, 1.0 / H->dt, H->r);
+    LL_LAUNCHED();
+    k_from_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, H->r, y);
+    LL_LAUNCHED();
+    LL_CU(cudaStreamSynchronize(H->s));
+    return LL_OK;
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+int ll_mg_vcycle(ll_mg_hierarchy* H, const double* r, double* z) {
+  if (!H || !r || !z) return LL_EINVAL;
+  try {
+    const GridGeom& g = H->g;
+    int nbs = cdiv(H->n2, kBlock);
+    k_to_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, r, H->bw);
+    LL_LAUNCHED();
+    if (H->prm.precision == LL_MIXED_FP32) {
+      vcycle<float>(H, H->bw, H->Z32.p);
+      k_from_rb<float, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, H->Z32.p, z);
+    } else {
+      vcycle<double>(H, H->bw, H->Z64.p);
+      k_from_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, H->Z64.p, z);
+    }
+    LL_LAUNCHED();
+    LL_CU(cudaStreamSynchronize(H->s));
+    return LL_OK;
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forward) {
+  if (!H || !b || !x || l < 0 || l >= H->nlev || H->prm.precision != LL_FP64) return LL_EINVAL;
+  if (l == H->nlev - 1 && l > 0) return LL_EINVAL;  // the coarsest level is solved, not smoothed
+  try {
+    const GridGeom& g = H->g;
+    cudaStream_t s = H->s;
+    if (l == 0) {
+      if (H->nlev == 1) return LL_EINVAL;
+      int nbs = cdiv(H->n2, kBlock), nb = cdiv(g.nh, kBlock);
+      k_to_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, b, H->bw);
+      LL_LAUNCHED();
+      k_to_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, x, H->xw);
+      LL_LAUNCHED();
+      for (int t = 0; t < 2; ++t) {
+        int c = forward ? t : 1 - t;
+        k0_smooth<double, 1><<<nb, kBlock, 0, s>>>(g, c, H->bw, H->xw.p, H->chat64, H->dinv64, nullptr, nullptr);
+        LL_LAUNCHED();
+      }
+      k_from_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, H->xw, x);
+      LL_LAUNCHED();
+    } else {
+      CLevel& L = H->lev[l];
+      LL_CU(cudaMemcpyAsync(L.b64.p, b, 3L * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      LL_CU(cudaMemcpyAsync(L.x64.p, x, 3L * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      smooth_level<double>(H, l, forward != 0);
+      LL_CU(cudaMemcpyAsync(x, L.x64.p, 3L * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    LL_CU(cudaStreamSynchronize(s));
+    return LL_OK;
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+}  // extern "C"

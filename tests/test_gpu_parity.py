@@ -1,0 +1,295 @@
+"""Parity of the sm_103a solver with the FP64 oracle, through the C ABI.
+
+Integer results (aggregates, colours) must match bit for bit.  Floating-point
+results must match within tolerances derived from float64 rounding:
+operators and single smoothing sweeps to 1e-12 of the largest entry, a
+V-cycle to 1e-11, solves to a relative difference of 1e-10 when both sides
+run to rtol 1e-12 (the FP64-path target), and the mixed-precision path to
+1e-8 of the FP64 solution.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_09102_b300 import inputs
+from tests import reference_forms as rf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2608_09102_b300 as ll  # noqa: E402
+
+DEV = "cuda:0"
+
+# (grid, h, alpha, dt, field generator, coarsest_cells)
+CASES = {
+    "2d": ((32, 32, 1), 1 / 32, 0.1, 4.0 / 32 ** 2, "smooth", 16),
+    "3d": ((12, 10, 8), 1 / 12, 0.02, 2.0 / 144, "vortex", 8),
+    "odd": ((13, 7, 5), 1 / 13, 0.3, 1e-3, "smooth", 8),
+    "1d": ((60, 1, 1), 1 / 60, 1.0, 1e-3, "smooth", 4),
+    "cube": ((8, 8, 8), 1 / 8, 0.1, 8.0 / 64, "vortex", 4),
+}
+
+
+def _field(kind, grid, seed=0):
+    nx, ny, nz = grid
+    if kind == "vortex":
+        return inputs.vortex(nx, ny, nz, seed=seed)
+    return inputs.smooth_field(nx, ny, nz, seed=seed)
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device=DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _pair(name, precision=ll.LL_FP64, rtol=1e-12, seed=0):
+    grid, h, alpha, dt, kind, cc = CASES[name]
+    m = _field(kind, grid, seed).reshape(-1)
+    po = oracle.Params(rtol=rtol, coarsest_cells=cc)
+    pg = ll.Params(rtol=rtol, coarsest_cells=cc, precision=precision)
+    return grid, h, alpha, dt, m, oracle.Hierarchy(grid, h, alpha, dt, m, po), ll.Hierarchy(_t(m), alpha, dt, h, grid, pg)
+
+
+def _cm_to_aos(v, n):
+    return np.ascontiguousarray(np.asarray(v).reshape(3, n).T).reshape(-1)
+
+
+def _aos_to_cm(v, n):
+    return np.ascontiguousarray(np.asarray(v).reshape(n, 3).T).reshape(-1)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hierarchy_structure_is_bit_exact(name):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    assert G.levels == O.nlevels
+    for l in range(O.nlevels):
+        assert G.level_cells(l) == O.cells(l)
+        assert np.array_equal(G.colours(l), O.colours(l)), l
+        if l < O.nlevels - 1:
+            assert np.array_equal(G.aggregates(l), O.agg(l)), l
+
+
+@pytest.mark.parametrize("seed", [1, 7])
+def test_aggregates_follow_the_seed(seed):
+    grid = (24, 20, 6)
+    m = inputs.smooth_field(*grid).reshape(-1)
+    O = oracle.Hierarchy(grid, 0.05, 0.1, 1e-3, m, oracle.Params(coarsest_cells=8, seed=seed))
+    G = ll.Hierarchy(_t(m), 0.1, 1e-3, 0.05, grid, ll.Params(coarsest_cells=8, seed=seed))
+    for l in range(O.nlevels - 1):
+        assert np.array_equal(G.aggregates(l), O.agg(l))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_galerkin_operators(name):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    for l in range(1, O.nlevels):
+        n = O.cells(l)
+        rp, ci, val = G.operator(l)
+        dense = np.zeros((3 * n, 3 * n))
+        for I in range(n):
+            for p in range(rp[I], rp[I + 1]):
+                dense[3 * I:3 * I + 3, 3 * ci[p]:3 * ci[p] + 3] = val[p]
+        perm = np.array([c * n + I for I in range(n) for c in range(3)])
+        ref = O.matrix(l).toarray()[np.ix_(perm, perm)]
+        np.testing.assert_allclose(dense, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_operator_apply(name):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    x = inputs.rhs_field(*grid, seed=3).reshape(-1)
+    y = torch.empty_like(_t(x))
+    G.apply(_t(x), y)
+    ref = O.apply(x)
+    np.testing.assert_allclose(_np(y), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("forward", [True, False])
+def test_smoother_sweeps(name, forward):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    n = O.cells(0)
+    b = inputs.rhs_field(*grid, seed=4).reshape(-1)
+    x0 = inputs.rhs_field(*grid, seed=5).reshape(-1)
+    x = _t(x0)
+    G.smooth(0, _t(b), x, forward)
+    ref = O.smooth(b, x0, forward, l=0)
+    np.testing.assert_allclose(_np(x), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    if O.nlevels > 2:
+        n1 = O.cells(1)
+        rng = np.random.default_rng(6)
+        b1, x1 = rng.standard_normal(3 * n1), rng.standard_normal(3 * n1)
+        xg = torch.tensor(_cm_to_aos(x1, n1), device=DEV)
+        G.smooth(1, torch.tensor(_cm_to_aos(b1, n1), device=DEV), xg, forward)
+        ref1 = O.smooth(b1, x1, forward, l=1)
+        np.testing.assert_allclose(_aos_to_cm(_np(xg), n1), ref1, rtol=0, atol=1e-12 * np.abs(ref1).max())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle(name):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    r = inputs.rhs_field(*grid, seed=8).reshape(-1)
+    z = torch.empty_like(_t(r))
+    G.vcycle(_t(r), z)
+    ref = O.vcycle(r)
+    assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_matches_oracle(name):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    b = m / dt
+    xo, sto, ito, rro = O.solve(b, np.zeros_like(b))
+    x = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(b), x)
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert rr < 1e-12
+    assert abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(_np(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", ["2d", "3d"])
+def test_time_steps_match_oracle(name):
+    grid, h, alpha, dt, kind, cc = CASES[name]
+    m0 = _field(kind, grid).reshape(-1)
+    mo, ito, rro, sto = oracle.step(m0, 3, grid, h, alpha, dt, oracle.Params(rtol=1e-12, coarsest_cells=cc))
+    mg = _t(m0)
+    st, its, rrs = ll.step(mg, 3, alpha, dt, h, grid, ll.Params(rtol=1e-12, coarsest_cells=cc))
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert np.all(np.abs(np.array(its) - ito) <= 1)
+    assert np.abs(_np(mg) - mo).max() <= 1e-10
+    nrm = np.linalg.norm(_np(mg).reshape(3, -1), axis=0)
+    np.testing.assert_allclose(nrm, 1.0, atol=1e-14)
+
+
+def test_host_buffers_round_trip():
+    grid, h, alpha, dt, kind, cc = CASES["2d"]
+    m0 = _field(kind, grid).reshape(-1)
+    mh = torch.tensor(m0)
+    md = _t(m0)
+    p = ll.Params(rtol=1e-10, coarsest_cells=cc)
+    ll.step(mh, 2, alpha, dt, h, grid, p)
+    ll.step(md, 2, alpha, dt, h, grid, p)
+    assert torch.equal(mh, md.cpu())
+
+
+def test_single_level_problem_is_solved_directly():
+    grid = (4, 4, 1)
+    m = inputs.smooth_field(*grid).reshape(-1)
+    O = oracle.Hierarchy(grid, 0.25, 0.1, 1e-2, m, oracle.Params(rtol=1e-13))
+    G = ll.Hierarchy(_t(m), 0.1, 1e-2, 0.25, grid, ll.Params(rtol=1e-13))
+    assert G.levels == O.nlevels == 1
+    b = inputs.rhs_field(*grid).reshape(-1)
+    x = torch.zeros(48, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(b), x)
+    xo, _, ito, _ = O.solve(b)
+    assert st == ll.LL_OK and it == ito == 1
+    assert np.linalg.norm(_np(x) - xo) <= 1e-12 * np.linalg.norm(xo)
+
+
+def test_statuses():
+    grid, h, alpha, dt, kind, cc = CASES["2d"]
+    m = _field(kind, grid).reshape(-1)
+    n3 = m.size
+    G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(maxit=1, coarsest_cells=cc))
+    x = torch.zeros(n3, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(m / dt), x)
+    assert st == ll.LL_NOT_CONVERGED and it == 1 and 0 < rr < 1
+    x = torch.ones(n3, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(torch.zeros(n3, dtype=torch.float64, device=DEV), x)
+    assert st == ll.LL_OK and it == 0 and float(x.abs().max()) == 0.0
+    bad = _t(m / dt)
+    bad[5] = float("nan")
+    st, it, rr = G.solve(bad, torch.zeros(n3, dtype=torch.float64, device=DEV))
+    assert st == ll.LL_BREAKDOWN
+
+
+@pytest.mark.parametrize("name", ["2d", "3d", "odd"])
+def test_mixed_precision_path(name):
+    grid, h, alpha, dt, m, O, G = _pair(name)
+    Gm = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-10, coarsest_cells=CASES[name][5],
+                                                          precision=ll.LL_MIXED_FP32))
+    b = m / dt
+    x64 = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    x32 = torch.zeros_like(x64)
+    G.solve(_t(b), x64, 1e-12)
+    st, it, rr = Gm.solve(_t(b), x32)
+    assert st == ll.LL_OK and rr < 1e-10
+    assert float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64)) <= 1e-8
+
+
+def test_config1_against_sparse_direct_solve():
+    """2-D 64x64, alpha 0.1, dt 1e-3, smooth field: the solution equals the
+    sparse direct solution within 1e-10."""
+    import scipy.sparse.linalg as spla
+
+    grid, h, alpha, dt = (64, 64, 1), 1 / 64, 0.1, 1e-3
+    m = inputs.smooth_field(*grid, seed=0).reshape(-1)
+    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(coarsest_cells=10 ** 6, max_levels=1))
+    xe = spla.spsolve(O.matrix(0).tocsc(), m / dt)
+    G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-12))
+    x = torch.zeros(m.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(m / dt), x)
+    assert st == ll.LL_OK
+    assert np.linalg.norm(_np(x) - xe) <= 1e-10 * np.linalg.norm(xe)
+
+
+# ---------------------------------------------------------------------------
+# full size (128^3, the time-stepping workload): aggregates bit-exact,
+# properties of the solve that hold at any size
+# ---------------------------------------------------------------------------
+
+FULL = (128, 128, 128)
+
+
+@pytest.fixture(scope="module")
+def full_case():
+    m = inputs.vortex(*FULL, seed=0).reshape(-1)
+    h, alpha, dt = 1 / 128, 0.02, 5e-4
+    G = ll.Hierarchy(_t(m), alpha, dt, h, FULL, ll.Params(rtol=1e-8))
+    return m, h, alpha, dt, G
+
+
+def test_full_size_level0_aggregates(full_case):
+    m, h, alpha, dt, G = full_case
+    agg, nc = oracle.grid_aggregates(FULL)
+    assert G.level_cells(1) == nc
+    assert np.array_equal(G.aggregates(0), agg)
+
+
+def test_full_size_solve_properties(full_case):
+    m, h, alpha, dt, G = full_case
+    b = m / dt
+    x = _t(m)
+    st, it, rr = G.solve(_t(b), x)
+    assert st == ll.LL_OK and rr < 1e-8
+    xs = _np(x)
+    r = b - oracle.operator_apply(FULL, h, alpha, dt, m, xs)
+    relres = np.linalg.norm(r) / np.linalg.norm(b)
+    assert relres < 1e-8 and abs(relres - rr) <= 1e-3 * rr
+    n = m.size // 3
+    mx = (m.reshape(3, n) * xs.reshape(3, n)).sum(0)
+    mr = (m.reshape(3, n) * r.reshape(3, n)).sum(0)
+    assert np.all(np.abs(mx - 1.0 + dt * mr) <= 1e-12)
+
+
+def test_full_size_dct_closed_form():
+    mdir = (0.36, 0.48, 0.8)
+    h, alpha, dt = 1 / 128, 0.02, 5e-4
+    m = inputs.constant_field(*FULL, direction=mdir).reshape(-1)
+    b = inputs.rhs_field(*FULL, seed=2).reshape(-1)
+    G = ll.Hierarchy(_t(m), alpha, dt, h, FULL, ll.Params(rtol=1e-12))
+    x = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(b), x)
+    assert st == ll.LL_OK
+    xe = rf.dct_solve(*FULL, h, alpha, dt, mdir, b)
+    assert np.linalg.norm(_np(x) - xe) <= 1e-10 * np.linalg.norm(xe)
