@@ -122,6 +122,13 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid grid,
             const ll_mg_params* p, void* cuda_stream, int* iters_per_step, double* relres_per_step);
 
+/* n_steps time steps on an existing hierarchy (same grid and parameters;
+ * alpha and dt are the hierarchy's): per step the numeric setup is redone for
+ * m~ = m, then solve and project as ll_step does.  Reuses the aggregates.
+ *   m device SoA 3*N float64, in/out; iters/relres host, optional, n_steps.
+ * Returns the worst status over the steps (errors stop early). */
+int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step);
+
 /* Release the hierarchy and all its device memory (NULL is ignored). */
 void ll_mg_destroy(ll_mg_hierarchy* H);
 
@@ -145,6 +152,28 @@ int ll_mg_level_blocks(const ll_mg_hierarchy* H, int l);
  * col (nnzb), val (9*nnzb, each block row-major, component (r, c) at
  * 3r + c, cell-major unknowns).  Values are float64 whatever the storage. */
 int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col, double* val);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all hierarchies, all threads). */
+long long ll_launch_count(void);
+
+/* Kernel timing by kind, for benchmarks.  While enabled, every kernel of a
+ * kind whose bit is set in `kinds` is bracketed by two CUDA events on the
+ * hierarchy's stream (no synchronisation is added).  Kinds: */
+#define LL_KIND_L0_SMOOTH 0   /* level-0 block Gauss-Seidel half-sweeps */
+#define LL_KIND_L0_RESTRICT 1 /* level-0 residual + restriction */
+#define LL_KIND_OUTER_APPLY 2 /* float64 operator of the GCR (A z) and true residual */
+#define LL_KIND_BSR_SMOOTH 3  /* coarse-level block Gauss-Seidel */
+#define LL_KIND_BSR_OTHER 4   /* coarse-level residual, restriction, prolongation, zeroing */
+#define LL_KIND_GCR_VECTOR 5  /* GCR dots, updates, reductions, scalar kernels */
+#define LL_KIND_COARSEST 6    /* coarsest-level LU solve */
+#define LL_KIND_NUMERIC 7     /* numeric setup: coefficients, Galerkin, LU factor */
+#define LL_NUM_KINDS 8
+/* Start (kinds != 0) or stop (kinds == 0) timing; starting clears totals. */
+int ll_mg_profile(ll_mg_hierarchy* H, unsigned int kinds);
+/* Total milliseconds and number of launches recorded for one kind since
+ * timing started (synchronises the stream). */
+int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long* launches);
 
 /* y = A_0 x on level 0 (device SoA buffers), float64. */
 int ll_mg_apply(ll_mg_hierarchy* H, const double* x, double* y);

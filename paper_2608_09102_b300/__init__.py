@@ -28,7 +28,7 @@ EXPORTS = (
     "ll_mg_default_params", "ll_mg_setup", "ll_mg_update", "ll_mg_solve", "ll_step", "ll_mg_destroy",
     "ll_status_string", "ll_mg_levels", "ll_mg_level_cells", "ll_mg_level_aggregates",
     "ll_mg_level_colours", "ll_mg_level_blocks", "ll_mg_level_operator", "ll_mg_apply", "ll_mg_vcycle",
-    "ll_mg_smooth",
+    "ll_mg_smooth", "ll_mg_step", "ll_launch_count",
 )
 
 
@@ -103,6 +103,8 @@ def load_library():
         "ll_mg_apply": (i, [vp, vp, vp]),
         "ll_mg_vcycle": (i, [vp, vp, vp]),
         "ll_mg_smooth": (i, [vp, i, vp, vp, i]),
+        "ll_mg_step": (i, [vp, vp, i, ip, dp]),
+        "ll_launch_count": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +193,20 @@ class Hierarchy:
         _check(st, "ll_mg_solve")
         return st, it.value, rr.value
 
+    def step(self, m, n_steps: int = 1):
+        """n_steps time steps on this hierarchy (``ll_mg_step``), in place.
+
+        ``m`` may be a CUDA tensor or a CPU tensor (copied to the device and
+        back).  Returns (status, iterations per step, relres per step)."""
+        dev = m if m.is_cuda else m.to("cuda", non_blocking=True)
+        its = (ctypes.c_int * max(1, n_steps))()
+        rrs = (ctypes.c_double * max(1, n_steps))()
+        st = load_library().ll_mg_step(self._h, _field(dev, self.n, "m"), int(n_steps), its, rrs)
+        _check(st, "ll_mg_step")
+        if dev is not m:
+            m.copy_(dev, non_blocking=False)
+        return st, list(its[:n_steps]), list(rrs[:n_steps])
+
     # -- introspection ---------------------------------------------------
     @property
     def levels(self) -> int:
@@ -239,6 +255,11 @@ class Hierarchy:
         n = self.n if l == 0 else self.level_cells(l)
         st = load_library().ll_mg_smooth(self._h, l, _field(b, n, "b"), _field(x, n, "x"), 1 if forward else 0)
         _check(st, "ll_mg_smooth", ok=(LL_OK,))
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(load_library().ll_launch_count())
 
 
 def step(m, n_steps: int, alpha, dt, h, grid, params: Params | None = None):

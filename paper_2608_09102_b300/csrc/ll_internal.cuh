@@ -21,7 +21,13 @@ struct Status {
     cudaError_t e_ = (call);                                          \
     if (e_ != cudaSuccess) throw ::llmg::Status{e_ == cudaErrorMemoryAllocation ? LL_ENOMEM : LL_ECUDA}; \
   } while (0)
-#define LL_LAUNCHED() LL_CU(cudaGetLastError())
+// called after every kernel launch: checks it and counts it
+void count_launch();
+#define LL_LAUNCHED()              \
+  do {                             \
+    LL_CU(cudaGetLastError());     \
+    ::llmg::count_launch();        \
+  } while (0)
 
 constexpr int kBlock = 256;
 constexpr int kRedBlocks = 592;   // 4 x 148 SMs: fixed grid of reduction kernels

@@ -1,6 +1,7 @@
 // Hierarchy, numeric setup, V-cycle, GCR and the C ABI of the sm_103a
 // aggregation-multigrid solver (see include/ll_mg.h for the contract).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -10,7 +11,12 @@
 #include "ll_kernels.cuh"
 #include "ll_setup.cuh"
 
+#include <atomic>
+
 namespace llmg {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   int n = 0, nnzb = 0, ncol = 0;
@@ -49,7 +55,9 @@ using namespace llmg;
 
 struct ll_mg_hierarchy {
   ll_mg_params prm;
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;     // the library's own stream (capturable)
+  cudaStream_t user = nullptr;  // the caller's stream
+  cudaEvent_t entry_ev = nullptr;
   GridGeom g;
   double alpha = 0, dt = 1, h = 1;
   int nlev = 1;
@@ -71,8 +79,51 @@ struct ll_mg_hierarchy {
   double* h_head = nullptr;  // pinned copy of the first scalars
   // time-step workspace (natural layout)
   DBuf<double> stepb, stepx;
+  // single-level hierarchies: cell-major scratch of the direct solve
+  DBuf<double> single_b, single_x;
+  // kernel timing (ll_mg_profile)
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pairs[LL_NUM_KINDS];
+  double prof_ms[LL_NUM_KINDS] = {0};
+  long long prof_n[LL_NUM_KINDS] = {0};
+  cudaEvent_t event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      LL_CU(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+  // CUDA graphs of the GCR iterations (one per position j in a cycle)
+  bool use_graphs = true;
+  int capturing = -1;  // j of the iteration being captured, or -1
+  double graph_dt = 0;
+  cudaGraphExec_t graphs[kMaxRestart] = {nullptr};
+  unsigned graph_mask[kMaxRestart] = {0};
+  long long graph_kernels[kMaxRestart] = {0};
+  struct GPair {
+    int kind;
+    cudaEvent_t b, e;
+  };
+  std::vector<GPair> gpairs[kMaxRestart];
+  void drop_graph(int j) {
+    if (graphs[j]) cudaGraphExecDestroy(graphs[j]);
+    graphs[j] = nullptr;
+    for (auto& q : gpairs[j]) {
+      cudaEventDestroy(q.b);
+      cudaEventDestroy(q.e);
+    }
+    gpairs[j].clear();
+  }
   ~ll_mg_hierarchy() {
+    if (s) cudaStreamSynchronize(s);
+    for (int j = 0; j < kMaxRestart; ++j) drop_graph(j);
     if (h_head) cudaFreeHost(h_head);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (entry_ev) cudaEventDestroy(entry_ev);
+    if (s) cudaStreamDestroy(s);
   }
   template <typename T> T* chat();
   template <typename T> T* dinv0();
@@ -86,6 +137,43 @@ template <> double* ll_mg_hierarchy::Z<double>() { return Z64; }
 template <> float* ll_mg_hierarchy::Z<float>() { return Z32; }
 
 namespace {
+
+// brackets the launches in its scope with CUDA events when their kind is timed
+struct ProfScope {
+  ll_mg_hierarchy* H;
+  int kind;
+  cudaEvent_t b = nullptr;
+  ProfScope(ll_mg_hierarchy* h, int k) : H(h), kind(k) {
+    if (!(H->prof_mask & (1u << kind))) return;
+    if (H->capturing >= 0) {  // inside a graph: event-record nodes of its own
+      LL_CU(cudaEventCreate(&b));
+      LL_CU(cudaEventRecordWithFlags(b, H->s, cudaEventRecordExternal));
+    } else {
+      b = H->event();
+      LL_CU(cudaEventRecord(b, H->s));
+    }
+  }
+  ~ProfScope() noexcept(false) {
+    if (!b) return;
+    if (H->capturing >= 0) {
+      cudaEvent_t e;
+      LL_CU(cudaEventCreate(&e));
+      LL_CU(cudaEventRecordWithFlags(e, H->s, cudaEventRecordExternal));
+      H->gpairs[H->capturing].push_back({kind, b, e});
+    } else {
+      cudaEvent_t e = H->event();
+      LL_CU(cudaEventRecord(e, H->s));
+      H->prof_pairs[kind].push_back({b, e});
+    }
+  }
+};
+
+// make the library stream wait for the work already queued on the caller's
+void enter(ll_mg_hierarchy* H) {
+  LL_CU(cudaEventRecord(H->entry_ev, H->user));
+  LL_CU(cudaStreamWaitEvent(H->s, H->entry_ev, 0));
+}
+#define LL_PROF(kind) ProfScope prof_scope_(H, kind)
 
 constexpr int kLanes = 4;  // lanes per block row in the BSR kernels
 constexpr int kDotChunk = 8;
@@ -198,6 +286,10 @@ void allocate(ll_mg_hierarchy* H) {
   LL_CU(cudaMallocHost((void**)&H->h_head, 8 * sizeof(double)));
   H->stepb.alloc(3 * H->g.n);
   H->stepx.alloc(3 * H->g.n);
+  if (H->nlev == 1) {
+    H->single_b.alloc(H->ncoarse3);
+    H->single_x.alloc(H->ncoarse3);
+  }
 }
 
 // dense level-0 operator (single-level hierarchies), unknown 3k + c, k natural
@@ -255,6 +347,7 @@ __global__ void k_cellmajor_to_rb(GridGeom g, const int* __restrict__ nat, const
 // numeric setup (every time step)
 // ---------------------------------------------------------------------------
 void numeric(ll_mg_hierarchy* H, const double* m) {
+  LL_PROF(LL_KIND_NUMERIC);
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
   bool mixed = H->prm.precision == LL_MIXED_FP32;
@@ -307,6 +400,7 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
 template <typename T>
 void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
   int N = H->ncoarse3;
+  LL_PROF(LL_KIND_COARSEST);
   k_lu_solve<T><<<1, 256, N * sizeof(double), H->s>>>(N, H->lu, H->perm, b, x);
   LL_LAUNCHED();
 }
@@ -318,6 +412,7 @@ void smooth_level(ll_mg_hierarchy* H, int l, bool forward) {
     int c = forward ? t : L.ncol - 1 - t;
     int a = L.h_cptr[c], cnt = L.h_cptr[c + 1] - a;
     if (cnt == 0) continue;
+    LL_PROF(LL_KIND_BSR_SMOOTH);
     kb_smooth<T, kLanes><<<cdiv((long)cnt * kLanes, kBlock), kBlock, 0, H->s>>>(
         cnt, L.crow.p + a, L.rowptr, L.col, L.val<T>(), L.dinv<T>(), L.b<T>(), L.x<T>());
     LL_LAUNCHED();
@@ -333,17 +428,26 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
     return;
   }
   CLevel& N = H->lev[l + 1];
-  k_zero<T><<<cdiv(3L * L.n, kBlock), kBlock, 0, s>>>(3L * L.n, L.x<T>());
-  LL_LAUNCHED();
+  {
+    LL_PROF(LL_KIND_BSR_OTHER);
+    k_zero<T><<<cdiv(3L * L.n, kBlock), kBlock, 0, s>>>(3L * L.n, L.x<T>());
+    LL_LAUNCHED();
+  }
   for (int sweep = 0; sweep < H->prm.nu_pre; ++sweep) smooth_level<T>(H, l, true);
-  kb_residual<T, kLanes><<<cdiv((long)L.n * kLanes, kBlock), kBlock, 0, s>>>(L.n, L.rowptr, L.col, L.val<T>(),
-                                                                              L.b<T>(), L.x<T>(), L.r<T>());
-  LL_LAUNCHED();
-  kb_restrict<T><<<cdiv(N.n, kBlock), kBlock, 0, s>>>(N.n, N.mptr, N.mem, L.r<T>(), N.b<T>());
-  LL_LAUNCHED();
+  {
+    LL_PROF(LL_KIND_BSR_OTHER);
+    kb_residual<T, kLanes><<<cdiv((long)L.n * kLanes, kBlock), kBlock, 0, s>>>(L.n, L.rowptr, L.col, L.val<T>(),
+                                                                                L.b<T>(), L.x<T>(), L.r<T>());
+    LL_LAUNCHED();
+    kb_restrict<T><<<cdiv(N.n, kBlock), kBlock, 0, s>>>(N.n, N.mptr, N.mem, L.r<T>(), N.b<T>());
+    LL_LAUNCHED();
+  }
   vcycle_coarse<T>(H, l + 1);
-  kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
-  LL_LAUNCHED();
+  {
+    LL_PROF(LL_KIND_BSR_OTHER);
+    kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
+    LL_LAUNCHED();
+  }
   for (int sweep = 0; sweep < H->prm.nu_post; ++sweep) smooth_level<T>(H, l, false);
 }
 
@@ -353,15 +457,11 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
   if (H->nlev == 1) {  // the whole problem is the coarsest level
-    DBuf<T> tb, tx;
-    tb.alloc(H->ncoarse3);
-    tx.alloc(H->ncoarse3);
-    k_rb_to_cellmajor<double, T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->nat_of_slot, r, tb);
+    k_rb_to_cellmajor<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->nat_of_slot, r, H->single_b);
     LL_LAUNCHED();
-    coarse_solve<T>(H, tb, tx);
-    k_cellmajor_to_rb<T, T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->nat_of_slot, tx, z);
+    coarse_solve<double>(H, H->single_b, H->single_x);
+    k_cellmajor_to_rb<double, T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->nat_of_slot, H->single_x, z);
     LL_LAUNCHED();
-    LL_CU(cudaStreamSynchronize(s));
     return;
   }
   CLevel& L1 = H->lev[1];
@@ -370,37 +470,65 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   T inv_dt = (T)(1.0 / H->dt);
   int nb = cdiv(g.nh, kBlock);
   if (H->prm.nu_pre >= 1) {
-    k0_smooth<T, 0><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
-    LL_LAUNCHED();
-    k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
-    LL_LAUNCHED();
-    for (int sweep = 1; sweep < H->prm.nu_pre; ++sweep) {
-      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+    {
+      LL_PROF(LL_KIND_L0_SMOOTH);
+      k0_smooth<T, 0><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
       LL_LAUNCHED();
+    }
+    {
+      LL_PROF(LL_KIND_L0_SMOOTH);
       k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
       LL_LAUNCHED();
     }
+    for (int sweep = 1; sweep < H->prm.nu_pre; ++sweep) {
+      {
+        LL_PROF(LL_KIND_L0_SMOOTH);
+        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+        LL_LAUNCHED();
+      }
+      {
+        LL_PROF(LL_KIND_L0_SMOOTH);
+        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+        LL_LAUNCHED();
+      }
+    }
+    LL_PROF(LL_KIND_L0_RESTRICT);
     k0_restrict<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
                                                           L1.b<T>());
+    LL_LAUNCHED();
   } else {
+    LL_PROF(LL_KIND_L0_RESTRICT);
     k_zero<T><<<cdiv(H->n3, kBlock), kBlock, 0, s>>>(H->n3, z);
     LL_LAUNCHED();
     k0_restrict_b<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, L1.n, L1.mptr, L1.mem, L1.b<T>());
+    LL_LAUNCHED();
   }
-  LL_LAUNCHED();
   vcycle_coarse<T>(H, 1);
   if (H->prm.nu_post >= 1) {
-    k0_smooth<T, 2><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, H->agg0, L1.x<T>());
-    LL_LAUNCHED();
-    k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
-    LL_LAUNCHED();
-    for (int sweep = 1; sweep < H->prm.nu_post; ++sweep) {
-      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+    {
+      LL_PROF(LL_KIND_L0_SMOOTH);
+      k0_smooth<T, 2><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, H->agg0, L1.x<T>());
       LL_LAUNCHED();
+    }
+    {
+      LL_PROF(LL_KIND_L0_SMOOTH);
       k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
       LL_LAUNCHED();
     }
+    for (int sweep = 1; sweep < H->prm.nu_post; ++sweep) {
+      {
+        LL_PROF(LL_KIND_L0_SMOOTH);
+        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+        LL_LAUNCHED();
+      }
+      {
+        LL_PROF(LL_KIND_L0_SMOOTH);
+        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+        LL_LAUNCHED();
+      }
+    }
   } else {
+    LL_PROF(LL_KIND_L0_RESTRICT);
     k0_prolong<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->agg0, L1.x<T>(), z);
     LL_LAUNCHED();
   }
@@ -415,15 +543,124 @@ void read_head(ll_mg_hierarchy* H) {
 }
 
 void finish(ll_mg_hierarchy* H, int nvals, double* out) {
+  LL_PROF(LL_KIND_GCR_VECTOR);
   k_finish<<<nvals, kBlock, 0, H->s>>>(H->partial, out);
   LL_LAUNCHED();
 }
 
 void true_residual(ll_mg_hierarchy* H) {
-  kg_residual<<<kRedBlocks, kBlock, 0, H->s>>>(H->g, H->bw, H->xw, H->chat64, 1.0 / H->dt, H->r, H->partial);
-  LL_LAUNCHED();
+  {
+    LL_PROF(LL_KIND_OUTER_APPLY);
+    kg_residual<<<kRedBlocks, kBlock, 0, H->s>>>(H->g, H->bw, H->xw, H->chat64, 1.0 / H->dt, H->r, H->partial);
+    LL_LAUNCHED();
+  }
   finish(H, 2, &H->scal.p->rn2);
   read_head(H);
+}
+
+// One GCR iteration j (Algorithm 1, steps 1-5) without host interaction:
+// z_j = V-cycle(r), c_j = A z_j, two classical Gram-Schmidt passes against
+// c_0..c_{j-1}, gamma_jj, alpha_j, r -= alpha_j c_j and |r|^2.
+template <typename T>
+void iteration_body(ll_mg_hierarchy* H, int j) {
+  cudaStream_t s = H->s;
+  const GridGeom& g = H->g;
+  long n3 = H->n3;
+  int nbs = cdiv(H->n2, kBlock), nbv = cdiv(n3, kBlock);
+  GcrScal* S = H->scal.p;
+  T* zj = H->Z<T>() + (size_t)j * n3;
+  double* cj = H->C.p + (size_t)j * n3;
+  vcycle<T>(H, H->r, zj);                                                       // step 1
+  {
+    LL_PROF(LL_KIND_OUTER_APPLY);
+    kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);      // step 2
+    LL_LAUNCHED();
+  }
+  for (int pass = 0; pass < 2 && j > 0; ++pass) {                                // step 3
+    for (int i0 = 0; i0 < j; i0 += kDotChunk) {
+      int cnt = std::min(kDotChunk, j - i0);
+      {
+        LL_PROF(LL_KIND_GCR_VECTOR);
+        kg_multidot<kDotChunk><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
+        LL_LAUNCHED();
+      }
+      finish(H, cnt, S->d + i0);
+    }
+    {
+      LL_PROF(LL_KIND_GCR_VECTOR);
+      k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0);
+      LL_LAUNCHED();
+    }
+    {
+      LL_PROF(LL_KIND_GCR_VECTOR);
+      kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef);
+      LL_LAUNCHED();
+    }
+  }
+  {
+    LL_PROF(LL_KIND_GCR_VECTOR);
+    kg_dot2<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->r, H->partial);             // step 4
+    LL_LAUNCHED();
+  }
+  finish(H, 2, &S->cc);
+  {
+    LL_PROF(LL_KIND_GCR_VECTOR);
+    k_norm_coef<<<1, 1, 0, s>>>(S, j);
+    LL_LAUNCHED();
+  }
+  {
+    LL_PROF(LL_KIND_GCR_VECTOR);
+    kg_rupdate<<<kRedBlocks, kBlock, 0, s>>>(n3, H->r, cj, &S->rcoef, H->partial); // step 5
+    LL_LAUNCHED();
+  }
+  finish(H, 1, &S->rn2);
+}
+
+// run iteration j, from a CUDA graph captured on first use (one launch
+// instead of a few hundred), then fold any graph-timed kernels into the totals
+template <typename T>
+void run_iteration(ll_mg_hierarchy* H, int j) {
+  if (!H->use_graphs) {
+    iteration_body<T>(H, j);
+    return;
+  }
+  if (H->graph_dt != H->dt) {
+    for (int q = 0; q < kMaxRestart; ++q) H->drop_graph(q);
+    H->graph_dt = H->dt;
+  }
+  if (H->graphs[j] && H->graph_mask[j] != H->prof_mask) H->drop_graph(j);
+  if (!H->graphs[j]) {
+    cudaGraph_t graph;
+    long long before = g_launches.load();
+    LL_CU(cudaStreamBeginCapture(H->s, cudaStreamCaptureModeThreadLocal));
+    H->capturing = j;
+    try {
+      iteration_body<T>(H, j);
+    } catch (Status) {
+      H->capturing = -1;
+      cudaStreamEndCapture(H->s, &graph);
+      throw;
+    }
+    H->capturing = -1;
+    LL_CU(cudaStreamEndCapture(H->s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&H->graphs[j], graph, 0);
+    cudaGraphDestroy(graph);
+    LL_CU(e);
+    H->graph_mask[j] = H->prof_mask;
+    H->graph_kernels[j] = g_launches.load() - before;  // counted per launch below
+    g_launches.fetch_sub(H->graph_kernels[j]);
+  }
+  LL_CU(cudaGraphLaunch(H->graphs[j], H->s));
+  g_launches.fetch_add(H->graph_kernels[j]);
+  if (!H->gpairs[j].empty()) {
+    LL_CU(cudaStreamSynchronize(H->s));
+    for (auto& q : H->gpairs[j]) {
+      float ms = 0;
+      LL_CU(cudaEventElapsedTime(&ms, q.b, q.e));
+      H->prof_ms[q.kind] += ms;
+      H->prof_n[q.kind] += 1;
+    }
+  }
 }
 
 template <typename T>
@@ -462,31 +699,7 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
     int jdone = 0;
     bool broke = false;
     for (int j = 0; j < m; ++j) {
-      T* zj = H->Z<T>() + (size_t)j * n3;
-      double* cj = H->C.p + (size_t)j * n3;
-      vcycle<T>(H, H->r, zj);                                                       // step 1
-      kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);        // step 2
-      LL_LAUNCHED();
-      for (int pass = 0; pass < 2 && j > 0; ++pass) {                                // step 3
-        for (int i0 = 0; i0 < j; i0 += kDotChunk) {
-          int cnt = std::min(kDotChunk, j - i0);
-          kg_multidot<kDotChunk><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
-          LL_LAUNCHED();
-          finish(H, cnt, S->d + i0);
-        }
-        k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0);
-        LL_LAUNCHED();
-        kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef);
-        LL_LAUNCHED();
-      }
-      kg_dot2<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->r, H->partial);             // step 4
-      LL_LAUNCHED();
-      finish(H, 2, &S->cc);
-      k_norm_coef<<<1, 1, 0, s>>>(S, j);
-      LL_LAUNCHED();
-      kg_rupdate<<<kRedBlocks, kBlock, 0, s>>>(n3, H->r, cj, &S->rcoef, H->partial); // step 5
-      LL_LAUNCHED();
-      finish(H, 1, &S->rn2);
+      run_iteration<T>(H, j);
       ++total;
       read_head(H);
       double gjj = H->h_head[4];
@@ -503,10 +716,16 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
       if (rj < rtol * bnorm) break;                                                  // step 6
     }
     if (jdone > 0) {
-      k_backsub<<<1, 1, 0, s>>>(S, jdone);
-      LL_LAUNCHED();
-      kg_xupdate<T><<<nbv, kBlock, 0, s>>>(n3, H->xw, H->Z<T>(), jdone, S->y);
-      LL_LAUNCHED();
+      {
+        LL_PROF(LL_KIND_GCR_VECTOR);
+        k_backsub<<<1, 1, 0, s>>>(S, jdone);
+        LL_LAUNCHED();
+      }
+      {
+        LL_PROF(LL_KIND_GCR_VECTOR);
+        kg_xupdate<T><<<nbv, kBlock, 0, s>>>(n3, H->xw, H->Z<T>(), jdone, S->y);
+        LL_LAUNCHED();
+      }
     }
     if (broke) {
       status = LL_BREAKDOWN;
@@ -541,7 +760,12 @@ int create(const double* m, double alpha, double dt, double h, ll_grid grid, con
     H = new ll_mg_hierarchy();
     ll_mg_default_params(&H->prm);
     if (p) H->prm = *p;
-    H->s = (cudaStream_t)stream;
+    H->user = (cudaStream_t)stream;
+    LL_CU(cudaStreamCreateWithFlags(&H->s, cudaStreamNonBlocking));
+    LL_CU(cudaEventCreateWithFlags(&H->entry_ev, cudaEventDisableTiming));
+    const char* ng = getenv("LLMG_NO_GRAPHS");
+    H->use_graphs = !(ng && ng[0] == '1');
+    enter(H);
     H->alpha = alpha;
     H->dt = dt;
     H->h = h;
@@ -606,6 +830,7 @@ int ll_mg_setup(const double* m_tilde, double alpha, double dt, double h, ll_gri
 int ll_mg_update(ll_mg_hierarchy* H, const double* m_tilde, double alpha, double dt) {
   if (!H || !m_tilde || !(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha)) return LL_EINVAL;
   try {
+    enter(H);
     H->alpha = alpha;
     H->dt = dt;
     numeric(H, m_tilde);
@@ -619,25 +844,22 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
                 double* rel_residual) {
   if (!H || !rhs || !x) return LL_EINVAL;
   try {
+    enter(H);
     return solve(H, rhs, x, rtol, iterations, rel_residual);
   } catch (Status st) {
     return st.code;
   }
 }
 
-int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p,
-            void* cuda_stream, int* iters_per_step, double* relres_per_step) {
-  if (!m || n_steps < 0 || !valid_problem(alpha, dt, h, grid)) return LL_EINVAL;
-  if (p && !valid_params(*p)) return LL_EINVAL;
-  if (n_steps == 0) return LL_OK;
-  ll_mg_hierarchy* H = nullptr;
-  int st = create(m, alpha, dt, h, grid, p, cuda_stream, &H);
-  if (st != LL_OK) return st;
+// time steps on an existing hierarchy; fresh = numeric setup already done for m
+static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step,
+                 bool fresh) {
   int worst = LL_OK;
+  double dt = H->dt;
   try {
     long n3 = 3 * H->g.n;
     for (int k = 0; k < n_steps; ++k) {
-      if (k > 0) numeric(H, m);
+      if (k > 0 || !fresh) numeric(H, m);
       k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
       LL_LAUNCHED();
       LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
@@ -655,9 +877,33 @@ int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid g
   } catch (Status e) {
     worst = e.code;
   }
+  return worst;
+}
+
+int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p,
+            void* cuda_stream, int* iters_per_step, double* relres_per_step) {
+  if (!m || n_steps < 0 || !valid_problem(alpha, dt, h, grid)) return LL_EINVAL;
+  if (p && !valid_params(*p)) return LL_EINVAL;
+  if (n_steps == 0) return LL_OK;
+  ll_mg_hierarchy* H = nullptr;
+  int st = create(m, alpha, dt, h, grid, p, cuda_stream, &H);
+  if (st != LL_OK) return st;
+  int worst = steps(H, m, n_steps, iters_per_step, relres_per_step, true);
   delete H;
   return worst;
 }
+
+int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step) {
+  if (!H || !m || n_steps < 0) return LL_EINVAL;
+  try {
+    enter(H);
+  } catch (Status st) {
+    return st.code;
+  }
+  return steps(H, m, n_steps, iters_per_step, relres_per_step, false);
+}
+
+long long ll_launch_count(void) { return g_launches.load(); }
 
 void ll_mg_destroy(ll_mg_hierarchy* H) {
   if (H) {
@@ -725,9 +971,37 @@ int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col,
   return LL_OK;
 }
 
+int ll_mg_profile(ll_mg_hierarchy* H, unsigned int kinds) {
+  if (!H) return LL_EINVAL;
+  if (cudaStreamSynchronize(H->s) != cudaSuccess) return LL_ECUDA;
+  H->prof_mask = kinds;
+  H->ev_used = 0;
+  for (auto& v : H->prof_pairs) v.clear();
+  for (int k = 0; k < LL_NUM_KINDS; ++k) {
+    H->prof_ms[k] = 0;
+    H->prof_n[k] = 0;
+  }
+  return LL_OK;
+}
+
+int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long* launches) {
+  if (!H || kind < 0 || kind >= LL_NUM_KINDS) return LL_EINVAL;
+  if (cudaStreamSynchronize(H->s) != cudaSuccess) return LL_ECUDA;
+  double tot = H->prof_ms[kind];
+  for (auto& pr : H->prof_pairs[kind]) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess) return LL_ECUDA;
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = H->prof_n[kind] + (long long)H->prof_pairs[kind].size();
+  return LL_OK;
+}
+
 int ll_mg_apply(ll_mg_hierarchy* H, const double* x, double* y) {
   if (!H || !x || !y) return LL_EINVAL;
   try {
+    enter(H);
     const GridGeom& g = H->g;
     int nbs = cdiv(H->n2, kBlock);
     k_to_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, x, H->xw);
@@ -746,6 +1020,7 @@ int ll_mg_apply(ll_mg_hierarchy* H, const double* x, double* y) {
 int ll_mg_vcycle(ll_mg_hierarchy* H, const double* r, double* z) {
   if (!H || !r || !z) return LL_EINVAL;
   try {
+    enter(H);
     const GridGeom& g = H->g;
     int nbs = cdiv(H->n2, kBlock);
     k_to_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, r, H->bw);
@@ -769,6 +1044,7 @@ int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forw
   if (!H || !b || !x || l < 0 || l >= H->nlev || H->prm.precision != LL_FP64) return LL_EINVAL;
   if (l == H->nlev - 1 && l > 0) return LL_EINVAL;  // the coarsest level is solved, not smoothed
   try {
+    enter(H);
     const GridGeom& g = H->g;
     cudaStream_t s = H->s;
     if (l == 0) {

@@ -21,7 +21,7 @@ def _declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(ll_[A-Za-z0-9_]+)\s*\(",
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][A-Za-z0-9_]*\s*\**\s+)+\**\s*(ll_[A-Za-z0-9_]+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names

@@ -234,7 +234,7 @@ def test_config1_against_sparse_direct_solve():
 
     grid, h, alpha, dt = (64, 64, 1), 1 / 64, 0.1, 1e-3
     m = inputs.smooth_field(*grid, seed=0).reshape(-1)
-    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(coarsest_cells=10 ** 6, max_levels=1))
+    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params())
     xe = spla.spsolve(O.matrix(0).tocsc(), m / dt)
     G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-12))
     x = torch.zeros(m.size, dtype=torch.float64, device=DEV)
