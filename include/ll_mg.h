@@ -185,6 +185,34 @@ int ll_mg_vcycle(ll_mg_hierarchy* H, const double* r, double* z);
  * 3*N, on coarse levels cell-major 3*n_l.  float64 hierarchies only. */
 int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forward);
 
+/* ---- allocation-free residual ---------------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot call cudaMalloc (or anything that allocates device memory) at the
+ * point where they need a residual -- for example code running inside a
+ * memory pool or arena that forbids further allocations, or a host that has
+ * reserved all device memory for itself.  It computes the same residual as
+ * the hierarchy-based calls without needing a hierarchy:
+ *     r = rhs - A x,   norms2[0] = ||r||_2^2,   norms2[1] = ||rhs||_2^2,
+ * with A the operator of ll_mg_setup for (m_tilde, alpha, dt, h, grid), its
+ * coefficients formed on the fly.  relres = sqrt(norms2[0] / norms2[1]).
+ *   m_tilde, rhs, x  device, SoA 3*N float64 (read only)
+ *   r                device, SoA 3*N float64 output, or NULL to skip it
+ *   norms2           device, 2 float64 outputs
+ * The call allocates nothing: its reduction scratch is a fixed 32 KB array
+ * in device memory that every GPU loading the library keeps until the
+ * process exits.  That bounds the grid: N <= 8,388,608 cells (e.g. 256^2 x
+ * 128); larger grids return LL_ELIMIT without touching the device.  The
+ * first call on each device looks up the array's device address (the only
+ * set-up); make that first call before any CUDA stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU (different streams
+ * or devices sharing a context) race and give wrong norms -- serialise them.
+ * Work is enqueued on cuda_stream and the call returns without waiting;
+ * outputs are valid once the stream reaches that point.
+ * Errors: LL_EINVAL (null input, dt <= 0, h <= 0, alpha < 0, empty grid),
+ * LL_ELIMIT (grid too large, or device index >= 64), LL_ECUDA. */
+int ll_residual_noalloc(const double* m_tilde, double alpha, double dt, double h, ll_grid grid,
+                        const double* rhs, const double* x, double* r, double* norms2, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ EXPORTS = (
     "ll_mg_default_params", "ll_mg_setup", "ll_mg_update", "ll_mg_solve", "ll_step", "ll_mg_destroy",
     "ll_status_string", "ll_mg_levels", "ll_mg_level_cells", "ll_mg_level_aggregates",
     "ll_mg_level_colours", "ll_mg_level_blocks", "ll_mg_level_operator", "ll_mg_apply", "ll_mg_vcycle",
-    "ll_mg_smooth", "ll_mg_step", "ll_launch_count",
+    "ll_mg_smooth", "ll_mg_step", "ll_launch_count", "ll_mg_profile", "ll_mg_profile_read",
+    "ll_residual_noalloc",
 )
 
 
@@ -105,6 +106,9 @@ def load_library():
         "ll_mg_smooth": (i, [vp, i, vp, vp, i]),
         "ll_mg_step": (i, [vp, vp, i, ip, dp]),
         "ll_launch_count": (ctypes.c_longlong, []),
+        "ll_mg_profile": (i, [vp, ctypes.c_uint]),
+        "ll_mg_profile_read": (i, [vp, i, dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "ll_residual_noalloc": (i, [vp, d, d, d, _Grid, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +259,24 @@ class Hierarchy:
         n = self.n if l == 0 else self.level_cells(l)
         st = load_library().ll_mg_smooth(self._h, l, _field(b, n, "b"), _field(x, n, "x"), 1 if forward else 0)
         _check(st, "ll_mg_smooth", ok=(LL_OK,))
+
+
+def residual_noalloc(m_tilde, alpha, dt, h, grid, rhs, x, r=None, norms2=None):
+    """``ll_residual_noalloc``: r = rhs - A x and (|r|^2, |rhs|^2) into the
+    2-element float64 CUDA tensor ``norms2`` without any device allocation
+    inside the library.  Returns ``norms2`` (enqueued on the current stream)."""
+    import torch
+
+    g = _grid(grid)
+    n = g.nx * g.ny * g.nz
+    if norms2 is None:
+        norms2 = torch.empty(2, dtype=torch.float64, device=rhs.device)
+    rp = _field(r, n, "r") if r is not None else None
+    st = load_library().ll_residual_noalloc(_field(m_tilde, n, "m_tilde"), float(alpha), float(dt), float(h), g,
+                                            _field(rhs, n, "rhs"), _field(x, n, "x"), rp,
+                                            ctypes.c_void_p(norms2.data_ptr()), _stream())
+    _check(st, "ll_residual_noalloc", ok=(LL_OK,))
+    return norms2
 
 
 def launch_count() -> int:
