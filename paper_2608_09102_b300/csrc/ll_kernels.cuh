@@ -255,6 +255,39 @@ __global__ void k_lu_factor(int N, double* __restrict__ a, int* __restrict__ per
   }
 }
 
+// Columns of the inverse from the LU factors: column j solves L U x = P e_j
+// (one thread per column, the column itself as workspace), stored
+// column-major: ainv[j*N + i] = (A^{-1})_ij.
+__global__ void k_lu_inverse(int N, const double* __restrict__ a, const int* __restrict__ perm,
+                             double* __restrict__ ainv) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    double* y = ainv + (long)j * N;
+    for (int i = 0; i < N; ++i) {  // forward, unit lower; (P e_j)_i = [perm_i == j]
+      double v = perm[i] == j ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= a[(long)i * N + k] * y[k];
+      y[i] = v;
+    }
+    for (int i = N - 1; i >= 0; --i) {  // backward
+      double v = y[i];
+      for (int k = i + 1; k < N; ++k) v -= a[(long)i * N + k] * y[k];
+      y[i] = v / a[(long)i * N + i];
+    }
+  }
+}
+
+// x = A^{-1} b with the column-major inverse; b staged in shared memory
+template <typename T>
+__global__ void kc_solve(int N, const double* __restrict__ ainv, const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ double sb[];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = (double)b[j];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double acc = 0.0;
+  for (int j = 0; j < N; ++j) acc += ainv[(long)j * N + i] * sb[j];
+  x[i] = (T)acc;
+}
+
 template <typename T>
 __global__ void k_lu_solve(int N, const double* __restrict__ a, const int* __restrict__ perm,
                            const T* __restrict__ b, T* __restrict__ x) {
@@ -316,9 +349,15 @@ __global__ void __launch_bounds__(256) k0_smooth(GridGeom g, int c, const double
     const T* C = chat + sl;
     T c0 = ld(C), c1 = ld(C + n2), c2 = ld(C + 2 * n2), c3 = ld(C + 3 * n2), c4 = ld(C + 4 * n2),
       c5 = ld(C + 5 * n2), c6 = ld(C + 6 * n2), c7 = ld(C + 7 * n2), c8 = ld(C + 8 * n2);
-    v0 -= c0 * s0 + c1 * s1 + c2 * s2;
-    v1 -= c3 * s0 + c4 * s1 + c5 * s2;
-    v2 -= c6 * s0 + c7 * s1 + c8 * s2;
+    v0 = fma(-c0, s0, v0);
+    v0 = fma(-c1, s1, v0);
+    v0 = fma(-c2, s2, v0);
+    v1 = fma(-c3, s0, v1);
+    v1 = fma(-c4, s1, v1);
+    v1 = fma(-c5, s2, v1);
+    v2 = fma(-c6, s0, v2);
+    v2 = fma(-c7, s1, v2);
+    v2 = fma(-c8, s2, v2);
   }
   const T* D = dinv + sl;
   T d0 = ld(D), d1 = ld(D + n2), d2 = ld(D + 2 * n2), d3 = ld(D + 3 * n2), d4 = ld(D + 4 * n2),
@@ -353,16 +392,39 @@ __device__ __forceinline__ void slot_apply(const GridGeom& g, int c, long sl, co
   y[2] = x2 * inv_dt + ld(C + 6 * n2) * s0 + ld(C + 7 * n2) * s1 + ld(C + 8 * n2) * s2;
 }
 
-// residual of one slot: r = b - A x
+// residual of one slot: r = b - x/dt - Chat (S - deg x), negated FMAs
 template <typename T, typename TX>
 __device__ __forceinline__ void slot_residual(const GridGeom& g, int c, long sl, const SlotPos& p, const double* b,
                                               const TX* x, const T* chat, T inv_dt, T* r) {
   long n2 = 2 * g.nh;
-  T y[3];
-  slot_apply<T, TX>(g, c, sl, p, x, chat, inv_dt, y);
-  r[0] = (T)b[sl] - y[0];
-  r[1] = (T)b[n2 + sl] - y[1];
-  r[2] = (T)b[2 * n2 + sl] - y[2];
+  long nb[6];
+  int d = slot_neighbours(g, c, p, nb);
+  T x0 = (T)x[sl], x1 = (T)x[n2 + sl], x2 = (T)x[2 * n2 + sl];
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int q = 0; q < d; ++q) {
+    long l = nb[q];
+    s0 += (T)x[l];
+    s1 += (T)x[n2 + l];
+    s2 += (T)x[2 * n2 + l];
+  }
+  T fd = (T)d;
+  s0 = fma(-fd, x0, s0);
+  s1 = fma(-fd, x1, s1);
+  s2 = fma(-fd, x2, s2);
+  const T* C = chat + sl;
+  T r0 = fma(-inv_dt, x0, (T)b[sl]), r1 = fma(-inv_dt, x1, (T)b[n2 + sl]), r2 = fma(-inv_dt, x2, (T)b[2 * n2 + sl]);
+  r0 = fma(-ld(C), s0, r0);
+  r0 = fma(-ld(C + n2), s1, r0);
+  r0 = fma(-ld(C + 2 * n2), s2, r0);
+  r1 = fma(-ld(C + 3 * n2), s0, r1);
+  r1 = fma(-ld(C + 4 * n2), s1, r1);
+  r1 = fma(-ld(C + 5 * n2), s2, r1);
+  r2 = fma(-ld(C + 6 * n2), s0, r2);
+  r2 = fma(-ld(C + 7 * n2), s1, r2);
+  r2 = fma(-ld(C + 8 * n2), s2, r2);
+  r[0] = r0;
+  r[1] = r1;
+  r[2] = r2;
 }
 
 // Residual and restriction (P^T) in one pass: bc_I = sum over the members k
@@ -371,9 +433,13 @@ __device__ __forceinline__ void slot_residual(const GridGeom& g, int c, long sl,
 template <typename T>
 __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* __restrict__ x,
                             const T* __restrict__ chat, T inv_dt, int nc, const int* __restrict__ mptr,
-                            const int* __restrict__ mem, T* __restrict__ bc) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nc) return;
+                            const int* __restrict__ mem, T* __restrict__ bc, int init_end,
+                            const T* __restrict__ dinvc, T* __restrict__ xc, const int* __restrict__ order) {
+  // thread t takes aggregate order[t]: neighbouring threads take neighbouring
+  // aggregates of the grid, so their member cells share cache lines
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  int I = order[t];
   T a0 = 0, a1 = 0, a2 = 0;
   for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
     long sl = mem[q];
@@ -388,6 +454,12 @@ __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* _
   bc[3L * I] = a0;
   bc[3L * I + 1] = a1;
   bc[3L * I + 2] = a2;
+  if (I < init_end) {  // first colour of the next level's forward sweep
+    const T* D = dinvc + 9L * I;
+    xc[3L * I] = D[0] * a0 + D[1] * a1 + D[2] * a2;
+    xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
+    xc[3L * I + 2] = D[6] * a0 + D[7] * a1 + D[8] * a2;
+  }
 }
 
 // restriction of b itself (no pre-smoothing: x = 0)
@@ -441,75 +513,124 @@ __device__ __forceinline__ void group_sum3(T& a, T& b, T& c) {
   }
 }
 
-// x_I = Dinv_I (b_I - sum_{J != I} A_IJ x_J) for the rows of one colour class
-template <typename T, int G>
-__global__ void kb_smooth(int nrows, const int* __restrict__ rows, const int* __restrict__ rowptr,
-                          const int* __restrict__ col, const T* __restrict__ val, const T* __restrict__ dinv,
-                          const T* __restrict__ b, T* __restrict__ x) {
-  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  long q = gt / G;
-  int lane = threadIdx.x % G;
-  bool active = q < nrows;
-  int I = active ? rows[q] : 0;
-  T a0 = 0, a1 = 0, a2 = 0;
-  if (active) {
-    for (int p = rowptr[I] + lane; p < rowptr[I + 1]; p += G) {
-      int J = col[p];
-      if (J == I) continue;
-      const T* A = val + 9L * p;
-      T x0 = x[3L * J], x1 = x[3L * J + 1], x2 = x[3L * J + 2];
-      a0 += A[0] * x0 + A[1] * x1 + A[2] * x2;
-      a1 += A[3] * x0 + A[4] * x1 + A[5] * x2;
-      a2 += A[6] * x0 + A[7] * x1 + A[8] * x2;
-    }
-  }
-  group_sum3<G>(a0, a1, a2);
-  if (active && lane == 0) {
-    T v0 = b[3L * I] - a0, v1 = b[3L * I + 1] - a1, v2 = b[3L * I + 2] - a2;
-    const T* D = dinv + 9L * I;
-    x[3L * I] = D[0] * v0 + D[1] * v1 + D[2] * v2;
-    x[3L * I + 1] = D[3] * v0 + D[4] * v1 + D[5] * v2;
-    x[3L * I + 2] = D[6] * v0 + D[7] * v1 + D[8] * v2;
-  }
-}
-
-// r = b - A x
-template <typename T, int G>
-__global__ void kb_residual(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                            const T* __restrict__ val, const T* __restrict__ b, const T* __restrict__ x,
-                            T* __restrict__ r) {
-  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  long I = gt / G;
-  int lane = threadIdx.x % G;
-  bool active = I < n;
-  T a0 = 0, a1 = 0, a2 = 0;
-  if (active) {
-    for (int p = rowptr[I] + lane; p < rowptr[I + 1]; p += G) {
-      int J = col[p];
-      const T* A = val + 9L * p;
-      T x0 = x[3L * J], x1 = x[3L * J + 1], x2 = x[3L * J + 2];
-      a0 += A[0] * x0 + A[1] * x1 + A[2] * x2;
-      a1 += A[3] * x0 + A[4] * x1 + A[5] * x2;
-      a2 += A[6] * x0 + A[7] * x1 + A[8] * x2;
-    }
-  }
-  group_sum3<G>(a0, a1, a2);
-  if (active && lane == 0) {
-    r[3 * I] = b[3 * I] - a0;
-    r[3 * I + 1] = b[3 * I + 1] - a1;
-    r[3 * I + 2] = b[3 * I + 2] - a2;
-  }
-}
-
-// bc_I = sum of r over the members of aggregate I
+// a -= A_IJ v  for one 3x3 block (negated fused multiply-adds)
 template <typename T>
-__global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __restrict__ mem,
-                            const T* __restrict__ r, T* __restrict__ bc) {
+__device__ __forceinline__ void block_msub(const T* __restrict__ A, T v0, T v1, T v2, T& a0, T& a1, T& a2) {
+  a0 = fma(-A[0], v0, a0);
+  a0 = fma(-A[1], v1, a0);
+  a0 = fma(-A[2], v2, a0);
+  a1 = fma(-A[3], v0, a1);
+  a1 = fma(-A[4], v1, a1);
+  a1 = fma(-A[5], v2, a1);
+  a2 = fma(-A[6], v0, a2);
+  a2 = fma(-A[7], v1, a2);
+  a2 = fma(-A[8], v2, a2);
+}
+
+// a -= sum over the blocks p = p0, p0 + G, ... < p1 of A_p v_{col p}, with the
+// column indices of U blocks loaded first, then their x values, then the
+// products: three dependent memory round trips per U blocks instead of per
+// block.  PROL adds the coarse correction e[agg[J]] to every v.
+template <typename T, int G, int U, bool PROL>
+__device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__ col, const T* __restrict__ val,
+                                         const T* __restrict__ x, const int* __restrict__ agg,
+                                         const T* __restrict__ e, T& a0, T& a1, T& a2) {
+  for (int base = p0; base < p1; base += G * U) {
+    int J[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) J[u] = base + u * G < p1 ? col[base + u * G] : -1;
+    T v[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (J[u] >= 0) {
+        v[u][0] = x[3L * J[u]];
+        v[u][1] = x[3L * J[u] + 1];
+        v[u][2] = x[3L * J[u] + 2];
+        if (PROL) {
+          long a = 3L * agg[J[u]];
+          v[u][0] += e[a];
+          v[u][1] += e[a + 1];
+          v[u][2] += e[a + 2];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (J[u] >= 0) block_msub(val + 9L * (base + u * G), v[u][0], v[u][1], v[u][2], a0, a1, a2);
+  }
+}
+
+// Block Gauss-Seidel update of one colour class, G lanes per row.  Coarse
+// levels are renumbered so that each colour class is the contiguous row range
+// [r0, r1), colours ascending, and every row's blocks are sorted by column:
+// the columns of lower colours form the prefix [rowptr_I, diag_I), those of
+// higher colours the suffix (diag_I, rowptr_{I+1}) (rows of one colour are not
+// coupled).  Hence
+//   MODE 0, forward sweep from x = 0: only the prefix (already updated) counts;
+//   MODE 1, plain sweep: prefix and suffix, all current;
+//   MODE 2, first backward sweep after the coarse correction e: the suffix
+//           was updated in this sweep, the prefix is read as x + e[agg] (the
+//           prolongation, never stored).
+// x_I = Dinv_I (b_I - sum_{J != I} A_IJ v_J); the lanes of a group share the
+// three output components.
+template <typename T, int G, int MODE>
+__global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
+                                                const int* __restrict__ diag, const int* __restrict__ col,
+                                                const T* __restrict__ val, const T* __restrict__ dinv,
+                                                const T* __restrict__ b, T* __restrict__ x,
+                                                const int* __restrict__ agg, const T* __restrict__ e) {
+  constexpr int U = 4;
+  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int I = r0 + (int)(gt / G);
+  int lane = threadIdx.x % G;
+  bool active = I < r1;
+  T a0 = 0, a1 = 0, a2 = 0;
+  if (active) {
+    int pd = diag[I];
+    row_msub<T, G, U, MODE == 2>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
+    if (MODE != 0) row_msub<T, G, U, false>(pd + 1 + lane, rowptr[I + 1], col, val, x, agg, e, a0, a1, a2);
+  }
+  group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
+  if (active) {
+    T v0 = b[3L * I] + a0, v1 = b[3L * I + 1] + a1, v2 = b[3L * I + 2] + a2;
+    for (int c = lane; c < 3; c += G) {
+      const T* D = dinv + 9L * I + 3 * c;
+      x[3L * I + c] = D[0] * v0 + D[1] * v1 + D[2] * v2;
+    }
+  }
+}
+
+// r = b - A x on the rows [0, rend), G lanes per row
+template <typename T, int G>
+__global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ b, const T* __restrict__ x,
+                                                   T* __restrict__ r) {
+  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int I = (int)(gt / G);
+  int lane = threadIdx.x % G;
+  bool active = I < rend;
+  T a0 = 0, a1 = 0, a2 = 0;
+  if (active) row_msub<T, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
+  group_sum3<G>(a0, a1, a2);
+  if (active)
+    for (int c = lane; c < 3; c += G) r[3L * I + c] = b[3L * I + c] + (c == 0 ? a0 : c == 1 ? a1 : a2);
+}
+
+// Restriction plus the first colour of the next level's forward sweep:
+// bc_I = sum of r over the members of aggregate I, skipping members
+// >= skip_from (the last colour of a forward sweep, whose residual vanishes);
+// for I < init_end, xc_I = Dinvc_I bc_I.
+template <typename T>
+__global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __restrict__ mem, int skip_from,
+                            const T* __restrict__ r, T* __restrict__ bc, int init_end, const T* __restrict__ dinvc,
+                            T* __restrict__ xc) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nc) return;
   T a0 = 0, a1 = 0, a2 = 0;
   for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
     long k = mem[q];
+    if (k >= skip_from) continue;
     a0 += r[3 * k];
     a1 += r[3 * k + 1];
     a2 += r[3 * k + 2];
@@ -517,6 +638,32 @@ __global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __r
   bc[3L * I] = a0;
   bc[3L * I + 1] = a1;
   bc[3L * I + 2] = a2;
+  if (I < init_end) {
+    const T* D = dinvc + 9L * I;
+    xc[3L * I] = D[0] * a0 + D[1] * a1 + D[2] * a2;
+    xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
+    xc[3L * I + 2] = D[6] * a0 + D[7] * a1 + D[8] * a2;
+  }
+}
+
+// cell-major permutation of a coarse vector: out[r] = in[perm[r]] (3 comps)
+template <typename T>
+__global__ void kb_gather3(int n, const int* __restrict__ perm, const T* __restrict__ in, T* __restrict__ out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  long o = 3L * perm[r];
+  out[3L * r] = in[o];
+  out[3L * r + 1] = in[o + 1];
+  out[3L * r + 2] = in[o + 2];
+}
+template <typename T>
+__global__ void kb_scatter3(int n, const int* __restrict__ perm, const T* __restrict__ in, T* __restrict__ out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  long o = 3L * perm[r];
+  out[o] = in[3L * r];
+  out[o + 1] = in[3L * r + 1];
+  out[o + 2] = in[3L * r + 2];
 }
 
 template <typename T>

@@ -792,4 +792,69 @@ void members_colour0(int nc, const int* mptr, const int* mem, long nh, DBuf<int>
   LL_CU(cudaStreamSynchronize(s));
 }
 
+// ---------------------------------------------------------------------------
+// renumbering of a level by colour classes (rows of one colour contiguous)
+// ---------------------------------------------------------------------------
+__global__ void k_invert_perm(int n, const int* __restrict__ n2o, int* __restrict__ o2n) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) o2n[n2o[r]] = r;
+}
+__global__ void k_perm_degree(int n, const int* __restrict__ rp, const int* __restrict__ n2o, int* __restrict__ d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) d[r] = rp[n2o[r] + 1] - rp[n2o[r]];
+}
+__global__ void k_perm_fill(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ w,
+                            const int* __restrict__ n2o, const int* __restrict__ o2n, const int* __restrict__ nrp,
+                            int* __restrict__ ncol, int* __restrict__ nw) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int o = n2o[r], q = nrp[r];
+  for (int p = rp[o]; p < rp[o + 1]; ++p, ++q) {
+    ncol[q] = o2n[col[p]];
+    nw[q] = w[p];
+  }
+}
+
+// out = g with node r of out being node n2o[r] of g (columns renumbered and
+// sorted ascending per row)
+void permute_graph(const DevGraph& g, const int* n2o, const int* o2n, DevGraph& out, cudaStream_t s) {
+  int n = g.n;
+  out.n = n;
+  out.nnz = g.nnz;
+  out.rowptr.alloc(n + 1);
+  out.col.alloc(g.nnz);
+  out.w.alloc(g.nnz);
+  DBuf<int> deg;
+  deg.alloc(n);
+  int nb = cdiv(n, kBlock);
+  k_perm_degree<<<nb, kBlock, 0, s>>>(n, g.rowptr, n2o, deg);
+  LL_LAUNCHED();
+  exclusive_scan(deg, out.rowptr, n, s);
+  k_perm_fill<<<nb, kBlock, 0, s>>>(n, g.rowptr, g.col, g.w, n2o, o2n, out.rowptr, out.col, out.w);
+  LL_LAUNCHED();
+  k_sort_segments<<<nb, kBlock, 0, s>>>(n, out.rowptr, out.col, out.w, nullptr);
+  LL_LAUNCHED();
+  LL_CU(cudaStreamSynchronize(s));
+}
+
+void invert_perm(int n, const int* n2o, int* o2n, cudaStream_t s) {
+  k_invert_perm<<<cdiv(n, kBlock), kBlock, 0, s>>>(n, n2o, o2n);
+  LL_LAUNCHED();
+}
+
+// out[i] = m2[m1[i]] (or -1 where m1[i] < 0); m1 indexed through idx when given:
+// out[i] = m2[m1[idx[i]]]
+__global__ void k_map_through(int n, const int* __restrict__ idx, const int* __restrict__ m1,
+                              const int* __restrict__ m2, int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int j = idx ? idx[i] : i;
+  int a = j < 0 ? -1 : m1[j];
+  out[i] = a < 0 ? -1 : m2[a];
+}
+void map_through(int n, const int* idx, const int* m1, const int* m2, int* out, cudaStream_t s) {
+  k_map_through<<<cdiv(n, kBlock), kBlock, 0, s>>>(n, idx, m1, m2, out);
+  LL_LAUNCHED();
+}
+
 }  // namespace llmg

@@ -23,5 +23,8 @@ void slot_map_bsr(int nf, const int* frp, const int* fcol, const int* agg, const
 void rb_maps(const GridGeom& g, const int* agg_nat, int* agg_rb, int* nat_of_slot, cudaStream_t s);
 void members_colour0(int nc, const int* mptr, const int* mem, long nh, DBuf<int>& optr, DBuf<int>& out,
                      cudaStream_t s);
+void permute_graph(const DevGraph& g, const int* n2o, const int* o2n, DevGraph& out, cudaStream_t s);
+void invert_perm(int n, const int* n2o, int* o2n, cudaStream_t s);
+void map_through(int n, const int* idx, const int* m1, const int* m2, int* out, cudaStream_t s);
 
 }  // namespace llmg

@@ -20,13 +20,19 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   int n = 0, nnzb = 0, ncol = 0;
+  // in the aggregation's own numbering (rank of the smallest member)
   DevGraph graph;                   // integer weight graph
+  DBuf<int> colour;                 // Jones-Plassmann colour of each cell
+  DBuf<int> agg_orig;               // this level -> next level
+  // renumbering by colour: new cell r is cell n2o[r]; colour c owns the new
+  // range [cs[c], cs[c+1])
+  DBuf<int> n2o, o2n;
+  std::vector<int> cs;
+  // below: new numbering
   DBuf<int> rowptr, col, diag;      // BSR pattern
-  DBuf<int> colour, cptr, crow;     // colouring and its classes
-  std::vector<int> h_cptr;
   DBuf<int> sptr, sidx, sw;         // Galerkin slot map from the finer level
   DBuf<int> mptr, mem;              // members in the finer level (level 1: red-black slots)
-  DBuf<int> mptr0, mem0;            // level 1: colour-0 members only
+  DBuf<int> mptr0, mem0;            // level 1: colour-0 slots only
   DBuf<int> agg;                    // this level -> next level
   DBuf<double> val64, dinv64;
   DBuf<float> val32, dinv32;
@@ -68,9 +74,9 @@ struct ll_mg_hierarchy {
   DBuf<double> chat64, dinv64;
   DBuf<float> chat32, dinv32;
   CLevel lev[kMaxLevels];
-  // coarsest dense LU
+  // coarsest dense LU and its inverse (column-major)
   int ncoarse3 = 0;
-  DBuf<double> lu;
+  DBuf<double> lu, ainv;
   DBuf<int> perm, lu_status, flag;
   // GCR workspace (red-black layout, 3*n2 doubles per vector)
   DBuf<double> Z64, C, r, xw, bw, partial;
@@ -175,8 +181,14 @@ void enter(ll_mg_hierarchy* H) {
 }
 #define LL_PROF(kind) ProfScope prof_scope_(H, kind)
 
-constexpr int kLanes = 4;  // lanes per block row in the BSR kernels
+// lanes per block row in the BSR kernels
+template <typename T> constexpr int lanes();
+template <> constexpr int lanes<double>() { return 4; }
+template <> constexpr int lanes<float>() { return 4; }
 constexpr int kDotChunk = 8;
+// Coarse-level kernels use small blocks: a colour class of a small level then
+// spreads over many SMs instead of queueing on the float64 units of one.
+constexpr int kCoarseBlock = 64;
 constexpr int kMaxCoarsestCells = 2048;
 
 void check_flag(ll_mg_hierarchy* H, int code) {
@@ -197,9 +209,10 @@ void symbolic(ll_mg_hierarchy* H) {
   H->nlev = 1;
   const DevGraph* cur = &H->graph0;
   int ncur = (int)g.n;
+  // aggregation and colouring in the aggregation's own numbering
   while (ncur > p.coarsest_cells && H->nlev < p.max_levels) {
     int l = H->nlev - 1;
-    DBuf<int>& agg = l == 0 ? H->agg_nat0 : H->lev[l].agg;
+    DBuf<int>& agg = l == 0 ? H->agg_nat0 : H->lev[l].agg_orig;
     agg.alloc(ncur);
     int nc = aggregate_level(*cur, p.rounds, p.seed, agg, s);
     if (3L * nc > 2L * ncur) {  // coarsening ratio below 1.5: stop here
@@ -208,35 +221,61 @@ void symbolic(ll_mg_hierarchy* H) {
     }
     CLevel& C = H->lev[l + 1];
     C.n = nc;
-    build_members(ncur, agg, nc, C.mptr, C.mem, s);
-    contract_graph(*cur, agg, nc, C.mptr, C.mem, C.graph, s);
-    bsr_pattern(C.graph, C.rowptr, C.col, C.diag, C.nnzb, s);
+    {
+      DBuf<int> mptr, mem;
+      build_members(ncur, agg, nc, mptr, mem, s);
+      contract_graph(*cur, agg, nc, mptr, mem, C.graph, s);
+    }
     C.colour.alloc(nc);
     C.ncol = colour_graph(C.graph, p.seed, C.colour, s);
     if (C.ncol < 0) throw Status{LL_ELIMIT};
-    colour_classes(nc, C.colour, C.ncol, C.cptr, C.crow, C.h_cptr, s);
-    if (l == 0) {
-      slot_map_level1(g, H->agg_nat0, C.graph, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, C.sw, s);
-    } else {
-      CLevel& F = H->lev[l];
-      slot_map_bsr(F.n, F.rowptr, F.col, F.agg, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, s);
+    {
+      DBuf<int> cptr;
+      colour_classes(nc, C.colour, C.ncol, cptr, C.n2o, C.cs, s);
     }
+    C.o2n.alloc(nc);
+    invert_perm(nc, C.n2o, C.o2n, s);
     H->nlev++;
     cur = &C.graph;
     ncur = nc;
   }
-  H->nat_of_slot.alloc(H->n2);
-  if (H->nlev > 1) {
-    H->agg0.alloc(H->n2);
-    rb_maps(g, H->agg_nat0, H->agg0, H->nat_of_slot, s);
-    CLevel& L1 = H->lev[1];
-    build_members((int)H->n2, H->agg0, L1.n, L1.mptr, L1.mem, s);  // red-black slots now
-    members_colour0(L1.n, L1.mptr, L1.mem, g.nh, L1.mptr0, L1.mem0, s);
-  } else {
-    rb_maps(g, nullptr, nullptr, H->nat_of_slot, s);
-  }
   int ncoarse = H->nlev == 1 ? (int)g.n : H->lev[H->nlev - 1].n;
   if (ncoarse > kMaxCoarsestCells) throw Status{LL_ELIMIT};
+  H->nat_of_slot.alloc(H->n2);
+  if (H->nlev == 1) {
+    rb_maps(g, nullptr, nullptr, H->nat_of_slot, s);
+    LL_CU(cudaStreamSynchronize(s));
+    return;
+  }
+  // operators, transfers and slot maps in the colour-class numbering
+  for (int l = 1; l < H->nlev; ++l) {
+    CLevel& C = H->lev[l];
+    DevGraph gn;
+    permute_graph(C.graph, C.n2o, C.o2n, gn, s);
+    bsr_pattern(gn, C.rowptr, C.col, C.diag, C.nnzb, s);
+    LL_CU(cudaStreamSynchronize(s));
+  }
+  CLevel& L1 = H->lev[1];
+  {
+    DBuf<int> agg_rb_orig, agg_nat_new;
+    agg_rb_orig.alloc(H->n2);
+    rb_maps(g, H->agg_nat0, agg_rb_orig, H->nat_of_slot, s);
+    H->agg0.alloc(H->n2);
+    map_through((int)H->n2, nullptr, agg_rb_orig, L1.o2n, H->agg0, s);
+    agg_nat_new.alloc(g.n);
+    map_through((int)g.n, nullptr, H->agg_nat0, L1.o2n, agg_nat_new, s);
+    slot_map_level1(g, agg_nat_new, L1.graph, L1.rowptr, L1.col, L1.nnzb, L1.sptr, L1.sidx, L1.sw, s);
+  }
+  build_members((int)H->n2, H->agg0, L1.n, L1.mptr, L1.mem, s);  // red-black slots
+  members_colour0(L1.n, L1.mptr, L1.mem, g.nh, L1.mptr0, L1.mem0, s);
+  for (int l = 1; l + 1 < H->nlev; ++l) {
+    CLevel& F = H->lev[l];
+    CLevel& C = H->lev[l + 1];
+    F.agg.alloc(F.n);
+    map_through(F.n, F.n2o, F.agg_orig, C.o2n, F.agg, s);
+    build_members(F.n, F.agg, C.n, C.mptr, C.mem, s);
+    slot_map_bsr(F.n, F.rowptr, F.col, F.agg, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, s);
+  }
   LL_CU(cudaStreamSynchronize(s));
 }
 
@@ -269,6 +308,7 @@ void allocate(ll_mg_hierarchy* H) {
   int nc = H->nlev == 1 ? (int)H->g.n : H->lev[H->nlev - 1].n;
   H->ncoarse3 = 3 * nc;
   H->lu.alloc((size_t)H->ncoarse3 * H->ncoarse3);
+  H->ainv.alloc((size_t)H->ncoarse3 * H->ncoarse3);
   H->perm.alloc(H->ncoarse3);
   H->lu_status.alloc(1);
   H->flag.alloc(1);
@@ -387,6 +427,8 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
   LL_LAUNCHED();
   k_lu_factor<<<1, 1024, 0, s>>>(N, H->lu, H->perm, H->lu_status);
   LL_LAUNCHED();
+  k_lu_inverse<<<cdiv(N, 128), 128, 0, s>>>(N, H->lu, H->perm, H->ainv);
+  LL_LAUNCHED();
   int st = 0;
   LL_CU(cudaMemcpyAsync(&st, H->lu_status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   LL_CU(cudaStreamSynchronize(s));
@@ -401,24 +443,32 @@ template <typename T>
 void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
   int N = H->ncoarse3;
   LL_PROF(LL_KIND_COARSEST);
-  k_lu_solve<T><<<1, 256, N * sizeof(double), H->s>>>(N, H->lu, H->perm, b, x);
+  kc_solve<T><<<cdiv(N, 32), 32, N * sizeof(double), H->s>>>(N, H->ainv, b, x);
   LL_LAUNCHED();
 }
 
+// one colour class of level l: rows [cs[t], cs[t+1])
+template <typename T, int MODE>
+void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e) {
+  CLevel& L = H->lev[l];
+  int r0 = L.cs[t], r1 = L.cs[t + 1];
+  if (r1 <= r0) return;
+  LL_PROF(LL_KIND_BSR_SMOOTH);
+  kb_sweep<T, lanes<T>(), MODE><<<cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, H->s>>>(
+      r0, r1, L.rowptr, L.diag, L.col, L.val<T>(), L.dinv<T>(), L.b<T>(), L.x<T>(), L.agg, e);
+  LL_LAUNCHED();
+}
+
+// one full plain block-GS sweep of level l (colours ascending or descending)
 template <typename T>
 void smooth_level(ll_mg_hierarchy* H, int l, bool forward) {
   CLevel& L = H->lev[l];
-  for (int t = 0; t < L.ncol; ++t) {
-    int c = forward ? t : L.ncol - 1 - t;
-    int a = L.h_cptr[c], cnt = L.h_cptr[c + 1] - a;
-    if (cnt == 0) continue;
-    LL_PROF(LL_KIND_BSR_SMOOTH);
-    kb_smooth<T, kLanes><<<cdiv((long)cnt * kLanes, kBlock), kBlock, 0, H->s>>>(
-        cnt, L.crow.p + a, L.rowptr, L.col, L.val<T>(), L.dinv<T>(), L.b<T>(), L.x<T>());
-    LL_LAUNCHED();
-  }
+  for (int k = 0; k < L.ncol; ++k) sweep_class<T, 1>(H, l, forward ? k : L.ncol - 1 - k, nullptr);
 }
 
+// V-cycle below level 0.  On entry b_l holds the restricted residual and,
+// when pre-smoothing is on, x_l already holds the colour-0 rows of the first
+// forward sweep (written by the restriction into this level).
 template <typename T>
 void vcycle_coarse(ll_mg_hierarchy* H, int l) {
   CLevel& L = H->lev[l];
@@ -428,27 +478,41 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
     return;
   }
   CLevel& N = H->lev[l + 1];
-  {
+  int K = L.ncol, nu_pre = H->prm.nu_pre, nu_post = H->prm.nu_post;
+  if (nu_pre == 0) {
     LL_PROF(LL_KIND_BSR_OTHER);
     k_zero<T><<<cdiv(3L * L.n, kBlock), kBlock, 0, s>>>(3L * L.n, L.x<T>());
     LL_LAUNCHED();
   }
-  for (int sweep = 0; sweep < H->prm.nu_pre; ++sweep) smooth_level<T>(H, l, true);
+  for (int sweep = 0; sweep < nu_pre; ++sweep)
+    for (int t = sweep == 0 ? 1 : 0; t < K; ++t) {
+      if (sweep == 0) sweep_class<T, 0>(H, l, t, nullptr);
+      else sweep_class<T, 1>(H, l, t, nullptr);
+    }
   {
     LL_PROF(LL_KIND_BSR_OTHER);
-    kb_residual<T, kLanes><<<cdiv((long)L.n * kLanes, kBlock), kBlock, 0, s>>>(L.n, L.rowptr, L.col, L.val<T>(),
-                                                                                L.b<T>(), L.x<T>(), L.r<T>());
-    LL_LAUNCHED();
-    kb_restrict<T><<<cdiv(N.n, kBlock), kBlock, 0, s>>>(N.n, N.mptr, N.mem, L.r<T>(), N.b<T>());
+    int skip_from = nu_pre >= 1 ? L.cs[K - 1] : L.n;  // the last forward colour has zero residual
+    int init_end = (nu_pre >= 1 && l + 1 < H->nlev - 1) ? N.cs[1] : 0;
+    if (skip_from > 0) {
+      kb_residual<T, lanes<T>()><<<cdiv((long)skip_from * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, s>>>(
+          skip_from, L.rowptr, L.col, L.val<T>(), L.b<T>(), L.x<T>(), L.r<T>());
+      LL_LAUNCHED();
+    }
+    kb_restrict<T><<<cdiv(N.n, kCoarseBlock), kCoarseBlock, 0, s>>>(N.n, N.mptr, N.mem, skip_from, L.r<T>(), N.b<T>(),
+                                                        init_end, N.dinv<T>(), N.x<T>());
     LL_LAUNCHED();
   }
   vcycle_coarse<T>(H, l + 1);
-  {
+  if (nu_post == 0) {
     LL_PROF(LL_KIND_BSR_OTHER);
     kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
     LL_LAUNCHED();
   }
-  for (int sweep = 0; sweep < H->prm.nu_post; ++sweep) smooth_level<T>(H, l, false);
+  for (int sweep = 0; sweep < nu_post; ++sweep)
+    for (int k = 0; k < K; ++k) {
+      if (sweep == 0) sweep_class<T, 2>(H, l, K - 1 - k, N.x<T>());
+      else sweep_class<T, 1>(H, l, K - 1 - k, nullptr);
+    }
 }
 
 // z = V-cycle(r) on level 0; r float64 red-black, z red-black in T
@@ -493,8 +557,9 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
       }
     }
     LL_PROF(LL_KIND_L0_RESTRICT);
+    int init_end = H->nlev > 2 ? L1.cs[1] : 0;  // level 1's first colour, unless it is the coarsest
     k0_restrict<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
-                                                          L1.b<T>());
+                                                          L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(), L1.o2n);
     LL_LAUNCHED();
   } else {
     LL_PROF(LL_KIND_L0_RESTRICT);
@@ -576,7 +641,9 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
     kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);      // step 2
     LL_LAUNCHED();
   }
-  for (int pass = 0; pass < 2 && j > 0; ++pass) {                                // step 3
+  // step 3: classical Gram-Schmidt applied twice (the same projection as the
+  // modified Gram-Schmidt loop of Algorithm 1), then step 4's |c|^2 and c.r
+  for (int pass = 0; pass < 2 && j > 0; ++pass) {
     for (int i0 = 0; i0 < j; i0 += kDotChunk) {
       int cnt = std::min(kDotChunk, j - i0);
       {
@@ -935,7 +1002,7 @@ int ll_mg_level_cells(const ll_mg_hierarchy* H, int l) {
 
 int ll_mg_level_aggregates(const ll_mg_hierarchy* H, int l, int* agg) {
   if (!H || !agg || l < 0 || l >= H->nlev - 1) return LL_EINVAL;
-  const int* src = l == 0 ? H->agg_nat0.p : H->lev[l].agg.p;
+  const int* src = l == 0 ? H->agg_nat0.p : H->lev[l].agg_orig.p;
   int n = ll_mg_level_cells(H, l);
   if (cudaMemcpy(agg, src, n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LL_ECUDA;
   return LL_OK;
@@ -964,10 +1031,30 @@ int ll_mg_level_blocks(const ll_mg_hierarchy* H, int l) {
 int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col, double* val) {
   if (!H || l < 1 || l >= H->nlev || !rowptr || !col || !val) return LL_EINVAL;
   const CLevel& C = H->lev[l];
-  if (cudaMemcpy(rowptr, C.rowptr.p, (C.n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(col, C.col.p, C.nnzb * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(val, C.val64.p, 9L * C.nnzb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+  // the operator is stored in the colour-class numbering; return it in the
+  // aggregation's numbering, columns ascending
+  std::vector<int> rp(C.n + 1), cl(C.nnzb), n2o(C.n), o2n(C.n);
+  std::vector<double> va(9L * C.nnzb);
+  if (cudaMemcpy(rp.data(), C.rowptr.p, (C.n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(cl.data(), C.col.p, C.nnzb * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(va.data(), C.val64.p, 9L * C.nnzb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(n2o.data(), C.n2o.p, C.n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LL_ECUDA;
+  for (int r = 0; r < C.n; ++r) o2n[n2o[r]] = r;
+  int q = 0;
+  rowptr[0] = 0;
+  for (int o = 0; o < C.n; ++o) {
+    int r = o2n[o];
+    std::vector<std::pair<int, int>> blocks;
+    for (int p = rp[r]; p < rp[r + 1]; ++p) blocks.push_back({n2o[cl[p]], p});
+    std::sort(blocks.begin(), blocks.end());
+    for (auto& bp : blocks) {
+      col[q] = bp.first;
+      for (int e = 0; e < 9; ++e) val[9L * q + e] = va[9L * bp.second + e];
+      ++q;
+    }
+    rowptr[o + 1] = q;
+  }
   return LL_OK;
 }
 
@@ -1061,12 +1148,16 @@ int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forw
       }
       k_from_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, H->xw, x);
       LL_LAUNCHED();
-    } else {
+    } else {  // vectors given in the aggregation's numbering
       CLevel& L = H->lev[l];
-      LL_CU(cudaMemcpyAsync(L.b64.p, b, 3L * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      LL_CU(cudaMemcpyAsync(L.x64.p, x, 3L * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      int nb = cdiv(L.n, kBlock);
+      kb_gather3<double><<<nb, kBlock, 0, s>>>(L.n, L.n2o, b, L.b64.p);
+      LL_LAUNCHED();
+      kb_gather3<double><<<nb, kBlock, 0, s>>>(L.n, L.n2o, x, L.x64.p);
+      LL_LAUNCHED();
       smooth_level<double>(H, l, forward != 0);
-      LL_CU(cudaMemcpyAsync(x, L.x64.p, 3L * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      kb_scatter3<double><<<nb, kBlock, 0, s>>>(L.n, L.n2o, L.x64.p, x);
+      LL_LAUNCHED();
     }
     LL_CU(cudaStreamSynchronize(s));
     return LL_OK;
