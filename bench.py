@@ -44,7 +44,7 @@ WORKLOAD = "3D 128^3 semi-implicit LL time steps, alpha 0.02, dt 5e-4, vortex + 
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 
 KIND_NAMES = ["l0_smooth", "l0_restrict", "outer_apply", "bsr_smooth", "bsr_other", "gcr_vector", "coarsest",
-              "numeric"]
+              "numeric", "coarse_tail"]
 
 
 def measured_peaks():

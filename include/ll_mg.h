@@ -65,7 +65,7 @@ typedef struct ll_grid {
 typedef struct ll_mg_params {
   double rtol;         /* stop when ||b - A x||_2 < rtol ||b||_2      (1e-8) */
   int maxit;           /* GCR iterations in total, over restarts      (1000) */
-  int restart;         /* GCR restart length, 1..64                   (20)   */
+  int restart;         /* GCR restart length, 1..64                   (10)   */
   int nu_pre;          /* forward block-GS sweeps before restriction  (1)    */
   int nu_post;         /* backward block-GS sweeps after prolongation (1)    */
   int coarsest_cells;  /* stop coarsening at or below this many cells (64)   */
@@ -168,7 +168,8 @@ long long ll_launch_count(void);
 #define LL_KIND_GCR_VECTOR 5  /* GCR dots, updates, reductions, scalar kernels */
 #define LL_KIND_COARSEST 6    /* coarsest-level LU solve */
 #define LL_KIND_NUMERIC 7     /* numeric setup: coefficients, Galerkin, LU factor */
-#define LL_NUM_KINDS 8
+#define LL_KIND_COARSE_TAIL 8 /* the small coarse levels, one thread-block-cluster kernel */
+#define LL_NUM_KINDS 9
 /* Start (kinds != 0) or stop (kinds == 0) timing; starting clears totals. */
 int ll_mg_profile(ll_mg_hierarchy* H, unsigned int kinds);
 /* Total milliseconds and number of launches recorded for one kind since

@@ -58,7 +58,7 @@ class Params:
 
     rtol: float = 1e-8
     maxit: int = 1000
-    restart: int = 20
+    restart: int = 10
     nu_pre: int = 1
     nu_post: int = 1
     coarsest_cells: int = 64

@@ -560,35 +560,30 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
   }
 }
 
-// Block Gauss-Seidel update of one colour class, G lanes per row.  Coarse
-// levels are renumbered so that each colour class is the contiguous row range
-// [r0, r1), colours ascending, and every row's blocks are sorted by column:
-// the columns of lower colours form the prefix [rowptr_I, diag_I), those of
-// higher colours the suffix (diag_I, rowptr_{I+1}) (rows of one colour are not
-// coupled).  Hence
+// Block Gauss-Seidel update of one row of a colour class, G lanes per row.
+// Coarse levels are renumbered so that each colour class is the contiguous
+// row range [r0, r1), colours ascending, and every row's blocks are sorted by
+// column: the columns of lower colours form the prefix [rowptr_I, diag_I),
+// those of higher colours the suffix (diag_I, rowptr_{I+1}) (rows of one
+// colour are not coupled).  Hence
 //   MODE 0, forward sweep from x = 0: only the prefix (already updated) counts;
 //   MODE 1, plain sweep: prefix and suffix, all current;
 //   MODE 2, first backward sweep after the coarse correction e: the suffix
 //           was updated in this sweep, the prefix is read as x + e[agg] (the
 //           prolongation, never stored).
 // x_I = Dinv_I (b_I - sum_{J != I} A_IJ v_J); the lanes of a group share the
-// three output components.
+// three output components.  Every lane of the warp must call this (shuffles).
 template <typename T, int G, int MODE>
-__global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
-                                                const int* __restrict__ diag, const int* __restrict__ col,
-                                                const T* __restrict__ val, const T* __restrict__ dinv,
-                                                const T* __restrict__ b, T* __restrict__ x,
-                                                const int* __restrict__ agg, const T* __restrict__ e) {
-  constexpr int U = 4;
-  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int I = r0 + (int)(gt / G);
-  int lane = threadIdx.x % G;
-  bool active = I < r1;
+__device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
+                                          const int* __restrict__ diag, const int* __restrict__ col,
+                                          const T* __restrict__ val, const T* __restrict__ dinv,
+                                          const T* __restrict__ b, T* __restrict__ x, const int* __restrict__ agg,
+                                          const T* __restrict__ e) {
   T a0 = 0, a1 = 0, a2 = 0;
   if (active) {
     int pd = diag[I];
-    row_msub<T, G, U, MODE == 2>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-    if (MODE != 0) row_msub<T, G, U, false>(pd + 1 + lane, rowptr[I + 1], col, val, x, agg, e, a0, a1, a2);
+    row_msub<T, G, 4, MODE == 2>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
+    if (MODE != 0) row_msub<T, G, 4, false>(pd + 1 + lane, rowptr[I + 1], col, val, x, agg, e, a0, a1, a2);
   }
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
   if (active) {
@@ -600,16 +595,22 @@ __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __res
   }
 }
 
-// r = b - A x on the rows [0, rend), G lanes per row
-template <typename T, int G>
-__global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restrict__ rowptr,
-                                                   const int* __restrict__ col, const T* __restrict__ val,
-                                                   const T* __restrict__ b, const T* __restrict__ x,
-                                                   T* __restrict__ r) {
+template <typename T, int G, int MODE>
+__global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
+                                                const int* __restrict__ diag, const int* __restrict__ col,
+                                                const T* __restrict__ val, const T* __restrict__ dinv,
+                                                const T* __restrict__ b, T* __restrict__ x,
+                                                const int* __restrict__ agg, const T* __restrict__ e) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int I = (int)(gt / G);
-  int lane = threadIdx.x % G;
-  bool active = I < rend;
+  int I = r0 + (int)(gt / G);
+  sweep_row<T, G, MODE>(I, threadIdx.x % G, I < r1, rowptr, diag, col, val, dinv, b, x, agg, e);
+}
+
+// r_I = b_I - (A x)_I, G lanes per row (all lanes of the warp call it)
+template <typename T, int G>
+__device__ __forceinline__ void residual_row(int I, int lane, bool active, const int* __restrict__ rowptr,
+                                             const int* __restrict__ col, const T* __restrict__ val,
+                                             const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   T a0 = 0, a1 = 0, a2 = 0;
   if (active) row_msub<T, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
   group_sum3<G>(a0, a1, a2);
@@ -617,16 +618,24 @@ __global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restri
     for (int c = lane; c < 3; c += G) r[3L * I + c] = b[3L * I + c] + (c == 0 ? a0 : c == 1 ? a1 : a2);
 }
 
+template <typename T, int G>
+__global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ b, const T* __restrict__ x,
+                                                   T* __restrict__ r) {
+  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int I = (int)(gt / G);
+  residual_row<T, G>(I, threadIdx.x % G, I < rend, rowptr, col, val, b, x, r);
+}
+
 // Restriction plus the first colour of the next level's forward sweep:
 // bc_I = sum of r over the members of aggregate I, skipping members
 // >= skip_from (the last colour of a forward sweep, whose residual vanishes);
 // for I < init_end, xc_I = Dinvc_I bc_I.
 template <typename T>
-__global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __restrict__ mem, int skip_from,
-                            const T* __restrict__ r, T* __restrict__ bc, int init_end, const T* __restrict__ dinvc,
-                            T* __restrict__ xc) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nc) return;
+__device__ __forceinline__ void restrict_row(int I, const int* __restrict__ mptr, const int* __restrict__ mem,
+                                             int skip_from, const T* __restrict__ r, T* __restrict__ bc, int init_end,
+                                             const T* __restrict__ dinvc, T* __restrict__ xc) {
   T a0 = 0, a1 = 0, a2 = 0;
   for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
     long k = mem[q];
@@ -644,6 +653,14 @@ __global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __r
     xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
     xc[3L * I + 2] = D[6] * a0 + D[7] * a1 + D[8] * a2;
   }
+}
+
+template <typename T>
+__global__ void kb_restrict(int nc, const int* __restrict__ mptr, const int* __restrict__ mem, int skip_from,
+                            const T* __restrict__ r, T* __restrict__ bc, int init_end, const T* __restrict__ dinvc,
+                            T* __restrict__ xc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < nc) restrict_row<T>(I, mptr, mem, skip_from, r, bc, init_end, dinvc, xc);
 }
 
 // cell-major permutation of a coarse vector: out[r] = in[perm[r]] (3 comps)

@@ -10,6 +10,7 @@
 #include "ll_internal.cuh"
 #include "ll_kernels.cuh"
 #include "ll_setup.cuh"
+#include "ll_tail.cuh"
 
 #include <atomic>
 
@@ -85,6 +86,11 @@ struct ll_mg_hierarchy {
   double* h_head = nullptr;  // pinned copy of the first scalars
   // time-step workspace (natural layout)
   DBuf<double> stepb, stepx;
+  // the small coarse levels as one cluster kernel
+  int tail_first = -1;  // first tail level, -1: no tail
+  int tail_cluster = 0;
+  DBuf<TailArgs<double>> tail64;
+  DBuf<TailArgs<float>> tail32;
   // single-level hierarchies: cell-major scratch of the direct solve
   DBuf<double> single_b, single_x;
   // kernel timing (ll_mg_profile)
@@ -189,6 +195,7 @@ constexpr int kDotChunk = 8;
 // Coarse-level kernels use small blocks: a colour class of a small level then
 // spreads over many SMs instead of queueing on the float64 units of one.
 constexpr int kCoarseBlock = 64;
+constexpr int kTailCells = 12000;  // levels at or below this size run in the cluster tail
 constexpr int kMaxCoarsestCells = 2048;
 
 void check_flag(ll_mg_hierarchy* H, int code) {
@@ -332,6 +339,128 @@ void allocate(ll_mg_hierarchy* H) {
   }
 }
 
+template <typename T>
+void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
+  TailArgs<T> A;
+  A.first = H->tail_first;
+  A.last = H->nlev - 1;
+  A.nu_pre = H->prm.nu_pre;
+  A.nu_post = H->prm.nu_post;
+  A.N = H->ncoarse3;
+  A.ainv = H->ainv;
+  for (int l = A.first; l <= A.last; ++l) {
+    CLevel& C = H->lev[l];
+    TailLevel<T>& L = A.L[l];
+    L.n = C.n;
+    L.ncol = C.ncol;
+    for (int c = 0; c <= C.ncol && c <= kTailMaxColours; ++c) L.cs[c] = C.cs[c];
+    L.rowptr = C.rowptr;
+    L.diag = C.diag;
+    L.col = C.col;
+    L.val = C.val<T>();
+    L.dinv = C.dinv<T>();
+    L.x = C.x<T>();
+    L.b = C.b<T>();
+    L.r = C.r<T>();
+    L.agg = C.agg;
+    L.mptr = C.mptr;
+    L.mem = C.mem;
+  }
+  dst.alloc(1);
+  LL_CU(cudaMemcpyAsync(dst.p, &A, sizeof(A), cudaMemcpyHostToDevice, H->s));
+  LL_CU(cudaStreamSynchronize(H->s));
+}
+
+// Decide whether the small coarse levels run as one cluster kernel: the
+// cluster must be schedulable (16 CTAs, else 8) and every tail level must
+// have at most kTailMaxColours colours.
+template <typename T>
+void setup_tail_for(ll_mg_hierarchy* H) {
+  auto kern = k_coarse_tail<T, 4>;
+  for (int cl : {16, 8}) {
+    if (cl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(kTailThreads);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = cl;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0) {
+      H->tail_cluster = cl;
+      break;
+    }
+    cudaGetLastError();
+  }
+  if (H->tail_cluster == 0) {
+    H->tail_first = -1;
+    return;
+  }
+  if (H->prm.precision == LL_MIXED_FP32) fill_tail<float>(H, H->tail32);
+  else fill_tail<double>(H, H->tail64);
+}
+
+void setup_tail(ll_mg_hierarchy* H) {
+  H->tail_first = -1;
+  const char* nt = getenv("LLMG_NO_TAIL");
+  if ((nt && nt[0] == '1') || H->nlev < 2) return;
+  for (int l = 1; l < H->nlev; ++l)
+    if (H->lev[l].n <= kTailCells) {
+      H->tail_first = l;
+      break;
+    }
+  if (H->tail_first < 0) return;
+  for (int l = H->tail_first; l < H->nlev; ++l)
+    if (H->lev[l].ncol > kTailMaxColours) {
+      H->tail_first = -1;
+      return;
+    }
+  if (H->prm.precision == LL_MIXED_FP32) setup_tail_for<float>(H);
+  else setup_tail_for<double>(H);
+}
+
+template <typename T>
+void launch_tail(ll_mg_hierarchy* H);
+template <>
+void launch_tail<double>(ll_mg_hierarchy* H) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(H->tail_cluster);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.stream = H->s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = H->tail_cluster;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  LL_CU(cudaLaunchKernelEx(&cfg, k_coarse_tail<double, 4>, (const TailArgs<double>*)H->tail64.p));
+  count_launch();
+}
+template <>
+void launch_tail<float>(ll_mg_hierarchy* H) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(H->tail_cluster);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.stream = H->s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = H->tail_cluster;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  LL_CU(cudaLaunchKernelEx(&cfg, k_coarse_tail<float, 4>, (const TailArgs<float>*)H->tail32.p));
+  count_launch();
+}
+
 // dense level-0 operator (single-level hierarchies), unknown 3k + c, k natural
 __global__ void k_dense_from_l0(GridGeom g, const double* __restrict__ chat64, double inv_dt,
                                 double* __restrict__ a) {
@@ -473,6 +602,11 @@ template <typename T>
 void vcycle_coarse(ll_mg_hierarchy* H, int l) {
   CLevel& L = H->lev[l];
   cudaStream_t s = H->s;
+  if (l == H->tail_first) {
+    LL_PROF(LL_KIND_COARSE_TAIL);
+    launch_tail<T>(H);
+    return;
+  }
   if (l == H->nlev - 1) {
     coarse_solve<T>(H, L.b<T>(), L.x<T>());
     return;
@@ -847,6 +981,7 @@ int create(const double* m, double alpha, double dt, double h, ll_grid grid, con
     H->n3 = 3 * H->n2;
     symbolic(H);
     allocate(H);
+    setup_tail(H);
     numeric(H, m);
     *out = H;
     return LL_OK;
@@ -870,7 +1005,7 @@ void ll_mg_default_params(ll_mg_params* p) {
   if (!p) return;
   p->rtol = 1e-8;
   p->maxit = 1000;
-  p->restart = 20;
+  p->restart = 10;
   p->nu_pre = 1;
   p->nu_post = 1;
   p->coarsest_cells = 64;
