@@ -162,33 +162,31 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic(kind: str, n_cells: int, precision: str):
-    """Algorithmic bytes and FP64-or-FP32 flops of one average launch of a
-    kernel kind at nu_pre = nu_post = 1, for the whole grid (level 0).
+# kinds whose arithmetic is float64 whatever the V-cycle precision
+FP64_KINDS = {"outer_apply", "gcr_vector", "coarsest", "numeric"}
 
-    l0_smooth: four half-sweeps per V-cycle over N/2 cells each (modes: from
-    zero, plain, with prolongation, plain).  Per updated cell and word size
-    w (8 or 4): rhs 3 float64 words, Chat 9 w, Dinv 9 w, the neighbours' x
-    once (3 w, each neighbour is shared), x written (3 w); the from-zero
-    sweep reads no Chat or neighbours; the prolongation sweep adds the coarse
-    correction (3 w per 4 cells).  FP64 ops per updated cell: neighbour sums
-    15 adds, b - Chat S 9 FMA, Dinv v 3 mul + 6 FMA (48 flop); from zero
-    Dinv b only (15 flop); prolongation adds 18 adds.
-    outer_apply: y = A x in float64 over N cells: x read once (24 B), Chat
-    (72 B), y written (24 B); neighbour sums 15 adds, S - deg x 3 FMA,
-    Chat (S - deg x) 3 mul + 6 FMA, + x/dt 3 FMA: 42 flop."""
-    w = 8 if precision == "fp64" else 4
-    half = n_cells / 2
-    if kind == "l0_smooth":
-        full = 24 + 9 * w + 9 * w + 3 * w + 3 * w
-        zero = 24 + 9 * w + 3 * w
-        prol = full + 3 * w / 4
-        byts = half * (zero + full + prol + full) / 4
-        flops = half * (15 + 48 + 66 + 48) / 4
-        return byts, flops
-    if kind == "outer_apply":
-        return n_cells * (24 + 72 + 24), n_cells * 42
-    return None, None
+
+def roofline(kind: str, ms: float, launches: int, flops: float, byts: float, precision: str, peaks: dict,
+             peak_src: str):
+    """Roofline entry of one kernel kind from the library's live event timing
+    and its algorithmic flop and byte counts (models stated in ll_mg.h).
+    float64 kernels are bound by the float64 pipe of this GPU (2 FMA per
+    clock per SM, measured); float32 V-cycle kernels by HBM."""
+    avg_ms = ms / max(launches, 1)
+    per_launch_flops = flops / max(launches, 1)
+    per_launch_bytes = byts / max(launches, 1)
+    ach_tf = per_launch_flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
+    ach_gb = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
+    common = {"kernel_kind": kind, "launches": launches, "avg_launch_ms": avg_ms,
+              "flops_per_launch": per_launch_flops, "bytes_per_launch": per_launch_bytes, "traffic": None}
+    if precision == "fp64" or kind in FP64_KINDS:
+        return dict(bound="alu", achieved=ach_tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=(ach_tf / FP64_PEAK_TFLOPS) if ach_tf else None,
+                    peak_source="derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x 2.032 GHz (probe: 1.13 TF at 1.94 GHz)",
+                    hbm_gbs=ach_gb, hbm_frac_of_measured=(ach_gb / peaks["hbm_gbs"]) if ach_gb else None, **common)
+    return dict(bound="hbm", achieved=ach_gb, peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=(ach_gb / peaks["hbm_gbs"]) if ach_gb else None, peak_source=peak_src,
+                tflops=ach_tf, **common)
 
 
 def run_ours(args):
@@ -226,8 +224,10 @@ def run_ours(args):
     def prof_read(kind):
         ms = ctypes.c_double(0)
         cnt = ctypes.c_longlong(0)
-        lib.ll_mg_profile_read(H._h, kind, ctypes.byref(ms), ctypes.byref(cnt))
-        return ms.value, cnt.value
+        fl = ctypes.c_double(0)
+        by = ctypes.c_double(0)
+        lib.ll_mg_profile_read(H._h, kind, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl), ctypes.byref(by))
+        return ms.value, cnt.value, fl.value, by.value
 
     # warm-up steps, with every kernel kind timed to find the dominant kernel
     prof_start((1 << len(KIND_NAMES)) - 1)
@@ -261,7 +261,7 @@ def run_ours(args):
         dist.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = ll.launch_count() - launches0
-    dom_ms, dom_launches = prof_read(KIND_NAMES.index(dominant))
+    dom_ms, dom_launches, dom_flops, dom_bytes = prof_read(KIND_NAMES.index(dominant))
     prof_start(0)
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
@@ -282,25 +282,7 @@ def run_ours(args):
         return
     value = UNKNOWNS * args.steps * world / (elapsed_ms * 1e-3)
     peaks, peak_src = measured_peaks()
-    avg_launch_ms = dom_ms / max(dom_launches, 1)
-    byts, flops = algorithmic(dominant, N_CELLS, args.precision)
-    roof = None
-    if byts is not None and avg_launch_ms > 0:
-        if args.precision == "fp64":
-            ach = flops / (avg_launch_ms * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dominant,
-                    "peak_source": "derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x 2.032 GHz",
-                    "bytes_per_launch": byts, "flops_per_launch": flops, "avg_launch_ms": avg_launch_ms,
-                    "hbm_frac_of_measured": byts / (avg_launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
-        else:
-            ach = byts / (avg_launch_ms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": dominant,
-                    "peak_source": peak_src, "bytes_per_launch": byts, "avg_launch_ms": avg_launch_ms}
-    else:
-        roof = {"bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
-                "kernel": dominant, "avg_launch_ms": avg_launch_ms}
+    roof = roofline(dominant, dom_ms, dom_launches, dom_flops, dom_bytes, args.precision, peaks, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -316,6 +298,11 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "kernel_breakdown_warmup_ms": {k: round(v[0], 3) for k, v in breakdown.items()},
+        "kernel_roofline_warmup": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                       for kk, vv in roofline(k, *breakdown[k], args.precision, peaks,
+                                                              peak_src).items()
+                                       if kk in ("bound", "achieved", "unit", "frac", "hbm_gbs", "tflops")}
+                                   for k in KIND_NAMES if breakdown[k][1] > 0},
         "e2e": {"value": UNKNOWNS * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": UNKNOWNS * 8,
                 "d2h_bytes_per_step": UNKNOWNS * 8, "steps": e2e_steps},
     }

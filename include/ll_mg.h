@@ -172,9 +172,21 @@ long long ll_launch_count(void);
 #define LL_NUM_KINDS 9
 /* Start (kinds != 0) or stop (kinds == 0) timing; starting clears totals. */
 int ll_mg_profile(ll_mg_hierarchy* H, unsigned int kinds);
-/* Total milliseconds and number of launches recorded for one kind since
- * timing started (synchronises the stream). */
-int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long* launches);
+/* Totals for one kind since timing started (synchronises the stream):
+ * milliseconds, launches, and the algorithmic floating-point operations and
+ * DRAM bytes of those launches (any output may be NULL).  "Algorithmic"
+ * counts what the arithmetic needs, each array touched once per launch, from
+ * per-unit models: with w the word size of the V-cycle (8 or 4 bytes),
+ *   level-0 half-sweep, per updated cell: 48 flop (15 from zero, 66 with the
+ *     prolongation), 24 + 24w bytes (24 + 12w from zero);
+ *   level-0 residual+restriction, per colour-0 cell: 48 flop, 24 + 15w bytes;
+ *   float64 operator / true residual, per cell: 42 flop, 120 / 144 bytes;
+ *   coarse sweep or residual, per 3x3 block read: 18 flop, 12w + 4 bytes,
+ *     plus per row 15 flop and 15w + 8 bytes;
+ *   GCR vector kernels, per element and basis vector: 2 flop, 8 bytes;
+ *   coarsest solve: 2 N^2 flop, 8 N^2 bytes. */
+int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long* launches, double* flops,
+                       double* bytes);
 
 /* y = A_0 x on level 0 (device SoA buffers), float64. */
 int ll_mg_apply(ll_mg_hierarchy* H, const double* x, double* y);

@@ -35,6 +35,9 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   DBuf<int> mptr, mem;              // members in the finer level (level 1: red-black slots)
   DBuf<int> mptr0, mem0;            // level 1: colour-0 slots only
   DBuf<int> agg;                    // this level -> next level
+  // host counts for the algorithmic work of the kernels (profiling only)
+  std::vector<long long> pre_blk, off_blk;  // per colour class: prefix / off-diagonal blocks
+  long long res_blk = 0;                    // blocks of the rows before the last colour
   DBuf<double> val64, dinv64;
   DBuf<float> val32, dinv32;
   DBuf<double> x64, b64, r64;
@@ -100,6 +103,9 @@ struct ll_mg_hierarchy {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pairs[LL_NUM_KINDS];
   double prof_ms[LL_NUM_KINDS] = {0};
   long long prof_n[LL_NUM_KINDS] = {0};
+  double prof_flops[LL_NUM_KINDS] = {0}, prof_bytes[LL_NUM_KINDS] = {0};
+  long long l0_cells[2] = {0, 0};  // real cells of each colour
+  double tail_flops = 0, tail_bytes = 0;  // one launch of the cluster tail
   cudaEvent_t event() {
     if (ev_used == ev_pool.size()) {
       cudaEvent_t e;
@@ -118,6 +124,7 @@ struct ll_mg_hierarchy {
   struct GPair {
     int kind;
     cudaEvent_t b, e;
+    double flops, bytes;
   };
   std::vector<GPair> gpairs[kMaxRestart];
   void drop_graph(int j) {
@@ -155,8 +162,13 @@ struct ProfScope {
   ll_mg_hierarchy* H;
   int kind;
   cudaEvent_t b = nullptr;
-  ProfScope(ll_mg_hierarchy* h, int k) : H(h), kind(k) {
+  double flops, bytes;  // algorithmic work of the launches in the scope
+  ProfScope(ll_mg_hierarchy* h, int k, double f = 0, double by = 0) : H(h), kind(k), flops(f), bytes(by) {
     if (!(H->prof_mask & (1u << kind))) return;
+    if (H->capturing < 0) {
+      H->prof_flops[kind] += flops;
+      H->prof_bytes[kind] += bytes;
+    }
     if (H->capturing >= 0) {  // inside a graph: event-record nodes of its own
       LL_CU(cudaEventCreate(&b));
       LL_CU(cudaEventRecordWithFlags(b, H->s, cudaEventRecordExternal));
@@ -171,7 +183,7 @@ struct ProfScope {
       cudaEvent_t e;
       LL_CU(cudaEventCreate(&e));
       LL_CU(cudaEventRecordWithFlags(e, H->s, cudaEventRecordExternal));
-      H->gpairs[H->capturing].push_back({kind, b, e});
+      H->gpairs[H->capturing].push_back({kind, b, e, flops, bytes});
     } else {
       cudaEvent_t e = H->event();
       LL_CU(cudaEventRecord(e, H->s));
@@ -186,6 +198,7 @@ void enter(ll_mg_hierarchy* H) {
   LL_CU(cudaStreamWaitEvent(H->s, H->entry_ev, 0));
 }
 #define LL_PROF(kind) ProfScope prof_scope_(H, kind)
+#define LL_PROFW(kind, flops, bytes) ProfScope prof_scope_(H, kind, flops, bytes)
 
 // lanes per block row in the BSR kernels
 template <typename T> constexpr int lanes();
@@ -339,6 +352,12 @@ void allocate(ll_mg_hierarchy* H) {
   }
 }
 
+// algorithmic work of coarse sweeps and residuals (the models in ll_mg.h)
+inline double sweep_flops(long long blocks, long long rows) { return 18.0 * blocks + 15.0 * rows; }
+inline double sweep_bytes(long long blocks, long long rows, int w) {
+  return (12.0 * w + 4) * blocks + (15.0 * w + 8) * rows;
+}
+
 template <typename T>
 void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
   TailArgs<T> A;
@@ -366,6 +385,25 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
     L.mptr = C.mptr;
     L.mem = C.mem;
   }
+  int w = (int)sizeof(T);
+  H->tail_flops = H->tail_bytes = 0;
+  for (int l = A.first; l < A.last; ++l) {
+    CLevel& C = H->lev[l];
+    for (int c = 0; c < C.ncol; ++c) {
+      long long rows = C.cs[c + 1] - C.cs[c];
+      if (c > 0) {
+        H->tail_flops += sweep_flops(C.pre_blk[c], rows);
+        H->tail_bytes += sweep_bytes(C.pre_blk[c], rows, w);
+      }
+      H->tail_flops += sweep_flops(C.off_blk[c], rows);
+      H->tail_bytes += sweep_bytes(C.off_blk[c], rows, w);
+    }
+    long long rrows = C.ncol > 0 ? C.cs[C.ncol - 1] : 0;
+    H->tail_flops += sweep_flops(C.res_blk, rrows);
+    H->tail_bytes += sweep_bytes(C.res_blk, rrows, w);
+  }
+  H->tail_flops += 2.0 * H->ncoarse3 * H->ncoarse3;
+  H->tail_bytes += 8.0 * H->ncoarse3 * H->ncoarse3;
   dst.alloc(1);
   LL_CU(cudaMemcpyAsync(dst.p, &A, sizeof(A), cudaMemcpyHostToDevice, H->s));
   LL_CU(cudaStreamSynchronize(H->s));
@@ -405,6 +443,29 @@ void setup_tail_for(ll_mg_hierarchy* H) {
   }
   if (H->prm.precision == LL_MIXED_FP32) fill_tail<float>(H, H->tail32);
   else fill_tail<double>(H, H->tail64);
+}
+
+// host counts behind the algorithmic flop and byte models of the kernels
+void setup_counts(ll_mg_hierarchy* H) {
+  const GridGeom& g = H->g;
+  for (long row = 0; row < (long)g.ny * g.nz; ++row) {
+    int y = (int)(row % g.ny), z = (int)(row / g.ny);
+    for (int c = 0; c < 2; ++c) H->l0_cells[c] += (g.nx - ((c + y + z) & 1) + 1) / 2;
+  }
+  for (int l = 1; l < H->nlev; ++l) {
+    CLevel& C = H->lev[l];
+    std::vector<int> rp(C.n + 1), dg(C.n);
+    LL_CU(cudaMemcpy(rp.data(), C.rowptr.p, (C.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    LL_CU(cudaMemcpy(dg.data(), C.diag.p, C.n * sizeof(int), cudaMemcpyDeviceToHost));
+    C.pre_blk.assign(C.ncol, 0);
+    C.off_blk.assign(C.ncol, 0);
+    for (int c = 0; c < C.ncol; ++c)
+      for (int I = C.cs[c]; I < C.cs[c + 1]; ++I) {
+        C.pre_blk[c] += dg[I] - rp[I];
+        C.off_blk[c] += rp[I + 1] - rp[I] - 1;
+      }
+    C.res_blk = rp[C.ncol > 0 ? C.cs[C.ncol - 1] : 0];
+  }
 }
 
 void setup_tail(ll_mg_hierarchy* H) {
@@ -571,7 +632,7 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
 template <typename T>
 void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
   int N = H->ncoarse3;
-  LL_PROF(LL_KIND_COARSEST);
+  LL_PROFW(LL_KIND_COARSEST, 2.0 * N * N, 8.0 * N * N);
   kc_solve<T><<<cdiv(N, 32), 32, N * sizeof(double), H->s>>>(N, H->ainv, b, x);
   LL_LAUNCHED();
 }
@@ -582,7 +643,8 @@ void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e) {
   CLevel& L = H->lev[l];
   int r0 = L.cs[t], r1 = L.cs[t + 1];
   if (r1 <= r0) return;
-  LL_PROF(LL_KIND_BSR_SMOOTH);
+  long long blk = MODE == 0 ? L.pre_blk[t] : L.off_blk[t];
+  LL_PROFW(LL_KIND_BSR_SMOOTH, sweep_flops(blk, r1 - r0), sweep_bytes(blk, r1 - r0, (int)sizeof(T)));
   kb_sweep<T, lanes<T>(), MODE><<<cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, H->s>>>(
       r0, r1, L.rowptr, L.diag, L.col, L.val<T>(), L.dinv<T>(), L.b<T>(), L.x<T>(), L.agg, e);
   LL_LAUNCHED();
@@ -603,7 +665,7 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
   CLevel& L = H->lev[l];
   cudaStream_t s = H->s;
   if (l == H->tail_first) {
-    LL_PROF(LL_KIND_COARSE_TAIL);
+    LL_PROFW(LL_KIND_COARSE_TAIL, H->tail_flops, H->tail_bytes);
     launch_tail<T>(H);
     return;
   }
@@ -624,8 +686,9 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
       else sweep_class<T, 1>(H, l, t, nullptr);
     }
   {
-    LL_PROF(LL_KIND_BSR_OTHER);
     int skip_from = nu_pre >= 1 ? L.cs[K - 1] : L.n;  // the last forward colour has zero residual
+    long long rblk = nu_pre >= 1 ? L.res_blk : (long long)L.nnzb;
+    LL_PROFW(LL_KIND_BSR_OTHER, sweep_flops(rblk, skip_from), sweep_bytes(rblk, skip_from, (int)sizeof(T)));
     int init_end = (nu_pre >= 1 && l + 1 < H->nlev - 1) ? N.cs[1] : 0;
     if (skip_from > 0) {
       kb_residual<T, lanes<T>()><<<cdiv((long)skip_from * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, s>>>(
@@ -669,28 +732,28 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   int nb = cdiv(g.nh, kBlock);
   if (H->prm.nu_pre >= 1) {
     {
-      LL_PROF(LL_KIND_L0_SMOOTH);
+      LL_PROFW(LL_KIND_L0_SMOOTH, 15.0 * H->l0_cells[0], (24 + 12 * (double)sizeof(T)) * H->l0_cells[0]);
       k0_smooth<T, 0><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
       LL_LAUNCHED();
     }
     {
-      LL_PROF(LL_KIND_L0_SMOOTH);
+      LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
       k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
       LL_LAUNCHED();
     }
     for (int sweep = 1; sweep < H->prm.nu_pre; ++sweep) {
       {
-        LL_PROF(LL_KIND_L0_SMOOTH);
+        LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
         k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
         LL_LAUNCHED();
       }
       {
-        LL_PROF(LL_KIND_L0_SMOOTH);
+        LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
         k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
         LL_LAUNCHED();
       }
     }
-    LL_PROF(LL_KIND_L0_RESTRICT);
+    LL_PROFW(LL_KIND_L0_RESTRICT, 48.0 * H->l0_cells[0], (24 + 15.0 * sizeof(T)) * H->l0_cells[0]);
     int init_end = H->nlev > 2 ? L1.cs[1] : 0;  // level 1's first colour, unless it is the coarsest
     k0_restrict<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
                                                           L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(), L1.o2n);
@@ -705,23 +768,23 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   vcycle_coarse<T>(H, 1);
   if (H->prm.nu_post >= 1) {
     {
-      LL_PROF(LL_KIND_L0_SMOOTH);
+      LL_PROFW(LL_KIND_L0_SMOOTH, 66.0 * H->l0_cells[1], (24 + 24.75 * (double)sizeof(T)) * H->l0_cells[1]);
       k0_smooth<T, 2><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, H->agg0, L1.x<T>());
       LL_LAUNCHED();
     }
     {
-      LL_PROF(LL_KIND_L0_SMOOTH);
+      LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
       k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
       LL_LAUNCHED();
     }
     for (int sweep = 1; sweep < H->prm.nu_post; ++sweep) {
       {
-        LL_PROF(LL_KIND_L0_SMOOTH);
+        LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
         k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
         LL_LAUNCHED();
       }
       {
-        LL_PROF(LL_KIND_L0_SMOOTH);
+        LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
         k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
         LL_LAUNCHED();
       }
@@ -749,7 +812,7 @@ void finish(ll_mg_hierarchy* H, int nvals, double* out) {
 
 void true_residual(ll_mg_hierarchy* H) {
   {
-    LL_PROF(LL_KIND_OUTER_APPLY);
+    LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * H->g.n, 144.0 * H->g.n);
     kg_residual<<<kRedBlocks, kBlock, 0, H->s>>>(H->g, H->bw, H->xw, H->chat64, 1.0 / H->dt, H->r, H->partial);
     LL_LAUNCHED();
   }
@@ -771,7 +834,7 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   double* cj = H->C.p + (size_t)j * n3;
   vcycle<T>(H, H->r, zj);                                                       // step 1
   {
-    LL_PROF(LL_KIND_OUTER_APPLY);
+    LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 120.0 * g.n);
     kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);      // step 2
     LL_LAUNCHED();
   }
@@ -781,7 +844,7 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
     for (int i0 = 0; i0 < j; i0 += kDotChunk) {
       int cnt = std::min(kDotChunk, j - i0);
       {
-        LL_PROF(LL_KIND_GCR_VECTOR);
+        LL_PROFW(LL_KIND_GCR_VECTOR, 2.0 * cnt * n3, 8.0 * (cnt + 1) * n3);
         kg_multidot<kDotChunk><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
         LL_LAUNCHED();
       }
@@ -793,13 +856,13 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
       LL_LAUNCHED();
     }
     {
-      LL_PROF(LL_KIND_GCR_VECTOR);
+      LL_PROFW(LL_KIND_GCR_VECTOR, 2.0 * j * n3, 8.0 * (j + 2) * n3);
       kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef);
       LL_LAUNCHED();
     }
   }
   {
-    LL_PROF(LL_KIND_GCR_VECTOR);
+    LL_PROFW(LL_KIND_GCR_VECTOR, 4.0 * n3, 16.0 * n3);
     kg_dot2<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->r, H->partial);             // step 4
     LL_LAUNCHED();
   }
@@ -810,7 +873,7 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
     LL_LAUNCHED();
   }
   {
-    LL_PROF(LL_KIND_GCR_VECTOR);
+    LL_PROFW(LL_KIND_GCR_VECTOR, 4.0 * n3, 24.0 * n3);
     kg_rupdate<<<kRedBlocks, kBlock, 0, s>>>(n3, H->r, cj, &S->rcoef, H->partial); // step 5
     LL_LAUNCHED();
   }
@@ -860,6 +923,8 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
       LL_CU(cudaEventElapsedTime(&ms, q.b, q.e));
       H->prof_ms[q.kind] += ms;
       H->prof_n[q.kind] += 1;
+      H->prof_flops[q.kind] += q.flops;
+      H->prof_bytes[q.kind] += q.bytes;
     }
   }
 }
@@ -923,7 +988,7 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
         LL_LAUNCHED();
       }
       {
-        LL_PROF(LL_KIND_GCR_VECTOR);
+        LL_PROFW(LL_KIND_GCR_VECTOR, 2.0 * jdone * n3, (16.0 + sizeof(T) * jdone) * n3);
         kg_xupdate<T><<<nbv, kBlock, 0, s>>>(n3, H->xw, H->Z<T>(), jdone, S->y);
         LL_LAUNCHED();
       }
@@ -981,6 +1046,7 @@ int create(const double* m, double alpha, double dt, double h, ll_grid grid, con
     H->n3 = 3 * H->n2;
     symbolic(H);
     allocate(H);
+    setup_counts(H);
     setup_tail(H);
     numeric(H, m);
     *out = H;
@@ -1202,11 +1268,14 @@ int ll_mg_profile(ll_mg_hierarchy* H, unsigned int kinds) {
   for (int k = 0; k < LL_NUM_KINDS; ++k) {
     H->prof_ms[k] = 0;
     H->prof_n[k] = 0;
+    H->prof_flops[k] = 0;
+    H->prof_bytes[k] = 0;
   }
   return LL_OK;
 }
 
-int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long* launches) {
+int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long* launches, double* flops,
+                       double* bytes) {
   if (!H || kind < 0 || kind >= LL_NUM_KINDS) return LL_EINVAL;
   if (cudaStreamSynchronize(H->s) != cudaSuccess) return LL_ECUDA;
   double tot = H->prof_ms[kind];
@@ -1217,6 +1286,8 @@ int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long
   }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = H->prof_n[kind] + (long long)H->prof_pairs[kind].size();
+  if (flops) *flops = H->prof_flops[kind];
+  if (bytes) *bytes = H->prof_bytes[kind];
   return LL_OK;
 }
 
