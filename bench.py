@@ -208,9 +208,17 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     dev = torch.device("cuda", local)
-    precision = ll.LL_FP64 if args.precision == "fp64" else ll.LL_MIXED_FP32
+    precision = {"fp64": ll.LL_FP64, "mixed": ll.LL_MIXED_FP32, "bf16": ll.LL_MIXED_BF16}[args.precision]
     m0 = inputs.vortex(*GRID, seed=0).reshape(-1)
     m = torch.tensor(m0, device=dev)
+    error_vs_fp64 = None
+    if precision != ll.LL_FP64:  # one step both ways from the same state
+        ma, mb = m.clone(), m.clone()
+        ll.Hierarchy(ma, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL)).step(ma, 1)
+        ll.Hierarchy(mb, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision)).step(mb, 1)
+        error_vs_fp64 = float(torch.linalg.norm(mb - ma) / torch.linalg.norm(ma))
+        del ma, mb
+        torch.cuda.empty_cache()
     t0 = time.perf_counter()
     H = ll.Hierarchy(m, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision))
     torch.cuda.synchronize()
@@ -286,13 +294,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(GRID), "h": H_SPACING, "alpha": ALPHA, "dt": DT,
                    "rtol": RTOL, "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
                    "levels": H.levels, "l2": "working set per step (~3 GB: GCR bases, operators) exceeds the 126 MB L2"},
         "iterations_per_step": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},
         "max_relres": float(max(rrs)),
+        "error_vs_fp64": error_vs_fp64,
         "setup_s": setup_s,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -322,7 +331,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "bf16"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

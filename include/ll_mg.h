@@ -56,6 +56,8 @@ extern "C" {
 /* ---- precision of the V-cycle preconditioner ----------------------------- */
 #define LL_FP64 0        /* everything in float64 */
 #define LL_MIXED_FP32 1  /* V-cycle vectors and operators in float32, GCR float64 */
+#define LL_MIXED_BF16 2  /* as LL_MIXED_FP32, coarse-level operators stored in bfloat16
+                            (widened to float32 for the arithmetic) */
 
 typedef struct ll_grid {
   int nx, ny, nz; /* cells per direction; ny = nz = 1 for 1-D, nz = 1 for 2-D */
@@ -72,7 +74,7 @@ typedef struct ll_mg_params {
   int max_levels;      /* at most this many levels, 1..32             (20)   */
   int rounds;          /* handshake rounds per matching pass          (32)   */
   unsigned int seed;   /* tie-break hash seed of matching, colouring  (0)    */
-  int precision;       /* LL_FP64 or LL_MIXED_FP32                    (LL_FP64) */
+  int precision;       /* LL_FP64, LL_MIXED_FP32 or LL_MIXED_BF16     (LL_FP64) */
 } ll_mg_params;
 
 typedef struct ll_mg_hierarchy ll_mg_hierarchy; /* opaque, library-owned */
@@ -128,6 +130,19 @@ int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid g
  *   m device SoA 3*N float64, in/out; iters/relres host, optional, n_steps.
  * Returns the worst status over the steps (errors stop early). */
 int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step);
+
+/* n_steps time steps of the full model with explicit source terms (the LLG
+ * scheme at the end of Sec. 2.1, without the stray field):
+ *   (m^{n+1} - m^n)/dt = -m^n x (eps Delta_h m^{n+1} + f^n)
+ *                        - alpha m^n x (m^n x (eps Delta_h m^{n+1} + f^n)),
+ *   f^n = -q (m2^n e2 + m3^n e3) + h_e   (anisotropy along e1, external field),
+ * i.e. the same operator with Delta_h scaled by eps and the right-hand side
+ * m^n/dt - C(m^n) f^n.  The exchange factor eps enters through the
+ * hierarchy's spacing: set it up with h/sqrt(eps).  Then as ll_mg_step
+ * (numeric setup per step, solve from the guess m^n, projection).
+ *   m  device SoA 3*N float64, in/out;  he  host, 3 doubles (NULL: zero). */
+int ll_mg_step_llg(ll_mg_hierarchy* H, double* m, int n_steps, double q, const double* he,
+                   int* iters_per_step, double* relres_per_step);
 
 /* Release the hierarchy and all its device memory (NULL is ignored). */
 void ll_mg_destroy(ll_mg_hierarchy* H);

@@ -103,6 +103,7 @@ def _load():
         "orc_free": (None, [vp]),
         "orc_solve": (i, [vp, _dp, _dp, d, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
         "orc_step": (i, [_dp, i, i, i, i, d, d, d, ctypes.POINTER(_Params), i, _ip, _dp]),
+        "orc_step_llg": (i, [_dp, i, i, i, i, d, d, d, ctypes.POINTER(_Params), d, _dp, _ip, _dp]),
         "orc_nlevels": (i, [vp]),
         "orc_level_cells": (i, [vp, i]),
         "orc_level_nnz": (i, [vp, i]),
@@ -260,6 +261,20 @@ def step(m, n_steps, grid, h, alpha, dt, params: Params | None = None, project: 
     cp = params._c()
     st = _load().orc_step(mm, int(n_steps), nx, ny, nz, float(h), float(alpha), float(dt),
                           ctypes.byref(cp), 1 if project else 0, its, rrs)
+    return mm, its[:n_steps], rrs[:n_steps], st
+
+
+def step_llg(m, n_steps, grid, h, alpha, dt, q=0.0, he=(0.0, 0.0, 0.0), params: Params | None = None):
+    """Steps of the full model with explicit anisotropy and external field
+    (eps folded into h); returns (m, iterations, relres, status)."""
+    params = params or Params()
+    nx, ny, nz = _grid3(grid)
+    mm = np.array(m, np.float64, copy=True).reshape(-1)
+    its = np.zeros(max(n_steps, 1), np.int32)
+    rrs = np.zeros(max(n_steps, 1), np.float64)
+    cp = params._c()
+    st = _load().orc_step_llg(mm, int(n_steps), nx, ny, nz, float(h), float(alpha), float(dt), ctypes.byref(cp),
+                              float(q), np.asarray(he, np.float64), its, rrs)
     return mm, its[:n_steps], rrs[:n_steps], st
 
 

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libllmg.so")
 
 LL_OK, LL_NOT_CONVERGED, LL_BREAKDOWN = 0, 1, 2
 LL_EINVAL, LL_ECUDA, LL_ENOMEM, LL_SINGULAR_COARSE, LL_ELIMIT = -1, -2, -3, -4, -5
-LL_FP64, LL_MIXED_FP32 = 0, 1
+LL_FP64, LL_MIXED_FP32, LL_MIXED_BF16 = 0, 1, 2
 
 # every symbol declared in include/ll_mg.h
 EXPORTS = (
@@ -29,7 +29,7 @@ EXPORTS = (
     "ll_status_string", "ll_mg_levels", "ll_mg_level_cells", "ll_mg_level_aggregates",
     "ll_mg_level_colours", "ll_mg_level_blocks", "ll_mg_level_operator", "ll_mg_apply", "ll_mg_vcycle",
     "ll_mg_smooth", "ll_mg_step", "ll_launch_count", "ll_mg_profile", "ll_mg_profile_read",
-    "ll_residual_noalloc",
+    "ll_residual_noalloc", "ll_mg_step_llg",
 )
 
 
@@ -109,6 +109,7 @@ def load_library():
         "ll_mg_profile": (i, [vp, ctypes.c_uint]),
         "ll_mg_profile_read": (i, [vp, i, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "ll_residual_noalloc": (i, [vp, d, d, d, _Grid, vp, vp, vp, vp, vp]),
+        "ll_mg_step_llg": (i, [vp, vp, i, d, vp, ip, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -207,6 +208,19 @@ class Hierarchy:
         rrs = (ctypes.c_double * max(1, n_steps))()
         st = load_library().ll_mg_step(self._h, _field(dev, self.n, "m"), int(n_steps), its, rrs)
         _check(st, "ll_mg_step")
+        if dev is not m:
+            m.copy_(dev, non_blocking=False)
+        return st, list(its[:n_steps]), list(rrs[:n_steps])
+
+    def step_llg(self, m, n_steps: int = 1, q: float = 0.0, he=(0.0, 0.0, 0.0)):
+        """Time steps with the explicit anisotropy and external-field terms
+        (``ll_mg_step_llg``); set the hierarchy up with h/sqrt(eps)."""
+        dev = m if m.is_cuda else m.to("cuda", non_blocking=True)
+        its = (ctypes.c_int * max(1, n_steps))()
+        rrs = (ctypes.c_double * max(1, n_steps))()
+        hev = (ctypes.c_double * 3)(*[float(v) for v in he])
+        st = load_library().ll_mg_step_llg(self._h, _field(dev, self.n, "m"), int(n_steps), float(q), hev, its, rrs)
+        _check(st, "ll_mg_step_llg")
         if dev is not m:
             m.copy_(dev, non_blocking=False)
         return st, list(its[:n_steps]), list(rrs[:n_steps])

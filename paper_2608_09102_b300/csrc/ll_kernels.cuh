@@ -2,6 +2,7 @@
 // Included by ll_solver.cu only.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "ll_internal.cuh"
@@ -171,6 +172,11 @@ template <typename T>
 __global__ void k_cast(long n, const double* __restrict__ in, T* __restrict__ out) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (T)in[i];
+}
+template <>
+__global__ void k_cast<__nv_bfloat16>(long n, const double* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __double2bfloat16(in[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -513,26 +519,36 @@ __device__ __forceinline__ void group_sum3(T& a, T& b, T& c) {
   }
 }
 
-// a -= A_IJ v  for one 3x3 block (negated fused multiply-adds)
-template <typename T>
-__device__ __forceinline__ void block_msub(const T* __restrict__ A, T v0, T v1, T v2, T& a0, T& a1, T& a2) {
-  a0 = fma(-A[0], v0, a0);
-  a0 = fma(-A[1], v1, a0);
-  a0 = fma(-A[2], v2, a0);
-  a1 = fma(-A[3], v0, a1);
-  a1 = fma(-A[4], v1, a1);
-  a1 = fma(-A[5], v2, a1);
-  a2 = fma(-A[6], v0, a2);
-  a2 = fma(-A[7], v1, a2);
-  a2 = fma(-A[8], v2, a2);
+// widen a stored matrix value to the arithmetic type
+template <typename T, typename TM>
+__device__ __forceinline__ T widen(TM v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+// a -= A_IJ v  for one 3x3 block stored as TM (negated fused multiply-adds)
+template <typename T, typename TM>
+__device__ __forceinline__ void block_msub(const TM* __restrict__ A, T v0, T v1, T v2, T& a0, T& a1, T& a2) {
+  a0 = fma(-widen<T, TM>(A[0]), v0, a0);
+  a0 = fma(-widen<T, TM>(A[1]), v1, a0);
+  a0 = fma(-widen<T, TM>(A[2]), v2, a0);
+  a1 = fma(-widen<T, TM>(A[3]), v0, a1);
+  a1 = fma(-widen<T, TM>(A[4]), v1, a1);
+  a1 = fma(-widen<T, TM>(A[5]), v2, a1);
+  a2 = fma(-widen<T, TM>(A[6]), v0, a2);
+  a2 = fma(-widen<T, TM>(A[7]), v1, a2);
+  a2 = fma(-widen<T, TM>(A[8]), v2, a2);
 }
 
 // a -= sum over the blocks p = p0, p0 + G, ... < p1 of A_p v_{col p}, with the
 // column indices of U blocks loaded first, then their x values, then the
 // products: three dependent memory round trips per U blocks instead of per
 // block.  PROL adds the coarse correction e[agg[J]] to every v.
-template <typename T, int G, int U, bool PROL>
-__device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__ col, const T* __restrict__ val,
+template <typename T, typename TM, int G, int U, bool PROL>
+__device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__ col, const TM* __restrict__ val,
                                          const T* __restrict__ x, const int* __restrict__ agg,
                                          const T* __restrict__ e, T& a0, T& a1, T& a2) {
   for (int base = p0; base < p1; base += G * U) {
@@ -556,7 +572,7 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (J[u] >= 0) block_msub(val + 9L * (base + u * G), v[u][0], v[u][1], v[u][2], a0, a1, a2);
+      if (J[u] >= 0) block_msub<T, TM>(val + 9L * (base + u * G), v[u][0], v[u][1], v[u][2], a0, a1, a2);
   }
 }
 
@@ -573,17 +589,17 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
 //           prolongation, never stored).
 // x_I = Dinv_I (b_I - sum_{J != I} A_IJ v_J); the lanes of a group share the
 // three output components.  Every lane of the warp must call this (shuffles).
-template <typename T, int G, int MODE>
+template <typename T, typename TM, int G, int MODE>
 __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
                                           const int* __restrict__ diag, const int* __restrict__ col,
-                                          const T* __restrict__ val, const T* __restrict__ dinv,
+                                          const TM* __restrict__ val, const T* __restrict__ dinv,
                                           const T* __restrict__ b, T* __restrict__ x, const int* __restrict__ agg,
                                           const T* __restrict__ e) {
   T a0 = 0, a1 = 0, a2 = 0;
   if (active) {
     int pd = diag[I];
-    row_msub<T, G, 4, MODE == 2>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-    if (MODE != 0) row_msub<T, G, 4, false>(pd + 1 + lane, rowptr[I + 1], col, val, x, agg, e, a0, a1, a2);
+    row_msub<T, TM, G, 4, MODE == 2>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
+    if (MODE != 0) row_msub<T, TM, G, 4, false>(pd + 1 + lane, rowptr[I + 1], col, val, x, agg, e, a0, a1, a2);
   }
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
   if (active) {
@@ -595,37 +611,38 @@ __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const in
   }
 }
 
-template <typename T, int G, int MODE>
+template <typename T, typename TM, int G, int MODE>
 __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
                                                 const int* __restrict__ diag, const int* __restrict__ col,
-                                                const T* __restrict__ val, const T* __restrict__ dinv,
+                                                const TM* __restrict__ val, const T* __restrict__ dinv,
                                                 const T* __restrict__ b, T* __restrict__ x,
                                                 const int* __restrict__ agg, const T* __restrict__ e) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int I = r0 + (int)(gt / G);
-  sweep_row<T, G, MODE>(I, threadIdx.x % G, I < r1, rowptr, diag, col, val, dinv, b, x, agg, e);
+  sweep_row<T, TM, G, MODE>(I, threadIdx.x % G, I < r1, rowptr, diag, col, val, dinv, b, x, agg, e);
 }
 
 // r_I = b_I - (A x)_I, G lanes per row (all lanes of the warp call it)
-template <typename T, int G>
+template <typename T, typename TM, int G>
 __device__ __forceinline__ void residual_row(int I, int lane, bool active, const int* __restrict__ rowptr,
-                                             const int* __restrict__ col, const T* __restrict__ val,
+                                             const int* __restrict__ col, const TM* __restrict__ val,
                                              const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   T a0 = 0, a1 = 0, a2 = 0;
-  if (active) row_msub<T, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
+  if (active)
+    row_msub<T, TM, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
   group_sum3<G>(a0, a1, a2);
   if (active)
     for (int c = lane; c < 3; c += G) r[3L * I + c] = b[3L * I + c] + (c == 0 ? a0 : c == 1 ? a1 : a2);
 }
 
-template <typename T, int G>
+template <typename T, typename TM, int G>
 __global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restrict__ rowptr,
-                                                   const int* __restrict__ col, const T* __restrict__ val,
+                                                   const int* __restrict__ col, const TM* __restrict__ val,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ r) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int I = (int)(gt / G);
-  residual_row<T, G>(I, threadIdx.x % G, I < rend, rowptr, col, val, b, x, r);
+  residual_row<T, TM, G>(I, threadIdx.x % G, I < rend, rowptr, col, val, b, x, r);
 }
 
 // Restriction plus the first colour of the next level's forward sweep:
@@ -918,6 +935,23 @@ __global__ void k_renormalise(long n, const double* __restrict__ x, double* __re
   m[k] = a / s;
   m[n + k] = b / s;
   m[2 * n + k] = c / s;
+}
+
+// rhs = m/dt - C(m) f with f = -q (0, m2, m3) + he  (explicit source terms)
+__global__ void k_rhs_llg(long n, const double* __restrict__ m, double alpha, double inv_dt, double q, double he0,
+                          double he1, double he2, double* __restrict__ b) {
+  long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double m1 = m[k], m2 = m[n + k], m3 = m[2 * n + k];
+  double f1 = he0, f2 = he1 - q * m2, f3 = he2 - q * m3;
+  double mm = m1 * m1 + m2 * m2 + m3 * m3, mf = m1 * f1 + m2 * f2 + m3 * f3;
+  // C(m) f = m x f + alpha (m (m.f) - |m|^2 f)
+  double c1 = m2 * f3 - m3 * f2 + alpha * (m1 * mf - mm * f1);
+  double c2 = m3 * f1 - m1 * f3 + alpha * (m2 * mf - mm * f2);
+  double c3 = m1 * f2 - m2 * f1 + alpha * (m3 * mf - mm * f3);
+  b[k] = m1 * inv_dt - c1;
+  b[n + k] = m2 * inv_dt - c2;
+  b[2 * n + k] = m3 * inv_dt - c3;
 }
 
 // rhs = m / dt

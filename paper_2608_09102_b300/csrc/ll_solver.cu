@@ -40,9 +40,11 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   long long res_blk = 0;                    // blocks of the rows before the last colour
   DBuf<double> val64, dinv64;
   DBuf<float> val32, dinv32;
+  DBuf<__nv_bfloat16> val16;        // bfloat16 storage of the operator (LL_MIXED_BF16)
   DBuf<double> x64, b64, r64;
   DBuf<float> x32, b32, r32;
   template <typename T> T* val();
+  template <typename TM> TM* valm();  // operator values in storage type TM
   template <typename T> T* dinv();
   template <typename T> T* x();
   template <typename T> T* b();
@@ -50,6 +52,9 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
 };
 template <> double* CLevel::val<double>() { return val64; }
 template <> float* CLevel::val<float>() { return val32; }
+template <> double* CLevel::valm<double>() { return val64; }
+template <> float* CLevel::valm<float>() { return val32; }
+template <> __nv_bfloat16* CLevel::valm<__nv_bfloat16>() { return val16; }
 template <> double* CLevel::dinv<double>() { return dinv64; }
 template <> float* CLevel::dinv<float>() { return dinv32; }
 template <> double* CLevel::x<double>() { return x64; }
@@ -92,8 +97,10 @@ struct ll_mg_hierarchy {
   // the small coarse levels as one cluster kernel
   int tail_first = -1;  // first tail level, -1: no tail
   int tail_cluster = 0;
-  DBuf<TailArgs<double>> tail64;
-  DBuf<TailArgs<float>> tail32;
+  DBuf<TailArgs<double, double>> tail64;
+  DBuf<TailArgs<float, float>> tail32;
+  DBuf<TailArgs<float, __nv_bfloat16>> tail16;
+  template <typename T, typename TM> DBuf<TailArgs<T, TM>>& tail();
   // single-level hierarchies: cell-major scratch of the direct solve
   DBuf<double> single_b, single_x;
   // kernel timing (ll_mg_profile)
@@ -152,6 +159,9 @@ template <> double* ll_mg_hierarchy::chat<double>() { return chat64; }
 template <> float* ll_mg_hierarchy::chat<float>() { return chat32; }
 template <> double* ll_mg_hierarchy::dinv0<double>() { return dinv64; }
 template <> float* ll_mg_hierarchy::dinv0<float>() { return dinv32; }
+template <> DBuf<TailArgs<double, double>>& ll_mg_hierarchy::tail<double, double>() { return tail64; }
+template <> DBuf<TailArgs<float, float>>& ll_mg_hierarchy::tail<float, float>() { return tail32; }
+template <> DBuf<TailArgs<float, __nv_bfloat16>>& ll_mg_hierarchy::tail<float, __nv_bfloat16>() { return tail16; }
 template <> double* ll_mg_hierarchy::Z<double>() { return Z64; }
 template <> float* ll_mg_hierarchy::Z<float>() { return Z32; }
 
@@ -300,7 +310,7 @@ void symbolic(ll_mg_hierarchy* H) {
 }
 
 void allocate(ll_mg_hierarchy* H) {
-  bool mixed = H->prm.precision == LL_MIXED_FP32;
+  bool mixed = H->prm.precision != LL_FP64;  // float32 V-cycle
   long n2 = H->n2;
   H->chat64.alloc(9 * n2);
   if (mixed) {
@@ -314,7 +324,8 @@ void allocate(ll_mg_hierarchy* H) {
     C.val64.alloc(9L * C.nnzb);
     C.dinv64.alloc(9L * C.n);
     if (mixed) {
-      C.val32.alloc(9L * C.nnzb);
+      if (H->prm.precision == LL_MIXED_BF16) C.val16.alloc(9L * C.nnzb);
+      else C.val32.alloc(9L * C.nnzb);
       C.dinv32.alloc(9L * C.n);
       C.x32.alloc(3L * C.n);
       C.b32.alloc(3L * C.n);
@@ -354,13 +365,13 @@ void allocate(ll_mg_hierarchy* H) {
 
 // algorithmic work of coarse sweeps and residuals (the models in ll_mg.h)
 inline double sweep_flops(long long blocks, long long rows) { return 18.0 * blocks + 15.0 * rows; }
-inline double sweep_bytes(long long blocks, long long rows, int w) {
-  return (12.0 * w + 4) * blocks + (15.0 * w + 8) * rows;
+inline double sweep_bytes(long long blocks, long long rows, int w, int wm) {
+  return (9.0 * wm + 3.0 * w + 4) * blocks + (15.0 * w + 8) * rows;
 }
 
-template <typename T>
-void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
-  TailArgs<T> A;
+template <typename T, typename TM>
+void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
+  TailArgs<T, TM> A;
   A.first = H->tail_first;
   A.last = H->nlev - 1;
   A.nu_pre = H->prm.nu_pre;
@@ -369,14 +380,14 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
   A.ainv = H->ainv;
   for (int l = A.first; l <= A.last; ++l) {
     CLevel& C = H->lev[l];
-    TailLevel<T>& L = A.L[l];
+    TailLevel<T, TM>& L = A.L[l];
     L.n = C.n;
     L.ncol = C.ncol;
     for (int c = 0; c <= C.ncol && c <= kTailMaxColours; ++c) L.cs[c] = C.cs[c];
     L.rowptr = C.rowptr;
     L.diag = C.diag;
     L.col = C.col;
-    L.val = C.val<T>();
+    L.val = C.valm<TM>();
     L.dinv = C.dinv<T>();
     L.x = C.x<T>();
     L.b = C.b<T>();
@@ -385,7 +396,7 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
     L.mptr = C.mptr;
     L.mem = C.mem;
   }
-  int w = (int)sizeof(T);
+  int w = (int)sizeof(T), wm = (int)sizeof(TM);
   H->tail_flops = H->tail_bytes = 0;
   for (int l = A.first; l < A.last; ++l) {
     CLevel& C = H->lev[l];
@@ -393,14 +404,14 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
       long long rows = C.cs[c + 1] - C.cs[c];
       if (c > 0) {
         H->tail_flops += sweep_flops(C.pre_blk[c], rows);
-        H->tail_bytes += sweep_bytes(C.pre_blk[c], rows, w);
+        H->tail_bytes += sweep_bytes(C.pre_blk[c], rows, w, wm);
       }
       H->tail_flops += sweep_flops(C.off_blk[c], rows);
-      H->tail_bytes += sweep_bytes(C.off_blk[c], rows, w);
+      H->tail_bytes += sweep_bytes(C.off_blk[c], rows, w, wm);
     }
     long long rrows = C.ncol > 0 ? C.cs[C.ncol - 1] : 0;
     H->tail_flops += sweep_flops(C.res_blk, rrows);
-    H->tail_bytes += sweep_bytes(C.res_blk, rrows, w);
+    H->tail_bytes += sweep_bytes(C.res_blk, rrows, w, wm);
   }
   H->tail_flops += 2.0 * H->ncoarse3 * H->ncoarse3;
   H->tail_bytes += 8.0 * H->ncoarse3 * H->ncoarse3;
@@ -412,9 +423,9 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T>>& dst) {
 // Decide whether the small coarse levels run as one cluster kernel: the
 // cluster must be schedulable (16 CTAs, else 8) and every tail level must
 // have at most kTailMaxColours colours.
-template <typename T>
+template <typename T, typename TM>
 void setup_tail_for(ll_mg_hierarchy* H) {
-  auto kern = k_coarse_tail<T, 4>;
+  auto kern = k_coarse_tail<T, TM, 4>;
   for (int cl : {16, 8}) {
     if (cl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
       cudaGetLastError();
@@ -441,8 +452,7 @@ void setup_tail_for(ll_mg_hierarchy* H) {
     H->tail_first = -1;
     return;
   }
-  if (H->prm.precision == LL_MIXED_FP32) fill_tail<float>(H, H->tail32);
-  else fill_tail<double>(H, H->tail64);
+  fill_tail<T, TM>(H, H->tail<T, TM>());
 }
 
 // host counts behind the algorithmic flop and byte models of the kernels
@@ -483,14 +493,13 @@ void setup_tail(ll_mg_hierarchy* H) {
       H->tail_first = -1;
       return;
     }
-  if (H->prm.precision == LL_MIXED_FP32) setup_tail_for<float>(H);
-  else setup_tail_for<double>(H);
+  if (H->prm.precision == LL_MIXED_BF16) setup_tail_for<float, __nv_bfloat16>(H);
+  else if (H->prm.precision == LL_MIXED_FP32) setup_tail_for<float, float>(H);
+  else setup_tail_for<double, double>(H);
 }
 
-template <typename T>
-void launch_tail(ll_mg_hierarchy* H);
-template <>
-void launch_tail<double>(ll_mg_hierarchy* H) {
+template <typename T, typename TM>
+void launch_tail(ll_mg_hierarchy* H) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(H->tail_cluster);
   cfg.blockDim = dim3(kTailThreads);
@@ -502,23 +511,7 @@ void launch_tail<double>(ll_mg_hierarchy* H) {
   at.val.clusterDim.z = 1;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
-  LL_CU(cudaLaunchKernelEx(&cfg, k_coarse_tail<double, 4>, (const TailArgs<double>*)H->tail64.p));
-  count_launch();
-}
-template <>
-void launch_tail<float>(ll_mg_hierarchy* H) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(H->tail_cluster);
-  cfg.blockDim = dim3(kTailThreads);
-  cfg.stream = H->s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = H->tail_cluster;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
-  LL_CU(cudaLaunchKernelEx(&cfg, k_coarse_tail<float, 4>, (const TailArgs<float>*)H->tail32.p));
+  LL_CU(cudaLaunchKernelEx(&cfg, k_coarse_tail<T, TM, 4>, (const TailArgs<T, TM>*)H->tail<T, TM>().p));
   count_launch();
 }
 
@@ -580,7 +573,7 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
   LL_PROF(LL_KIND_NUMERIC);
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
-  bool mixed = H->prm.precision == LL_MIXED_FP32;
+  bool mixed = H->prm.precision != LL_FP64;  // float32 V-cycle
   H->flag.zero(s);
   double ih2 = 1.0 / (H->h * H->h), inv_dt = 1.0 / H->dt;
   int nb = cdiv(H->n2, kBlock);
@@ -599,7 +592,10 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
                                                     C.val64, C.dinv64, H->flag);
     LL_LAUNCHED();
     if (mixed) {
-      k_cast<float><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val32);
+      if (H->prm.precision == LL_MIXED_BF16)
+        k_cast<__nv_bfloat16><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val16);
+      else
+        k_cast<float><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val32);
       LL_LAUNCHED();
       k_cast<float><<<cdiv(9L * C.n, kBlock), kBlock, 0, s>>>(9L * C.n, C.dinv64, C.dinv32);
       LL_LAUNCHED();
@@ -638,35 +634,35 @@ void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
 }
 
 // one colour class of level l: rows [cs[t], cs[t+1])
-template <typename T, int MODE>
+template <typename T, typename TM, int MODE>
 void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e) {
   CLevel& L = H->lev[l];
   int r0 = L.cs[t], r1 = L.cs[t + 1];
   if (r1 <= r0) return;
   long long blk = MODE == 0 ? L.pre_blk[t] : L.off_blk[t];
-  LL_PROFW(LL_KIND_BSR_SMOOTH, sweep_flops(blk, r1 - r0), sweep_bytes(blk, r1 - r0, (int)sizeof(T)));
-  kb_sweep<T, lanes<T>(), MODE><<<cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, H->s>>>(
-      r0, r1, L.rowptr, L.diag, L.col, L.val<T>(), L.dinv<T>(), L.b<T>(), L.x<T>(), L.agg, e);
+  LL_PROFW(LL_KIND_BSR_SMOOTH, sweep_flops(blk, r1 - r0), sweep_bytes(blk, r1 - r0, (int)sizeof(T), (int)sizeof(TM)));
+  kb_sweep<T, TM, lanes<T>(), MODE><<<cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, H->s>>>(
+      r0, r1, L.rowptr, L.diag, L.col, L.valm<TM>(), L.dinv<T>(), L.b<T>(), L.x<T>(), L.agg, e);
   LL_LAUNCHED();
 }
 
 // one full plain block-GS sweep of level l (colours ascending or descending)
-template <typename T>
+template <typename T, typename TM>
 void smooth_level(ll_mg_hierarchy* H, int l, bool forward) {
   CLevel& L = H->lev[l];
-  for (int k = 0; k < L.ncol; ++k) sweep_class<T, 1>(H, l, forward ? k : L.ncol - 1 - k, nullptr);
+  for (int k = 0; k < L.ncol; ++k) sweep_class<T, TM, 1>(H, l, forward ? k : L.ncol - 1 - k, nullptr);
 }
 
 // V-cycle below level 0.  On entry b_l holds the restricted residual and,
 // when pre-smoothing is on, x_l already holds the colour-0 rows of the first
 // forward sweep (written by the restriction into this level).
-template <typename T>
+template <typename T, typename TM>
 void vcycle_coarse(ll_mg_hierarchy* H, int l) {
   CLevel& L = H->lev[l];
   cudaStream_t s = H->s;
   if (l == H->tail_first) {
     LL_PROFW(LL_KIND_COARSE_TAIL, H->tail_flops, H->tail_bytes);
-    launch_tail<T>(H);
+    launch_tail<T, TM>(H);
     return;
   }
   if (l == H->nlev - 1) {
@@ -682,24 +678,25 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
   }
   for (int sweep = 0; sweep < nu_pre; ++sweep)
     for (int t = sweep == 0 ? 1 : 0; t < K; ++t) {
-      if (sweep == 0) sweep_class<T, 0>(H, l, t, nullptr);
-      else sweep_class<T, 1>(H, l, t, nullptr);
+      if (sweep == 0) sweep_class<T, TM, 0>(H, l, t, nullptr);
+      else sweep_class<T, TM, 1>(H, l, t, nullptr);
     }
   {
     int skip_from = nu_pre >= 1 ? L.cs[K - 1] : L.n;  // the last forward colour has zero residual
     long long rblk = nu_pre >= 1 ? L.res_blk : (long long)L.nnzb;
-    LL_PROFW(LL_KIND_BSR_OTHER, sweep_flops(rblk, skip_from), sweep_bytes(rblk, skip_from, (int)sizeof(T)));
+    LL_PROFW(LL_KIND_BSR_OTHER, sweep_flops(rblk, skip_from),
+             sweep_bytes(rblk, skip_from, (int)sizeof(T), (int)sizeof(TM)));
     int init_end = (nu_pre >= 1 && l + 1 < H->nlev - 1) ? N.cs[1] : 0;
     if (skip_from > 0) {
-      kb_residual<T, lanes<T>()><<<cdiv((long)skip_from * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, s>>>(
-          skip_from, L.rowptr, L.col, L.val<T>(), L.b<T>(), L.x<T>(), L.r<T>());
+      kb_residual<T, TM, lanes<T>()><<<cdiv((long)skip_from * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, s>>>(
+          skip_from, L.rowptr, L.col, L.valm<TM>(), L.b<T>(), L.x<T>(), L.r<T>());
       LL_LAUNCHED();
     }
     kb_restrict<T><<<cdiv(N.n, kCoarseBlock), kCoarseBlock, 0, s>>>(N.n, N.mptr, N.mem, skip_from, L.r<T>(), N.b<T>(),
                                                         init_end, N.dinv<T>(), N.x<T>());
     LL_LAUNCHED();
   }
-  vcycle_coarse<T>(H, l + 1);
+  vcycle_coarse<T, TM>(H, l + 1);
   if (nu_post == 0) {
     LL_PROF(LL_KIND_BSR_OTHER);
     kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
@@ -707,13 +704,13 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
   }
   for (int sweep = 0; sweep < nu_post; ++sweep)
     for (int k = 0; k < K; ++k) {
-      if (sweep == 0) sweep_class<T, 2>(H, l, K - 1 - k, N.x<T>());
-      else sweep_class<T, 1>(H, l, K - 1 - k, nullptr);
+      if (sweep == 0) sweep_class<T, TM, 2>(H, l, K - 1 - k, N.x<T>());
+      else sweep_class<T, TM, 1>(H, l, K - 1 - k, nullptr);
     }
 }
 
 // z = V-cycle(r) on level 0; r float64 red-black, z red-black in T
-template <typename T>
+template <typename T, typename TM>
 void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
@@ -765,7 +762,7 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
     k0_restrict_b<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, L1.n, L1.mptr, L1.mem, L1.b<T>());
     LL_LAUNCHED();
   }
-  vcycle_coarse<T>(H, 1);
+  vcycle_coarse<T, TM>(H, 1);
   if (H->prm.nu_post >= 1) {
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 66.0 * H->l0_cells[1], (24 + 24.75 * (double)sizeof(T)) * H->l0_cells[1]);
@@ -823,7 +820,7 @@ void true_residual(ll_mg_hierarchy* H) {
 // One GCR iteration j (Algorithm 1, steps 1-5) without host interaction:
 // z_j = V-cycle(r), c_j = A z_j, two classical Gram-Schmidt passes against
 // c_0..c_{j-1}, gamma_jj, alpha_j, r -= alpha_j c_j and |r|^2.
-template <typename T>
+template <typename T, typename TM>
 void iteration_body(ll_mg_hierarchy* H, int j) {
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
@@ -832,7 +829,7 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   GcrScal* S = H->scal.p;
   T* zj = H->Z<T>() + (size_t)j * n3;
   double* cj = H->C.p + (size_t)j * n3;
-  vcycle<T>(H, H->r, zj);                                                       // step 1
+  vcycle<T, TM>(H, H->r, zj);                                                       // step 1
   {
     LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 120.0 * g.n);
     kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);      // step 2
@@ -882,10 +879,10 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
 
 // run iteration j, from a CUDA graph captured on first use (one launch
 // instead of a few hundred), then fold any graph-timed kernels into the totals
-template <typename T>
+template <typename T, typename TM>
 void run_iteration(ll_mg_hierarchy* H, int j) {
   if (!H->use_graphs) {
-    iteration_body<T>(H, j);
+    iteration_body<T, TM>(H, j);
     return;
   }
   if (H->graph_dt != H->dt) {
@@ -899,7 +896,7 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
     LL_CU(cudaStreamBeginCapture(H->s, cudaStreamCaptureModeThreadLocal));
     H->capturing = j;
     try {
-      iteration_body<T>(H, j);
+      iteration_body<T, TM>(H, j);
     } catch (Status) {
       H->capturing = -1;
       cudaStreamEndCapture(H->s, &graph);
@@ -929,7 +926,7 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
   }
 }
 
-template <typename T>
+template <typename T, typename TM>
 int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int* iters, double* relres) {
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
@@ -965,7 +962,7 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
     int jdone = 0;
     bool broke = false;
     for (int j = 0; j < m; ++j) {
-      run_iteration<T>(H, j);
+      run_iteration<T, TM>(H, j);
       ++total;
       read_head(H);
       double gjj = H->h_head[4];
@@ -1009,14 +1006,16 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
 
 int solve(ll_mg_hierarchy* H, const double* b, double* x, double rtol, int* it, double* rr) {
   if (rtol <= 0) rtol = H->prm.rtol;
-  if (H->prm.precision == LL_MIXED_FP32) return gcr<float>(H, b, x, rtol, it, rr);
-  return gcr<double>(H, b, x, rtol, it, rr);
+  if (H->prm.precision == LL_MIXED_BF16) return gcr<float, __nv_bfloat16>(H, b, x, rtol, it, rr);
+  if (H->prm.precision == LL_MIXED_FP32) return gcr<float, float>(H, b, x, rtol, it, rr);
+  return gcr<double, double>(H, b, x, rtol, it, rr);
 }
 
 bool valid_params(const ll_mg_params& p) {
   return p.rtol >= 0 && p.maxit >= 0 && p.restart >= 1 && p.restart <= kMaxRestart && p.nu_pre >= 0 &&
          p.nu_pre <= 16 && p.nu_post >= 0 && p.nu_post <= 16 && p.coarsest_cells >= 1 && p.max_levels >= 1 &&
-         p.max_levels <= kMaxLevels && p.rounds >= 1 && (p.precision == LL_FP64 || p.precision == LL_MIXED_FP32);
+         p.max_levels <= kMaxLevels && p.rounds >= 1 &&
+         (p.precision == LL_FP64 || p.precision == LL_MIXED_FP32 || p.precision == LL_MIXED_BF16);
 }
 
 int create(const double* m, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p, void* stream,
@@ -1119,16 +1118,21 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
   }
 }
 
-// time steps on an existing hierarchy; fresh = numeric setup already done for m
+// time steps on an existing hierarchy; fresh = numeric setup already done for
+// m; src = explicit source terms (q, he0, he1, he2) or NULL
 static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step,
-                 bool fresh) {
+                 bool fresh, const double* src = nullptr) {
   int worst = LL_OK;
   double dt = H->dt;
   try {
     long n3 = 3 * H->g.n;
     for (int k = 0; k < n_steps; ++k) {
       if (k > 0 || !fresh) numeric(H, m);
-      k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
+      if (src)
+        k_rhs_llg<<<cdiv(H->g.n, kBlock), kBlock, 0, H->s>>>(H->g.n, m, H->alpha, 1.0 / dt, src[0], src[1], src[2],
+                                                             src[3], H->stepb);
+      else
+        k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
       LL_LAUNCHED();
       LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
       int it = 0;
@@ -1169,6 +1173,19 @@ int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, 
     return st.code;
   }
   return steps(H, m, n_steps, iters_per_step, relres_per_step, false);
+}
+
+int ll_mg_step_llg(ll_mg_hierarchy* H, double* m, int n_steps, double q, const double* he, int* iters_per_step,
+                   double* relres_per_step) {
+  if (!H || !m || n_steps < 0 || !isfinite(q)) return LL_EINVAL;
+  double src[4] = {q, he ? he[0] : 0.0, he ? he[1] : 0.0, he ? he[2] : 0.0};
+  if (!isfinite(src[1]) || !isfinite(src[2]) || !isfinite(src[3])) return LL_EINVAL;
+  try {
+    enter(H);
+  } catch (Status st) {
+    return st.code;
+  }
+  return steps(H, m, n_steps, iters_per_step, relres_per_step, false, src);
 }
 
 long long ll_launch_count(void) { return g_launches.load(); }
@@ -1318,11 +1335,12 @@ int ll_mg_vcycle(ll_mg_hierarchy* H, const double* r, double* z) {
     int nbs = cdiv(H->n2, kBlock);
     k_to_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, r, H->bw);
     LL_LAUNCHED();
-    if (H->prm.precision == LL_MIXED_FP32) {
-      vcycle<float>(H, H->bw, H->Z32.p);
+    if (H->prm.precision != LL_FP64) {
+      if (H->prm.precision == LL_MIXED_BF16) vcycle<float, __nv_bfloat16>(H, H->bw, H->Z32.p);
+      else vcycle<float, float>(H, H->bw, H->Z32.p);
       k_from_rb<float, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, H->Z32.p, z);
     } else {
-      vcycle<double>(H, H->bw, H->Z64.p);
+      vcycle<double, double>(H, H->bw, H->Z64.p);
       k_from_rb<double, double><<<nbs, kBlock, 0, H->s>>>(g, H->nat_of_slot, H->Z64.p, z);
     }
     LL_LAUNCHED();
@@ -1361,7 +1379,7 @@ int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forw
       LL_LAUNCHED();
       kb_gather3<double><<<nb, kBlock, 0, s>>>(L.n, L.n2o, x, L.x64.p);
       LL_LAUNCHED();
-      smooth_level<double>(H, l, forward != 0);
+      smooth_level<double, double>(H, l, forward != 0);
       kb_scatter3<double><<<nb, kBlock, 0, s>>>(L.n, L.n2o, L.x64.p, x);
       LL_LAUNCHED();
     }

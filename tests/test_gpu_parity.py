@@ -171,6 +171,21 @@ def test_time_steps_match_oracle(name):
     np.testing.assert_allclose(nrm, 1.0, atol=1e-14)
 
 
+@pytest.mark.parametrize("name", ["2d", "3d"])
+def test_source_term_steps_match_oracle(name):
+    grid, h, alpha, dt, kind, cc = CASES[name]
+    m0 = _field(kind, grid).reshape(-1)
+    q, he = 0.3, (0.2, -0.1, 0.5)
+    mo, ito, rro, sto = oracle.step_llg(m0, 3, grid, h, alpha, dt, q, he,
+                                        oracle.Params(rtol=1e-12, coarsest_cells=cc))
+    mg = _t(m0)
+    G = ll.Hierarchy(mg, alpha, dt, h, grid, ll.Params(rtol=1e-12, coarsest_cells=cc))
+    st, its, rrs = G.step_llg(mg, 3, q, he)
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert np.all(np.abs(np.array(its) - ito) <= 1)
+    assert np.abs(_np(mg) - mo).max() <= 1e-10
+
+
 def test_host_buffers_round_trip():
     grid, h, alpha, dt, kind, cc = CASES["2d"]
     m0 = _field(kind, grid).reshape(-1)
@@ -213,11 +228,15 @@ def test_statuses():
     assert st == ll.LL_BREAKDOWN
 
 
+@pytest.mark.parametrize("precision", [ll.LL_MIXED_FP32, ll.LL_MIXED_BF16])
 @pytest.mark.parametrize("name", ["2d", "3d", "odd"])
-def test_mixed_precision_path(name):
+def test_mixed_precision_path(name, precision):
+    """float32 V-cycle (coarse operators in float32 or bfloat16) inside the
+    float64 GCR: same true relative residual, solution within 1e-8 of the
+    float64 path."""
     grid, h, alpha, dt, m, O, G = _pair(name)
     Gm = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-10, coarsest_cells=CASES[name][5],
-                                                          precision=ll.LL_MIXED_FP32))
+                                                          precision=precision))
     b = m / dt
     x64 = torch.zeros(b.size, dtype=torch.float64, device=DEV)
     x32 = torch.zeros_like(x64)

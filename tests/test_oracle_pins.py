@@ -424,3 +424,53 @@ def test_first_order_convergence_in_time():
         errs.append(np.abs(m - ms.m(T).reshape(-1)).max())
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 1.7 < r1 < 2.3 and 1.7 < r2 < 2.3, errs
+
+
+# --------------------------------------------------------------------------
+# source terms of the full model (Sec. 2.1: anisotropy, external field)
+# --------------------------------------------------------------------------
+
+def _llg_rhs_uniform_step(m, dt, alpha, q, he):
+    """A uniform field has Delta_h m = 0, so one step is the explicit update
+    m - dt (m x f + alpha m x (m x f)), f = -q (0, m2, m3) + he, then the
+    projection (cross products written out with numpy, independently of the
+    oracle's 3x3 coefficient)."""
+    f = np.array([he[0], he[1] - q * m[1], he[2] - q * m[2]])
+    c1 = np.cross(m, f)
+    v = m - dt * (c1 + alpha * np.cross(m, c1))
+    return v / np.linalg.norm(v)
+
+
+def test_source_terms_on_a_uniform_field_match_the_explicit_update():
+    grid, h, alpha, dt, q, he = (6, 5, 4), 0.1, 0.3, 2e-2, 0.7, (0.2, -0.4, 0.5)
+    d = np.array([0.3, 0.5, -0.8])
+    d /= np.linalg.norm(d)
+    m = inputs.constant_field(*grid, direction=d).reshape(-1)
+    out, its, rrs, st = oracle.step_llg(m, 3, grid, h, alpha, dt, q, he, oracle.Params(rtol=1e-13))
+    assert st == oracle.OK
+    ref = d.copy()
+    for _ in range(3):
+        ref = _llg_rhs_uniform_step(ref, dt, alpha, q, he)
+    np.testing.assert_allclose(out.reshape(3, -1), np.repeat(ref[:, None], 120, axis=1), atol=1e-12)
+
+
+def test_damping_turns_the_field_towards_the_applied_field():
+    """With alpha > 0 the term -alpha m x (m x h_e) pulls m towards h_e:
+    the mean of m . h_e grows step by step."""
+    n = 16
+    m = inputs.smooth_field(n, n, 1, seed=6).reshape(-1)
+    he = np.array([0.0, 0.0, 40.0])
+    dots = []
+    for _ in range(4):
+        m, its, rrs, st = oracle.step_llg(m, 1, (n, n, 1), 1 / n, 0.5, 1e-3, 0.0, he, oracle.Params(rtol=1e-12))
+        assert st == oracle.OK
+        dots.append(float((m.reshape(3, -1).T @ he).mean()))
+    assert all(b > a for a, b in zip(dots, dots[1:])), dots
+
+
+def test_zero_sources_reduce_to_the_plain_step():
+    n = 12
+    m = inputs.vortex(n, n, 1, seed=1).reshape(-1)
+    a, _, _, _ = oracle.step_llg(m, 2, (n, n, 1), 1 / n, 0.1, 1e-3, 0.0, (0, 0, 0), oracle.Params(rtol=1e-12))
+    b, _, _, _ = oracle.step(m, 2, (n, n, 1), 1 / n, 0.1, 1e-3, oracle.Params(rtol=1e-12))
+    np.testing.assert_allclose(a, b, atol=1e-13)
