@@ -58,6 +58,7 @@ class _Params(ctypes.Structure):
         ("rounds", ctypes.c_int),
         ("seed", ctypes.c_uint32),
         ("prec", ctypes.c_int),
+        ("kcycle", ctypes.c_int),
     ]
 
 
@@ -67,6 +68,7 @@ class Params:
 
     prec: 0 = aggregation V-cycle, 1 = none (plain GCR), 2 = exact (dense LU
     of the whole operator, tiny grids only).
+    kcycle: coarse levels 1..kcycle are solved by two inner GCR steps (K-cycle).
     """
 
     rtol: float = 1e-8
@@ -79,11 +81,12 @@ class Params:
     rounds: int = 32
     seed: int = 0
     prec: int = 0
+    kcycle: int = 0
 
     def _c(self) -> _Params:
         return _Params(self.rtol, self.maxit, self.restart, self.nu_pre, self.nu_post,
                        self.coarsest_cells, self.max_levels, self.rounds, self.seed & 0xFFFFFFFF,
-                       self.prec)
+                       self.prec, self.kcycle)
 
 
 _lib = None
@@ -119,6 +122,7 @@ def _load():
         "orc_vcycle": (None, [vp, _dp, _dp]),
         "orc_vcycle_level": (None, [vp, i, _dp, _dp]),
         "orc_coarse_solve": (None, [vp, _dp]),
+        "orc_kinner": (None, [vp, i, _dp, _dp]),
         "orc_aggregate_graph": (i, [i, _ip, _ip, _ip, i, u32, _ip]),
         "orc_matching_pass": (i, [i, _ip, _ip, _ip, i, u32, i, _ip]),
         "orc_colour_graph": (i, [i, _ip, _ip, u32, _ip]),
@@ -230,6 +234,13 @@ class Hierarchy:
         z = np.zeros_like(r)
         _lib.orc_vcycle_level(self._h, l, r, z)
         return z
+
+    def kinner(self, r, l: int) -> np.ndarray:
+        """Two preconditioned GCR steps on level l from zero (K-cycle)."""
+        r = np.ascontiguousarray(r, np.float64).reshape(-1)
+        e = np.zeros_like(r)
+        _lib.orc_kinner(self._h, l, r, e)
+        return e
 
     def coarse_solve(self, b) -> np.ndarray:
         x = np.array(b, np.float64, copy=True).reshape(-1)

@@ -643,6 +643,7 @@ typedef struct {
   int maxit, restart, nu_pre, nu_post, coarsest_cells, max_levels, rounds;
   uint32_t seed;
   int prec; /* 0 = V-cycle, 1 = none (plain GCR), 2 = exact dense LU of A */
+  int kcycle; /* levels 1..kcycle (not the coarsest) are solved by two inner GCR steps */
 } orc_params;
 
 typedef struct {
@@ -810,8 +811,54 @@ static void gs_sweep(const level_t *L, const double *b, double *x, int forward) 
   }
 }
 
+static double dot(int n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static void vcycle(const orc_hier *H, int l, const double *b, double *x);
+
+/* K-cycle coarse solve (the Krylov acceleration of each level that Sec. 3.1
+ * describes for AGMG): two steps of preconditioned GCR (Algorithm 1 with
+ * modified Gram-Schmidt) on A_l e = r from e = 0, the cycle of level l as
+ * the preconditioner. */
+static void kinner(const orc_hier *H, int l, const double *r, double *e) {
+  const csr_t *A = &H->lev[l].A;
+  int nn = A->nrows;
+  double *z1 = (double *)xmalloc((size_t)nn * sizeof(double));
+  double *z2 = (double *)xmalloc((size_t)nn * sizeof(double));
+  double *c1 = (double *)xmalloc((size_t)nn * sizeof(double));
+  double *c2 = (double *)xmalloc((size_t)nn * sizeof(double));
+  double *r1 = (double *)xmalloc((size_t)nn * sizeof(double));
+  vcycle(H, l, r, z1);
+  csr_matvec(A, z1, c1);
+  double g11 = sqrt(dot(nn, c1, c1));
+  /* A direction whose image A z vanishes (only z = 0 for a regular A)
+   * contributes nothing and is dropped instead of normalised. */
+  for (int i = 0; i < nn; ++i) c1[i] = g11 > 0 ? c1[i] / g11 : 0.0;
+  double a1 = dot(nn, c1, r);
+  for (int i = 0; i < nn; ++i) r1[i] = r[i] - a1 * c1[i];
+  vcycle(H, l, r1, z2);
+  csr_matvec(A, z2, c2);
+  double g12 = dot(nn, c1, c2);
+  for (int i = 0; i < nn; ++i) c2[i] -= g12 * c1[i];
+  double g22 = sqrt(dot(nn, c2, c2));
+  for (int i = 0; i < nn; ++i) c2[i] = g22 > 0 ? c2[i] / g22 : 0.0;
+  double a2 = dot(nn, c2, r1);
+  double y2 = g22 > 0 ? a2 / g22 : 0.0, y1 = g11 > 0 ? (a1 - g12 * y2) / g11 : 0.0;
+  for (int i = 0; i < nn; ++i) e[i] = y1 * z1[i] + y2 * z2[i];
+  free(z1);
+  free(z2);
+  free(c1);
+  free(c2);
+  free(r1);
+}
+
 /* V-cycle on level l for A_l x = b, starting from x = 0 (Sec. 3: smoother
- * plus coarse-grid correction, applied recursively down to an exact solve). */
+ * plus coarse-grid correction, applied recursively down to an exact solve).
+ * With prm.kcycle > 0 the coarse problem of levels 1..kcycle is solved by
+ * kinner instead (a K-cycle). */
 static void vcycle(const orc_hier *H, int l, const double *b, double *x) {
   const level_t *L = &H->lev[l];
   int nn = 3 * L->n;
@@ -829,7 +876,8 @@ static void vcycle(const orc_hier *H, int l, const double *b, double *x) {
   double *bc = (double *)xmalloc((size_t)nc * sizeof(double));
   double *xc = (double *)xmalloc((size_t)nc * sizeof(double));
   csr_matvec(&L->Pt, r, bc); /* restriction = P^T */
-  vcycle(H, l + 1, bc, xc);
+  if (l + 1 < H->nlev - 1 && l + 1 <= H->prm.kcycle) kinner(H, l + 1, bc, xc);
+  else vcycle(H, l + 1, bc, xc);
   csr_matvec(&L->P, xc, r); /* prolongation */
   for (int i = 0; i < nn; ++i) x[i] += r[i];
   for (int s = 0; s < H->prm.nu_post; ++s) gs_sweep(L, b, x, 0);
@@ -854,11 +902,6 @@ static void precondition(const orc_hier *H, const double *r, double *z) {
 /* preconditioned GCR, Algorithm 1                                            */
 /* ------------------------------------------------------------------------ */
 
-static double dot(int n, const double *a, const double *b) {
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += a[i] * b[i];
-  return s;
-}
 
 /* Status codes shared in meaning with the library's header. */
 enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2 };
@@ -1078,6 +1121,7 @@ void orc_smooth(const orc_hier *H, int l, const double *b, double *x, int forwar
 }
 void orc_vcycle(const orc_hier *H, const double *r, double *z) { vcycle(H, 0, r, z); }
 void orc_vcycle_level(const orc_hier *H, int l, const double *r, double *z) { vcycle(H, l, r, z); }
+void orc_kinner(const orc_hier *H, int l, const double *r, double *e) { kinner(H, l, r, e); }
 void orc_coarse_solve(const orc_hier *H, double *x) {
   lu_solve(3 * H->lev[H->nlev - 1].n, H->lu, H->piv, x);
 }

@@ -474,3 +474,54 @@ def test_zero_sources_reduce_to_the_plain_step():
     a, _, _, _ = oracle.step_llg(m, 2, (n, n, 1), 1 / n, 0.1, 1e-3, 0.0, (0, 0, 0), oracle.Params(rtol=1e-12))
     b, _, _, _ = oracle.step(m, 2, (n, n, 1), 1 / n, 0.1, 1e-3, oracle.Params(rtol=1e-12))
     np.testing.assert_allclose(a, b, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# K-cycle (Krylov acceleration of the coarse levels, Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def test_kcycle_inner_steps_minimise_the_residual():
+    """Two GCR steps return the e in span{z1, z2} (z1 = B r, z2 = B r1) that
+    minimises |r - A e|: checked by an independent least-squares solve."""
+    grid = (20, 18, 1)
+    m = inputs.vortex(*grid, seed=2).reshape(-1)
+    H = oracle.Hierarchy(grid, 1 / 20, 0.1, 2e-3, m, oracle.Params(coarsest_cells=8, kcycle=1))
+    assert H.nlevels >= 3
+    A = H.matrix(1)
+    r = np.random.default_rng(4).standard_normal(A.shape[0])
+    e = H.kinner(r, 1)
+    z1 = H.vcycle(r, l=1)
+    Az1 = A @ z1
+    a1 = (Az1 @ r) / (Az1 @ Az1)
+    r1 = r - a1 * Az1
+    z2 = H.vcycle(r1, l=1)
+    Z = np.column_stack([z1, z2])
+    y, *_ = np.linalg.lstsq(A @ Z, r, rcond=None)
+    np.testing.assert_allclose(e, Z @ y, rtol=0, atol=1e-10 * np.abs(Z @ y).max())
+
+
+@pytest.mark.parametrize("kcycle", [1, 3])
+def test_kcycle_solve_matches_dct_closed_form(kcycle):
+    grid, mdir, alpha = (24, 20, 12), (0.3, -0.4, 0.8), 0.05
+    nx, ny, nz = grid
+    h, dt = 1.0 / nx, 6.0 / nx ** 2
+    m = inputs.constant_field(*grid, mdir).reshape(-1)
+    b = inputs.rhs_field(*grid, seed=7).reshape(-1)
+    H = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-13, coarsest_cells=8, kcycle=kcycle))
+    x, st, it, rr = H.solve(b)
+    assert st == oracle.OK
+    xe = rf.dct_solve(nx, ny, nz, h, alpha, dt, mdir, b)
+    assert np.linalg.norm(x - xe) <= 1e-10 * np.linalg.norm(xe)
+
+
+def test_kcycle_reduces_iterations():
+    grid = (24, 24, 24)
+    m = inputs.vortex(*grid, seed=0).reshape(-1)
+    dt = 8.19 / 24 ** 2
+    its = []
+    for k in (0, 2):
+        H = oracle.Hierarchy(grid, 1 / 24, 0.02, dt, m, oracle.Params(kcycle=k))
+        _, st, it, _ = H.solve(m / dt, m)
+        assert st == oracle.OK
+        its.append(it)
+    assert its[1] < its[0], its
