@@ -215,12 +215,13 @@ def run_ours(args):
     if precision != ll.LL_FP64:  # one step both ways from the same state
         ma, mb = m.clone(), m.clone()
         ll.Hierarchy(ma, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL)).step(ma, 1)
-        ll.Hierarchy(mb, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision)).step(mb, 1)
+        ll.Hierarchy(mb, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision,
+                                                               kcycle=args.kcycle)).step(mb, 1)
         error_vs_fp64 = float(torch.linalg.norm(mb - ma) / torch.linalg.norm(ma))
         del ma, mb
         torch.cuda.empty_cache()
     t0 = time.perf_counter()
-    H = ll.Hierarchy(m, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision))
+    H = ll.Hierarchy(m, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision, kcycle=args.kcycle))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     lib = ll.load_library()
@@ -297,7 +298,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(GRID), "h": H_SPACING, "alpha": ALPHA, "dt": DT,
-                   "rtol": RTOL, "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "rtol": RTOL, "precision": args.precision, "kcycle": args.kcycle, "parallelism": "replicas" if world > 1 else "single",
                    "levels": H.levels, "l2": "working set per step (~3 GB: GCR bases, operators) exceeds the 126 MB L2"},
         "iterations_per_step": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},
         "max_relres": float(max(rrs)),
@@ -332,6 +333,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed", "bf16"], default="fp64")
+    ap.add_argument("--kcycle", type=int, default=0,
+                    help="coarse levels 1..K solved by two inner GCR steps (K-cycle); 0 = V-cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

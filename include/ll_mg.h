@@ -75,6 +75,8 @@ typedef struct ll_mg_params {
   int rounds;          /* handshake rounds per matching pass          (32)   */
   unsigned int seed;   /* tie-break hash seed of matching, colouring  (0)    */
   int precision;       /* LL_FP64, LL_MIXED_FP32 or LL_MIXED_BF16     (LL_FP64) */
+  int kcycle;          /* coarse levels 1..kcycle are solved by two inner
+                          GCR steps (K-cycle, Sec. 3.1); 0: V-cycle   (0)    */
 } ll_mg_params;
 
 typedef struct ll_mg_hierarchy ll_mg_hierarchy; /* opaque, library-owned */

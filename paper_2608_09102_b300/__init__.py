@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
         ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
         ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("coarsest_cells", ctypes.c_int),
         ("max_levels", ctypes.c_int), ("rounds", ctypes.c_int), ("seed", ctypes.c_uint),
-        ("precision", ctypes.c_int),
+        ("precision", ctypes.c_int), ("kcycle", ctypes.c_int),
     ]
 
 
@@ -66,10 +66,11 @@ class Params:
     rounds: int = 32
     seed: int = 0
     precision: int = LL_FP64
+    kcycle: int = 0
 
     def _c(self) -> _Params:
         return _Params(self.rtol, self.maxit, self.restart, self.nu_pre, self.nu_post, self.coarsest_cells,
-                       self.max_levels, self.rounds, self.seed & 0xFFFFFFFF, self.precision)
+                       self.max_levels, self.rounds, self.seed & 0xFFFFFFFF, self.precision, self.kcycle)
 
 
 _lib = None
@@ -127,7 +128,7 @@ def default_params() -> Params:
     c = _Params()
     load_library().ll_mg_default_params(ctypes.byref(c))
     return Params(c.rtol, c.maxit, c.restart, c.nu_pre, c.nu_post, c.coarsest_cells, c.max_levels, c.rounds,
-                  c.seed, c.precision)
+                  c.seed, c.precision, c.kcycle)
 
 
 def _grid(grid) -> _Grid:

@@ -747,6 +747,63 @@ __global__ void k_finish(const double* __restrict__ partial, double* __restrict_
   if (threadIdx.x == 0) out[q] = sh[0];
 }
 
+// ---------------------------------------------------------------------------
+// K-cycle: two inner GCR steps on a coarse level (scalars on the device)
+// ---------------------------------------------------------------------------
+// y = A x, G lanes per row
+template <typename T, typename TM, int G>
+__global__ void __launch_bounds__(256) kb_spmv(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                               const TM* __restrict__ val, const T* __restrict__ x,
+                                               T* __restrict__ y) {
+  long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int I = (int)(gt / G);
+  int lane = threadIdx.x % G;
+  bool active = I < n;
+  T a0 = 0, a1 = 0, a2 = 0;
+  if (active)
+    row_msub<T, TM, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
+  group_sum3<G>(a0, a1, a2);
+  if (active)
+    for (int c = lane; c < 3; c += G) y[3L * I + c] = -(c == 0 ? a0 : c == 1 ? a1 : a2);
+}
+
+// partial dots u_q . v_q (q < NQ) of coarse vectors, accumulated in float64
+template <typename T, int NQ>
+__global__ void __launch_bounds__(256) kd_dots(long n, const T* __restrict__ u0, const T* __restrict__ v0,
+                                               const T* __restrict__ u1, const T* __restrict__ v1,
+                                               double* __restrict__ partial) {
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    acc[0] += (double)u0[i] * (double)v0[i];
+    if (NQ > 1) acc[NQ - 1] += (double)u1[i] * (double)v1[i];
+  }
+  block_reduce_store<NQ>(acc, partial, NQ);
+}
+
+// y = u - (ks[num] / ks[den]) v   (ks: the level's device scalars); a zero
+// denominator means v = 0 and the coefficient is taken as 0
+template <typename T>
+__global__ void kk_axpy(long n, const T* u, const T* __restrict__ v, const double* __restrict__ ks,
+                        int num, int den, T* y) {  // y may alias u
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  double d = ks[den];
+  if (i < n) y[i] = u[i] - (T)(d > 0 ? ks[num] / d : 0.0) * v[i];
+}
+
+// x = y1 z1 + y2 x with y2 = d2r/d22, y1 = (d1r - d12 y2)/d11:
+// the minimiser of |r - A e| over span{z1, z2} (back substitution of the
+// 2x2 Gram-Schmidt triangle); ks = {d11, d1r, d12, d22, d2r}
+template <typename T>
+__global__ void kk_combine(long n, const T* __restrict__ z1, T* __restrict__ x, const double* __restrict__ ks) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double y2 = ks[3] > 0 ? ks[4] / ks[3] : 0.0;  // a direction with zero image is dropped
+  double y1 = ks[0] > 0 ? (ks[1] - ks[2] * y2) / ks[0] : 0.0;
+  x[i] = (T)(y1 * (double)z1[i] + y2 * (double)x[i]);
+}
+
 // y = A x (float64); pads stay zero.  TX = storage type of x.
 template <typename TX>
 __global__ void __launch_bounds__(256) kg_apply(GridGeom g, const TX* __restrict__ x, const double* __restrict__ chat,

@@ -43,6 +43,9 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   DBuf<__nv_bfloat16> val16;        // bfloat16 storage of the operator (LL_MIXED_BF16)
   DBuf<double> x64, b64, r64;
   DBuf<float> x32, b32, r32;
+  DBuf<double> k64[4];  // K-cycle vectors: r, z1, c1, c2
+  DBuf<float> k32[4];
+  template <typename T> T* kv(int i);
   template <typename T> T* val();
   template <typename TM> TM* valm();  // operator values in storage type TM
   template <typename T> T* dinv();
@@ -61,6 +64,8 @@ template <> double* CLevel::x<double>() { return x64; }
 template <> float* CLevel::x<float>() { return x32; }
 template <> double* CLevel::b<double>() { return b64; }
 template <> float* CLevel::b<float>() { return b32; }
+template <> double* CLevel::kv<double>(int i) { return k64[i]; }
+template <> float* CLevel::kv<float>(int i) { return k32[i]; }
 template <> double* CLevel::r<double>() { return r64; }
 template <> float* CLevel::r<float>() { return r32; }
 
@@ -91,6 +96,7 @@ struct ll_mg_hierarchy {
   DBuf<double> Z64, C, r, xw, bw, partial;
   DBuf<float> Z32;
   DBuf<GcrScal> scal;
+  DBuf<double> kscal;  // K-cycle scalars, 8 per level
   double* h_head = nullptr;  // pinned copy of the first scalars
   // time-step workspace (natural layout)
   DBuf<double> stepb, stepx;
@@ -336,6 +342,12 @@ void allocate(ll_mg_hierarchy* H) {
       C.r64.alloc(3L * C.n);
     }
   }
+  for (int l = 1; l < H->nlev - 1 && l <= H->prm.kcycle; ++l)
+    for (int q = 0; q < 4; ++q) {
+      if (mixed) H->lev[l].k32[q].alloc(3L * H->lev[l].n);
+      else H->lev[l].k64[q].alloc(3L * H->lev[l].n);
+    }
+  H->kscal.alloc(8 * kMaxLevels);
   int nc = H->nlev == 1 ? (int)H->g.n : H->lev[H->nlev - 1].n;
   H->ncoarse3 = 3 * nc;
   H->lu.alloc((size_t)H->ncoarse3 * H->ncoarse3);
@@ -487,7 +499,11 @@ void setup_tail(ll_mg_hierarchy* H) {
       H->tail_first = l;
       break;
     }
-  if (H->tail_first < 0) return;
+  if (H->tail_first >= 0 && H->tail_first <= H->prm.kcycle) H->tail_first = H->prm.kcycle + 1;  // K levels stay out
+  if (H->tail_first < 0 || H->tail_first >= H->nlev) {
+    H->tail_first = -1;
+    return;
+  }
   for (int l = H->tail_first; l < H->nlev; ++l)
     if (H->lev[l].ncol > kTailMaxColours) {
       H->tail_first = -1;
@@ -657,7 +673,67 @@ void smooth_level(ll_mg_hierarchy* H, int l, bool forward) {
 // when pre-smoothing is on, x_l already holds the colour-0 rows of the first
 // forward sweep (written by the restriction into this level).
 template <typename T, typename TM>
-void vcycle_coarse(ll_mg_hierarchy* H, int l) {
+void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done = true);
+
+// The coarse problem of level l (a K level): two GCR steps from zero,
+// preconditioned by the cycle of level l (the same formulas as the oracle's
+// K-cycle).  On entry L.b holds the restricted residual r and x holds the
+// first colour of the first forward sweep; on exit L.x is the correction.
+template <typename T, typename TM>
+void kinner(ll_mg_hierarchy* H, int l) {
+  CLevel& L = H->lev[l];
+  cudaStream_t s = H->s;
+  long n3 = 3L * L.n;
+  int nb = cdiv(n3, kBlock), nbs = cdiv((long)L.n * lanes<T>(), kCoarseBlock);
+  double* ks = H->kscal.p + 8 * l;
+  T *kr = L.kv<T>(0), *kz1 = L.kv<T>(1), *kc1 = L.kv<T>(2), *kc2 = L.kv<T>(3);
+  double kflops = 18.0 * L.nnzb + 8.0 * n3, kbytes = (double)L.nnzb * (9 * sizeof(TM) + 4 + 3 * sizeof(T)) + 4.0 * n3 * sizeof(T);
+  {
+    LL_PROFW(LL_KIND_BSR_OTHER, 0.0, 2.0 * n3 * sizeof(T));
+    LL_CU(cudaMemcpyAsync(kr, L.b<T>(), n3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+  vcycle_coarse<T, TM>(H, l, true);  // z1 = B r
+  {  // c1 = A z1; d11 = c1.c1, d1r = c1.r; r1 = r - (d1r/d11) c1 (into L.b)
+    LL_PROFW(LL_KIND_BSR_OTHER, kflops, kbytes);
+    LL_CU(cudaMemcpyAsync(kz1, L.x<T>(), n3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    kb_spmv<T, TM, lanes<T>()><<<nbs, kCoarseBlock, 0, s>>>(L.n, L.rowptr, L.col, L.valm<TM>(), kz1, kc1);
+    LL_LAUNCHED();
+    kd_dots<T, 2><<<kRedBlocks, kBlock, 0, s>>>(n3, kc1, kc1, kc1, kr, H->partial);
+    LL_LAUNCHED();
+    k_finish<<<2, kBlock, 0, s>>>(H->partial, ks);
+    LL_LAUNCHED();
+    kk_axpy<T><<<nb, kBlock, 0, s>>>(n3, kr, kc1, ks, 1, 0, L.b<T>());
+    LL_LAUNCHED();
+  }
+  vcycle_coarse<T, TM>(H, l, false);  // z2 = B r1 (in L.x)
+  {  // c2 = A z2 - (d12/d11) c1; d22 = c2.c2, d2r = c2.r1; x = y1 z1 + y2 z2
+    LL_PROFW(LL_KIND_BSR_OTHER, kflops + 4.0 * n3, kbytes + 3.0 * n3 * sizeof(T));
+    kb_spmv<T, TM, lanes<T>()><<<nbs, kCoarseBlock, 0, s>>>(L.n, L.rowptr, L.col, L.valm<TM>(), L.x<T>(), kc2);
+    LL_LAUNCHED();
+    kd_dots<T, 1><<<kRedBlocks, kBlock, 0, s>>>(n3, kc1, kc2, nullptr, nullptr, H->partial);
+    LL_LAUNCHED();
+    k_finish<<<1, kBlock, 0, s>>>(H->partial, ks + 2);
+    LL_LAUNCHED();
+    kk_axpy<T><<<nb, kBlock, 0, s>>>(n3, kc2, kc1, ks, 2, 0, kc2);
+    LL_LAUNCHED();
+    kd_dots<T, 2><<<kRedBlocks, kBlock, 0, s>>>(n3, kc2, kc2, kc2, L.b<T>(), H->partial);
+    LL_LAUNCHED();
+    k_finish<<<2, kBlock, 0, s>>>(H->partial, ks + 3);
+    LL_LAUNCHED();
+    kk_combine<T><<<nb, kBlock, 0, s>>>(n3, kz1, L.x<T>(), ks);
+    LL_LAUNCHED();
+  }
+}
+
+// the coarse problem of level l: a K level's two inner steps, or one cycle
+template <typename T, typename TM>
+void coarse_problem(ll_mg_hierarchy* H, int l) {
+  if (l <= H->prm.kcycle && l < H->nlev - 1) kinner<T, TM>(H, l);
+  else vcycle_coarse<T, TM>(H, l, true);
+}
+
+template <typename T, typename TM>
+void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
   CLevel& L = H->lev[l];
   cudaStream_t s = H->s;
   if (l == H->tail_first) {
@@ -677,7 +753,7 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
     LL_LAUNCHED();
   }
   for (int sweep = 0; sweep < nu_pre; ++sweep)
-    for (int t = sweep == 0 ? 1 : 0; t < K; ++t) {
+    for (int t = (sweep == 0 && init0_done) ? 1 : 0; t < K; ++t) {
       if (sweep == 0) sweep_class<T, TM, 0>(H, l, t, nullptr);
       else sweep_class<T, TM, 1>(H, l, t, nullptr);
     }
@@ -696,7 +772,7 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l) {
                                                         init_end, N.dinv<T>(), N.x<T>());
     LL_LAUNCHED();
   }
-  vcycle_coarse<T, TM>(H, l + 1);
+  coarse_problem<T, TM>(H, l + 1);
   if (nu_post == 0) {
     LL_PROF(LL_KIND_BSR_OTHER);
     kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
@@ -762,7 +838,7 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
     k0_restrict_b<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, L1.n, L1.mptr, L1.mem, L1.b<T>());
     LL_LAUNCHED();
   }
-  vcycle_coarse<T, TM>(H, 1);
+  coarse_problem<T, TM>(H, 1);
   if (H->prm.nu_post >= 1) {
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 66.0 * H->l0_cells[1], (24 + 24.75 * (double)sizeof(T)) * H->l0_cells[1]);
@@ -1015,7 +1091,8 @@ bool valid_params(const ll_mg_params& p) {
   return p.rtol >= 0 && p.maxit >= 0 && p.restart >= 1 && p.restart <= kMaxRestart && p.nu_pre >= 0 &&
          p.nu_pre <= 16 && p.nu_post >= 0 && p.nu_post <= 16 && p.coarsest_cells >= 1 && p.max_levels >= 1 &&
          p.max_levels <= kMaxLevels && p.rounds >= 1 &&
-         (p.precision == LL_FP64 || p.precision == LL_MIXED_FP32 || p.precision == LL_MIXED_BF16);
+         (p.precision == LL_FP64 || p.precision == LL_MIXED_FP32 || p.precision == LL_MIXED_BF16) &&
+         p.kcycle >= 0 && p.kcycle <= kMaxLevels;
 }
 
 int create(const double* m, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p, void* stream,
@@ -1078,6 +1155,7 @@ void ll_mg_default_params(ll_mg_params* p) {
   p->rounds = 32;
   p->seed = 0;
   p->precision = LL_FP64;
+  p->kcycle = 0;
 }
 
 static bool valid_problem(double alpha, double dt, double h, ll_grid grid) {

@@ -70,6 +70,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.ll_mg_setup(dummy, 0.1, 1e-3, 0.1, g, ctypes.byref(bad), None, ctypes.byref(out)) == ll.LL_EINVAL
     bad = ll.Params(precision=7)._c()
     assert lib.ll_mg_setup(dummy, 0.1, 1e-3, 0.1, g, ctypes.byref(bad), None, ctypes.byref(out)) == ll.LL_EINVAL
+    bad = ll.Params(kcycle=-1)._c()
+    assert lib.ll_mg_setup(dummy, 0.1, 1e-3, 0.1, g, ctypes.byref(bad), None, ctypes.byref(out)) == ll.LL_EINVAL
     assert lib.ll_mg_solve(None, dummy, dummy, 0.0, None, None) == ll.LL_EINVAL
     assert lib.ll_step(None, 1, 0.1, 1e-3, 0.1, g, None, None, None, None) == ll.LL_EINVAL
     assert lib.ll_mg_levels(None) == -1

@@ -246,6 +246,69 @@ def test_mixed_precision_path(name, precision):
     assert float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64)) <= 1e-8
 
 
+def _kpair(name, kcycle, precision=ll.LL_FP64, rtol=1e-12):
+    grid, h, alpha, dt, kind, cc = CASES[name]
+    m = _field(kind, grid).reshape(-1)
+    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=rtol, coarsest_cells=cc, kcycle=kcycle))
+    G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=rtol, coarsest_cells=cc, kcycle=kcycle,
+                                                          precision=precision))
+    return grid, h, alpha, dt, m, O, G
+
+
+@pytest.mark.parametrize("kcycle", [1, 2, 20])
+@pytest.mark.parametrize("name", ["2d", "3d", "odd", "cube"])
+def test_kcycle_preconditioner(name, kcycle):
+    """The K-cycle preconditioner (two inner GCR steps on levels 1..kcycle)
+    applied to one residual: same vector as the oracle's to 1e-11."""
+    grid, h, alpha, dt, m, O, G = _kpair(name, kcycle)
+    r = inputs.rhs_field(*grid, seed=8).reshape(-1)
+    z = torch.empty_like(_t(r))
+    for _ in range(2):  # the second call reuses the level scalars
+        G.vcycle(_t(r), z)
+    ref = O.vcycle(r)
+    assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("kcycle", [1, 20])
+@pytest.mark.parametrize("name", ["2d", "3d", "odd"])
+def test_kcycle_solve_matches_oracle(name, kcycle):
+    grid, h, alpha, dt, m, O, G = _kpair(name, kcycle)
+    b = m / dt
+    xo, sto, ito, rro = O.solve(b, np.zeros_like(b))
+    x = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(b), x)
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert rr < 1e-12
+    assert abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(_np(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("precision", [ll.LL_MIXED_FP32, ll.LL_MIXED_BF16])
+def test_kcycle_mixed_precision(precision):
+    grid, h, alpha, dt, m, O, G = _kpair("3d", 2)
+    Gm = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-10, coarsest_cells=CASES["3d"][5], kcycle=2,
+                                                          precision=precision))
+    b = m / dt
+    x64 = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    x32 = torch.zeros_like(x64)
+    G.solve(_t(b), x64, 1e-12)
+    st, it, rr = Gm.solve(_t(b), x32)
+    assert st == ll.LL_OK and rr < 1e-10
+    assert float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64)) <= 1e-8
+
+
+def test_kcycle_steps_match_oracle():
+    grid, h, alpha, dt, kind, cc = CASES["3d"]
+    m0 = _field(kind, grid).reshape(-1)
+    mo, ito, rro, sto = oracle.step(m0, 3, grid, h, alpha, dt, oracle.Params(rtol=1e-12, coarsest_cells=cc,
+                                                                              kcycle=1))
+    mg = _t(m0)
+    st, its, rrs = ll.step(mg, 3, alpha, dt, h, grid, ll.Params(rtol=1e-12, coarsest_cells=cc, kcycle=1))
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert np.all(np.abs(np.array(its) - ito) <= 1)
+    assert np.abs(_np(mg) - mo).max() <= 1e-10
+
+
 def test_config1_against_sparse_direct_solve():
     """2-D 64x64, alpha 0.1, dt 1e-3, smooth field: the solution equals the
     sparse direct solution within 1e-10."""
