@@ -34,6 +34,7 @@ constexpr int kRedBlocks = 592;   // 4 x 148 SMs: fixed grid of reduction kernel
 constexpr int kMaxRestart = 64;
 constexpr int kMaxColours = 128;
 constexpr int kMaxLevels = 32;
+constexpr int kRowLanes = 4;  // lanes per block row in the coarse-level kernels
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 

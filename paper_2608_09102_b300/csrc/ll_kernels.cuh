@@ -576,6 +576,46 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
   }
 }
 
+// a -= sum over the off-diagonal blocks of row [p0, p1) with diagonal pd, in
+// one lane-strided loop over the row's off-diagonal slots q (prefix then
+// suffix, the diagonal skipped): a row visits ceil((p1 - p0 - 1) / G) slots
+// instead of separate prefix and suffix loops.  PROL adds e[agg[J]] to the
+// prefix columns only.
+template <typename T, typename TM, int G, int U, bool PROL>
+__device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, const int* __restrict__ col,
+                                             const TM* __restrict__ val, const T* __restrict__ x,
+                                             const int* __restrict__ agg, const T* __restrict__ e, T& a0, T& a1,
+                                             T& a2) {
+  int npre = pd - p0, noff = p1 - p0 - 1;
+  for (int base = lane; base < noff; base += G * U) {
+    int J[U], P[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int q = base + u * G;
+      P[u] = p0 + q + (q >= npre ? 1 : 0);
+      J[u] = q < noff ? col[P[u]] : -1;
+    }
+    T v[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (J[u] >= 0) {
+        v[u][0] = x[3L * J[u]];
+        v[u][1] = x[3L * J[u] + 1];
+        v[u][2] = x[3L * J[u] + 2];
+        if (PROL && base + u * G < npre) {
+          long a = 3L * agg[J[u]];
+          v[u][0] += e[a];
+          v[u][1] += e[a + 1];
+          v[u][2] += e[a + 2];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (J[u] >= 0) block_msub<T, TM>(val + 9L * P[u], v[u][0], v[u][1], v[u][2], a0, a1, a2);
+  }
+}
+
 // Block Gauss-Seidel update of one row of a colour class, G lanes per row.
 // Coarse levels are renumbered so that each colour class is the contiguous
 // row range [r0, r1), colours ascending, and every row's blocks are sorted by
@@ -598,8 +638,8 @@ __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const in
   T a0 = 0, a1 = 0, a2 = 0;
   if (active) {
     int pd = diag[I];
-    row_msub<T, TM, G, 4, MODE == 2>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-    if (MODE != 0) row_msub<T, TM, G, 4, false>(pd + 1 + lane, rowptr[I + 1], col, val, x, agg, e, a0, a1, a2);
+    if (MODE == 0) row_msub<T, TM, G, 4, false>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
+    else row_msub_off<T, TM, G, 4, MODE == 2>(rowptr[I], pd, rowptr[I + 1], lane, col, val, x, agg, e, a0, a1, a2);
   }
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
   if (active) {

@@ -525,32 +525,76 @@ int colour_graph(const DevGraph& g, uint32_t seed, int* colour, cudaStream_t s) 
   return mx + 1;
 }
 
-__global__ void k_eq_flag(int n, const int* __restrict__ v, int c, int* __restrict__ flag) {
+// Row-work key of a coarse row: the number of kRowLanes-wide block slots its
+// forward sweep visits (neighbours of lower colour) and its backward sweep
+// visits (all neighbours), 16 x ceil(pre / lanes) + ceil(deg / lanes), each
+// capped at 15.  Rows of one colour class are ordered by this key, so the
+// rows that share a warp in the sweeps need the same number of slots and few
+// float64 lanes idle.
+__global__ void k_row_work_keys(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const int* __restrict__ colour, int* __restrict__ key) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) flag[i] = v[i] == c ? 1 : 0;
-}
-__global__ void k_scatter_class(int n, const int* __restrict__ v, int c, const int* __restrict__ pos, int base,
-                                int* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && v[i] == c) out[base + pos[i]] = i;
+  if (i >= n) return;
+  int pre = 0, deg = rp[i + 1] - rp[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) pre += colour[ci[p]] < colour[i];
+  int sp = min((pre + kRowLanes - 1) / kRowLanes, 15), sd = min((deg + kRowLanes - 1) / kRowLanes, 15);
+  key[i] = 16 * sp + sd;
 }
 
-// rows of each colour, ascending: crow[cptr[c] .. cptr[c+1])
-void colour_classes(int n, const int* colour, int ncol, DBuf<int>& cptr, DBuf<int>& crow, std::vector<int>& h_cptr,
-                    cudaStream_t s) {
-  DBuf<int> flag, pos;
+void row_work_keys(const DevGraph& g, const int* colour, DBuf<int>& key, cudaStream_t s) {
+  key.alloc(g.n);
+  k_row_work_keys<<<cdiv(g.n, kBlock), kBlock, 0, s>>>(g.n, g.rowptr, g.col, colour, key);
+  LL_LAUNCHED();
+}
+
+__global__ void k_class_hist(int n, const int* __restrict__ colour, const int* __restrict__ key, int nkeys,
+                             int* __restrict__ hist) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&hist[colour[i] * nkeys + key[i]], 1);  // counts only: order-independent
+}
+__global__ void k_eq_flag(int n, const int* __restrict__ v, int c, const int* __restrict__ key, int k,
+                          int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = (v[i] == c && key[i] == k) ? 1 : 0;
+}
+__global__ void k_scatter_class(int n, const int* __restrict__ flag, const int* __restrict__ pos, int base,
+                                int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[base + pos[i]] = i;
+}
+
+// rows of each colour, crow[cptr[c] .. cptr[c+1]), ordered by (key, index):
+// a stable, deterministic bucket order built from one scan per non-empty
+// (colour, key) bucket
+void colour_classes(int n, const int* colour, int ncol, const int* key, int nkeys, DBuf<int>& cptr, DBuf<int>& crow,
+                    std::vector<int>& h_cptr, cudaStream_t s) {
+  DBuf<int> flag, pos, hist;
   flag.alloc(n);
   pos.alloc(n + 1);
   crow.alloc(n);
-  h_cptr.assign(ncol + 1, 0);
+  hist.alloc((long)ncol * nkeys);
+  LL_CU(cudaMemsetAsync(hist.p, 0, (size_t)ncol * nkeys * sizeof(int), s));
   int nb = cdiv(n, kBlock);
+  k_class_hist<<<nb, kBlock, 0, s>>>(n, colour, key, nkeys, hist);
+  LL_LAUNCHED();
+  std::vector<int> h_hist((size_t)ncol * nkeys);
+  LL_CU(cudaMemcpyAsync(h_hist.data(), hist.p, h_hist.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  LL_CU(cudaStreamSynchronize(s));
+  h_cptr.assign(ncol + 1, 0);
+  int base = 0;
   for (int c = 0; c < ncol; ++c) {
-    k_eq_flag<<<nb, kBlock, 0, s>>>(n, colour, c, flag);
-    LL_LAUNCHED();
-    int cnt = exclusive_scan(flag, pos, n, s);
-    k_scatter_class<<<nb, kBlock, 0, s>>>(n, colour, c, pos, h_cptr[c], crow);
-    LL_LAUNCHED();
-    h_cptr[c + 1] = h_cptr[c] + cnt;
+    for (int k = 0; k < nkeys; ++k) {
+      int cnt = h_hist[(size_t)c * nkeys + k];
+      if (cnt == 0) continue;
+      k_eq_flag<<<nb, kBlock, 0, s>>>(n, colour, c, key, k, flag);
+      LL_LAUNCHED();
+      int got = exclusive_scan(flag, pos, n, s);
+      if (got != cnt) throw Status{LL_ECUDA};
+      k_scatter_class<<<nb, kBlock, 0, s>>>(n, flag, pos, base, crow);
+      LL_LAUNCHED();
+      base += cnt;
+    }
+    h_cptr[c + 1] = base;
   }
   LL_CU(cudaStreamSynchronize(s));
   cptr.alloc(ncol + 1);

@@ -218,8 +218,8 @@ void enter(ll_mg_hierarchy* H) {
 
 // lanes per block row in the BSR kernels
 template <typename T> constexpr int lanes();
-template <> constexpr int lanes<double>() { return 4; }
-template <> constexpr int lanes<float>() { return 4; }
+template <> constexpr int lanes<double>() { return kRowLanes; }
+template <> constexpr int lanes<float>() { return kRowLanes; }
 constexpr int kDotChunk = 8;
 // Coarse-level kernels use small blocks: a colour class of a small level then
 // spreads over many SMs instead of queueing on the float64 units of one.
@@ -266,8 +266,9 @@ void symbolic(ll_mg_hierarchy* H) {
     C.ncol = colour_graph(C.graph, p.seed, C.colour, s);
     if (C.ncol < 0) throw Status{LL_ELIMIT};
     {
-      DBuf<int> cptr;
-      colour_classes(nc, C.colour, C.ncol, cptr, C.n2o, C.cs, s);
+      DBuf<int> cptr, key;
+      row_work_keys(C.graph, C.colour, key, s);
+      colour_classes(nc, C.colour, C.ncol, key, kRowKeys, cptr, C.n2o, C.cs, s);
     }
     C.o2n.alloc(nc);
     invert_perm(nc, C.n2o, C.o2n, s);
