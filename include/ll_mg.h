@@ -243,6 +243,54 @@ int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forw
 int ll_residual_noalloc(const double* m_tilde, double alpha, double dt, double h, ll_grid grid,
                         const double* rhs, const double* x, double* r, double* norms2, void* cuda_stream);
 
+/* ---- batches of independent instances -------------------------------------
+ * Many independent problems (each its own grid, alpha, dt and h; the
+ * parameter-study and ensemble setting) solved together.  Each instance gets
+ * the hierarchy ll_mg_setup would build for it (same aggregates, colours and
+ * Galerkin operators, Sec. 3); the batch concatenates them level by level so
+ * that each smoothing step, residual, transfer and coarsest solve of the
+ * V-cycle is one launch for all instances, and runs GCR (Algorithm 1) in
+ * lockstep with separate scalars, stopping tests and restarts per instance.
+ * The paper solves one problem at a time; its results per instance are
+ * unchanged up to rounding.
+ *   count     number of instances, >= 1
+ *   m_tilde   host array of count device pointers, each SoA 3*N_i float64
+ *   alpha, dt, h, grids   host arrays of count values (as ll_mg_setup)
+ *   p         parameters shared by all instances, or NULL for the defaults;
+ *             precision LL_FP64 or LL_MIXED_FP32, kcycle 0 (LL_EINVAL
+ *             otherwise)
+ * Every instance must coarsen at least once (more cells than
+ * p->coarsest_cells), else LL_EINVAL.  The batch owns all its memory;
+ * m_tilde is not retained.  Errors as ll_mg_setup. */
+typedef struct ll_mg_batch ll_mg_batch;
+int ll_mg_batch_setup(int count, const double* const* m_tilde, const double* alpha, const double* dt,
+                      const double* h, const ll_grid* grids, const ll_mg_params* p, void* cuda_stream,
+                      ll_mg_batch** out);
+/* Numeric setup of every instance for new (m_tilde, alpha, dt); the grids
+ * and the aggregation stay.  Arrays as in ll_mg_batch_setup. */
+int ll_mg_batch_update(ll_mg_batch* B, const double* const* m_tilde, const double* alpha, const double* dt);
+/* Solve A_i x_i = rhs_i for every instance from the guesses in x_i.
+ *   rhs, x        host arrays of count device pointers (SoA 3*N_i float64)
+ *   rtol          stopping tolerance of every instance, or <= 0: p->rtol
+ *   iterations    host, count ints, or NULL: GCR iterations per instance
+ *   rel_residual  host, count doubles, or NULL: true relative residuals
+ *   status        host, count ints, or NULL: LL_OK / LL_NOT_CONVERGED /
+ *                 LL_BREAKDOWN per instance
+ * Returns LL_OK when every instance converged, else LL_BREAKDOWN if any
+ * instance broke down, else LL_NOT_CONVERGED; x holds every instance's
+ * final iterate in all three cases.  Blocks until done. */
+int ll_mg_batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x, double rtol, int* iterations,
+                      double* rel_residual, int* status);
+int ll_mg_batch_count(const ll_mg_batch* B);
+/* levels of the concatenated hierarchy (the deepest instance's count) */
+int ll_mg_batch_levels(const ll_mg_batch* B);
+/* rows (cells of all instances) and colour classes of a concatenated level */
+long long ll_mg_batch_level_rows(const ll_mg_batch* B, int level);
+int ll_mg_batch_level_colours(const ll_mg_batch* B, int level);
+/* levels of instance i's own hierarchy */
+int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i);
+void ll_mg_batch_destroy(ll_mg_batch* B);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,9 @@ EXPORTS = (
     "ll_status_string", "ll_mg_levels", "ll_mg_level_cells", "ll_mg_level_aggregates",
     "ll_mg_level_colours", "ll_mg_level_blocks", "ll_mg_level_operator", "ll_mg_apply", "ll_mg_vcycle",
     "ll_mg_smooth", "ll_mg_step", "ll_launch_count", "ll_mg_profile", "ll_mg_profile_read",
-    "ll_residual_noalloc", "ll_mg_step_llg",
+    "ll_residual_noalloc", "ll_mg_step_llg", "ll_mg_batch_setup", "ll_mg_batch_update", "ll_mg_batch_solve",
+    "ll_mg_batch_count", "ll_mg_batch_levels", "ll_mg_batch_level_rows", "ll_mg_batch_level_colours",
+    "ll_mg_batch_instance_levels", "ll_mg_batch_destroy",
 )
 
 
@@ -108,9 +110,18 @@ def load_library():
         "ll_mg_step": (i, [vp, vp, i, ip, dp]),
         "ll_launch_count": (ctypes.c_longlong, []),
         "ll_mg_profile": (i, [vp, ctypes.c_uint]),
-        "ll_mg_profile_read": (i, [vp, i, dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "ll_mg_profile_read": (i, [vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
         "ll_residual_noalloc": (i, [vp, d, d, d, _Grid, vp, vp, vp, vp, vp]),
         "ll_mg_step_llg": (i, [vp, vp, i, d, vp, ip, dp]),
+        "ll_mg_batch_setup": (i, [i, vp, vp, vp, vp, vp, P, vp, ctypes.POINTER(vp)]),
+        "ll_mg_batch_update": (i, [vp, vp, vp, vp]),
+        "ll_mg_batch_solve": (i, [vp, vp, vp, d, vp, vp, vp]),
+        "ll_mg_batch_count": (i, [vp]),
+        "ll_mg_batch_levels": (i, [vp]),
+        "ll_mg_batch_level_rows": (ctypes.c_longlong, [vp, i]),
+        "ll_mg_batch_level_colours": (i, [vp, i]),
+        "ll_mg_batch_instance_levels": (i, [vp, i]),
+        "ll_mg_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -292,6 +303,73 @@ def residual_noalloc(m_tilde, alpha, dt, h, grid, rhs, x, r=None, norms2=None):
                                             ctypes.c_void_p(norms2.data_ptr()), _stream())
     _check(st, "ll_residual_noalloc", ok=(LL_OK,))
     return norms2
+
+
+def _ptrs(tensors, ns, name):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for k, (t, n) in enumerate(zip(tensors, ns)):
+        arr[k] = _field(t, n, "%s[%d]" % (name, k)).value
+    return arr
+
+
+class Batch:
+    """Independent instances solved together (``ll_mg_batch_setup``): one
+    hierarchy per instance, concatenated level by level, GCR in lockstep."""
+
+    def __init__(self, m_tildes, alphas, dts, hs, grids, params: Params | None = None):
+        lib = load_library()
+        self.count = len(m_tildes)
+        gs = [_grid(g) for g in grids]
+        self.grids = [(g.nx, g.ny, g.nz) for g in gs]
+        self.ns = [g.nx * g.ny * g.nz for g in gs]
+        self.params = params or Params()
+        self._cp = self.params._c()
+        garr = (_Grid * self.count)(*gs)
+        dv = lambda v: (ctypes.c_double * self.count)(*[float(a) for a in v])  # noqa: E731
+        self._h = ctypes.c_void_p()
+        st = lib.ll_mg_batch_setup(self.count, _ptrs(m_tildes, self.ns, "m_tilde"), dv(alphas), dv(dts), dv(hs),
+                                   garr, ctypes.byref(self._cp), _stream(), ctypes.byref(self._h))
+        _check(st, "ll_mg_batch_setup", ok=(LL_OK,))
+
+    def close(self):
+        if self._h:
+            load_library().ll_mg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, m_tildes, alphas, dts):
+        dv = lambda v: (ctypes.c_double * self.count)(*[float(a) for a in v])  # noqa: E731
+        st = load_library().ll_mg_batch_update(self._h, _ptrs(m_tildes, self.ns, "m_tilde"), dv(alphas), dv(dts))
+        _check(st, "ll_mg_batch_update", ok=(LL_OK,))
+
+    def solve(self, rhs, x, rtol: float = 0.0):
+        """Solve every instance in place; returns (status, iterations,
+        true relative residuals, per-instance statuses)."""
+        its = (ctypes.c_int * self.count)()
+        rrs = (ctypes.c_double * self.count)()
+        sts = (ctypes.c_int * self.count)()
+        st = load_library().ll_mg_batch_solve(self._h, _ptrs(rhs, self.ns, "rhs"), _ptrs(x, self.ns, "x"),
+                                              float(rtol), its, rrs, sts)
+        _check(st, "ll_mg_batch_solve")
+        return st, list(its), list(rrs), list(sts)
+
+    @property
+    def levels(self) -> int:
+        return load_library().ll_mg_batch_levels(self._h)
+
+    def level_rows(self, level: int) -> int:
+        return int(load_library().ll_mg_batch_level_rows(self._h, level))
+
+    def level_colours(self, level: int) -> int:
+        return load_library().ll_mg_batch_level_colours(self._h, level)
+
+    def instance_levels(self, i: int) -> int:
+        return load_library().ll_mg_batch_instance_levels(self._h, i)
 
 
 def launch_count() -> int:

@@ -1,0 +1,605 @@
+// Batched solves of many independent instances (ll_mg_batch_*).
+//
+// Every instance gets its own hierarchy (the same aggregation, colouring and
+// Galerkin operators as a single solve).  The batch then concatenates the
+// instances level by level into one union hierarchy: union level l holds the
+// rows of every instance that has a level l, colour class by colour class
+// (class t of the union = class t of every instance, instance after
+// instance), followed by the rows of the instances whose coarsest level l is.
+// Instances are never coupled, so one launch per colour class smooths every
+// instance at once and the V-cycle of the single solver runs unchanged on the
+// union; level 0 is a BSR level here (red and black slots as its two
+// classes).  The dense coarsest solves of all instances that end at level l
+// are one launch.  GCR runs in lockstep with one set of scalars per instance
+// (Algorithm 1 per instance); an instance that has converged keeps its
+// residual and stops contributing to its solution.
+//
+// Included by ll_solver.cu after the single-instance solver.
+#pragma once
+
+struct ll_mg_batch {
+  ll_mg_params prm;
+  int ninst = 0;
+  cudaStream_t user = nullptr;
+  cudaEvent_t entry_ev = nullptr;
+  std::vector<ll_mg_hierarchy*> inst;
+  ll_mg_hierarchy* U = nullptr;  // union hierarchy; its stream is the batch's
+  // rmap[i][l]: rows of instance i's level l (l = 0: red-black slots) -> union rows
+  // bmap[i][l] (l >= 1): blocks of instance i's level l -> union blocks
+  std::vector<std::vector<llmg::DBuf<int>*>> rmap, bmap;
+  std::vector<std::vector<int>> eoff;  // union row of instance i's coarsest level (per level, -1 if not ending)
+  int S0 = 0;                          // union rows of level-0 class 0
+  std::vector<int> off0;               // union row of instance i's first colour-0 slot
+  // GCR workspace in union level-0 order (3 doubles per row)
+  long n3 = 0;
+  llmg::DBuf<double> Z64, C, r, xw, bw, partial, head;
+  llmg::DBuf<float> Z32;
+  llmg::DBuf<GcrScal> scal;
+  llmg::DBuf<Chunk> chunks;
+  int nchunks = 0;
+  llmg::DBuf<int> iptr, act, jdone;
+  double* h_head = nullptr;  // pinned, 2 per instance
+  int* h_flags = nullptr;    // pinned staging of act / jdone
+  cudaGraphExec_t graphs[llmg::kMaxRestart] = {nullptr};
+  long long graph_kernels[llmg::kMaxRestart] = {0};
+  ~ll_mg_batch() {
+    if (U && U->s) cudaStreamSynchronize(U->s);
+    for (auto& g : graphs)
+      if (g) cudaGraphExecDestroy(g);
+    for (auto& v : rmap)
+      for (auto* b : v) delete b;
+    for (auto& v : bmap)
+      for (auto* b : v) delete b;
+    if (h_head) cudaFreeHost(h_head);
+    if (h_flags) cudaFreeHost(h_flags);
+    for (auto* H : inst) delete H;
+    if (entry_ev) cudaEventDestroy(entry_ev);
+    delete U;
+  }
+};
+
+namespace {
+
+constexpr long kChunkElems = 3 * 2048;  // elements of one GCR chunk (one block)
+constexpr int kFieldRn2 = 0, kFieldBn2 = 1, kFieldCc = 2;
+constexpr int kFieldD = (int)(offsetof(GcrScal, d) / sizeof(double));
+
+void batch_enter(ll_mg_batch* B) {
+  LL_CU(cudaEventRecord(B->entry_ev, B->user));
+  LL_CU(cudaStreamWaitEvent(B->U->s, B->entry_ev, 0));
+}
+
+// exclusive scan of per-row counts into a row pointer (n + 1 entries)
+int scan_counts(llmg::DBuf<int>& cnt, llmg::DBuf<int>& ptr, int n, cudaStream_t s) {
+  ptr.alloc(n + 1);
+  return exclusive_scan(cnt, ptr, n, s);
+}
+
+// the union hierarchy's structure: row maps, patterns, members, aggregates
+void batch_symbolic(ll_mg_batch* B) {
+  ll_mg_hierarchy* U = B->U;
+  cudaStream_t s = U->s;
+  int ni = B->ninst;
+  int nlev = 0;
+  for (auto* H : B->inst) nlev = std::max(nlev, H->nlev);
+  U->nlev = nlev;
+  B->rmap.assign(ni, std::vector<DBuf<int>*>(nlev, nullptr));
+  B->bmap.assign(ni, std::vector<DBuf<int>*>(nlev, nullptr));
+  B->eoff.assign(ni, std::vector<int>(nlev, -1));
+  // ---- row maps, level 0: class c = every instance's colour-c slots
+  B->off0.assign(ni, 0);
+  long s0 = 0;
+  for (int i = 0; i < ni; ++i) {
+    B->off0[i] = (int)s0;
+    s0 += B->inst[i]->g.nh;
+  }
+  if (2 * s0 >= (1L << 30)) throw Status{LL_ELIMIT};
+  B->S0 = (int)s0;
+  {
+    CLevel& L = U->lev[0];
+    L.n = (int)(2 * s0);
+    L.ncol = 2;
+    L.cs = {0, (int)s0, (int)(2 * s0)};
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      B->rmap[i][0] = new DBuf<int>();
+      B->rmap[i][0]->alloc(H->n2);
+      kb_union_slotmap<<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g.nh, B->off0[i], (int)s0 + B->off0[i],
+                                                             *B->rmap[i][0]);
+      LL_LAUNCHED();
+    }
+  }
+  // ---- row maps, levels >= 1
+  for (int l = 1; l < nlev; ++l) {
+    CLevel& L = U->lev[l];
+    int K = 0;
+    for (auto* H : B->inst)
+      if (H->nlev - 1 > l) K = std::max(K, H->lev[l].ncol);
+    std::vector<std::vector<int>> off(ni, std::vector<int>(std::max(K, 1), 0));
+    L.cs.assign(K + 1, 0);
+    int row = 0;
+    for (int t = 0; t < K; ++t) {
+      L.cs[t] = row;
+      for (int i = 0; i < ni; ++i) {
+        ll_mg_hierarchy* H = B->inst[i];
+        if (H->nlev - 1 > l && t < H->lev[l].ncol) {
+          off[i][t] = row;
+          row += H->lev[l].cs[t + 1] - H->lev[l].cs[t];
+        }
+      }
+    }
+    L.cs[K] = row;
+    L.ncol = K;
+    std::vector<CoarseTask> tasks;
+    int maxN = 0;
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      if (H->nlev - 1 == l) {
+        B->eoff[i][l] = row;
+        tasks.push_back({row, 3 * H->lev[l].n, H->ainv.p});
+        maxN = std::max(maxN, 3 * H->lev[l].n);
+        row += H->lev[l].n;
+      }
+    }
+    L.n = row;
+    U->uc_n[l] = (int)tasks.size();
+    U->uc_maxN[l] = maxN;
+    if (!tasks.empty()) {
+      U->uc_tasks[l].alloc(tasks.size());
+      LL_CU(cudaMemcpyAsync(U->uc_tasks[l].p, tasks.data(), tasks.size() * sizeof(CoarseTask),
+                            cudaMemcpyHostToDevice, s));
+    }
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      if (H->nlev <= l) continue;
+      CLevel& Li = H->lev[l];
+      bool ending = H->nlev - 1 == l;
+      int ncls = ending ? 0 : Li.ncol;
+      std::vector<int> tab;
+      if (ending) {
+        tab = {0, B->eoff[i][l]};
+      } else {
+        tab.assign(Li.cs.begin(), Li.cs.begin() + ncls + 1);
+        for (int t = 0; t < ncls; ++t) tab.push_back(off[i][t]);
+      }
+      DBuf<int> dtab;
+      dtab.alloc(tab.size());
+      LL_CU(cudaMemcpyAsync(dtab.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      B->rmap[i][l] = new DBuf<int>();
+      B->rmap[i][l]->alloc(Li.n);
+      kb_union_rowmap<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, ncls, dtab, *B->rmap[i][l]);
+      LL_LAUNCHED();
+      LL_CU(cudaStreamSynchronize(s));  // dtab and tab go out of scope
+    }
+  }
+  // ---- patterns
+  for (int l = 0; l < nlev; ++l) {
+    CLevel& L = U->lev[l];
+    DBuf<int> cnt;
+    cnt.alloc(L.n + 1);
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      if (H->nlev <= l) continue;
+      if (l == 0) {
+        kb_union_l0_count<<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, *B->rmap[i][0], cnt);
+      } else {
+        CLevel& Li = H->lev[l];
+        kb_union_rowcount<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, *B->rmap[i][l], cnt);
+      }
+      LL_LAUNCHED();
+    }
+    L.nnzb = scan_counts(cnt, L.rowptr, L.n, s);
+    L.col.alloc(L.nnzb);
+    L.diag.alloc(L.n);
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      if (H->nlev <= l) continue;
+      if (l == 0) {
+        kb_union_l0_pattern<<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, *B->rmap[i][0], L.rowptr, L.col, L.diag);
+      } else {
+        CLevel& Li = H->lev[l];
+        B->bmap[i][l] = new DBuf<int>();
+        B->bmap[i][l]->alloc(Li.nnzb);
+        kb_union_pattern<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, Li.col, Li.diag, *B->rmap[i][l],
+                                                               L.rowptr, L.col, L.diag, *B->bmap[i][l]);
+      }
+      LL_LAUNCHED();
+    }
+  }
+  // ---- members of level l in level l-1, aggregates of level l-1 in level l
+  for (int l = 1; l < nlev; ++l) {
+    CLevel& L = U->lev[l];
+    CLevel& F = U->lev[l - 1];
+    DBuf<int> cnt;
+    cnt.alloc(L.n + 1);
+    F.agg.alloc(F.n);
+    kb_fill_int<<<cdiv(F.n, kBlock), kBlock, 0, s>>>(F.n, -1, F.agg);
+    LL_LAUNCHED();
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      if (H->nlev <= l) continue;
+      CLevel& Li = H->lev[l];
+      kb_union_memcount<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.mptr, *B->rmap[i][l], cnt);
+      LL_LAUNCHED();
+    }
+    int nm = scan_counts(cnt, L.mptr, L.n, s);
+    L.mem.alloc(nm);
+    for (int i = 0; i < ni; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      if (H->nlev <= l) continue;
+      CLevel& Li = H->lev[l];
+      kb_union_members<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.mptr, Li.mem, *B->rmap[i][l],
+                                                             *B->rmap[i][l - 1], L.mptr, L.mem);
+      LL_LAUNCHED();
+      const int* fagg = l == 1 ? H->agg0.p : H->lev[l - 1].agg.p;
+      long fn = l == 1 ? H->n2 : H->lev[l - 1].n;
+      kb_union_agg<<<cdiv(fn, kBlock), kBlock, 0, s>>>(fn, fagg, *B->rmap[i][l - 1], *B->rmap[i][l], F.agg);
+      LL_LAUNCHED();
+    }
+  }
+  LL_CU(cudaStreamSynchronize(s));
+  // ---- host counts of the work models (profiling)
+  for (int l = 0; l < nlev; ++l) {
+    CLevel& L = U->lev[l];
+    std::vector<int> rp(L.n + 1), dg(L.n);
+    LL_CU(cudaMemcpy(rp.data(), L.rowptr.p, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    LL_CU(cudaMemcpy(dg.data(), L.diag.p, L.n * sizeof(int), cudaMemcpyDeviceToHost));
+    L.pre_blk.assign(L.ncol, 0);
+    L.off_blk.assign(L.ncol, 0);
+    for (int c = 0; c < L.ncol; ++c)
+      for (int I = L.cs[c]; I < L.cs[c + 1]; ++I) {
+        L.pre_blk[c] += dg[I] - rp[I];
+        L.off_blk[c] += rp[I + 1] - rp[I] - 1;
+      }
+    L.res_blk = rp[L.ncol > 0 ? L.cs[L.ncol - 1] : 0];
+  }
+}
+
+void batch_allocate(ll_mg_batch* B) {
+  ll_mg_hierarchy* U = B->U;
+  bool mixed = B->prm.precision != LL_FP64;
+  for (int l = 0; l < U->nlev; ++l) {
+    CLevel& L = U->lev[l];
+    if (l == 0 || !mixed) L.val64.alloc(9L * L.nnzb);  // level 0: also the float64 outer operator
+    if (mixed) {
+      L.val32.alloc(9L * L.nnzb);
+      L.dinv32.alloc(9L * L.n);
+      L.x32.alloc(3L * L.n);
+      L.b32.alloc(3L * L.n);
+      L.r32.alloc(3L * L.n);
+    } else {
+      L.dinv64.alloc(9L * L.n);
+      L.x64.alloc(3L * L.n);
+      L.b64.alloc(3L * L.n);
+      L.r64.alloc(3L * L.n);
+    }
+  }
+  int ni = B->ninst;
+  B->n3 = 3L * U->lev[0].n;
+  int m = B->prm.restart;
+  if (mixed) B->Z32.alloc((size_t)m * B->n3);
+  else B->Z64.alloc((size_t)m * B->n3);
+  B->C.alloc((size_t)m * B->n3);
+  B->r.alloc(B->n3);
+  B->xw.alloc(B->n3);
+  B->bw.alloc(B->n3);
+  // chunks: instance-major, each instance's colour-0 rows then colour-1 rows
+  std::vector<Chunk> ch;
+  std::vector<int> ip(1, 0);
+  for (int i = 0; i < ni; ++i) {
+    long nh = B->inst[i]->g.nh;
+    for (long base : {(long)B->off0[i], (long)B->S0 + B->off0[i]}) {
+      long e0 = 3 * base, e1 = 3 * (base + nh);
+      for (long e = e0; e < e1; e += kChunkElems) ch.push_back({i, e, std::min(e1, e + kChunkElems)});
+    }
+    ip.push_back((int)ch.size());
+  }
+  B->nchunks = (int)ch.size();
+  B->chunks.alloc(ch.size());
+  LL_CU(cudaMemcpyAsync(B->chunks.p, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, U->s));
+  B->iptr.alloc(ip.size());
+  LL_CU(cudaMemcpyAsync(B->iptr.p, ip.data(), ip.size() * sizeof(int), cudaMemcpyHostToDevice, U->s));
+  B->partial.alloc((size_t)kDotChunk * B->nchunks);
+  B->scal.alloc(ni);
+  B->scal.zero(U->s);
+  B->head.alloc(2 * ni);
+  B->act.alloc(ni);
+  B->jdone.alloc(ni);
+  LL_CU(cudaMallocHost((void**)&B->h_head, 2 * ni * sizeof(double)));
+  LL_CU(cudaMallocHost((void**)&B->h_flags, ni * sizeof(int)));
+  LL_CU(cudaStreamSynchronize(U->s));
+}
+
+// numeric values of the union from the instances' numeric setups
+template <typename T, typename TM>
+void batch_values(ll_mg_batch* B) {
+  ll_mg_hierarchy* U = B->U;
+  cudaStream_t s = U->s;
+  for (auto* H : B->inst) LL_CU(cudaStreamSynchronize(H->s));
+  bool mixed = !std::is_same<T, double>::value;
+  for (int i = 0; i < B->ninst; ++i) {
+    ll_mg_hierarchy* H = B->inst[i];
+    CLevel& L0 = U->lev[0];
+    kb_union_l0_values<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, *B->rmap[i][0], L0.rowptr, L0.diag,
+                                                                H->chat64, H->dinv0<T>(), 1.0 / H->dt, L0.val64,
+                                                                mixed ? (T*)L0.val32.p : (T*)nullptr, L0.dinv<T>());
+    LL_LAUNCHED();
+    for (int l = 1; l < H->nlev; ++l) {
+      CLevel& Li = H->lev[l];
+      CLevel& L = U->lev[l];
+      kb_union_values<TM, T><<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, *B->bmap[i][l],
+                                                                   *B->rmap[i][l], Li.valm<TM>(), Li.dinv<T>(),
+                                                                   L.valm<TM>(), L.dinv<T>());
+      LL_LAUNCHED();
+    }
+  }
+  LL_CU(cudaStreamSynchronize(s));
+}
+
+void batch_refresh(ll_mg_batch* B) {
+  if (B->prm.precision == LL_MIXED_FP32) batch_values<float, float>(B);
+  else batch_values<double, double>(B);
+}
+
+void batch_finish(ll_mg_batch* B, int nvals, int field) {
+  kgb_finish<<<dim3(B->ninst, nvals), kBlock, 0, B->U->s>>>(B->partial, B->nchunks, B->iptr, B->scal, field);
+  LL_LAUNCHED();
+}
+
+// one lockstep GCR iteration j of every instance (no host interaction)
+template <typename T, typename TM>
+void batch_iteration_body(ll_mg_batch* B, int j) {
+  ll_mg_hierarchy* U = B->U;
+  cudaStream_t s = U->s;
+  CLevel& L0 = U->lev[0];
+  long n3 = B->n3;
+  int ni = B->ninst, nch = B->nchunks;
+  GcrScal* S = B->scal.p;
+  T* Zbase = std::is_same<T, double>::value ? (T*)B->Z64.p : (T*)B->Z32.p;
+  T* zj = Zbase + (size_t)j * n3;
+  double* cj = B->C.p + (size_t)j * n3;
+  k_convert<double, T><<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, B->r, L0.b<T>());  // step 1
+  LL_LAUNCHED();
+  vcycle_coarse<T, TM>(U, 0, false);
+  LL_CU(cudaMemcpyAsync(zj, L0.x<T>(), n3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  kgb_apply<T><<<cdiv(L0.n, kBlock), kBlock, 0, s>>>(L0.n, L0.rowptr, L0.col, L0.val64, zj, cj);  // step 2
+  LL_LAUNCHED();
+  for (int pass = 0; pass < 2 && j > 0; ++pass) {  // step 3: CGS2
+    for (int i0 = 0; i0 < j; i0 += kDotChunk) {
+      int cnt = std::min(kDotChunk, j - i0);
+      kgb_multidot<kDotChunk><<<nch, kBlock, 0, s>>>(B->chunks, nch, B->C, n3, i0, cnt, cj, B->partial);
+      LL_LAUNCHED();
+      batch_finish(B, cnt, kFieldD + i0);
+    }
+    kgb_gs_coef<<<cdiv(ni, 64), 64, 0, s>>>(S, ni, j, pass == 0);
+    LL_LAUNCHED();
+    kgb_multiaxpy<<<nch, kBlock, 0, s>>>(B->chunks, cj, B->C, n3, j, S);
+    LL_LAUNCHED();
+  }
+  kgb_dot2<<<nch, kBlock, 0, s>>>(B->chunks, nch, cj, B->r, B->partial);  // step 4
+  LL_LAUNCHED();
+  batch_finish(B, 2, kFieldCc);
+  kgb_norm_coef<<<cdiv(ni, 64), 64, 0, s>>>(S, ni, j, B->act);
+  LL_LAUNCHED();
+  kgb_rupdate<<<nch, kBlock, 0, s>>>(B->chunks, nch, B->r, cj, S, B->partial);  // step 5
+  LL_LAUNCHED();
+  batch_finish(B, 1, kFieldRn2);
+  kgb_head<<<cdiv(ni, 64), 64, 0, s>>>(S, ni, B->head);
+  LL_LAUNCHED();
+  LL_CU(cudaMemcpyAsync(B->h_head, B->head.p, 2 * ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+template <typename T, typename TM>
+void batch_run_iteration(ll_mg_batch* B, int j) {
+  cudaStream_t s = B->U->s;
+  if (!B->U->use_graphs) {
+    batch_iteration_body<T, TM>(B, j);
+  } else {
+    if (!B->graphs[j]) {
+      cudaGraph_t graph;
+      long long before = g_launches.load();
+      LL_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        batch_iteration_body<T, TM>(B, j);
+      } catch (Status) {
+        cudaStreamEndCapture(s, &graph);
+        throw;
+      }
+      LL_CU(cudaStreamEndCapture(s, &graph));
+      cudaError_t e = cudaGraphInstantiate(&B->graphs[j], graph, 0);
+      cudaGraphDestroy(graph);
+      LL_CU(e);
+      B->graph_kernels[j] = g_launches.load() - before;
+      g_launches.fetch_sub(B->graph_kernels[j]);
+    }
+    LL_CU(cudaGraphLaunch(B->graphs[j], s));
+    g_launches.fetch_add(B->graph_kernels[j]);
+  }
+  LL_CU(cudaStreamSynchronize(s));
+}
+
+void batch_upload(ll_mg_batch* B, const std::vector<int>& v, int* dst) {
+  std::copy(v.begin(), v.end(), B->h_flags);
+  LL_CU(cudaMemcpyAsync(dst, B->h_flags, v.size() * sizeof(int), cudaMemcpyHostToDevice, B->U->s));
+  LL_CU(cudaStreamSynchronize(B->U->s));  // h_flags is reused
+}
+
+void batch_true_residual(ll_mg_batch* B) {
+  ll_mg_hierarchy* U = B->U;
+  CLevel& L0 = U->lev[0];
+  kgb_residual<<<B->nchunks, kBlock, 0, U->s>>>(B->chunks, B->nchunks, L0.rowptr, L0.col, L0.val64, B->bw, B->xw,
+                                                B->r, B->partial);
+  LL_LAUNCHED();
+  batch_finish(B, 2, kFieldRn2);
+  kgb_head2<<<cdiv(B->ninst, 64), 64, 0, U->s>>>(B->scal, B->ninst, B->head);
+  LL_LAUNCHED();
+  LL_CU(cudaMemcpyAsync(B->h_head, B->head.p, 2 * B->ninst * sizeof(double), cudaMemcpyDeviceToHost, U->s));
+  LL_CU(cudaStreamSynchronize(U->s));
+}
+
+// GCR (Algorithm 1) on every instance in lockstep, restarts of prm.restart;
+// per instance the same decisions as the single solve
+template <typename T, typename TM>
+int batch_gcr(ll_mg_batch* B, double rtol, int* iters, double* relres, int* status, std::vector<int>& zero) {
+  ll_mg_hierarchy* U = B->U;
+  cudaStream_t s = U->s;
+  int ni = B->ninst;
+  long n3 = B->n3;
+  T* Zbase = std::is_same<T, double>::value ? (T*)B->Z64.p : (T*)B->Z32.p;
+  std::vector<int> total(ni, 0), st(ni, LL_NOT_CONVERGED), done(ni, 0), act(ni, 0), jd(ni, 0);
+  std::vector<double> bnorm(ni, 0.0);
+  for (;;) {
+    batch_true_residual(B);
+    int running = 0;
+    int tmin = 1 << 30;
+    for (int i = 0; i < ni; ++i) {
+      act[i] = 0;
+      if (done[i]) continue;
+      double rn2 = B->h_head[2 * i];
+      bnorm[i] = sqrt(B->h_head[2 * i + 1]);
+      if (bnorm[i] == 0.0) {  // zero right-hand side: x = 0 below
+        st[i] = LL_OK;
+        done[i] = 2;
+      } else if (!isfinite(rn2)) {
+        st[i] = LL_BREAKDOWN;
+        done[i] = 1;
+      } else if (sqrt(rn2) < rtol * bnorm[i]) {
+        st[i] = LL_OK;
+        done[i] = 1;
+      } else if (total[i] >= B->prm.maxit) {
+        done[i] = 1;
+      } else {
+        act[i] = 1;
+        ++running;
+        tmin = std::min(tmin, total[i]);
+      }
+    }
+    if (running == 0) break;
+    int m = std::min(B->prm.restart, B->prm.maxit - tmin);
+    std::fill(jd.begin(), jd.end(), 0);
+    batch_upload(B, act, B->act);
+    std::vector<int> cyc = act;  // still iterating in this cycle
+    for (int j = 0; j < m; ++j) {
+      batch_run_iteration<T, TM>(B, j);
+      bool changed = false;
+      int left = 0;
+      for (int i = 0; i < ni; ++i) {
+        if (!cyc[i]) continue;
+        ++total[i];
+        double rn2 = B->h_head[2 * i], gjj = B->h_head[2 * i + 1];
+        if (!(gjj > 0.0) || !isfinite(gjj) || !isfinite(rn2)) {
+          st[i] = LL_BREAKDOWN;
+          done[i] = 1;
+          cyc[i] = 0;
+          changed = true;
+          continue;
+        }
+        jd[i] = j + 1;
+        if (sqrt(rn2) < rtol * bnorm[i] || total[i] >= B->prm.maxit) {  // step 6
+          cyc[i] = 0;
+          changed = true;
+          continue;
+        }
+        ++left;
+      }
+      if (left == 0) break;
+      if (changed) batch_upload(B, cyc, B->act);
+    }
+    batch_upload(B, jd, B->jdone);
+    kgb_backsub<<<cdiv(ni, 64), 64, 0, s>>>(B->scal, ni, B->jdone);
+    LL_LAUNCHED();
+    kgb_xupdate<T><<<B->nchunks, kBlock, 0, s>>>(B->chunks, B->xw, Zbase, n3, B->scal, B->jdone);
+    LL_LAUNCHED();
+  }
+  batch_true_residual(B);
+  zero.assign(ni, 0);
+  for (int i = 0; i < ni; ++i) {
+    zero[i] = done[i] == 2;
+    double bn = sqrt(B->h_head[2 * i + 1]);
+    if (iters) iters[i] = total[i];
+    if (relres) relres[i] = bn > 0 ? sqrt(B->h_head[2 * i]) / bn : 0.0;
+    if (status) status[i] = st[i];
+  }
+  int worst = LL_OK;
+  for (int i = 0; i < ni; ++i)
+    if (st[i] == LL_BREAKDOWN) worst = LL_BREAKDOWN;
+    else if (st[i] == LL_NOT_CONVERGED && worst == LL_OK) worst = LL_NOT_CONVERGED;
+  return worst;
+}
+
+int batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x, double rtol, int* iters, double* relres,
+                int* status) {
+  ll_mg_hierarchy* U = B->U;
+  cudaStream_t s = U->s;
+  if (rtol <= 0) rtol = B->prm.rtol;
+  for (int i = 0; i < B->ninst; ++i) {
+    ll_mg_hierarchy* H = B->inst[i];
+    kb_union_in<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *B->rmap[i][0],
+                                                                      rhs[i], B->bw);
+    LL_LAUNCHED();
+    kb_union_in<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *B->rmap[i][0], x[i],
+                                                                      B->xw);
+    LL_LAUNCHED();
+  }
+  std::vector<int> zero;
+  int rc = B->prm.precision == LL_MIXED_FP32 ? batch_gcr<float, float>(B, rtol, iters, relres, status, zero)
+                                              : batch_gcr<double, double>(B, rtol, iters, relres, status, zero);
+  for (int i = 0; i < B->ninst; ++i) {
+    ll_mg_hierarchy* H = B->inst[i];
+    if (zero[i]) {  // zero right-hand side: the solution is zero
+      LL_CU(cudaMemsetAsync(x[i], 0, 3 * H->g.n * sizeof(double), s));
+      continue;
+    }
+    kb_union_out<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *B->rmap[i][0],
+                                                                       B->xw, x[i]);
+    LL_LAUNCHED();
+  }
+  LL_CU(cudaStreamSynchronize(s));
+  return rc;
+}
+
+int batch_create(int count, const double* const* m, const double* alpha, const double* dt, const double* h,
+                 const ll_grid* grids, const ll_mg_params* p, void* stream, ll_mg_batch** out) {
+  ll_mg_batch* B = nullptr;
+  try {
+    B = new ll_mg_batch();
+    ll_mg_default_params(&B->prm);
+    if (p) B->prm = *p;
+    B->ninst = count;
+    B->user = (cudaStream_t)stream;
+    LL_CU(cudaEventCreateWithFlags(&B->entry_ev, cudaEventDisableTiming));
+    B->U = new ll_mg_hierarchy();
+    ll_mg_hierarchy* U = B->U;
+    U->prm = B->prm;
+    U->union_mode = true;
+    U->tail_first = -1;
+    U->user = B->user;
+    LL_CU(cudaStreamCreateWithFlags(&U->s, cudaStreamNonBlocking));
+    LL_CU(cudaEventCreateWithFlags(&U->entry_ev, cudaEventDisableTiming));
+    const char* ng = getenv("LLMG_NO_GRAPHS");
+    U->use_graphs = !(ng && ng[0] == '1');
+    batch_enter(B);
+    LL_CU(cudaStreamSynchronize(U->s));  // the callers' fields are ready
+    ll_mg_params ip = B->prm;
+    for (int i = 0; i < count; ++i) {
+      ll_mg_hierarchy* H = nullptr;
+      int rc = create(m[i], alpha[i], dt[i], h[i], grids[i], &ip, nullptr, &H);
+      if (rc != LL_OK) throw Status{rc};
+      B->inst.push_back(H);
+      if (H->nlev < 2) throw Status{LL_EINVAL};  // too small to coarsen: solve it alone
+    }
+    batch_symbolic(B);
+    batch_allocate(B);
+    batch_refresh(B);
+    *out = B;
+    return LL_OK;
+  } catch (Status st) {
+    delete B;
+    return st.code;
+  } catch (std::bad_alloc&) {
+    delete B;
+    return LL_ENOMEM;
+  }
+}
+
+}  // namespace

@@ -1,0 +1,422 @@
+// Device kernels of the batched solver: assembly of the union hierarchy from
+// per-instance hierarchies, the dense solves of the instances whose coarsest
+// level is reached, and the GCR vector kernels with one set of scalars per
+// instance.  Included by ll_solver.cu only.
+#pragma once
+
+#include "ll_kernels.cuh"
+
+namespace llmg {
+
+// ---------------------------------------------------------------------------
+// union assembly (integer bookkeeping, once per batch)
+// ---------------------------------------------------------------------------
+// Local row r of one instance's level (colour-class numbering, classes
+// [cs[t], cs[t+1]) for t < ncls) -> union row: off[t] + r - cs[t]; rows of an
+// instance whose coarsest level this is (ncls == 0) map to off[0] + r.
+// tab = {cs[0..ncls], off[0..max(ncls,1))}.
+__global__ void kb_union_rowmap(int n, int ncls, const int* __restrict__ tab, int* __restrict__ map) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  if (ncls == 0) {
+    map[r] = tab[1] + r;
+    return;
+  }
+  int t = 0;
+  while (t + 1 < ncls && r >= tab[t + 1]) ++t;
+  map[r] = tab[ncls + 1 + t] + r - tab[t];
+}
+
+__global__ void kb_fill_int(long n, int v, int* __restrict__ p) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// level-0 slots of one instance -> union rows: colour c slots go to the
+// union's class c at offset off[c]
+__global__ void kb_union_slotmap(long nh, int off0, int off1, int* __restrict__ map) {
+  long s = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (s >= 2 * nh) return;
+  map[s] = s < nh ? off0 + (int)s : off1 + (int)(s - nh);
+}
+
+// number of blocks of each union row (from one instance's BSR level)
+__global__ void kb_union_rowcount(int n, const int* __restrict__ rp, const int* __restrict__ map,
+                                  int* __restrict__ cnt) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) cnt[map[r]] = rp[r + 1] - rp[r];
+}
+
+// pattern of one instance's BSR level inside the union: rows keep their
+// block order, columns go through the row map (monotone within an
+// instance, so sorted rows stay sorted and the diagonal keeps its place)
+__global__ void kb_union_pattern(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const int* __restrict__ dg, const int* __restrict__ map,
+                                 const int* __restrict__ urp, int* __restrict__ ucol, int* __restrict__ udiag,
+                                 int* __restrict__ bmap) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int R = map[r];
+  int o = urp[R] - rp[r];
+  for (int p = rp[r]; p < rp[r + 1]; ++p) {
+    ucol[o + p] = map[col[p]];
+    bmap[p] = o + p;
+  }
+  udiag[R] = o + dg[r];
+}
+
+// members of one instance's level-(l+1) rows, mapped into the union level l
+__global__ void kb_union_memcount(int n, const int* __restrict__ mptr, const int* __restrict__ map,
+                                  int* __restrict__ cnt) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) cnt[map[r]] = mptr[r + 1] - mptr[r];
+}
+__global__ void kb_union_members(int n, const int* __restrict__ mptr, const int* __restrict__ mem,
+                                 const int* __restrict__ map, const int* __restrict__ fmap,
+                                 const int* __restrict__ umptr, int* __restrict__ umem) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int o = umptr[map[r]] - mptr[r];
+  for (int p = mptr[r]; p < mptr[r + 1]; ++p) umem[o + p] = fmap[mem[p]];
+}
+
+// union agg of one instance's level l: its rows -> union rows of level l+1
+// (-1 where the instance has no aggregate, i.e. padding slots)
+__global__ void kb_union_agg(long n, const int* __restrict__ agg, const int* __restrict__ map,
+                             const int* __restrict__ cmap, int* __restrict__ uagg) {
+  long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int a = agg[r];
+  uagg[map[r]] = a < 0 ? -1 : cmap[a];
+}
+
+// level 0 of one instance as union BSR rows: the diagonal block first for
+// colour 0 (all neighbours have the higher colour 1), last for colour 1
+__global__ void kb_union_l0_count(GridGeom g, const int* __restrict__ map, int* __restrict__ cnt) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (sl >= 2 * g.nh) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  long nb[6];
+  cnt[map[sl]] = p.real ? 1 + slot_neighbours(g, c, p, nb) : 1;
+}
+__global__ void kb_union_l0_pattern(GridGeom g, const int* __restrict__ map, const int* __restrict__ urp,
+                                    int* __restrict__ ucol, int* __restrict__ udiag) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (sl >= 2 * g.nh) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  int R = map[sl];
+  int o = urp[R];
+  long nb[6];
+  int d = p.real ? slot_neighbours(g, c, p, nb) : 0;
+  if (c == 0) {
+    udiag[R] = o;
+    ucol[o++] = R;
+    for (int q = 0; q < d; ++q) ucol[o++] = map[nb[q]];
+  } else {
+    for (int q = 0; q < d; ++q) ucol[o++] = map[nb[q]];
+    udiag[R] = o;
+    ucol[o] = R;
+  }
+}
+
+// level-0 values of one instance (per step): off-diagonal blocks C^_k, the
+// diagonal I/dt - deg C^_k, and D^-1; a padding slot gets I/dt and dt I.
+// val64 is the float64 operator, valt/dinvt the V-cycle copies.
+template <typename T>
+__global__ void kb_union_l0_values(GridGeom g, const int* __restrict__ map, const int* __restrict__ urp,
+                                   const int* __restrict__ udiag, const double* __restrict__ chat,
+                                   const T* __restrict__ dinv, double inv_dt, double* __restrict__ val64,
+                                   T* __restrict__ valt, T* __restrict__ dinvt) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  int R = map[sl];
+  long nb[6];
+  int d = p.real ? slot_neighbours(g, c, p, nb) : 0;
+  double C[9], D[9];
+  for (int e = 0; e < 9; ++e) C[e] = p.real ? chat[e * n2 + sl] : 0.0;
+  for (int e = 0; e < 9; ++e) D[e] = ((e % 4) == 0 ? inv_dt : 0.0) - d * C[e];
+  for (int q = urp[R]; q < urp[R + 1]; ++q) {
+    const double* src = q == udiag[R] ? D : C;
+    for (int e = 0; e < 9; ++e) {
+      val64[9L * q + e] = src[e];
+      if (valt) valt[9L * q + e] = (T)src[e];
+    }
+  }
+  for (int e = 0; e < 9; ++e) dinvt[9L * R + e] = p.real ? dinv[e * n2 + sl] : ((e % 4) == 0 ? (T)(1.0 / inv_dt) : (T)0);
+}
+
+// coarse values of one instance's level (per step): blocks through bmap,
+// D^-1 through the row map
+template <typename TM, typename T>
+__global__ void kb_union_values(int n, const int* __restrict__ rp, const int* __restrict__ bmap,
+                                const int* __restrict__ map, const TM* __restrict__ val, const T* __restrict__ dinv,
+                                TM* __restrict__ uval, T* __restrict__ udinv) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int p = rp[r]; p < rp[r + 1]; ++p)
+    for (int e = 0; e < 9; ++e) uval[9L * bmap[p] + e] = val[9L * p + e];
+  long R = map[r];
+  for (int e = 0; e < 9; ++e) udinv[9 * R + e] = dinv[9L * r + e];
+}
+
+// natural SoA vector of one instance <-> union level-0 rows (cell-major)
+template <typename TI, typename TO>
+__global__ void kb_union_in(GridGeom g, const int* __restrict__ nat_of_slot, const int* __restrict__ map,
+                            const TI* __restrict__ in, TO* __restrict__ out) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (sl >= 2 * g.nh) return;
+  int k = nat_of_slot[sl];
+  long R = map[sl];
+  for (int c = 0; c < 3; ++c) out[3 * R + c] = k < 0 ? (TO)0 : (TO)in[c * g.n + k];
+}
+template <typename TI, typename TO>
+__global__ void kb_union_out(GridGeom g, const int* __restrict__ nat_of_slot, const int* __restrict__ map,
+                             const TI* __restrict__ in, TO* __restrict__ out) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (sl >= 2 * g.nh) return;
+  int k = nat_of_slot[sl];
+  if (k < 0) return;
+  long R = map[sl];
+  for (int c = 0; c < 3; ++c) out[c * g.n + k] = (TO)in[3 * R + c];
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle pieces
+// ---------------------------------------------------------------------------
+// x = A_i^{-1} b for every instance i whose coarsest level this is (one task
+// per instance: its rows start at row0, N = 3 x cells, column-major inverse)
+template <typename T>
+__global__ void kc_solve_batch(const CoarseTask* __restrict__ tasks, const T* __restrict__ b, T* __restrict__ x) {
+  CoarseTask t = tasks[blockIdx.y];
+  if (blockIdx.x * blockDim.x >= t.N) return;  // whole block past this task
+  extern __shared__ double sb[];
+  const T* bb = b + 3L * t.row0;
+  for (int j = threadIdx.x; j < t.N; j += blockDim.x) sb[j] = (double)bb[j];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.N) return;
+  double acc = 0.0;
+  for (int j = 0; j < t.N; ++j) acc += t.ainv[(long)j * t.N + i] * sb[j];
+  x[3L * t.row0 + i] = (T)acc;
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(long n, const TI* __restrict__ in, TO* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (TO)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// GCR with per-instance scalars.  Vectors are in union level-0 order; a chunk
+// is an element range of one instance, one block per chunk; partial sums go
+// to partial[q * nchunks + chunk] and are added per instance in chunk order.
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void chunk_reduce_store(double* v, double* partial, int nvals, int nchunks) {
+  __shared__ double sh[NV][kBlock / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double a = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < nvals && threadIdx.x < NV) {
+    double a = 0;
+    for (int w = 0; w < kBlock / 32; ++w) a += sh[threadIdx.x][w];
+    partial[(long)threadIdx.x * nchunks + blockIdx.x] = a;
+  }
+}
+
+// ((double*)&S[i])[field + q] = sum of partial[q][chunks of instance i]
+__global__ void kgb_finish(const double* __restrict__ partial, int nchunks, const int* __restrict__ iptr,
+                           GcrScal* __restrict__ S, int field) {
+  __shared__ double sh[kBlock];
+  int i = blockIdx.x, q = blockIdx.y;
+  double a = 0;
+  for (int k = iptr[i] + threadIdx.x; k < iptr[i + 1]; k += kBlock) a += partial[(long)q * nchunks + k];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kBlock / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) reinterpret_cast<double*>(S + i)[field + q] = sh[0];
+}
+
+template <int NV>
+__global__ void __launch_bounds__(256) kgb_multidot(const Chunk* __restrict__ ch, int nchunks,
+                                                    const double* __restrict__ C, long n3, int i0, int cnt,
+                                                    const double* __restrict__ v, double* __restrict__ partial) {
+  Chunk k = ch[blockIdx.x];
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0;
+  for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
+    double vt = v[t];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q < cnt) acc[q] += C[(long)(i0 + q) * n3 + t] * vt;
+  }
+  chunk_reduce_store<NV>(acc, partial, cnt, nchunks);
+}
+
+__global__ void __launch_bounds__(256) kgb_multiaxpy(const Chunk* __restrict__ ch, double* __restrict__ v,
+                                                     const double* __restrict__ C, long n3, int j,
+                                                     const GcrScal* __restrict__ S) {
+  Chunk k = ch[blockIdx.x];
+  const double* coef = S[k.inst].coef;
+  for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
+    double a = v[t];
+    for (int i = 0; i < j; ++i) a -= coef[i] * C[(long)i * n3 + t];
+    v[t] = a;
+  }
+}
+
+__global__ void __launch_bounds__(256) kgb_dot2(const Chunk* __restrict__ ch, int nchunks,
+                                                const double* __restrict__ c, const double* __restrict__ r,
+                                                double* __restrict__ partial) {
+  Chunk k = ch[blockIdx.x];
+  double acc[2] = {0, 0};
+  for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
+    double ct = c[t];
+    acc[0] += ct * ct;
+    acc[1] += ct * r[t];
+  }
+  chunk_reduce_store<2>(acc, partial, 2, nchunks);
+}
+
+__global__ void __launch_bounds__(256) kgb_rupdate(const Chunk* __restrict__ ch, int nchunks, double* __restrict__ r,
+                                                   const double* __restrict__ c, const GcrScal* __restrict__ S,
+                                                   double* __restrict__ partial) {
+  Chunk k = ch[blockIdx.x];
+  double f = S[k.inst].rcoef;
+  double acc[1] = {0};
+  for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
+    double v = r[t] - f * c[t];
+    r[t] = v;
+    acc[0] += v * v;
+  }
+  chunk_reduce_store<1>(acc, partial, 1, nchunks);
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) kgb_xupdate(const Chunk* __restrict__ ch, double* __restrict__ x,
+                                                   const TZ* __restrict__ Z, long n3, const GcrScal* __restrict__ S,
+                                                   const int* __restrict__ jdone) {
+  Chunk k = ch[blockIdx.x];
+  int m = jdone[k.inst];
+  const double* y = S[k.inst].y;
+  for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
+    double a = x[t];
+    for (int q = 0; q < m; ++q) a += y[q] * (double)Z[(long)q * n3 + t];
+    x[t] = a;
+  }
+}
+
+// y = A x on union level 0 in float64 (x stored as TX), one thread per row
+template <typename TX>
+__global__ void __launch_bounds__(256) kgb_apply(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                                 const double* __restrict__ val, const TX* __restrict__ x,
+                                                 double* __restrict__ y) {
+  int R = blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= n) return;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int p = rp[R]; p < rp[R + 1]; ++p) {
+    const double* A = val + 9L * p;
+    long J = 3L * col[p];
+    double v0 = (double)x[J], v1 = (double)x[J + 1], v2 = (double)x[J + 2];
+    a0 = fma(A[0], v0, fma(A[1], v1, fma(A[2], v2, a0)));
+    a1 = fma(A[3], v0, fma(A[4], v1, fma(A[5], v2, a1)));
+    a2 = fma(A[6], v0, fma(A[7], v1, fma(A[8], v2, a2)));
+  }
+  y[3L * R] = a0;
+  y[3L * R + 1] = a1;
+  y[3L * R + 2] = a2;
+}
+
+// r = b - A x on the rows of each chunk, partial |r|^2 and |b|^2
+__global__ void __launch_bounds__(256) kgb_residual(const Chunk* __restrict__ ch, int nchunks,
+                                                   const int* __restrict__ rp, const int* __restrict__ col,
+                                                   const double* __restrict__ val, const double* __restrict__ b,
+                                                   const double* __restrict__ x, double* __restrict__ r,
+                                                   double* __restrict__ partial) {
+  Chunk k = ch[blockIdx.x];
+  double acc[2] = {0, 0};
+  for (long R = k.e0 / 3 + threadIdx.x; R < k.e1 / 3; R += blockDim.x) {
+    double a0 = b[3 * R], a1 = b[3 * R + 1], a2 = b[3 * R + 2];
+    acc[1] += a0 * a0 + a1 * a1 + a2 * a2;
+    for (int p = rp[R]; p < rp[R + 1]; ++p) {
+      const double* A = val + 9L * p;
+      long J = 3L * col[p];
+      double v0 = x[J], v1 = x[J + 1], v2 = x[J + 2];
+      a0 = fma(-A[0], v0, fma(-A[1], v1, fma(-A[2], v2, a0)));
+      a1 = fma(-A[3], v0, fma(-A[4], v1, fma(-A[5], v2, a1)));
+      a2 = fma(-A[6], v0, fma(-A[7], v1, fma(-A[8], v2, a2)));
+    }
+    r[3 * R] = a0;
+    r[3 * R + 1] = a1;
+    r[3 * R + 2] = a2;
+    acc[0] += a0 * a0 + a1 * a1 + a2 * a2;
+  }
+  chunk_reduce_store<2>(acc, partial, 2, nchunks);
+}
+
+// per-instance scalar updates (one thread per instance, the same formulas as
+// the single-instance kernels)
+__global__ void kgb_gs_coef(GcrScal* S, int ninst, int j, int first) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  GcrScal& s = S[i];
+  for (int q = 0; q < j; ++q) {
+    double gm = s.s[q] * s.d[q];
+    s.gam[q * kMaxRestart + j] = first ? gm : s.gam[q * kMaxRestart + j] + gm;
+    s.coef[q] = gm * s.s[q];
+  }
+}
+// as k_norm_coef; an instance that is not active keeps its residual
+__global__ void kgb_norm_coef(GcrScal* S, int ninst, int j, const int* __restrict__ act) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  GcrScal& s = S[i];
+  double g = sqrt(s.cc);
+  s.gjj = g;
+  s.gam[j * kMaxRestart + j] = g;
+  double sj = 1.0 / g;
+  s.s[j] = sj;
+  s.alpha[j] = sj * s.cr;
+  s.rcoef = act[i] ? s.alpha[j] * sj : 0.0;
+}
+__global__ void kgb_backsub(GcrScal* S, int ninst, const int* __restrict__ jdone) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  GcrScal& s = S[i];
+  int m = jdone[i];
+  for (int q = m - 1; q >= 0; --q) {
+    double a = s.alpha[q];
+    for (int k = q + 1; k < m; ++k) a -= s.gam[q * kMaxRestart + k] * s.y[k];
+    s.y[q] = a / s.gam[q * kMaxRestart + q];
+  }
+}
+// the scalars the host reads each iteration: {rn2, gjj} per instance
+__global__ void kgb_head(const GcrScal* __restrict__ S, int ninst, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  out[2 * i] = S[i].rn2;
+  out[2 * i + 1] = S[i].gjj;
+}
+__global__ void kgb_head2(const GcrScal* __restrict__ S, int ninst, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  out[2 * i] = S[i].rn2;
+  out[2 * i + 1] = S[i].bn2;
+}
+
+}  // namespace llmg

@@ -85,6 +85,18 @@ __host__ __device__ __forceinline__ uint32_t node_key(uint32_t v, uint32_t seed)
 // ---------------------------------------------------------------------------
 // graphs and levels
 // ---------------------------------------------------------------------------
+// batched solves: the dense solve of one instance whose coarsest level is
+// reached (its rows start at union row row0; N = 3 x cells), and one element
+// range [e0, e1) of one instance's part of a union vector
+struct CoarseTask {
+  int row0, N;
+  const double* ainv;
+};
+struct Chunk {
+  int inst;
+  long e0, e1;
+};
+
 struct DevGraph {  // CSR, no self loops, integer weights
   int n = 0;
   int nnz = 0;

@@ -743,7 +743,7 @@ __global__ void kb_scatter3(int n, const int* __restrict__ perm, const T* __rest
 template <typename T>
 __global__ void kb_prolong(int n, const int* __restrict__ agg, const T* __restrict__ e, T* __restrict__ x) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= n) return;
+  if (I >= n || agg[I] < 0) return;  // -1: no aggregate (padding rows of a batch)
   long a = 3L * agg[I];
   x[3L * I] += e[a];
   x[3L * I + 1] += e[a + 1];

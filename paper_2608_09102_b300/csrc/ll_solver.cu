@@ -5,12 +5,15 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <new>
+#include <type_traits>
 
 #include "ll_internal.cuh"
 #include "ll_kernels.cuh"
 #include "ll_setup.cuh"
 #include "ll_tail.cuh"
+#include "ll_batch_kernels.cuh"
 
 #include <atomic>
 
@@ -109,6 +112,11 @@ struct ll_mg_hierarchy {
   template <typename T, typename TM> DBuf<TailArgs<T, TM>>& tail();
   // single-level hierarchies: cell-major scratch of the direct solve
   DBuf<double> single_b, single_x;
+  // union hierarchy of a batch: level 0 is a BSR level too, and the
+  // instances whose coarsest level is l are solved densely at level l
+  bool union_mode = false;
+  DBuf<CoarseTask> uc_tasks[kMaxLevels];
+  int uc_n[kMaxLevels] = {0}, uc_maxN[kMaxLevels] = {0};
   // kernel timing (ll_mg_profile)
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -733,10 +741,25 @@ void coarse_problem(ll_mg_hierarchy* H, int l) {
   else vcycle_coarse<T, TM>(H, l, true);
 }
 
+// union hierarchies: dense solves of the instances whose coarsest level is l
+template <typename T>
+void union_coarse(ll_mg_hierarchy* H, int l) {
+  if (H->uc_n[l] == 0) return;
+  CLevel& L = H->lev[l];
+  LL_PROF(LL_KIND_COARSEST);
+  kc_solve_batch<T><<<dim3(cdiv(H->uc_maxN[l], 32), H->uc_n[l]), 32, H->uc_maxN[l] * sizeof(double), H->s>>>(
+      H->uc_tasks[l], L.b<T>(), L.x<T>());
+  LL_LAUNCHED();
+}
+
 template <typename T, typename TM>
 void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
   CLevel& L = H->lev[l];
   cudaStream_t s = H->s;
+  if (H->union_mode && l == H->nlev - 1) {
+    union_coarse<T>(H, l);
+    return;
+  }
   if (l == H->tail_first) {
     LL_PROFW(LL_KIND_COARSE_TAIL, H->tail_flops, H->tail_bytes);
     launch_tail<T, TM>(H);
@@ -773,6 +796,7 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
                                                         init_end, N.dinv<T>(), N.x<T>());
     LL_LAUNCHED();
   }
+  if (H->union_mode) union_coarse<T>(H, l);  // rows past the colour classes
   coarse_problem<T, TM>(H, l + 1);
   if (nu_post == 0) {
     LL_PROF(LL_KIND_BSR_OTHER);
@@ -1139,6 +1163,8 @@ int create(const double* m, double alpha, double dt, double h, ll_grid grid, con
 
 }  // namespace
 
+#include "ll_batch.cuh"
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1468,5 +1494,69 @@ int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forw
     return st.code;
   }
 }
+
+// ---------------------------------------------------------------------------
+// batches of independent instances
+// ---------------------------------------------------------------------------
+int ll_mg_batch_setup(int count, const double* const* m_tilde, const double* alpha, const double* dt,
+                      const double* h, const ll_grid* grids, const ll_mg_params* p, void* cuda_stream,
+                      ll_mg_batch** out) {
+  if (count < 1 || !m_tilde || !alpha || !dt || !h || !grids || !out) return LL_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!m_tilde[i] || !valid_problem(alpha[i], dt[i], h[i], grids[i])) return LL_EINVAL;
+  if (p && !valid_params(*p)) return LL_EINVAL;
+  if (p && (p->kcycle != 0 || p->precision == LL_MIXED_BF16)) return LL_EINVAL;
+  return batch_create(count, m_tilde, alpha, dt, h, grids, p, cuda_stream, out);
+}
+
+int ll_mg_batch_update(ll_mg_batch* B, const double* const* m_tilde, const double* alpha, const double* dt) {
+  if (!B || !m_tilde || !alpha || !dt) return LL_EINVAL;
+  for (int i = 0; i < B->ninst; ++i)
+    if (!m_tilde[i] || !(dt[i] > 0) || !(alpha[i] >= 0) || !isfinite(dt[i]) || !isfinite(alpha[i])) return LL_EINVAL;
+  try {
+    batch_enter(B);
+    LL_CU(cudaStreamSynchronize(B->U->s));
+    for (int i = 0; i < B->ninst; ++i) {
+      ll_mg_hierarchy* H = B->inst[i];
+      H->alpha = alpha[i];
+      H->dt = dt[i];
+      numeric(H, m_tilde[i]);
+    }
+    batch_refresh(B);
+    return LL_OK;
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+int ll_mg_batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x, double rtol, int* iterations,
+                      double* rel_residual, int* status) {
+  if (!B || !rhs || !x) return LL_EINVAL;
+  for (int i = 0; i < B->ninst; ++i)
+    if (!rhs[i] || !x[i]) return LL_EINVAL;
+  try {
+    batch_enter(B);
+    return batch_solve(B, rhs, x, rtol, iterations, rel_residual, status);
+  } catch (Status st) {
+    return st.code;
+  }
+}
+
+int ll_mg_batch_count(const ll_mg_batch* B) { return B ? B->ninst : 0; }
+int ll_mg_batch_levels(const ll_mg_batch* B) { return B ? B->U->nlev : 0; }
+long long ll_mg_batch_level_rows(const ll_mg_batch* B, int level) {
+  if (!B || level < 0 || level >= B->U->nlev) return -1;
+  return B->U->lev[level].n;
+}
+int ll_mg_batch_level_colours(const ll_mg_batch* B, int level) {
+  if (!B || level < 0 || level >= B->U->nlev) return -1;
+  return B->U->lev[level].ncol;
+}
+int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i) {
+  if (!B || i < 0 || i >= B->ninst) return -1;
+  return B->inst[i]->nlev;
+}
+
+void ll_mg_batch_destroy(ll_mg_batch* B) { delete B; }
 
 }  // extern "C"

@@ -132,3 +132,23 @@ def rhs_field(nx: int, ny: int = 1, nz: int = 1, seed: int = 0):
     """A generic right-hand side: i.i.d. N(0,1) per unknown."""
     rng = np.random.Generator(np.random.PCG64(seed + 1000003))
     return rng.standard_normal((3, nz, ny, nx))
+
+
+BATCH_SIDES = (32, 48, 64, 96, 128, 192, 256)
+
+
+def batch_instances(count: int, seed: int = 0, sides=BATCH_SIDES, alpha_range=(0.005, 1.0),
+                    dt_range=(1e-5, 1e-2)):
+    """Ragged batch of independent 2-D instances: side uniform from ``sides``
+    (h = 1/side, square grid), alpha and dt log-uniform in their ranges, a
+    smooth unit field per instance (seed = seed * 100003 + index).  Returns a
+    list of dicts with keys grid, h, alpha, dt, seed."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    out = []
+    for i in range(count):
+        side = int(sides[rng.integers(len(sides))])
+        a = float(np.exp(rng.uniform(np.log(alpha_range[0]), np.log(alpha_range[1]))))
+        dt = float(np.exp(rng.uniform(np.log(dt_range[0]), np.log(dt_range[1]))))
+        out.append({"grid": (side, side, 1), "h": 1.0 / side, "alpha": a, "dt": dt,
+                    "seed": seed * 100003 + i})
+    return out
