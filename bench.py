@@ -326,6 +326,98 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# ragged batch of independent instances (measured on request)
+# ---------------------------------------------------------------------------
+BATCH_COUNT = 512
+BATCH_WORKLOAD = ("512 independent 2-D instances, sides uniform from {32,48,64,96,128,192,256}, h = 1/side, "
+                  "alpha log-uniform [0.005, 1], dt log-uniform [1e-5, 1e-2], smooth unit fields; one step = "
+                  "numeric setup + solve of every instance to rtol 1e-8")
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2608_09102_b300 as ll
+    from paper_2608_09102_b300 import build, inputs
+
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    precision = {"fp64": ll.LL_FP64, "mixed": ll.LL_MIXED_FP32}[args.precision]
+    spec = inputs.batch_instances(args.batch_count, seed=0)
+    ms = [torch.tensor(inputs.smooth_field(*s["grid"], seed=s["seed"]).reshape(-1), device=dev) for s in spec]
+    alphas = [s["alpha"] for s in spec]
+    dts = [s["dt"] for s in spec]
+    ns = [int(np.prod(s["grid"])) for s in spec]
+    params = ll.Params(rtol=RTOL, precision=precision, maxit=args.batch_maxit)
+    t0 = time.perf_counter()
+    B = ll.Batch(ms, alphas, dts, [s["h"] for s in spec], [s["grid"] for s in spec], params)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    rhs = [m / dt for m, dt in zip(ms, dts)]
+    xs = [torch.zeros_like(m) for m in ms]
+
+    def step():
+        B.update(ms, alphas, dts)
+        for x in xs:
+            x.zero_()
+        return B.solve(rhs, xs)
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    launches0 = ll.launch_count()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st, its, rrs, sts = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = ll.launch_count() - launches0
+    conv = [k for k in range(len(spec)) if sts[k] == ll.LL_OK]
+    solved = 3 * sum(ns[k] for k in conv)
+    total = 3 * sum(ns)
+    # end to end: host (pinned) right-hand sides in, solutions out, every step
+    hr = [r.cpu().pin_memory() for r in rhs]
+    hx = [torch.empty_like(h).pin_memory() for h in hr]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        for d, h in zip(rhs, hr):
+            d.copy_(h, non_blocking=True)
+        step()
+        for h, x in zip(hx, xs):
+            h.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    line = {
+        "metric": METRIC, "value": solved * args.steps / (elapsed_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "instances": len(spec), "cells": sum(ns), "unknowns": total,
+                   "precision": args.precision, "maxit": args.batch_maxit,
+                   "l2": "working set (~6 GB) exceeds the 126 MB L2"},
+        "converged": len(conv), "unknowns_converged": solved,
+        "not_converged": [{"side": spec[k]["grid"][0], "alpha": spec[k]["alpha"], "dt": spec[k]["dt"],
+                           "status": sts[k], "relres": rrs[k], "iterations": its[k]}
+                          for k in range(len(spec)) if sts[k] != ll.LL_OK],
+        "iterations": {"mean": float(np.mean(its)), "median": float(np.median(its)), "max": int(max(its)),
+                       "lockstep": int(max(its))},
+        "levels": B.levels, "setup_s": setup_s, "gpu_launches": int(launches), "clocks": clocks,
+        "e2e": {"value": solved * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "steps": e2e_steps},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,9 +428,15 @@ def main():
     ap.add_argument("--kcycle", type=int, default=0,
                     help="coarse levels 1..K solved by two inner GCR steps (K-cycle); 0 = V-cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["step128", "batch512"], default="step128",
+                    help="step128: the 128^3 time-stepping workload; batch512: the ragged batch")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
+    ap.add_argument("--batch-maxit", type=int, default=300)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch512":
+        run_batch(args)
     else:
         run_ours(args)
 
