@@ -103,6 +103,9 @@ def _load():
     vp, i, d, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint32
     sig = {
         "orc_setup": (vp, [i, i, i, d, d, d, _dp, ctypes.POINTER(_Params)]),
+        "orc_setup_adjoint": (vp, [i, i, i, d, d, d, _dp, ctypes.POINTER(_Params)]),
+        "orc_step_vjp": (i, [i, i, i, d, d, d, ctypes.POINTER(_Params), _dp, _dp, _dp, _dp, ctypes.POINTER(d),
+                             ctypes.POINTER(i), ctypes.POINTER(d)]),
         "orc_free": (None, [vp]),
         "orc_solve": (i, [vp, _dp, _dp, d, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
         "orc_step": (i, [_dp, i, i, i, i, d, d, d, ctypes.POINTER(_Params), i, _ip, _dp]),
@@ -157,7 +160,9 @@ class Hierarchy:
     """Oracle hierarchy for one time step: operator, aggregates, Galerkin
     levels, colourings and the coarsest LU."""
 
-    def __init__(self, grid, h, alpha, dt, m_tilde, params: Params | None = None):
+    def __init__(self, grid, h, alpha, dt, m_tilde, params: Params | None = None, adjoint: bool = False):
+        """adjoint=True: the hierarchy of A^T (same aggregation, every level
+        operator transposed), for adjoint solves."""
         self.grid = _grid3(grid)
         nx, ny, nz = self.grid
         self.n = nx * ny * nz
@@ -165,8 +170,8 @@ class Hierarchy:
         self.params = params or Params()
         self._cp = self.params._c()
         lib = _load()
-        self._h = lib.orc_setup(nx, ny, nz, self.h, self.alpha, self.dt, _soa(m_tilde, self.n),
-                                ctypes.byref(self._cp))
+        setup = lib.orc_setup_adjoint if adjoint else lib.orc_setup
+        self._h = setup(nx, ny, nz, self.h, self.alpha, self.dt, _soa(m_tilde, self.n), ctypes.byref(self._cp))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -275,7 +280,54 @@ def step(m, n_steps, grid, h, alpha, dt, params: Params | None = None, project: 
     return mm, its[:n_steps], rrs[:n_steps], st
 
 
-def step_llg(m, n_steps, grid, h, alpha, dt, q=0.0, he=(0.0, 0.0, 0.0), params: Params | None = None):
+def step_vjp(m, x, g, grid, h, alpha, dt, params: Params | None = None):
+    """Vector-Jacobian product of one step m -> x/|x| (A(m) x = m/dt):
+    returns (dL/dm, dL/dalpha, status, adjoint iterations, relres) for
+    g = dL/dm^{n+1} and the step's solution x."""
+    params = params or Params()
+    nx, ny, nz = _grid3(grid)
+    n = nx * ny * nz
+    mbar = np.zeros(3 * n)
+    abar = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    cp = params._c()
+    st = _load().orc_step_vjp(nx, ny, nz, float(h), float(alpha), float(dt), ctypes.byref(cp), _soa(m, n),
+                              _soa(x, n), _soa(g, n), mbar, ctypes.byref(abar), ctypes.byref(it),
+                              ctypes.byref(rr))
+    return mbar, abar.value, st, it.value, rr.value
+
+
+def forward_states(m0, n_steps, grid, h, alpha, dt, params: Params | None = None):
+    """n_steps plain steps from m0 keeping every state and every solution x:
+    returns (ms, xs) with ms[0] = m0, ms[k+1] = xs[k]/|xs[k]|."""
+    params = params or Params()
+    nx, ny, nz = _grid3(grid)
+    n = nx * ny * nz
+    ms = [np.array(m0, np.float64).reshape(-1)]
+    xs = []
+    for _ in range(n_steps):
+        H = Hierarchy(grid, h, alpha, dt, ms[-1], params)
+        b = ms[-1] / dt
+        x, st, it, rr = H.solve(b, ms[-1].copy())
+        xs.append(x)
+        v = x.reshape(3, n)
+        ms.append((v / np.sqrt(np.sum(v * v, axis=0))).reshape(-1))
+    return ms, xs
+
+
+def loss_gradient(m0, m_target, n_steps, grid, h, alpha, dt, params: Params | None = None):
+    """L = 0.5 |m^N - m_target|^2 after n_steps steps, and its gradients with
+    respect to m0 and alpha by the adjoint recursion (step_vjp backwards)."""
+    ms, xs = forward_states(m0, n_steps, grid, h, alpha, dt, params)
+    diff = ms[-1] - np.asarray(m_target, np.float64).reshape(-1)
+    loss = 0.5 * float(diff @ diff)
+    g = diff.copy()
+    abar = 0.0
+    for k in range(n_steps - 1, -1, -1):
+        g, a, st, it, rr = step_vjp(ms[k], xs[k], g, grid, h, alpha, dt, params)
+        abar += a
+    return loss, g, abar
     """Steps of the full model with explicit anisotropy and external field
     (eps folded into h); returns (m, iterations, relres, status)."""
     params = params or Params()

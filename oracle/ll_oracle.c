@@ -1091,6 +1091,88 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
 /* accessors for the test harness                                             */
 /* ------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------ */
+/* differentiation of the time step (adjoint)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Hierarchy of the transposed operator A^T: the aggregation, colouring and
+ * transfers of A's hierarchy, every level operator transposed.  Since
+ * (P^T A P)^T = P^T A^T P these are the Galerkin operators of A^T, and the
+ * smoother, cycle and GCR of Sec. 3 then act on A^T unchanged. */
+orc_hier *orc_setup_adjoint(int nx, int ny, int nz, double h, double alpha, double dt, const double *m,
+                            const orc_params *prm) {
+  orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
+  for (int l = 0; l < H->nlev; ++l) {
+    csr_t t = csr_transpose(&H->lev[l].A);
+    csr_free(&H->lev[l].A);
+    H->lev[l].A = t;
+  }
+  level_t *Lc = &H->lev[H->nlev - 1];
+  int nn = 3 * Lc->n;
+  free(H->lu);
+  H->lu = csr_to_dense(&Lc->A);
+  H->singular = lu_factor(nn, H->lu, H->piv);
+  if (prm->prec == 2) {
+    int n0 = 3 * H->lev[0].n;
+    free(H->exact_lu);
+    H->exact_lu = csr_to_dense(&H->lev[0].A);
+    lu_factor(n0, H->exact_lu, H->exact_piv);
+  }
+  return H;
+}
+
+/* Vector-Jacobian product of one step.  The step takes m = m^n to
+ * m^{n+1}_k = x_k / |x_k| with A(m) x = m/dt (m~ = m^n); given x and
+ * g = dL/dm^{n+1} it returns mbar = dL/dm^n and abar = dL/dalpha:
+ *   xbar_k = (g_k - (u_k . g_k) u_k) / |x_k|,  u = x/|x|   (projection)
+ *   A^T lambda = xbar                                     (adjoint solve)
+ *   mbar_k = lambda_k/dt - [ y_k x lambda_k
+ *            + alpha ((m_k . y_k) lambda_k + (lambda_k . m_k) y_k
+ *                     - 2 (lambda_k . y_k) m_k) ]
+ *   abar = - sum_k lambda_k . (m_k (m_k . y_k) - |m_k|^2 y_k)
+ * with y = Delta_h x per component: the derivative of
+ * lambda^T (b - A x) with b = m/dt and (A x)_k = x_k/dt + C(m_k) y_k. */
+int orc_step_vjp(int nx, int ny, int nz, double h, double alpha, double dt, const orc_params *prm,
+                 const double *m, const double *x, const double *g, double *mbar, double *abar, int *iters,
+                 double *relres) {
+  int n = nx * ny * nz;
+  double *xbar = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *lam = (double *)xcalloc((size_t)3 * n, sizeof(double));
+  double *y = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  for (int k = 0; k < n; ++k) {
+    double v[3] = {x[k], x[n + k], x[2 * n + k]};
+    double nrm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double u[3] = {v[0] / nrm, v[1] / nrm, v[2] / nrm};
+    double ug = u[0] * g[k] + u[1] * g[n + k] + u[2] * g[2 * n + k];
+    for (int c = 0; c < 3; ++c) xbar[c * n + k] = (g[c * n + k] - ug * u[c]) / nrm;
+  }
+  orc_hier *H = orc_setup_adjoint(nx, ny, nz, h, alpha, dt, m, prm);
+  int st = orc_solve(H, xbar, lam, prm->rtol, iters, relres, NULL);
+  orc_free(H);
+  csr_t L = assemble_laplacian(nx, ny, nz, h);
+  for (int c = 0; c < 3; ++c) csr_matvec(&L, x + (size_t)c * n, y + (size_t)c * n);
+  csr_free(&L);
+  double a = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double mk[3] = {m[k], m[n + k], m[2 * n + k]};
+    double yk[3] = {y[k], y[n + k], y[2 * n + k]};
+    double lk[3] = {lam[k], lam[n + k], lam[2 * n + k]};
+    double my = mk[0] * yk[0] + mk[1] * yk[1] + mk[2] * yk[2];
+    double lm = lk[0] * mk[0] + lk[1] * mk[1] + lk[2] * mk[2];
+    double ly = lk[0] * yk[0] + lk[1] * yk[1] + lk[2] * yk[2];
+    double mm = mk[0] * mk[0] + mk[1] * mk[1] + mk[2] * mk[2];
+    double yxl[3] = {yk[1] * lk[2] - yk[2] * lk[1], yk[2] * lk[0] - yk[0] * lk[2], yk[0] * lk[1] - yk[1] * lk[0]};
+    for (int c = 0; c < 3; ++c)
+      mbar[c * n + k] = lk[c] / dt - (yxl[c] + alpha * (my * lk[c] + lm * yk[c] - 2.0 * ly * mk[c]));
+    a += lm * my - mm * ly;
+  }
+  *abar = -a;
+  free(xbar);
+  free(lam);
+  free(y);
+  return st;
+}
+
 int orc_nlevels(const orc_hier *H) { return H->nlev; }
 int orc_level_cells(const orc_hier *H, int l) { return H->lev[l].n; }
 int orc_level_nnz(const orc_hier *H, int l) { return H->lev[l].A.rowptr[H->lev[l].A.nrows]; }
