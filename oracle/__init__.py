@@ -328,6 +328,9 @@ def loss_gradient(m0, m_target, n_steps, grid, h, alpha, dt, params: Params | No
         g, a, st, it, rr = step_vjp(ms[k], xs[k], g, grid, h, alpha, dt, params)
         abar += a
     return loss, g, abar
+
+
+def step_llg(m, n_steps, grid, h, alpha, dt, q=0.0, he=(0.0, 0.0, 0.0), params: Params | None = None):
     """Steps of the full model with explicit anisotropy and external field
     (eps folded into h); returns (m, iterations, relres, status)."""
     params = params or Params()
