@@ -291,6 +291,42 @@ int ll_mg_batch_level_colours(const ll_mg_batch* B, int level);
 int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i);
 void ll_mg_batch_destroy(ll_mg_batch* B);
 
+/* ---- differentiation of the time step (adjoint) ----------------------------
+ * A loss L on a later state depends on m^n through every step
+ *     m^{n+1}_k = x_k / |x_k|,   A(m^n) x = m^n / dt   (m~ = m^n, Sec. 2.1).
+ * The paper derives no adjoint; these calls give the exact discrete gradient
+ * of that map (up to the solver tolerances), for gradient-based fitting of
+ * initial states and damping.
+ *
+ * ll_mg_step_save: n_steps steps as ll_mg_step, also storing each step's
+ * solution before the projection: x_save (device) receives n_steps vectors
+ * of 3*N float64 (SoA), step k at offset 3*N*k.  Blocks until done. */
+int ll_mg_step_save(ll_mg_hierarchy* H, double* m, int n_steps, double* x_save, int* iters_per_step,
+                    double* relres_per_step);
+/* A one-instance batch (see above) that solves with the transposed operator
+ * A^T: the same aggregation and colouring as A's hierarchy, every level
+ * operator transposed ((P^T A P)^T = P^T A^T P), the transposed smoother and
+ * coarsest solve.  ll_mg_batch_update / ll_mg_batch_solve then solve
+ * A(m~)^T lambda = rhs.  Arguments and errors as ll_mg_setup; precision
+ * LL_FP64 or LL_MIXED_FP32, kcycle 0. */
+int ll_mg_adjoint_setup(const double* m_tilde, double alpha, double dt, double h, ll_grid grid,
+                        const ll_mg_params* p, void* cuda_stream, ll_mg_batch** out);
+/* Vector-Jacobian product of one step, on an adjoint context T:
+ *   m, x      device SoA 3*N: the step's input state m^n and its solution x
+ *             (ll_mg_step_save)
+ *   g         device SoA 3*N: dL/dm^{n+1}
+ *   m_bar     device SoA 3*N output: dL/dm^n
+ *   alpha_bar host output (or NULL): this step's part of dL/dalpha
+ *   rtol      tolerance of the adjoint solve (<= 0: the context's)
+ * With u = x/|x|:  xbar = (g - (u.g) u)/|x|,  A^T lambda = xbar,
+ *   m_bar = lambda/dt - [y x lambda + alpha((m.y) lambda + (lambda.m) y
+ *           - 2 (lambda.y) m)],   alpha_bar = -sum lambda.(m (m.y) - |m|^2 y),
+ * y = Delta_h x per cell.  Returns the adjoint solve's status (LL_OK,
+ * LL_NOT_CONVERGED, LL_BREAKDOWN; outputs written in all three) or an
+ * error.  Blocks until done. */
+int ll_mg_step_vjp(ll_mg_batch* T, const double* m, double alpha, double dt, const double* x, const double* g,
+                   double* m_bar, double* alpha_bar, double rtol, int* iterations, double* rel_residual);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,8 @@ EXPORTS = (
     "ll_mg_smooth", "ll_mg_step", "ll_launch_count", "ll_mg_profile", "ll_mg_profile_read",
     "ll_residual_noalloc", "ll_mg_step_llg", "ll_mg_batch_setup", "ll_mg_batch_update", "ll_mg_batch_solve",
     "ll_mg_batch_count", "ll_mg_batch_levels", "ll_mg_batch_level_rows", "ll_mg_batch_level_colours",
-    "ll_mg_batch_instance_levels", "ll_mg_batch_destroy",
+    "ll_mg_batch_instance_levels", "ll_mg_batch_destroy", "ll_mg_step_save", "ll_mg_adjoint_setup",
+    "ll_mg_step_vjp",
 )
 
 
@@ -122,6 +123,9 @@ def load_library():
         "ll_mg_batch_level_colours": (i, [vp, i]),
         "ll_mg_batch_instance_levels": (i, [vp, i]),
         "ll_mg_batch_destroy": (None, [vp]),
+        "ll_mg_step_save": (i, [vp, vp, i, vp, ip, dp]),
+        "ll_mg_adjoint_setup": (i, [vp, d, d, d, _Grid, P, vp, ctypes.POINTER(vp)]),
+        "ll_mg_step_vjp": (i, [vp, vp, d, d, vp, vp, vp, dp, d, ip, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -224,6 +228,22 @@ class Hierarchy:
             m.copy_(dev, non_blocking=False)
         return st, list(its[:n_steps]), list(rrs[:n_steps])
 
+    def step_save(self, m, x_save, n_steps: int = 1):
+        """n_steps steps in place (``ll_mg_step_save``); x_save (CUDA,
+        3*N*n_steps) receives each step's solution before the projection."""
+        import torch
+
+        if x_save.dtype != torch.float64 or not x_save.is_cuda:
+            raise TypeError("x_save must be a float64 CUDA tensor")
+        if x_save.numel() != 3 * self.n * n_steps or not x_save.is_contiguous():
+            raise ValueError("x_save must hold 3*N*n_steps contiguous values")
+        its = (ctypes.c_int * max(1, n_steps))()
+        rrs = (ctypes.c_double * max(1, n_steps))()
+        st = load_library().ll_mg_step_save(self._h, _field(m, self.n, "m"), int(n_steps),
+                                            ctypes.c_void_p(x_save.data_ptr()), its, rrs)
+        _check(st, "ll_mg_step_save")
+        return st, list(its[:n_steps]), list(rrs[:n_steps])
+
     def step_llg(self, m, n_steps: int = 1, q: float = 0.0, he=(0.0, 0.0, 0.0)):
         """Time steps with the explicit anisotropy and external-field terms
         (``ll_mg_step_llg``); set the hierarchy up with h/sqrt(eps)."""
@@ -303,6 +323,137 @@ def residual_noalloc(m_tilde, alpha, dt, h, grid, rhs, x, r=None, norms2=None):
                                             ctypes.c_void_p(norms2.data_ptr()), _stream())
     _check(st, "ll_residual_noalloc", ok=(LL_OK,))
     return norms2
+
+
+class Adjoint:
+    """Solves with A(m~)^T and vector-Jacobian products of single steps
+    (``ll_mg_adjoint_setup`` / ``ll_mg_step_vjp``)."""
+
+    def __init__(self, m_tilde, alpha, dt, h, grid, params: Params | None = None):
+        lib = load_library()
+        g = _grid(grid)
+        self.grid = (g.nx, g.ny, g.nz)
+        self.n = g.nx * g.ny * g.nz
+        self.params = params or Params()
+        self._cp = self.params._c()
+        self._h = ctypes.c_void_p()
+        st = lib.ll_mg_adjoint_setup(_field(m_tilde, self.n, "m_tilde"), float(alpha), float(dt), float(h), g,
+                                     ctypes.byref(self._cp), _stream(), ctypes.byref(self._h))
+        _check(st, "ll_mg_adjoint_setup", ok=(LL_OK,))
+
+    def close(self):
+        if self._h:
+            load_library().ll_mg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, m_tilde, alpha, dt):
+        a = (ctypes.c_double * 1)(float(alpha))
+        d = (ctypes.c_double * 1)(float(dt))
+        st = load_library().ll_mg_batch_update(self._h, _ptrs([m_tilde], [self.n], "m_tilde"), a, d)
+        _check(st, "ll_mg_batch_update", ok=(LL_OK,))
+
+    def solve(self, rhs, lam, rtol: float = 0.0):
+        """A^T lam = rhs in place; returns (status, iterations, relres)."""
+        its = (ctypes.c_int * 1)()
+        rrs = (ctypes.c_double * 1)()
+        sts = (ctypes.c_int * 1)()
+        st = load_library().ll_mg_batch_solve(self._h, _ptrs([rhs], [self.n], "rhs"), _ptrs([lam], [self.n], "x"),
+                                              float(rtol), its, rrs, sts)
+        _check(st, "ll_mg_batch_solve")
+        return st, its[0], rrs[0]
+
+    def vjp(self, m, alpha, dt, x, g, m_bar=None, rtol: float = 0.0):
+        """(dL/dm^n, dL/dalpha part, status, iterations, relres) of one step
+        m^n -> x/|x| for g = dL/dm^{n+1}."""
+        import torch
+
+        if m_bar is None:
+            m_bar = torch.empty_like(m)
+        ab = ctypes.c_double(0.0)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load_library().ll_mg_step_vjp(self._h, _field(m, self.n, "m"), float(alpha), float(dt),
+                                           _field(x, self.n, "x"), _field(g, self.n, "g"),
+                                           _field(m_bar, self.n, "m_bar"), ctypes.byref(ab), float(rtol),
+                                           ctypes.byref(it), ctypes.byref(rr))
+        _check(st, "ll_mg_step_vjp")
+        return m_bar, ab.value, st, it.value, rr.value
+
+
+def _steps_function():
+    import torch
+
+    class _Steps(torch.autograd.Function):
+        """m^N of n_steps semi-implicit steps, differentiable in m^0 and
+        alpha; the backward pass recomputes each segment of `checkpoint`
+        steps from its stored initial state, then runs the step VJPs
+        backwards through it."""
+
+        @staticmethod
+        def forward(ctx, m0, alpha, n_steps, dt, h, grid, params, checkpoint):
+            a = float(alpha)
+            H = Hierarchy(m0.detach(), a, dt, h, grid, params)
+            m = m0.detach().clone()
+            x = torch.empty_like(m)
+            ckpt = {0: m.clone()}
+            for k in range(n_steps):
+                H.step_save(m, x)
+                if (k + 1) % checkpoint == 0 and k + 1 < n_steps:
+                    ckpt[k + 1] = m.clone()
+            ctx.H, ctx.ckpt, ctx.cfg = H, ckpt, (a, n_steps, dt, h, grid, params, checkpoint)
+            ctx.save_for_backward(m0)
+            return m
+
+        @staticmethod
+        def backward(ctx, g_out):
+            (m0,) = ctx.saved_tensors
+            a, n_steps, dt, h, grid, params, checkpoint = ctx.cfg
+            H = ctx.H
+            T = Adjoint(m0.detach(), a, dt, h, grid, params)
+            g = g_out.detach().contiguous().clone()
+            abar = 0.0
+            x = torch.empty_like(g)
+            for s0 in sorted(ctx.ckpt, reverse=True):
+                s1 = min(s0 + checkpoint, n_steps)
+                m = ctx.ckpt[s0].clone()
+                ms, xs = [], []
+                for _ in range(s0, s1):  # recompute the segment's states and solutions
+                    ms.append(m.clone())
+                    H.step_save(m, x)
+                    xs.append(x.clone())
+                for k in range(len(ms) - 1, -1, -1):
+                    g, ak, st, it, rr = T.vjp(ms[k], a, dt, xs[k], g)
+                    abar += ak
+            T.close()
+            galpha = torch.tensor(abar, dtype=torch.float64) if ctx.needs_input_grad[1] else None
+            return g, galpha, None, None, None, None, None, None
+
+    return _Steps
+
+
+_STEPS = None
+
+
+def steps_autograd(m0, alpha, n_steps: int, dt, h, grid, params: Params | None = None, checkpoint: int = 5):
+    """m^N after n_steps steps from m0 (float64 CUDA tensor), differentiable
+    with respect to m0 and alpha (a float or a 0-dim float64 tensor) through
+    the library's adjoint; states are stored every `checkpoint` steps and the
+    rest recomputed in the backward pass."""
+    import torch
+
+    global _STEPS
+    if _STEPS is None:
+        _STEPS = _steps_function()
+    if not isinstance(alpha, torch.Tensor):
+        alpha = torch.tensor(float(alpha), dtype=torch.float64)
+    return _STEPS.apply(m0, alpha, int(n_steps), float(dt), float(h), tuple(grid), params or Params(),
+                        int(checkpoint))
 
 
 def _ptrs(tensors, ns, name):

@@ -20,13 +20,15 @@
 struct ll_mg_batch {
   ll_mg_params prm;
   int ninst = 0;
+  bool transposed = false;  // the instances' A^T (adjoint solves)
   cudaStream_t user = nullptr;
   cudaEvent_t entry_ev = nullptr;
   std::vector<ll_mg_hierarchy*> inst;
   ll_mg_hierarchy* U = nullptr;  // union hierarchy; its stream is the batch's
   // rmap[i][l]: rows of instance i's level l (l = 0: red-black slots) -> union rows
   // bmap[i][l] (l >= 1): blocks of instance i's level l -> union blocks
-  std::vector<std::vector<llmg::DBuf<int>*>> rmap, bmap;
+  std::vector<std::vector<llmg::DBuf<int>*>> rmap, bmap, tmap;  // tmap: transposed block positions
+  llmg::DBuf<int> bad;
   std::vector<std::vector<int>> eoff;  // union row of instance i's coarsest level (per level, -1 if not ending)
   int S0 = 0;                          // union rows of level-0 class 0
   std::vector<int> off0;               // union row of instance i's first colour-0 slot
@@ -49,6 +51,8 @@ struct ll_mg_batch {
     for (auto& v : rmap)
       for (auto* b : v) delete b;
     for (auto& v : bmap)
+      for (auto* b : v) delete b;
+    for (auto& v : tmap)
       for (auto* b : v) delete b;
     if (h_head) cudaFreeHost(h_head);
     if (h_flags) cudaFreeHost(h_flags);
@@ -85,6 +89,7 @@ void batch_symbolic(ll_mg_batch* B) {
   U->nlev = nlev;
   B->rmap.assign(ni, std::vector<DBuf<int>*>(nlev, nullptr));
   B->bmap.assign(ni, std::vector<DBuf<int>*>(nlev, nullptr));
+  B->tmap.assign(ni, std::vector<DBuf<int>*>(nlev, nullptr));
   B->eoff.assign(ni, std::vector<int>(nlev, -1));
   // ---- row maps, level 0: class c = every instance's colour-c slots
   B->off0.assign(ni, 0);
@@ -202,6 +207,12 @@ void batch_symbolic(ll_mg_batch* B) {
         B->bmap[i][l]->alloc(Li.nnzb);
         kb_union_pattern<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, Li.col, Li.diag, *B->rmap[i][l],
                                                                L.rowptr, L.col, L.diag, *B->bmap[i][l]);
+        if (B->transposed) {
+          LL_LAUNCHED();
+          B->tmap[i][l] = new DBuf<int>();
+          B->tmap[i][l]->alloc(Li.nnzb);
+          kb_transpose_pos<<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, Li.col, *B->tmap[i][l]);
+        }
       }
       LL_LAUNCHED();
     }
@@ -317,21 +328,39 @@ void batch_values(ll_mg_batch* B) {
   cudaStream_t s = U->s;
   for (auto* H : B->inst) LL_CU(cudaStreamSynchronize(H->s));
   bool mixed = !std::is_same<T, double>::value;
+  if (B->transposed) B->bad.zero(s);
   for (int i = 0; i < B->ninst; ++i) {
     ll_mg_hierarchy* H = B->inst[i];
     CLevel& L0 = U->lev[0];
-    kb_union_l0_values<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, *B->rmap[i][0], L0.rowptr, L0.diag,
-                                                                H->chat64, H->dinv0<T>(), 1.0 / H->dt, L0.val64,
-                                                                mixed ? (T*)L0.val32.p : (T*)nullptr, L0.dinv<T>());
+    T* valt = mixed ? (T*)L0.val32.p : (T*)nullptr;
+    if (B->transposed)
+      kb_union_l0_values_t<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, *B->rmap[i][0], L0.rowptr, H->chat64,
+                                                                    H->dinv0<T>(), 1.0 / H->dt, L0.val64, valt,
+                                                                    L0.dinv<T>());
+    else
+      kb_union_l0_values<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, *B->rmap[i][0], L0.rowptr, L0.diag,
+                                                                  H->chat64, H->dinv0<T>(), 1.0 / H->dt, L0.val64,
+                                                                  valt, L0.dinv<T>());
     LL_LAUNCHED();
     for (int l = 1; l < H->nlev; ++l) {
       CLevel& Li = H->lev[l];
       CLevel& L = U->lev[l];
-      kb_union_values<TM, T><<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, *B->bmap[i][l],
-                                                                   *B->rmap[i][l], Li.valm<TM>(), Li.dinv<T>(),
-                                                                   L.valm<TM>(), L.dinv<T>());
+      if (B->transposed)
+        kb_union_values_t<TM, T><<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(
+            Li.n, Li.rowptr, *B->bmap[i][l], *B->tmap[i][l], *B->rmap[i][l], Li.valm<TM>(), Li.dinv<T>(),
+            L.valm<TM>(), L.dinv<T>(), B->bad);
+      else
+        kb_union_values<TM, T><<<cdiv(Li.n, kBlock), kBlock, 0, s>>>(Li.n, Li.rowptr, *B->bmap[i][l],
+                                                                     *B->rmap[i][l], Li.valm<TM>(), Li.dinv<T>(),
+                                                                     L.valm<TM>(), L.dinv<T>());
       LL_LAUNCHED();
     }
+  }
+  if (B->transposed) {
+    int bad = 0;
+    LL_CU(cudaMemcpyAsync(&bad, B->bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CU(cudaStreamSynchronize(s));
+    if (bad) throw Status{LL_ECUDA};  // a pattern without its transpose: not a Galerkin level
   }
   LL_CU(cudaStreamSynchronize(s));
 }
@@ -559,12 +588,15 @@ int batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x, doub
 }
 
 int batch_create(int count, const double* const* m, const double* alpha, const double* dt, const double* h,
-                 const ll_grid* grids, const ll_mg_params* p, void* stream, ll_mg_batch** out) {
+                 const ll_grid* grids, const ll_mg_params* p, void* stream, ll_mg_batch** out,
+                 bool transposed = false) {
   ll_mg_batch* B = nullptr;
   try {
     B = new ll_mg_batch();
     ll_mg_default_params(&B->prm);
     if (p) B->prm = *p;
+    B->transposed = transposed;
+    if (transposed) B->bad.alloc(1);
     B->ninst = count;
     B->user = (cudaStream_t)stream;
     LL_CU(cudaEventCreateWithFlags(&B->entry_ev, cudaEventDisableTiming));

@@ -164,6 +164,143 @@ __global__ void kb_union_values(int n, const int* __restrict__ rp, const int* __
   for (int e = 0; e < 9; ++e) udinv[9 * R + e] = dinv[9L * r + e];
 }
 
+// ---- the transposed operator A^T (adjoint solves) -------------------------
+// level 0: (A^T)_kk = I/dt - deg C^_k^T, (A^T)_kj = C^_j^T for a face
+// neighbour j (A_kj = C^_k couples row k through its own coefficient, so the
+// transpose carries the neighbour's); D^-1 transposed.  Same block order as
+// kb_union_l0_pattern.
+template <typename T>
+__global__ void kb_union_l0_values_t(GridGeom g, const int* __restrict__ map, const int* __restrict__ urp,
+                                     const double* __restrict__ chat, const T* __restrict__ dinv, double inv_dt,
+                                     double* __restrict__ val64, T* __restrict__ valt, T* __restrict__ dinvt) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  int R = map[sl];
+  long nb[6];
+  int d = p.real ? slot_neighbours(g, c, p, nb) : 0;
+  double D[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      D[3 * a + b] = (a == b ? inv_dt : 0.0) - (p.real ? d * chat[(3 * b + a) * n2 + sl] : 0.0);
+  int q = urp[R];
+  auto put = [&](const double* blk) {
+    for (int e = 0; e < 9; ++e) {
+      val64[9L * q + e] = blk[e];
+      if (valt) valt[9L * q + e] = (T)blk[e];
+    }
+    ++q;
+  };
+  if (c == 0) put(D);
+  for (int t = 0; t < d; ++t) {
+    double Cn[9];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Cn[3 * a + b] = chat[(3 * b + a) * n2 + nb[t]];
+    put(Cn);
+  }
+  if (c == 1) put(D);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      dinvt[9L * R + 3 * a + b] = p.real ? dinv[(3 * b + a) * n2 + sl] : (a == b ? (T)(1.0 / inv_dt) : (T)0);
+}
+
+// coarse levels: block position of (J, I) for every block (I, J) of a BSR
+// level with a symmetric pattern (-1 if absent, which a Galerkin pattern
+// built from an undirected graph never is)
+__global__ void kb_transpose_pos(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 int* __restrict__ tpos) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int p = rp[r]; p < rp[r + 1]; ++p) {
+    int J = col[p], f = -1;
+    for (int q = rp[J]; q < rp[J + 1]; ++q)
+      if (col[q] == r) f = q;
+    tpos[p] = f;
+  }
+}
+// (A^T)_IJ = (A_JI)^T through tpos and bmap; D^-1 transposed
+template <typename TM, typename T>
+__global__ void kb_union_values_t(int n, const int* __restrict__ rp, const int* __restrict__ bmap,
+                                  const int* __restrict__ tpos, const int* __restrict__ map,
+                                  const TM* __restrict__ val, const T* __restrict__ dinv, TM* __restrict__ uval,
+                                  T* __restrict__ udinv, int* __restrict__ bad) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int p = rp[r]; p < rp[r + 1]; ++p) {
+    int t = tpos[p];
+    if (t < 0) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) uval[9L * bmap[p] + 3 * a + b] = val[9L * t + 3 * b + a];
+  }
+  long R = map[r];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) udinv[9 * R + 3 * a + b] = dinv[9L * r + 3 * b + a];
+}
+
+// ---- one step's vector-Jacobian product (natural SoA, float64) ------------
+// xbar = (g - (u.g) u)/|x|, u = x/|x|: the transpose of the projection's
+// Jacobian applied to g
+__global__ void k_vjp_xbar(long n, const double* __restrict__ x, const double* __restrict__ g,
+                           double* __restrict__ xbar) {
+  long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double v0 = x[k], v1 = x[n + k], v2 = x[2 * n + k];
+  double nrm = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+  double u0 = v0 / nrm, u1 = v1 / nrm, u2 = v2 / nrm;
+  double g0 = g[k], g1 = g[n + k], g2 = g[2 * n + k];
+  double ug = u0 * g0 + u1 * g1 + u2 * g2;
+  xbar[k] = (g0 - ug * u0) / nrm;
+  xbar[n + k] = (g1 - ug * u1) / nrm;
+  xbar[2 * n + k] = (g2 - ug * u2) / nrm;
+}
+
+// mbar_k = lambda_k/dt - [y x lambda + alpha((m.y) lambda + (lambda.m) y
+// - 2 (lambda.y) m)]_k with y = Delta_h x, and partial sums of
+// lambda.(m (m.y) - |m|^2 y) (dL/dalpha is minus their total)
+__global__ void __launch_bounds__(256) k_vjp_param(int nx, int ny, int nz, const double* __restrict__ m,
+                                                   const double* __restrict__ x, const double* __restrict__ lam,
+                                                   double alpha, double inv_dt, double ih2,
+                                                   double* __restrict__ mbar, double* __restrict__ partial) {
+  long n = (long)nx * ny * nz;
+  double acc[1] = {0};
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int i = (int)(k % nx);
+    long t = k / nx;
+    int j = (int)(t % ny), l = (int)(t / ny);
+    long nxy = (long)nx * ny;
+    long nb[6];
+    int d = 0;
+    if (l > 0) nb[d++] = k - nxy;
+    if (j > 0) nb[d++] = k - nx;
+    if (i > 0) nb[d++] = k - 1;
+    if (i < nx - 1) nb[d++] = k + 1;
+    if (j < ny - 1) nb[d++] = k + nx;
+    if (l < nz - 1) nb[d++] = k + nxy;
+    double y[3];
+    for (int c = 0; c < 3; ++c) {
+      double s = 0;
+      for (int q = 0; q < d; ++q) s += x[c * n + nb[q]];
+      y[c] = (s - d * x[c * n + k]) * ih2;
+    }
+    double mk[3] = {m[k], m[n + k], m[2 * n + k]};
+    double lk[3] = {lam[k], lam[n + k], lam[2 * n + k]};
+    double my = mk[0] * y[0] + mk[1] * y[1] + mk[2] * y[2];
+    double lm = lk[0] * mk[0] + lk[1] * mk[1] + lk[2] * mk[2];
+    double ly = lk[0] * y[0] + lk[1] * y[1] + lk[2] * y[2];
+    double mm = mk[0] * mk[0] + mk[1] * mk[1] + mk[2] * mk[2];
+    double yxl[3] = {y[1] * lk[2] - y[2] * lk[1], y[2] * lk[0] - y[0] * lk[2], y[0] * lk[1] - y[1] * lk[0]};
+    for (int c = 0; c < 3; ++c)
+      mbar[c * n + k] = lk[c] * inv_dt - (yxl[c] + alpha * (my * lk[c] + lm * y[c] - 2.0 * ly * mk[c]));
+    acc[0] += lm * my - mm * ly;
+  }
+  block_reduce_store<1>(acc, partial, 1);
+}
+
 // natural SoA vector of one instance <-> union level-0 rows (cell-major)
 template <typename TI, typename TO>
 __global__ void kb_union_in(GridGeom g, const int* __restrict__ nat_of_slot, const int* __restrict__ map,

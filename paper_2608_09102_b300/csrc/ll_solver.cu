@@ -1226,7 +1226,7 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 // time steps on an existing hierarchy; fresh = numeric setup already done for
 // m; src = explicit source terms (q, he0, he1, he2) or NULL
 static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step,
-                 bool fresh, const double* src = nullptr) {
+                 bool fresh, const double* src = nullptr, double* x_save = nullptr) {
   int worst = LL_OK;
   double dt = H->dt;
   try {
@@ -1246,6 +1246,9 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
       if (iters_per_step) iters_per_step[k] = it;
       if (relres_per_step) relres_per_step[k] = rr;
       worst = std::max(worst, s2);
+      if (x_save)  // the solution before the projection, step k
+        LL_CU(cudaMemcpyAsync(x_save + (size_t)k * n3, H->stepx.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                              H->s));
       H->flag.zero(H->s);
       k_renormalise<<<cdiv(H->g.n, kBlock), kBlock, 0, H->s>>>(H->g.n, H->stepx, m, H->flag);
       LL_LAUNCHED();
@@ -1291,6 +1294,19 @@ int ll_mg_step_llg(ll_mg_hierarchy* H, double* m, int n_steps, double q, const d
     return st.code;
   }
   return steps(H, m, n_steps, iters_per_step, relres_per_step, false, src);
+}
+
+int ll_mg_step_save(ll_mg_hierarchy* H, double* m, int n_steps, double* x_save, int* iters_per_step,
+                    double* relres_per_step) {
+  if (!H || !m || !x_save || n_steps < 0) return LL_EINVAL;
+  try {
+    enter(H);
+  } catch (Status st) {
+    return st.code;
+  }
+  int st = steps(H, m, n_steps, iters_per_step, relres_per_step, false, nullptr, x_save);
+  cudaStreamSynchronize(H->s);
+  return st;
 }
 
 long long ll_launch_count(void) { return g_launches.load(); }
@@ -1558,5 +1574,53 @@ int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i) {
 }
 
 void ll_mg_batch_destroy(ll_mg_batch* B) { delete B; }
+
+// ---------------------------------------------------------------------------
+// adjoint: A^T solves and the vector-Jacobian product of one step
+// ---------------------------------------------------------------------------
+int ll_mg_adjoint_setup(const double* m_tilde, double alpha, double dt, double h, ll_grid grid,
+                        const ll_mg_params* p, void* cuda_stream, ll_mg_batch** out) {
+  if (!m_tilde || !out || !valid_problem(alpha, dt, h, grid)) return LL_EINVAL;
+  if (p && !valid_params(*p)) return LL_EINVAL;
+  if (p && (p->kcycle != 0 || p->precision == LL_MIXED_BF16)) return LL_EINVAL;
+  const double* ms[1] = {m_tilde};
+  return batch_create(1, ms, &alpha, &dt, &h, &grid, p, cuda_stream, out, true);
+}
+
+int ll_mg_step_vjp(ll_mg_batch* T, const double* m, double alpha, double dt, const double* x, const double* g,
+                   double* m_bar, double* alpha_bar, double rtol, int* iterations, double* rel_residual) {
+  if (!T || !T->transposed || T->ninst != 1 || !m || !x || !g || !m_bar) return LL_EINVAL;
+  if (!(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha)) return LL_EINVAL;
+  try {
+    batch_enter(T);
+    LL_CU(cudaStreamSynchronize(T->U->s));
+    ll_mg_hierarchy* H = T->inst[0];
+    cudaStream_t s = T->U->s;
+    H->alpha = alpha;
+    H->dt = dt;
+    numeric(H, m);
+    batch_refresh(T);
+    long n = H->g.n;
+    k_vjp_xbar<<<cdiv(n, kBlock), kBlock, 0, s>>>(n, x, g, H->stepb);
+    LL_LAUNCHED();
+    LL_CU(cudaMemsetAsync(H->stepx.p, 0, 3 * n * sizeof(double), s));
+    const double* rhs[1] = {H->stepb.p};
+    double* lam[1] = {H->stepx.p};
+    int st1 = LL_OK;
+    int rc = batch_solve(T, rhs, lam, rtol, iterations, rel_residual, &st1);
+    k_vjp_param<<<kRedBlocks, kBlock, 0, s>>>(H->g.nx, H->g.ny, H->g.nz, m, x, H->stepx, alpha, 1.0 / dt,
+                                              1.0 / (H->h * H->h), m_bar, H->partial);
+    LL_LAUNCHED();
+    k_finish<<<1, kBlock, 0, s>>>(H->partial, H->partial.p + kRedBlocks);
+    LL_LAUNCHED();
+    double a = 0;
+    LL_CU(cudaMemcpyAsync(&a, H->partial.p + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LL_CU(cudaStreamSynchronize(s));
+    if (alpha_bar) *alpha_bar = -a;
+    return rc;
+  } catch (Status st) {
+    return st.code;
+  }
+}
 
 }  // extern "C"
