@@ -418,6 +418,64 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# differentiation workload (measured on request)
+# ---------------------------------------------------------------------------
+GRAD_WORKLOAD = ("3-D 96^3, alpha 0.1, dt 1e-3, 20 steps, loss 0.5|m^20 - m_target|^2 (smooth unit fields, seeds "
+                 "0 and 1), gradient in m^0 and alpha by the adjoint with checkpoints every 5 steps, rtol 1e-8")
+
+
+def run_grad(args):
+    import torch
+
+    import paper_2608_09102_b300 as ll
+    from paper_2608_09102_b300 import build, inputs
+
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    grid, alpha, dt, n_steps, h = (96, 96, 96), 0.1, 1e-3, 20, 1.0 / 96
+    n = 96 ** 3
+    m0 = torch.tensor(inputs.smooth_field(*grid, seed=0).reshape(-1), device=dev)
+    mt = torch.tensor(inputs.smooth_field(*grid, seed=1).reshape(-1), device=dev)
+    precision = {"fp64": ll.LL_FP64, "mixed": ll.LL_MIXED_FP32}[args.precision]
+    p = ll.Params(rtol=RTOL, precision=precision)
+
+    def grad():
+        m = m0.clone().requires_grad_(True)
+        a = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+        mN = ll.steps_autograd(m, a, n_steps, dt, h, grid, p, checkpoint=5)
+        loss = 0.5 * torch.sum((mN - mt) ** 2)
+        loss.backward()
+        return float(loss.detach()), m.grad, float(a.grad)
+
+    for _ in range(args.warmup):
+        grad()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    launches0 = ll.launch_count()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        loss, gm, ga = grad()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    solves = 3 * n_steps  # forward, recomputed forward, adjoint
+    line = {"metric": "gradient evaluations/s", "value": 1e3 / ms, "unit": "gradients/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision], "data": "synthetic",
+            "config": {"workload": GRAD_WORKLOAD, "unknowns": 3 * n, "precision": args.precision},
+            "unknown_solves_per_s": solves * 3 * n / (ms * 1e-3), "solves_per_gradient": solves,
+            "loss": loss, "grad_norm_m0": float(torch.linalg.norm(gm)), "grad_alpha": ga,
+            "gpu_launches": int(ll.launch_count() - launches0), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,8 +486,9 @@ def main():
     ap.add_argument("--kcycle", type=int, default=0,
                     help="coarse levels 1..K solved by two inner GCR steps (K-cycle); 0 = V-cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["step128", "batch512"], default="step128",
-                    help="step128: the 128^3 time-stepping workload; batch512: the ragged batch")
+    ap.add_argument("--workload", choices=["step128", "batch512", "grad96"], default="step128",
+                    help="step128: the 128^3 time-stepping workload; batch512: the ragged batch; "
+                         "grad96: the 96^3 differentiation workload")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--batch-maxit", type=int, default=300)
     args = ap.parse_args()
@@ -437,6 +496,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch512":
         run_batch(args)
+    elif args.workload == "grad96":
+        run_grad(args)
     else:
         run_ours(args)
 
