@@ -262,7 +262,9 @@ void batch_symbolic(ll_mg_batch* B) {
         L.pre_blk[c] += dg[I] - rp[I];
         L.off_blk[c] += rp[I + 1] - rp[I] - 1;
       }
-    L.res_blk = rp[L.ncol > 0 ? L.cs[L.ncol - 1] : 0];
+    L.res_blk = 0;
+    for (int I = 0; I < (L.ncol > 0 ? L.cs[L.ncol - 1] : 0); ++I)
+      L.res_blk += B->prm.nu_pre == 1 ? rp[I + 1] - dg[I] - 1 : rp[I + 1] - rp[I];
   }
 }
 

@@ -436,7 +436,31 @@ __device__ __forceinline__ void slot_residual(const GridGeom& g, int c, long sl,
 // Residual and restriction (P^T) in one pass: bc_I = sum over the members k
 // of aggregate I of (b - A x)_k.  After a forward half-sweep of colour 1 the
 // colour-1 residuals vanish, so only the colour-0 members are listed.
+// Residual of a colour-0 cell right after one forward red-black sweep from
+// x = 0: the cell was solved with its neighbours (all colour 1) still zero,
+// so b_k - D_k x_k = 0 and only the neighbours' later update remains:
+//   r_k = - C^_k sum_{j ~ k} x_j   (exact up to rounding).
 template <typename T>
+__device__ __forceinline__ void slot_residual_after_sweep(const GridGeom& g, long sl, const SlotPos& p,
+                                                          const T* x, const T* chat, T* r) {
+  long n2 = 2 * g.nh;
+  long nb[6];
+  int d = slot_neighbours(g, 0, p, nb);
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int q = 0; q < d; ++q) {
+    long l = nb[q];
+    s0 += x[l];
+    s1 += x[n2 + l];
+    s2 += x[2 * n2 + l];
+  }
+  const T* C = chat + sl;
+  r[0] = -(ld(C) * s0 + ld(C + n2) * s1 + ld(C + 2 * n2) * s2);
+  r[1] = -(ld(C + 3 * n2) * s0 + ld(C + 4 * n2) * s1 + ld(C + 5 * n2) * s2);
+  r[2] = -(ld(C + 6 * n2) * s0 + ld(C + 7 * n2) * s1 + ld(C + 8 * n2) * s2);
+}
+
+// SHORT: one forward sweep preceded (the residual of slot_residual_after_sweep)
+template <typename T, bool SHORT>
 __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* __restrict__ x,
                             const T* __restrict__ chat, T inv_dt, int nc, const int* __restrict__ mptr,
                             const int* __restrict__ mem, T* __restrict__ bc, int init_end,
@@ -452,7 +476,8 @@ __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* _
     int c = (int)(sl / g.nh);
     SlotPos p = slot_pos(g, c, sl % g.nh);
     T r[3];
-    slot_residual<T, T>(g, c, sl, p, b, x, chat, inv_dt, r);
+    if (SHORT) slot_residual_after_sweep<T>(g, sl, p, x, chat, r);
+    else slot_residual<T, T>(g, c, sl, p, b, x, chat, inv_dt, r);
     a0 += r[0];
     a1 += r[1];
     a2 += r[2];
@@ -529,18 +554,27 @@ __device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
 
+// Loads of the operator, its structure and the transfers, which no kernel
+// of a solve writes, go through the read-only data path: its cache lines
+// survive the cluster barriers of the coarse tail (whose acquire side
+// invalidates the coherent L1 lines), so a phase reads them from L1.
+template <typename V>
+__device__ __forceinline__ V ro(const V* p) {
+  return __ldg(p);
+}
+
 // a -= A_IJ v  for one 3x3 block stored as TM (negated fused multiply-adds)
 template <typename T, typename TM>
 __device__ __forceinline__ void block_msub(const TM* __restrict__ A, T v0, T v1, T v2, T& a0, T& a1, T& a2) {
-  a0 = fma(-widen<T, TM>(A[0]), v0, a0);
-  a0 = fma(-widen<T, TM>(A[1]), v1, a0);
-  a0 = fma(-widen<T, TM>(A[2]), v2, a0);
-  a1 = fma(-widen<T, TM>(A[3]), v0, a1);
-  a1 = fma(-widen<T, TM>(A[4]), v1, a1);
-  a1 = fma(-widen<T, TM>(A[5]), v2, a1);
-  a2 = fma(-widen<T, TM>(A[6]), v0, a2);
-  a2 = fma(-widen<T, TM>(A[7]), v1, a2);
-  a2 = fma(-widen<T, TM>(A[8]), v2, a2);
+  a0 = fma(-widen<T, TM>(ro(A + 0)), v0, a0);
+  a0 = fma(-widen<T, TM>(ro(A + 1)), v1, a0);
+  a0 = fma(-widen<T, TM>(ro(A + 2)), v2, a0);
+  a1 = fma(-widen<T, TM>(ro(A + 3)), v0, a1);
+  a1 = fma(-widen<T, TM>(ro(A + 4)), v1, a1);
+  a1 = fma(-widen<T, TM>(ro(A + 5)), v2, a1);
+  a2 = fma(-widen<T, TM>(ro(A + 6)), v0, a2);
+  a2 = fma(-widen<T, TM>(ro(A + 7)), v1, a2);
+  a2 = fma(-widen<T, TM>(ro(A + 8)), v2, a2);
 }
 
 // a -= sum over the blocks p = p0, p0 + G, ... < p1 of A_p v_{col p}, with the
@@ -554,7 +588,7 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
   for (int base = p0; base < p1; base += G * U) {
     int J[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) J[u] = base + u * G < p1 ? col[base + u * G] : -1;
+    for (int u = 0; u < U; ++u) J[u] = base + u * G < p1 ? ro(col + base + u * G) : -1;
     T v[U][3];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -563,7 +597,7 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
         v[u][1] = x[3L * J[u] + 1];
         v[u][2] = x[3L * J[u] + 2];
         if (PROL) {
-          long a = 3L * agg[J[u]];
+          long a = 3L * ro(agg + J[u]);
           v[u][0] += e[a];
           v[u][1] += e[a + 1];
           v[u][2] += e[a + 2];
@@ -593,7 +627,7 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
     for (int u = 0; u < U; ++u) {
       int q = base + u * G;
       P[u] = p0 + q + (q >= npre ? 1 : 0);
-      J[u] = q < noff ? col[P[u]] : -1;
+      J[u] = q < noff ? ro(col + P[u]) : -1;
     }
     T v[U][3];
 #pragma unroll
@@ -603,7 +637,7 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
         v[u][1] = x[3L * J[u] + 1];
         v[u][2] = x[3L * J[u] + 2];
         if (PROL && base + u * G < npre) {
-          long a = 3L * agg[J[u]];
+          long a = 3L * ro(agg + J[u]);
           v[u][0] += e[a];
           v[u][1] += e[a + 1];
           v[u][2] += e[a + 2];
@@ -629,26 +663,31 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
 //           prolongation, never stored).
 // x_I = Dinv_I (b_I - sum_{J != I} A_IJ v_J); the lanes of a group share the
 // three output components.  Every lane of the warp must call this (shuffles).
-template <typename T, typename TM, int G, int MODE>
+template <typename T, typename TM, int G, int MODE, int U = 4>
 __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
                                           const int* __restrict__ diag, const int* __restrict__ col,
                                           const TM* __restrict__ val, const T* __restrict__ dinv,
                                           const T* __restrict__ b, T* __restrict__ x, const int* __restrict__ agg,
                                           const T* __restrict__ e) {
-  T a0 = 0, a1 = 0, a2 = 0;
+  static_assert(G >= 3, "one lane per output component");
+  T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, d0 = 0, d1 = 0, d2 = 0;
   if (active) {
-    int pd = diag[I];
-    if (MODE == 0) row_msub<T, TM, G, 4, false>(rowptr[I] + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-    else row_msub_off<T, TM, G, 4, MODE == 2>(rowptr[I], pd, rowptr[I + 1], lane, col, val, x, agg, e, a0, a1, a2);
+    // b and this lane's row of D^-1 first: off the row's dependent chain
+    b0 = b[3L * I];
+    b1 = b[3L * I + 1];
+    b2 = b[3L * I + 2];
+    if (lane < 3) {
+      const T* D = dinv + 9L * I + 3 * lane;
+      d0 = ro(D);
+      d1 = ro(D + 1);
+      d2 = ro(D + 2);
+    }
+    int p0 = ro(rowptr + I), pd = ro(diag + I);
+    if (MODE == 0) row_msub<T, TM, G, U, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
+    else row_msub_off<T, TM, G, U, MODE == 2>(p0, pd, ro(rowptr + I + 1), lane, col, val, x, agg, e, a0, a1, a2);
   }
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
-  if (active) {
-    T v0 = b[3L * I] + a0, v1 = b[3L * I + 1] + a1, v2 = b[3L * I + 2] + a2;
-    for (int c = lane; c < 3; c += G) {
-      const T* D = dinv + 9L * I + 3 * c;
-      x[3L * I + c] = D[0] * v0 + D[1] * v1 + D[2] * v2;
-    }
-  }
+  if (active && lane < 3) x[3L * I + lane] = d0 * (b0 + a0) + d1 * (b1 + a1) + d2 * (b2 + a2);
 }
 
 template <typename T, typename TM, int G, int MODE>
@@ -662,27 +701,37 @@ __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __res
   sweep_row<T, TM, G, MODE>(I, threadIdx.x % G, I < r1, rowptr, diag, col, val, dinv, b, x, agg, e);
 }
 
-// r_I = b_I - (A x)_I, G lanes per row (all lanes of the warp call it)
-template <typename T, typename TM, int G>
+// r_I = b_I - (A x)_I, G lanes per row (all lanes of the warp call it).
+// SUFFIX: right after one forward block-GS sweep from x = 0, row I was
+// updated as x_I = D_I^-1 (b_I - sum_{J < I} A_IJ x_J) with every lower
+// colour already final, so b_I - sum_{J <= I} A_IJ x_J = 0 and the residual
+// is only the part of the columns updated later:
+//   r_I = - sum_{J in higher colours} A_IJ x_J   (exact up to rounding),
+// half of the off-diagonal blocks and no b.
+template <typename T, typename TM, int G, bool SUFFIX = false, int U = 4>
 __device__ __forceinline__ void residual_row(int I, int lane, bool active, const int* __restrict__ rowptr,
-                                             const int* __restrict__ col, const TM* __restrict__ val,
-                                             const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
-  T a0 = 0, a1 = 0, a2 = 0;
-  if (active)
-    row_msub<T, TM, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
+                                             const int* __restrict__ diag, const int* __restrict__ col,
+                                             const TM* __restrict__ val, const T* __restrict__ b,
+                                             const T* __restrict__ x, T* __restrict__ r) {
+  static_assert(G >= 3, "one lane per output component");
+  T a0 = 0, a1 = 0, a2 = 0, bc = 0;
+  if (active) {
+    if (!SUFFIX && lane < 3) bc = b[3L * I + lane];
+    int p0 = SUFFIX ? ro(diag + I) + 1 : ro(rowptr + I);
+    row_msub<T, TM, G, U, false>(p0 + lane, ro(rowptr + I + 1), col, val, x, nullptr, nullptr, a0, a1, a2);
+  }
   group_sum3<G>(a0, a1, a2);
-  if (active)
-    for (int c = lane; c < 3; c += G) r[3L * I + c] = b[3L * I + c] + (c == 0 ? a0 : c == 1 ? a1 : a2);
+  if (active && lane < 3) r[3L * I + lane] = bc + (lane == 0 ? a0 : lane == 1 ? a1 : a2);
 }
 
-template <typename T, typename TM, int G>
+template <typename T, typename TM, int G, bool SUFFIX>
 __global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restrict__ rowptr,
-                                                   const int* __restrict__ col, const TM* __restrict__ val,
-                                                   const T* __restrict__ b, const T* __restrict__ x,
-                                                   T* __restrict__ r) {
+                                                   const int* __restrict__ diag, const int* __restrict__ col,
+                                                   const TM* __restrict__ val, const T* __restrict__ b,
+                                                   const T* __restrict__ x, T* __restrict__ r) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int I = (int)(gt / G);
-  residual_row<T, TM, G>(I, threadIdx.x % G, I < rend, rowptr, col, val, b, x, r);
+  residual_row<T, TM, G, SUFFIX>(I, threadIdx.x % G, I < rend, rowptr, diag, col, val, b, x, r);
 }
 
 // Restriction plus the first colour of the next level's forward sweep:
@@ -694,8 +743,9 @@ __device__ __forceinline__ void restrict_row(int I, const int* __restrict__ mptr
                                              int skip_from, const T* __restrict__ r, T* __restrict__ bc, int init_end,
                                              const T* __restrict__ dinvc, T* __restrict__ xc) {
   T a0 = 0, a1 = 0, a2 = 0;
-  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
-    long k = mem[q];
+  int q1 = ro(mptr + I + 1);
+  for (int q = ro(mptr + I); q < q1; ++q) {
+    long k = ro(mem + q);
     if (k >= skip_from) continue;
     a0 += r[3 * k];
     a1 += r[3 * k + 1];
@@ -706,9 +756,9 @@ __device__ __forceinline__ void restrict_row(int I, const int* __restrict__ mptr
   bc[3L * I + 2] = a2;
   if (I < init_end) {
     const T* D = dinvc + 9L * I;
-    xc[3L * I] = D[0] * a0 + D[1] * a1 + D[2] * a2;
-    xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
-    xc[3L * I + 2] = D[6] * a0 + D[7] * a1 + D[8] * a2;
+    xc[3L * I] = ro(D) * a0 + ro(D + 1) * a1 + ro(D + 2) * a2;
+    xc[3L * I + 1] = ro(D + 3) * a0 + ro(D + 4) * a1 + ro(D + 5) * a2;
+    xc[3L * I + 2] = ro(D + 6) * a0 + ro(D + 7) * a1 + ro(D + 8) * a2;
   }
 }
 

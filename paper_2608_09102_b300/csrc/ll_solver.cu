@@ -40,7 +40,7 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   DBuf<int> agg;                    // this level -> next level
   // host counts for the algorithmic work of the kernels (profiling only)
   std::vector<long long> pre_blk, off_blk;  // per colour class: prefix / off-diagonal blocks
-  long long res_blk = 0;                    // blocks of the rows before the last colour
+  long long res_blk = 0;                    // blocks the residual reads (rows before the last colour)
   DBuf<double> val64, dinv64;
   DBuf<float> val32, dinv32;
   DBuf<__nv_bfloat16> val16;        // bfloat16 storage of the operator (LL_MIXED_BF16)
@@ -232,6 +232,8 @@ constexpr int kDotChunk = 8;
 // Coarse-level kernels use small blocks: a colour class of a small level then
 // spreads over many SMs instead of queueing on the float64 units of one.
 constexpr int kCoarseBlock = 64;
+// tail levels with at most this many cells run on one CTA (see k_coarse_tail)
+constexpr int kSoloCells = 200;
 constexpr int kTailCells = 12000;  // levels at or below this size run in the cluster tail
 constexpr int kMaxCoarsestCells = 2048;
 
@@ -395,6 +397,8 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
   TailArgs<T, TM> A;
   A.first = H->tail_first;
   A.last = H->nlev - 1;
+  A.solo_first = A.last;  // the coarsest level at least
+  while (A.solo_first > A.first && H->lev[A.solo_first - 1].n <= kSoloCells) --A.solo_first;
   A.nu_pre = H->prm.nu_pre;
   A.nu_post = H->prm.nu_post;
   A.N = H->ncoarse3;
@@ -404,6 +408,8 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
     TailLevel<T, TM>& L = A.L[l];
     L.n = C.n;
     L.ncol = C.ncol;
+    L.nnzb = C.nnzb;
+    L.nmem = l > A.first ? (int)C.mem.n : 0;
     for (int c = 0; c <= C.ncol && c <= kTailMaxColours; ++c) L.cs[c] = C.cs[c];
     L.rowptr = C.rowptr;
     L.diag = C.diag;
@@ -495,7 +501,9 @@ void setup_counts(ll_mg_hierarchy* H) {
         C.pre_blk[c] += dg[I] - rp[I];
         C.off_blk[c] += rp[I + 1] - rp[I] - 1;
       }
-    C.res_blk = rp[C.ncol > 0 ? C.cs[C.ncol - 1] : 0];
+    C.res_blk = 0;  // blocks the residual reads (one forward sweep: the higher colours' only)
+    for (int I = 0; I < (C.ncol > 0 ? C.cs[C.ncol - 1] : 0); ++I)
+      C.res_blk += H->prm.nu_pre == 1 ? rp[I + 1] - dg[I] - 1 : rp[I + 1] - rp[I];
   }
 }
 
@@ -788,8 +796,13 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
              sweep_bytes(rblk, skip_from, (int)sizeof(T), (int)sizeof(TM)));
     int init_end = (nu_pre >= 1 && l + 1 < H->nlev - 1) ? N.cs[1] : 0;
     if (skip_from > 0) {
-      kb_residual<T, TM, lanes<T>()><<<cdiv((long)skip_from * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, s>>>(
-          skip_from, L.rowptr, L.col, L.valm<TM>(), L.b<T>(), L.x<T>(), L.r<T>());
+      int nbr = cdiv((long)skip_from * lanes<T>(), kCoarseBlock);
+      if (nu_pre == 1)  // right after one forward sweep: the higher colours' part only
+        kb_residual<T, TM, lanes<T>(), true><<<nbr, kCoarseBlock, 0, s>>>(skip_from, L.rowptr, L.diag, L.col,
+                                                                         L.valm<TM>(), L.b<T>(), L.x<T>(), L.r<T>());
+      else
+        kb_residual<T, TM, lanes<T>(), false><<<nbr, kCoarseBlock, 0, s>>>(skip_from, L.rowptr, L.diag, L.col,
+                                                                          L.valm<TM>(), L.b<T>(), L.x<T>(), L.r<T>());
       LL_LAUNCHED();
     }
     kb_restrict<T><<<cdiv(N.n, kCoarseBlock), kCoarseBlock, 0, s>>>(N.n, N.mptr, N.mem, skip_from, L.r<T>(), N.b<T>(),
@@ -851,10 +864,18 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
         LL_LAUNCHED();
       }
     }
-    LL_PROFW(LL_KIND_L0_RESTRICT, 48.0 * H->l0_cells[0], (24 + 15.0 * sizeof(T)) * H->l0_cells[0]);
     int init_end = H->nlev > 2 ? L1.cs[1] : 0;  // level 1's first colour, unless it is the coarsest
-    k0_restrict<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
-                                                          L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(), L1.o2n);
+    if (H->prm.nu_pre == 1) {  // right after one forward sweep: the neighbours' part only
+      LL_PROFW(LL_KIND_L0_RESTRICT, 33.0 * H->l0_cells[0], (8 + 27.0 * sizeof(T)) * H->l0_cells[0]);
+      k0_restrict<T, true><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
+                                                                  L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
+                                                                  L1.o2n);
+    } else {
+      LL_PROFW(LL_KIND_L0_RESTRICT, 48.0 * H->l0_cells[0], (24 + 15.0 * sizeof(T)) * H->l0_cells[0]);
+      k0_restrict<T, false><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
+                                                                   L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
+                                                                   L1.o2n);
+    }
     LL_LAUNCHED();
   } else {
     LL_PROF(LL_KIND_L0_RESTRICT);

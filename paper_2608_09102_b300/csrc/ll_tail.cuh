@@ -21,11 +21,12 @@
 namespace llmg {
 
 constexpr int kTailThreads = 256;  // per CTA
+constexpr int kTailUnroll = 4;  // blocks per lane loaded before the products
 constexpr int kTailMaxColours = 64;
 
 template <typename T, typename TM>
 struct TailLevel {
-  int n = 0, ncol = 0;
+  int n = 0, ncol = 0, nnzb = 0, nmem = 0;
   int cs[kTailMaxColours + 1] = {0};  // colour class starts
   const int* rowptr = nullptr;
   const int* diag = nullptr;
@@ -43,6 +44,7 @@ struct TailLevel {
 template <typename T, typename TM>
 struct TailArgs {
   int first = 0, last = 0;  // tail levels [first, last]; last is the coarsest
+  int solo_first = 0;       // levels [solo_first, last] run on the cluster's first CTA alone
   int nu_pre = 1, nu_post = 1;
   int N = 0;                       // unknowns of the coarsest level
   const double* ainv = nullptr;    // its inverse, column-major
@@ -54,7 +56,15 @@ __device__ __forceinline__ void tail_sync() {
   cooperative_groups::this_cluster().sync();
 }
 
-// one colour class of level L with G lanes per row, spread over the cluster
+// barrier between the phases: the whole cluster, or one CTA
+struct ClusterPhase {
+  __device__ void operator()() const { tail_sync(); }
+};
+struct CtaPhase {
+  __device__ void operator()() const { __syncthreads(); }
+};
+
+// one colour class of level L with G lanes per row, spread over the threads
 template <typename T, typename TM, int G, int MODE>
 __device__ __forceinline__ void tail_sweep(const TailLevel<T, TM>& L, int t, const T* e, long tid, long nthreads) {
   int r0 = L.cs[t], r1 = L.cs[t + 1];
@@ -62,74 +72,134 @@ __device__ __forceinline__ void tail_sweep(const TailLevel<T, TM>& L, int t, con
   for (long base = 0; base < work; base += nthreads) {  // uniform trip count
     long g = base + tid;
     int I = r0 + (int)(g / G);
-    sweep_row<T, TM, G, MODE>(I, (int)(g % G), g < work, L.rowptr, L.diag, L.col, L.val, L.dinv, L.b, L.x, L.agg,
-                              e);
+    sweep_row<T, TM, G, MODE, kTailUnroll>(I, (int)(g % G), g < work, L.rowptr, L.diag, L.col, L.val, L.dinv, L.b,
+                                           L.x, L.agg, e);
   }
 }
 
+// pre-smoothing, residual and restriction of level l
+template <typename T, typename TM, int G, typename Sync>
+__device__ __forceinline__ void tail_down(const TailArgs<T, TM>& A, int l, long tid, long nthreads, Sync sync) {
+  const TailLevel<T, TM>& L = A.L[l];
+  const TailLevel<T, TM>& N = A.L[l + 1];
+  int K = L.ncol;
+  if (A.nu_pre == 0) {
+    for (long i = tid; i < 3L * L.n; i += nthreads) L.x[i] = (T)0;
+    sync();
+  }
+  for (int sweep = 0; sweep < A.nu_pre; ++sweep)
+    for (int t = sweep == 0 ? 1 : 0; t < K; ++t) {  // colour 0 was written by the restriction
+      if (sweep == 0) tail_sweep<T, TM, G, 0>(L, t, nullptr, tid, nthreads);
+      else tail_sweep<T, TM, G, 1>(L, t, nullptr, tid, nthreads);
+      sync();
+    }
+  int skip_from = A.nu_pre >= 1 ? L.cs[K - 1] : L.n;
+  long work = (long)skip_from * G;
+  for (long base = 0; base < work; base += nthreads) {
+    long g = base + tid;
+    if (A.nu_pre == 1)  // right after one forward sweep: the higher colours' part only
+      residual_row<T, TM, G, true, kTailUnroll>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag, L.col,
+                                                L.val, L.b, L.x, L.r);
+    else
+      residual_row<T, TM, G, false, kTailUnroll>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag, L.col,
+                                                 L.val, L.b, L.x, L.r);
+  }
+  sync();
+  int init_end = (A.nu_pre >= 1 && l + 1 < A.last) ? N.cs[1] : 0;
+  for (long I = tid; I < N.n; I += nthreads)
+    restrict_row<T>((int)I, N.mptr, N.mem, skip_from, L.r, N.b, init_end, N.dinv, N.x);
+  sync();
+}
+
+// coarsest: x = A^{-1} b
+template <typename T, typename TM, typename Sync>
+__device__ __forceinline__ void tail_coarsest(const TailArgs<T, TM>& A, long tid, long nthreads, Sync sync) {
+  const TailLevel<T, TM>& C = A.L[A.last];
+  for (long i = tid; i < A.N; i += nthreads) {
+    double acc = 0.0;
+    for (int j = 0; j < A.N; ++j) acc += ro(A.ainv + (long)j * A.N + i) * (double)C.b[j];
+    C.x[i] = (T)acc;
+  }
+  sync();
+}
+
+// backward sweeps of level l with the prolongation folded into the first
+template <typename T, typename TM, int G, typename Sync>
+__device__ __forceinline__ void tail_up(const TailArgs<T, TM>& A, int l, long tid, long nthreads, Sync sync) {
+  const TailLevel<T, TM>& L = A.L[l];
+  const TailLevel<T, TM>& N = A.L[l + 1];
+  int K = L.ncol;
+  if (A.nu_post == 0) {
+    for (long I = tid; I < L.n; I += nthreads) {
+      long a = 3L * L.agg[I];
+      L.x[3 * I] += N.x[a];
+      L.x[3 * I + 1] += N.x[a + 1];
+      L.x[3 * I + 2] += N.x[a + 2];
+    }
+    sync();
+  }
+  for (int sweep = 0; sweep < A.nu_post; ++sweep)
+    for (int k = 0; k < K; ++k) {
+      if (sweep == 0) tail_sweep<T, TM, G, 2>(L, K - 1 - k, N.x, tid, nthreads);
+      else tail_sweep<T, TM, G, 1>(L, K - 1 - k, nullptr, tid, nthreads);
+      sync();
+    }
+}
+
+// Ask L2 for the bytes [p, p + bytes) (128-byte lines, spread over the
+// threads); nothing waits for them.
+__device__ __forceinline__ void l2_prefetch(const void* p, long bytes, long tid, long nthreads) {
+  const char* c = (const char*)p;
+  for (long o = tid * 128; o < bytes; o += nthreads * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
+// The operators and transfers of the tail levels are read once per V-cycle
+// and the fine levels' traffic in between evicts them from L2, so each
+// phase would wait for DRAM on its first loads.  One prefetch of all of
+// them at the start overlaps those misses.
+template <typename T, typename TM>
+__device__ void tail_prefetch(const TailArgs<T, TM>& A, long tid, long nthreads) {
+  for (int l = A.first; l <= A.last; ++l) {
+    const TailLevel<T, TM>& L = A.L[l];
+    l2_prefetch(L.rowptr, (L.n + 1) * 4L, tid, nthreads);
+    l2_prefetch(L.diag, L.n * 4L, tid, nthreads);
+    l2_prefetch(L.col, L.nnzb * 4L, tid, nthreads);
+    l2_prefetch(L.val, L.nnzb * 9L * (long)sizeof(TM), tid, nthreads);
+    l2_prefetch(L.dinv, L.n * 9L * (long)sizeof(T), tid, nthreads);
+    if (l < A.last) l2_prefetch(L.agg, L.n * 4L, tid, nthreads);
+    if (l > A.first) {
+      l2_prefetch(L.mptr, (L.n + 1) * 4L, tid, nthreads);
+      l2_prefetch(L.mem, L.nmem * 4L, tid, nthreads);
+    }
+  }
+  l2_prefetch(A.ainv, (long)A.N * A.N * 8, tid, nthreads);
+}
+
+// The levels from `first` run on the whole cluster, phases separated by
+// cluster barriers.  The smallest levels (from `solo_first`) hold only a few
+// hundred rows: there a phase is latency, and the first CTA runs them alone
+// with CTA barriers, which cost far less than cluster-wide ones, while the
+// other CTAs wait at the next cluster barrier.
 template <typename T, typename TM, int G>
 __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const TailArgs<T, TM>* __restrict__ args) {
   const TailArgs<T, TM>& A = *args;
   long nthreads = (long)gridDim.x * blockDim.x;  // the grid is one cluster
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  // ---- down: pre-smoothing, residual, restriction
-  for (int l = A.first; l < A.last; ++l) {
-    const TailLevel<T, TM>& L = A.L[l];
-    const TailLevel<T, TM>& N = A.L[l + 1];
-    int K = L.ncol;
-    if (A.nu_pre == 0) {
-      for (long i = tid; i < 3L * L.n; i += nthreads) L.x[i] = (T)0;
-      tail_sync();
+  tail_prefetch(A, tid, nthreads);
+  for (int l = A.first; l < A.solo_first && l < A.last; ++l) tail_down<T, TM, G>(A, l, tid, nthreads, ClusterPhase());
+  if (A.solo_first >= A.last) {
+    tail_coarsest<T, TM>(A, tid, nthreads, ClusterPhase());
+  } else {
+    if (blockIdx.x == 0) {  // uniform per CTA; no cluster barrier inside
+      long t = threadIdx.x, nt = blockDim.x;
+      for (int l = A.solo_first; l < A.last; ++l) tail_down<T, TM, G>(A, l, t, nt, CtaPhase());
+      tail_coarsest<T, TM>(A, t, nt, CtaPhase());
+      for (int l = A.last - 1; l >= A.solo_first; --l) tail_up<T, TM, G>(A, l, t, nt, CtaPhase());
     }
-    for (int sweep = 0; sweep < A.nu_pre; ++sweep)
-      for (int t = sweep == 0 ? 1 : 0; t < K; ++t) {  // colour 0 was written by the restriction
-        if (sweep == 0) tail_sweep<T, TM, G, 0>(L, t, nullptr, tid, nthreads);
-        else tail_sweep<T, TM, G, 1>(L, t, nullptr, tid, nthreads);
-        tail_sync();
-      }
-    int skip_from = A.nu_pre >= 1 ? L.cs[K - 1] : L.n;
-    long work = (long)skip_from * G;
-    for (long base = 0; base < work; base += nthreads) {
-      long g = base + tid;
-      residual_row<T, TM, G>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.col, L.val, L.b, L.x, L.r);
-    }
-    tail_sync();
-    int init_end = (A.nu_pre >= 1 && l + 1 < A.last) ? N.cs[1] : 0;
-    for (long I = tid; I < N.n; I += nthreads)
-      restrict_row<T>((int)I, N.mptr, N.mem, skip_from, L.r, N.b, init_end, N.dinv, N.x);
-    tail_sync();
+    tail_sync();  // the first CTA's results, visible to the cluster
   }
-  // ---- coarsest: x = A^{-1} b
-  {
-    const TailLevel<T, TM>& C = A.L[A.last];
-    for (long i = tid; i < A.N; i += nthreads) {
-      double acc = 0.0;
-      for (int j = 0; j < A.N; ++j) acc += A.ainv[(long)j * A.N + i] * (double)C.b[j];
-      C.x[i] = (T)acc;
-    }
-    tail_sync();
-  }
-  // ---- up: backward sweeps with the prolongation folded into the first
-  for (int l = A.last - 1; l >= A.first; --l) {
-    const TailLevel<T, TM>& L = A.L[l];
-    const TailLevel<T, TM>& N = A.L[l + 1];
-    int K = L.ncol;
-    if (A.nu_post == 0) {
-      for (long I = tid; I < L.n; I += nthreads) {
-        long a = 3L * L.agg[I];
-        L.x[3 * I] += N.x[a];
-        L.x[3 * I + 1] += N.x[a + 1];
-        L.x[3 * I + 2] += N.x[a + 2];
-      }
-      tail_sync();
-    }
-    for (int sweep = 0; sweep < A.nu_post; ++sweep)
-      for (int k = 0; k < K; ++k) {
-        if (sweep == 0) tail_sweep<T, TM, G, 2>(L, K - 1 - k, N.x, tid, nthreads);
-        else tail_sweep<T, TM, G, 1>(L, K - 1 - k, nullptr, tid, nthreads);
-        tail_sync();
-      }
-  }
+  for (int l = (A.solo_first < A.last ? A.solo_first : A.last) - 1; l >= A.first; --l)
+    tail_up<T, TM, G>(A, l, tid, nthreads, ClusterPhase());
 }
 
 }  // namespace llmg
