@@ -672,22 +672,17 @@ __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const in
   static_assert(G >= 3, "one lane per output component");
   T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, d0 = 0, d1 = 0, d2 = 0;
   if (active) {
-    // b and this lane's row of D^-1 first: off the row's dependent chain
-    b0 = b[3L * I];
-    b1 = b[3L * I + 1];
-    b2 = b[3L * I + 2];
-    if (lane < 3) {
-      const T* D = dinv + 9L * I + 3 * lane;
-      d0 = ro(D);
-      d1 = ro(D + 1);
-      d2 = ro(D + 2);
-    }
     int p0 = ro(rowptr + I), pd = ro(diag + I);
     if (MODE == 0) row_msub<T, TM, G, U, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
     else row_msub_off<T, TM, G, U, MODE == 2>(p0, pd, ro(rowptr + I + 1), lane, col, val, x, agg, e, a0, a1, a2);
   }
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
-  if (active && lane < 3) x[3L * I + lane] = d0 * (b0 + a0) + d1 * (b1 + a1) + d2 * (b2 + a2);
+  if (active && lane < 3) {
+    b0 = b[3L * I]; b1 = b[3L * I + 1]; b2 = b[3L * I + 2];
+    const T* D = dinv + 9L * I + 3 * lane;
+    d0 = ro(D); d1 = ro(D + 1); d2 = ro(D + 2);
+    x[3L * I + lane] = d0 * (b0 + a0) + d1 * (b1 + a1) + d2 * (b2 + a2);
+  }
 }
 
 template <typename T, typename TM, int G, int MODE>
