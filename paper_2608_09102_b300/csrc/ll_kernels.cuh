@@ -663,18 +663,19 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
 //           prolongation, never stored).
 // x_I = Dinv_I (b_I - sum_{J != I} A_IJ v_J); the lanes of a group share the
 // three output components.  Every lane of the warp must call this (shuffles).
+// sweep_row with the row's block range already loaded: p0 = rowptr_I,
+// pd = diag_I, p1 = rowptr_{I+1}
 template <typename T, typename TM, int G, int MODE, int U = 4>
-__device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
-                                          const int* __restrict__ diag, const int* __restrict__ col,
-                                          const TM* __restrict__ val, const T* __restrict__ dinv,
-                                          const T* __restrict__ b, T* __restrict__ x, const int* __restrict__ agg,
-                                          const T* __restrict__ e) {
+__device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p0, int pd, int p1,
+                                             const int* __restrict__ col, const TM* __restrict__ val,
+                                             const T* __restrict__ dinv, const T* __restrict__ b,
+                                             T* __restrict__ x, const int* __restrict__ agg,
+                                             const T* __restrict__ e) {
   static_assert(G >= 3, "one lane per output component");
   T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, d0 = 0, d1 = 0, d2 = 0;
   if (active) {
-    int p0 = ro(rowptr + I), pd = ro(diag + I);
     if (MODE == 0) row_msub<T, TM, G, U, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-    else row_msub_off<T, TM, G, U, MODE == 2>(p0, pd, ro(rowptr + I + 1), lane, col, val, x, agg, e, a0, a1, a2);
+    else row_msub_off<T, TM, G, U, MODE == 2>(p0, pd, p1, lane, col, val, x, agg, e, a0, a1, a2);
   }
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
   if (active && lane < 3) {
@@ -685,6 +686,22 @@ __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const in
   }
 }
 
+template <typename T, typename TM, int G, int MODE, int U = 4>
+__device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
+                                          const int* __restrict__ diag, const int* __restrict__ col,
+                                          const TM* __restrict__ val, const T* __restrict__ dinv,
+                                          const T* __restrict__ b, T* __restrict__ x, const int* __restrict__ agg,
+                                          const T* __restrict__ e) {
+  int p0 = 0, pd = 0, p1 = 0;
+  if (active) {
+    p0 = ro(rowptr + I);
+    pd = ro(diag + I);
+    p1 = MODE == 0 ? 0 : ro(rowptr + I + 1);
+  }
+  sweep_row_at<T, TM, G, MODE, U>(I, lane, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
+}
+
+
 template <typename T, typename TM, int G, int MODE>
 __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
                                                 const int* __restrict__ diag, const int* __restrict__ col,
@@ -693,7 +710,30 @@ __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __res
                                                 const int* __restrict__ agg, const T* __restrict__ e) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int I = r0 + (int)(gt / G);
-  sweep_row<T, TM, G, MODE>(I, threadIdx.x % G, I < r1, rowptr, diag, col, val, dinv, b, x, agg, e);
+  bool active = I < r1;
+  int p0 = 0, pd = 0, p1 = 0;
+  if (active) {
+    p0 = ro(rowptr + I);
+    pd = ro(diag + I);
+    p1 = MODE == 0 ? 0 : ro(rowptr + I + 1);
+  }
+  sweep_row_at<T, TM, G, MODE>(I, threadIdx.x % G, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
+}
+
+// residual_row with the row's block range [p0, p1) already loaded
+template <typename T, typename TM, int G, bool SUFFIX, int U = 4>
+__device__ __forceinline__ void residual_row_at(int I, int lane, bool active, int p0, int p1,
+                                                const int* __restrict__ col, const TM* __restrict__ val,
+                                                const T* __restrict__ b, const T* __restrict__ x,
+                                                T* __restrict__ r) {
+  static_assert(G >= 3, "one lane per output component");
+  T a0 = 0, a1 = 0, a2 = 0, bc = 0;
+  if (active) {
+    if (!SUFFIX && lane < 3) bc = b[3L * I + lane];
+    row_msub<T, TM, G, U, false>(p0 + lane, p1, col, val, x, nullptr, nullptr, a0, a1, a2);
+  }
+  group_sum3<G>(a0, a1, a2);
+  if (active && lane < 3) r[3L * I + lane] = bc + (lane == 0 ? a0 : lane == 1 ? a1 : a2);
 }
 
 // r_I = b_I - (A x)_I, G lanes per row (all lanes of the warp call it).
@@ -708,15 +748,12 @@ __device__ __forceinline__ void residual_row(int I, int lane, bool active, const
                                              const int* __restrict__ diag, const int* __restrict__ col,
                                              const TM* __restrict__ val, const T* __restrict__ b,
                                              const T* __restrict__ x, T* __restrict__ r) {
-  static_assert(G >= 3, "one lane per output component");
-  T a0 = 0, a1 = 0, a2 = 0, bc = 0;
+  int p0 = 0, p1 = 0;
   if (active) {
-    if (!SUFFIX && lane < 3) bc = b[3L * I + lane];
-    int p0 = SUFFIX ? ro(diag + I) + 1 : ro(rowptr + I);
-    row_msub<T, TM, G, U, false>(p0 + lane, ro(rowptr + I + 1), col, val, x, nullptr, nullptr, a0, a1, a2);
+    p0 = SUFFIX ? ro(diag + I) + 1 : ro(rowptr + I);
+    p1 = ro(rowptr + I + 1);
   }
-  group_sum3<G>(a0, a1, a2);
-  if (active && lane < 3) r[3L * I + lane] = bc + (lane == 0 ? a0 : lane == 1 ? a1 : a2);
+  residual_row_at<T, TM, G, SUFFIX, U>(I, lane, active, p0, p1, col, val, b, x, r);
 }
 
 template <typename T, typename TM, int G, bool SUFFIX>
@@ -726,7 +763,13 @@ __global__ void __launch_bounds__(256) kb_residual(int rend, const int* __restri
                                                    const T* __restrict__ x, T* __restrict__ r) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int I = (int)(gt / G);
-  residual_row<T, TM, G, SUFFIX>(I, threadIdx.x % G, I < rend, rowptr, diag, col, val, b, x, r);
+  bool active = I < rend;
+  int p0 = 0, p1 = 0;
+  if (active) {
+    p0 = SUFFIX ? ro(diag + I) + 1 : ro(rowptr + I);
+    p1 = ro(rowptr + I + 1);
+  }
+  residual_row_at<T, TM, G, SUFFIX>(I, threadIdx.x % G, active, p0, p1, col, val, b, x, r);
 }
 
 // Restriction plus the first colour of the next level's forward sweep:

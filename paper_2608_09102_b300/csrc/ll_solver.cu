@@ -123,7 +123,7 @@ struct ll_mg_hierarchy {
   size_t ev_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pairs[LL_NUM_KINDS];
   double prof_ms[LL_NUM_KINDS] = {0};
-  long long prof_n[LL_NUM_KINDS] = {0};
+  long long prof_n[LL_NUM_KINDS] = {0};  // kernel launches timed
   double prof_flops[LL_NUM_KINDS] = {0}, prof_bytes[LL_NUM_KINDS] = {0};
   long long l0_cells[2] = {0, 0};  // real cells of each colour
   double tail_flops = 0, tail_bytes = 0;  // one launch of the cluster tail
@@ -146,6 +146,7 @@ struct ll_mg_hierarchy {
     int kind;
     cudaEvent_t b, e;
     double flops, bytes;
+    int nl;  // kernel launches between b and e
   };
   std::vector<GPair> gpairs[kMaxRestart];
   void drop_graph(int j) {
@@ -187,8 +188,10 @@ struct ProfScope {
   int kind;
   cudaEvent_t b = nullptr;
   double flops, bytes;  // algorithmic work of the launches in the scope
-  ProfScope(ll_mg_hierarchy* h, int k, double f = 0, double by = 0) : H(h), kind(k), flops(f), bytes(by) {
-    if (!(H->prof_mask & (1u << kind))) return;
+  int nl;               // kernel launches in the scope
+  ProfScope(ll_mg_hierarchy* h, int k, double f = 0, double by = 0, int n = 1)
+      : H(h), kind(k), flops(f), bytes(by), nl(n) {
+    if (kind >= LL_NUM_KINDS || !(H->prof_mask & (1u << kind))) return;
     if (H->capturing < 0) {
       H->prof_flops[kind] += flops;
       H->prof_bytes[kind] += bytes;
@@ -207,11 +210,12 @@ struct ProfScope {
       cudaEvent_t e;
       LL_CU(cudaEventCreate(&e));
       LL_CU(cudaEventRecordWithFlags(e, H->s, cudaEventRecordExternal));
-      H->gpairs[H->capturing].push_back({kind, b, e, flops, bytes});
+      H->gpairs[H->capturing].push_back({kind, b, e, flops, bytes, nl});
     } else {
       cudaEvent_t e = H->event();
       LL_CU(cudaEventRecord(e, H->s));
       H->prof_pairs[kind].push_back({b, e});
+      H->prof_n[kind] += nl;
     }
   }
 };
@@ -223,6 +227,14 @@ void enter(ll_mg_hierarchy* H) {
 }
 #define LL_PROF(kind) ProfScope prof_scope_(H, kind)
 #define LL_PROFW(kind, flops, bytes) ProfScope prof_scope_(H, kind, flops, bytes)
+#define LL_PROFN(kind, flops, bytes, n) ProfScope prof_scope_(H, kind, flops, bytes, n)
+
+// launch on the library stream, counted
+template <typename... KP, typename... A>
+void launch_k(ll_mg_hierarchy* H, void (*k)(KP...), long grid, int block, A... args) {
+  k<<<(unsigned)grid, block, 0, H->s>>>(args...);
+  LL_LAUNCHED();
+}
 
 // lanes per block row in the BSR kernels
 template <typename T> constexpr int lanes();
@@ -667,16 +679,28 @@ void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
 }
 
 // one colour class of level l: rows [cs[t], cs[t+1])
+// work model of one class sweep
 template <typename T, typename TM, int MODE>
-void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e) {
+void class_work(const CLevel& L, int t, double& flops, double& bytes) {
+  int rows = L.cs[t + 1] - L.cs[t];
+  long long blk = MODE == 0 ? L.pre_blk[t] : L.off_blk[t];
+  flops += rows > 0 ? sweep_flops(blk, rows) : 0.0;
+  bytes += rows > 0 ? sweep_bytes(blk, rows, (int)sizeof(T), (int)sizeof(TM)) : 0.0;
+}
+
+// one colour class of level l: rows [cs[t], cs[t+1]); timed on its own
+// unless the caller times a group of classes (timed = false)
+template <typename T, typename TM, int MODE>
+void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e, bool timed = true) {
   CLevel& L = H->lev[l];
   int r0 = L.cs[t], r1 = L.cs[t + 1];
   if (r1 <= r0) return;
-  long long blk = MODE == 0 ? L.pre_blk[t] : L.off_blk[t];
-  LL_PROFW(LL_KIND_BSR_SMOOTH, sweep_flops(blk, r1 - r0), sweep_bytes(blk, r1 - r0, (int)sizeof(T), (int)sizeof(TM)));
-  kb_sweep<T, TM, lanes<T>(), MODE><<<cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock), kCoarseBlock, 0, H->s>>>(
-      r0, r1, L.rowptr, L.diag, L.col, L.valm<TM>(), L.dinv<T>(), L.b<T>(), L.x<T>(), L.agg, e);
-  LL_LAUNCHED();
+  double f = 0, by = 0;
+  if (timed) class_work<T, TM, MODE>(L, t, f, by);
+  ProfScope prof_scope_(H, timed ? LL_KIND_BSR_SMOOTH : LL_NUM_KINDS, f, by);
+  launch_k(H, kb_sweep<T, TM, lanes<T>(), MODE>, cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock),
+           kCoarseBlock, r0, r1, (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col,
+           (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
 }
 
 // one full plain block-GS sweep of level l (colours ascending or descending)
@@ -784,11 +808,21 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
     k_zero<T><<<cdiv(3L * L.n, kBlock), kBlock, 0, s>>>(3L * L.n, L.x<T>());
     LL_LAUNCHED();
   }
-  for (int sweep = 0; sweep < nu_pre; ++sweep)
-    for (int t = (sweep == 0 && init0_done) ? 1 : 0; t < K; ++t) {
-      if (sweep == 0) sweep_class<T, TM, 0>(H, l, t, nullptr);
-      else sweep_class<T, TM, 1>(H, l, t, nullptr);
+  for (int sweep = 0; sweep < nu_pre; ++sweep) {  // one timing scope per sweep of the level
+    int t0 = (sweep == 0 && init0_done) ? 1 : 0;
+    double f = 0, by = 0;
+    int nl = 0;
+    for (int t = t0; t < K; ++t) {
+      if (sweep == 0) class_work<T, TM, 0>(L, t, f, by);
+      else class_work<T, TM, 1>(L, t, f, by);
+      nl += L.cs[t + 1] > L.cs[t];
     }
+    LL_PROFN(LL_KIND_BSR_SMOOTH, f, by, nl);
+    for (int t = t0; t < K; ++t) {
+      if (sweep == 0) sweep_class<T, TM, 0>(H, l, t, nullptr, false);
+      else sweep_class<T, TM, 1>(H, l, t, nullptr, false);
+    }
+  }
   {
     int skip_from = nu_pre >= 1 ? L.cs[K - 1] : L.n;  // the last forward colour has zero residual
     long long rblk = nu_pre >= 1 ? L.res_blk : (long long)L.nnzb;
@@ -798,16 +832,16 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
     if (skip_from > 0) {
       int nbr = cdiv((long)skip_from * lanes<T>(), kCoarseBlock);
       if (nu_pre == 1)  // right after one forward sweep: the higher colours' part only
-        kb_residual<T, TM, lanes<T>(), true><<<nbr, kCoarseBlock, 0, s>>>(skip_from, L.rowptr, L.diag, L.col,
-                                                                         L.valm<TM>(), L.b<T>(), L.x<T>(), L.r<T>());
+        launch_k(H, kb_residual<T, TM, lanes<T>(), true>, nbr, kCoarseBlock, skip_from, (const int*)L.rowptr,
+                 (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.b<T>(),
+                 (const T*)L.x<T>(), L.r<T>());
       else
-        kb_residual<T, TM, lanes<T>(), false><<<nbr, kCoarseBlock, 0, s>>>(skip_from, L.rowptr, L.diag, L.col,
-                                                                          L.valm<TM>(), L.b<T>(), L.x<T>(), L.r<T>());
-      LL_LAUNCHED();
+        launch_k(H, kb_residual<T, TM, lanes<T>(), false>, nbr, kCoarseBlock, skip_from, (const int*)L.rowptr,
+                 (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.b<T>(),
+                 (const T*)L.x<T>(), L.r<T>());
     }
-    kb_restrict<T><<<cdiv(N.n, kCoarseBlock), kCoarseBlock, 0, s>>>(N.n, N.mptr, N.mem, skip_from, L.r<T>(), N.b<T>(),
-                                                        init_end, N.dinv<T>(), N.x<T>());
-    LL_LAUNCHED();
+    launch_k(H, kb_restrict<T>, cdiv(N.n, kCoarseBlock), kCoarseBlock, N.n, (const int*)N.mptr,
+             (const int*)N.mem, skip_from, (const T*)L.r<T>(), N.b<T>(), init_end, (const T*)N.dinv<T>(), N.x<T>());
   }
   if (H->union_mode) union_coarse<T>(H, l);  // rows past the colour classes
   coarse_problem<T, TM>(H, l + 1);
@@ -816,11 +850,20 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
     kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
     LL_LAUNCHED();
   }
-  for (int sweep = 0; sweep < nu_post; ++sweep)
-    for (int k = 0; k < K; ++k) {
-      if (sweep == 0) sweep_class<T, TM, 2>(H, l, K - 1 - k, N.x<T>());
-      else sweep_class<T, TM, 1>(H, l, K - 1 - k, nullptr);
+  for (int sweep = 0; sweep < nu_post; ++sweep) {
+    double f = 0, by = 0;
+    int nl = 0;
+    for (int t = 0; t < K; ++t) {
+      if (sweep == 0) class_work<T, TM, 2>(L, t, f, by);
+      else class_work<T, TM, 1>(L, t, f, by);
+      nl += L.cs[t + 1] > L.cs[t];
     }
+    LL_PROFN(LL_KIND_BSR_SMOOTH, f, by, nl);
+    for (int k = 0; k < K; ++k) {
+      if (sweep == 0) sweep_class<T, TM, 2>(H, l, K - 1 - k, N.x<T>(), false);
+      else sweep_class<T, TM, 1>(H, l, K - 1 - k, nullptr, false);
+    }
+  }
 }
 
 // z = V-cycle(r) on level 0; r float64 red-black, z red-black in T
@@ -1041,7 +1084,7 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
       float ms = 0;
       LL_CU(cudaEventElapsedTime(&ms, q.b, q.e));
       H->prof_ms[q.kind] += ms;
-      H->prof_n[q.kind] += 1;
+      H->prof_n[q.kind] += q.nl;
       H->prof_flops[q.kind] += q.flops;
       H->prof_bytes[q.kind] += q.bytes;
     }
@@ -1444,7 +1487,7 @@ int ll_mg_profile_read(ll_mg_hierarchy* H, int kind, double* total_ms, long long
     tot += ms;
   }
   if (total_ms) *total_ms = tot;
-  if (launches) *launches = H->prof_n[kind] + (long long)H->prof_pairs[kind].size();
+  if (launches) *launches = H->prof_n[kind];
   if (flops) *flops = H->prof_flops[kind];
   if (bytes) *bytes = H->prof_bytes[kind];
   return LL_OK;
