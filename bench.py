@@ -43,6 +43,13 @@ WORKLOAD = "3D 128^3 semi-implicit LL time steps, alpha 0.02, dt 5e-4, vortex + 
 # at 1.94 GHz, i.e. the same 2 FMA/clk/SM)
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 
+# DRAM traffic of the float64 coarse sweeps per launch over the algorithmic
+# bytes: ncu dram__bytes_read.sum + dram__bytes_write.sum on 400 kb_sweep
+# launches of the --grid 96 case, against the library's byte model for the
+# same launches (profiles/kb_sweep_96cube_fp64.md).  Scaled by the bytes a
+# launch processes to the traffic of a 128^3 launch.
+KB_SWEEP_TRAFFIC_RATIO = 9.667e6 / 9.293e6
+
 KIND_NAMES = ["l0_smooth", "l0_restrict", "outer_apply", "bsr_smooth", "bsr_other", "gcr_vector", "coarsest",
               "numeric", "coarse_tail"]
 
@@ -292,6 +299,10 @@ def run_ours(args):
     value = UNKNOWNS * args.steps * world / (elapsed_ms * 1e-3)
     peaks, peak_src = measured_peaks()
     roof = roofline(dominant, dom_ms, dom_launches, dom_flops, dom_bytes, args.precision, peaks, peak_src)
+    if dominant == "bsr_smooth" and args.precision == "fp64" and roof.get("bytes_per_launch"):
+        roof["traffic"] = KB_SWEEP_TRAFFIC_RATIO * roof["bytes_per_launch"]
+        roof["traffic_source"] = ("ncu DRAM bytes of kb_sweep at 96^3 / algorithmic bytes = %.3f, times this "
+                                  "launch's algorithmic bytes" % KB_SWEEP_TRAFFIC_RATIO)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -491,7 +502,16 @@ def main():
                          "grad96: the 96^3 differentiation workload")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--batch-maxit", type=int, default=300)
+    ap.add_argument("--grid", type=int, default=128,
+                    help="cube side of the step workload (default 128; smaller sides are profiling cases)")
     args = ap.parse_args()
+    if args.grid != 128:
+        global GRID, H_SPACING, N_CELLS, UNKNOWNS, WORKLOAD
+        GRID = (args.grid,) * 3
+        H_SPACING = 1.0 / args.grid
+        N_CELLS = args.grid ** 3
+        UNKNOWNS = 3 * N_CELLS
+        WORKLOAD = WORKLOAD.replace("128^3", "%d^3 (profiling case)" % args.grid)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch512":
