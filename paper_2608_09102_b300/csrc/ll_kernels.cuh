@@ -935,8 +935,8 @@ __global__ void kk_combine(long n, const T* __restrict__ z1, T* __restrict__ x, 
 // y = A x (float64); pads stay zero.  TX = storage type of x.
 template <typename TX>
 __global__ void __launch_bounds__(256) kg_apply(GridGeom g, const TX* __restrict__ x, const double* __restrict__ chat,
-                                                double inv_dt, double* __restrict__ y) {
-  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+                                                double inv_dt, double* __restrict__ y, long s0 = 0) {
+  long sl = s0 + blockIdx.x * (long)blockDim.x + threadIdx.x;  // slots [s0, 2 Nh)
   long n2 = 2 * g.nh;
   if (sl >= n2) return;
   int c = (int)(sl / g.nh);
@@ -952,6 +952,19 @@ __global__ void __launch_bounds__(256) kg_apply(GridGeom g, const TX* __restrict
   y[sl] = v[0];
   y[n2 + sl] = v[1];
   y[2 * n2 + sl] = v[2];
+}
+
+// y = r on the colour-0 slots [0, Nh): the product A z there when z leaves a
+// block Gauss-Seidel sweep whose last half-sweep updated colour 0 with its
+// (colour-1) neighbours final -- then D_k z_k = r_k - C^_k sum_j z_j, so
+// (A z)_k = D_k z_k + C^_k sum_j z_j = r_k (exact up to rounding)
+__global__ void kg_copy_colour0(GridGeom g, const double* __restrict__ r, double* __restrict__ y) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= g.nh) return;
+  y[sl] = r[sl];
+  y[n2 + sl] = r[n2 + sl];
+  y[2 * n2 + sl] = r[2 * n2 + sl];
 }
 
 // r = b - A x, partial sums of |r|^2 and |b|^2
