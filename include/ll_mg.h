@@ -289,6 +289,15 @@ long long ll_mg_batch_level_rows(const ll_mg_batch* B, int level);
 int ll_mg_batch_level_colours(const ll_mg_batch* B, int level);
 /* levels of instance i's own hierarchy */
 int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i);
+/* Compaction: when, at a restart boundary, the instances still iterating
+ * hold under half of the concatenated rows, they continue (from their
+ * current iterates, as after any restart) in a sub-batch of their own, so
+ * that the converged instances cost nothing more.  Each instance's
+ * arithmetic is the same either way.  Sub-batches are built on first use and
+ * kept (ll_mg_batch_update refreshes them); this returns how many exist.
+ * Setting the environment variable LLMG_BATCH_NO_COMPACT=1 turns compaction
+ * off. */
+int ll_mg_batch_subbatches(const ll_mg_batch* B);
 void ll_mg_batch_destroy(ll_mg_batch* B);
 
 /* ---- differentiation of the time step (adjoint) ----------------------------

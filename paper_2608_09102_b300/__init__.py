@@ -31,7 +31,7 @@ EXPORTS = (
     "ll_mg_smooth", "ll_mg_step", "ll_launch_count", "ll_mg_profile", "ll_mg_profile_read",
     "ll_residual_noalloc", "ll_mg_step_llg", "ll_mg_batch_setup", "ll_mg_batch_update", "ll_mg_batch_solve",
     "ll_mg_batch_count", "ll_mg_batch_levels", "ll_mg_batch_level_rows", "ll_mg_batch_level_colours",
-    "ll_mg_batch_instance_levels", "ll_mg_batch_destroy", "ll_mg_step_save", "ll_mg_adjoint_setup",
+    "ll_mg_batch_instance_levels", "ll_mg_batch_destroy", "ll_mg_step_save", "ll_mg_batch_subbatches", "ll_mg_adjoint_setup",
     "ll_mg_step_vjp",
 )
 
@@ -122,6 +122,7 @@ def load_library():
         "ll_mg_batch_level_rows": (ctypes.c_longlong, [vp, i]),
         "ll_mg_batch_level_colours": (i, [vp, i]),
         "ll_mg_batch_instance_levels": (i, [vp, i]),
+        "ll_mg_batch_subbatches": (i, [vp]),
         "ll_mg_batch_destroy": (None, [vp]),
         "ll_mg_step_save": (i, [vp, vp, i, vp, ip, dp]),
         "ll_mg_adjoint_setup": (i, [vp, d, d, d, _Grid, P, vp, ctypes.POINTER(vp)]),
@@ -521,6 +522,11 @@ class Batch:
 
     def instance_levels(self, i: int) -> int:
         return load_library().ll_mg_batch_instance_levels(self._h, i)
+
+    @property
+    def subbatches(self) -> int:
+        """Compacted sub-batches built so far (ll_mg_batch_subbatches)."""
+        return load_library().ll_mg_batch_subbatches(self._h)
 
 
 def launch_count() -> int:

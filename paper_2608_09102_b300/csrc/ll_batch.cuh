@@ -20,6 +20,8 @@
 struct ll_mg_batch {
   ll_mg_params prm;
   int ninst = 0;
+  bool owns = true;  // false: a compacted sub-batch sharing its parent's instance hierarchies
+  std::map<std::vector<int>, ll_mg_batch*> children;  // sub-batches by instance subset
   bool transposed = false;  // the instances' A^T (adjoint solves)
   cudaStream_t user = nullptr;
   cudaEvent_t entry_ev = nullptr;
@@ -56,7 +58,9 @@ struct ll_mg_batch {
       for (auto* b : v) delete b;
     if (h_head) cudaFreeHost(h_head);
     if (h_flags) cudaFreeHost(h_flags);
-    for (auto* H : inst) delete H;
+    for (auto& c : children) delete c.second;
+    if (owns)
+      for (auto* H : inst) delete H;
     if (entry_ev) cudaEventDestroy(entry_ev);
     delete U;
   }
@@ -468,44 +472,68 @@ void batch_true_residual(ll_mg_batch* B) {
   LL_CU(cudaStreamSynchronize(U->s));
 }
 
+// The solve's state of one instance, kept across sub-batches.
+struct InstState {
+  int total = 0;              // GCR iterations so far
+  int st = LL_NOT_CONVERGED;  // final status once done
+  int done = 0;               // 0 running, 1 finished, 2 finished with a zero right-hand side (x = 0)
+  double relres = 0;
+  bool paused = false;        // stopped at a restart boundary to continue in a smaller sub-batch
+};
+
 // GCR (Algorithm 1) on every instance in lockstep, restarts of prm.restart;
-// per instance the same decisions as the single solve
+// per instance the same decisions as the single solve.  With compact, the
+// solve pauses at a restart boundary once the instances still iterating
+// hold under half of the union's rows: they continue in a sub-batch of their
+// own, from their current iterate, exactly as a restart would.
 template <typename T, typename TM>
-int batch_gcr(ll_mg_batch* B, double rtol, int* iters, double* relres, int* status, std::vector<int>& zero) {
+void batch_gcr(ll_mg_batch* B, double rtol, std::vector<InstState*>& S, bool compact) {
   ll_mg_hierarchy* U = B->U;
   cudaStream_t s = U->s;
   int ni = B->ninst;
   long n3 = B->n3;
   T* Zbase = std::is_same<T, double>::value ? (T*)B->Z64.p : (T*)B->Z32.p;
-  std::vector<int> total(ni, 0), st(ni, LL_NOT_CONVERGED), done(ni, 0), act(ni, 0), jd(ni, 0);
+  std::vector<int> act(ni, 0), jd(ni, 0);
   std::vector<double> bnorm(ni, 0.0);
+  long rows_all = 0;
+  for (int i = 0; i < ni; ++i) rows_all += B->inst[i]->n2;
   for (;;) {
     batch_true_residual(B);
     int running = 0;
+    long rows_running = 0;
     int tmin = 1 << 30;
     for (int i = 0; i < ni; ++i) {
       act[i] = 0;
-      if (done[i]) continue;
+      InstState& q = *S[i];
+      int& total = q.total;
+      int& st = q.st;
+      int& done = q.done;
+      if (done) continue;
       double rn2 = B->h_head[2 * i];
       bnorm[i] = sqrt(B->h_head[2 * i + 1]);
       if (bnorm[i] == 0.0) {  // zero right-hand side: x = 0 below
-        st[i] = LL_OK;
-        done[i] = 2;
+        st = LL_OK;
+        done = 2;
       } else if (!isfinite(rn2)) {
-        st[i] = LL_BREAKDOWN;
-        done[i] = 1;
+        st = LL_BREAKDOWN;
+        done = 1;
       } else if (sqrt(rn2) < rtol * bnorm[i]) {
-        st[i] = LL_OK;
-        done[i] = 1;
-      } else if (total[i] >= B->prm.maxit) {
-        done[i] = 1;
+        st = LL_OK;
+        done = 1;
+      } else if (total >= B->prm.maxit) {
+        done = 1;
       } else {
         act[i] = 1;
         ++running;
-        tmin = std::min(tmin, total[i]);
+        rows_running += B->inst[i]->n2;
+        tmin = std::min(tmin, total);
       }
     }
     if (running == 0) break;
+    if (compact && 2 * rows_running < rows_all) {
+      for (int i = 0; i < ni; ++i) S[i]->paused = act[i] != 0;
+      break;
+    }
     int m = std::min(B->prm.restart, B->prm.maxit - tmin);
     std::fill(jd.begin(), jd.end(), 0);
     batch_upload(B, act, B->act);
@@ -516,17 +544,18 @@ int batch_gcr(ll_mg_batch* B, double rtol, int* iters, double* relres, int* stat
       int left = 0;
       for (int i = 0; i < ni; ++i) {
         if (!cyc[i]) continue;
-        ++total[i];
+        InstState& q = *S[i];
+        ++q.total;
         double rn2 = B->h_head[2 * i], gjj = B->h_head[2 * i + 1];
         if (!(gjj > 0.0) || !isfinite(gjj) || !isfinite(rn2)) {
-          st[i] = LL_BREAKDOWN;
-          done[i] = 1;
+          q.st = LL_BREAKDOWN;
+          q.done = 1;
           cyc[i] = 0;
           changed = true;
           continue;
         }
         jd[i] = j + 1;
-        if (sqrt(rn2) < rtol * bnorm[i] || total[i] >= B->prm.maxit) {  // step 6
+        if (sqrt(rn2) < rtol * bnorm[i] || q.total >= B->prm.maxit) {  // step 6
           cyc[i] = 0;
           changed = true;
           continue;
@@ -543,50 +572,109 @@ int batch_gcr(ll_mg_batch* B, double rtol, int* iters, double* relres, int* stat
     LL_LAUNCHED();
   }
   batch_true_residual(B);
-  zero.assign(ni, 0);
   for (int i = 0; i < ni; ++i) {
-    zero[i] = done[i] == 2;
+    if (S[i]->paused || !S[i]->done) continue;
     double bn = sqrt(B->h_head[2 * i + 1]);
-    if (iters) iters[i] = total[i];
-    if (relres) relres[i] = bn > 0 ? sqrt(B->h_head[2 * i]) / bn : 0.0;
-    if (status) status[i] = st[i];
+    S[i]->relres = bn > 0 ? sqrt(B->h_head[2 * i]) / bn : 0.0;
   }
-  int worst = LL_OK;
-  for (int i = 0; i < ni; ++i)
-    if (st[i] == LL_BREAKDOWN) worst = LL_BREAKDOWN;
-    else if (st[i] == LL_NOT_CONVERGED && worst == LL_OK) worst = LL_NOT_CONVERGED;
-  return worst;
+}
+
+// the union hierarchy and workspace of a set of instance hierarchies
+void batch_build(ll_mg_batch* B) {
+  B->U = new ll_mg_hierarchy();
+  ll_mg_hierarchy* U = B->U;
+  U->prm = B->prm;
+  U->union_mode = true;
+  U->tail_first = -1;
+  U->user = B->user;
+  LL_CU(cudaStreamCreateWithFlags(&U->s, cudaStreamNonBlocking));
+  LL_CU(cudaEventCreateWithFlags(&U->entry_ev, cudaEventDisableTiming));
+  const char* ng = getenv("LLMG_NO_GRAPHS");
+  U->use_graphs = !(ng && ng[0] == '1');
+}
+
+// the sub-batch of B's instances `sub` (ascending), built once and kept
+ll_mg_batch* batch_child(ll_mg_batch* B, const std::vector<int>& sub) {
+  auto it = B->children.find(sub);
+  if (it != B->children.end()) return it->second;
+  ll_mg_batch* C = new ll_mg_batch();
+  try {
+    C->prm = B->prm;
+    C->ninst = (int)sub.size();
+    C->owns = false;
+    C->transposed = B->transposed;
+    if (C->transposed) C->bad.alloc(1);
+    C->user = B->U->s;
+    LL_CU(cudaEventCreateWithFlags(&C->entry_ev, cudaEventDisableTiming));
+    for (int i : sub) C->inst.push_back(B->inst[i]);
+    batch_build(C);
+    batch_symbolic(C);
+    batch_allocate(C);
+    batch_refresh(C);
+  } catch (...) {
+    delete C;
+    throw;
+  }
+  B->children[sub] = C;
+  return C;
 }
 
 int batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x, double rtol, int* iters, double* relres,
                 int* status) {
-  ll_mg_hierarchy* U = B->U;
-  cudaStream_t s = U->s;
   if (rtol <= 0) rtol = B->prm.rtol;
-  for (int i = 0; i < B->ninst; ++i) {
-    ll_mg_hierarchy* H = B->inst[i];
-    kb_union_in<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *B->rmap[i][0],
-                                                                      rhs[i], B->bw);
-    LL_LAUNCHED();
-    kb_union_in<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *B->rmap[i][0], x[i],
-                                                                      B->xw);
-    LL_LAUNCHED();
-  }
-  std::vector<int> zero;
-  int rc = B->prm.precision == LL_MIXED_FP32 ? batch_gcr<float, float>(B, rtol, iters, relres, status, zero)
-                                              : batch_gcr<double, double>(B, rtol, iters, relres, status, zero);
-  for (int i = 0; i < B->ninst; ++i) {
-    ll_mg_hierarchy* H = B->inst[i];
-    if (zero[i]) {  // zero right-hand side: the solution is zero
-      LL_CU(cudaMemsetAsync(x[i], 0, 3 * H->g.n * sizeof(double), s));
-      continue;
+  const char* nc = getenv("LLMG_BATCH_NO_COMPACT");
+  bool compact = !(nc && nc[0] == '1');
+  int ni = B->ninst;
+  std::vector<InstState> state(ni);
+  ll_mg_batch* cur = B;
+  std::vector<int> idx(ni);
+  for (int i = 0; i < ni; ++i) idx[i] = i;
+  for (;;) {
+    cudaStream_t s = cur->U->s;
+    for (int k = 0; k < cur->ninst; ++k) {
+      ll_mg_hierarchy* H = cur->inst[k];
+      kb_union_in<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *cur->rmap[k][0],
+                                                                        rhs[idx[k]], cur->bw);
+      LL_LAUNCHED();
+      kb_union_in<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *cur->rmap[k][0],
+                                                                        x[idx[k]], cur->xw);
+      LL_LAUNCHED();
     }
-    kb_union_out<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot, *B->rmap[i][0],
-                                                                       B->xw, x[i]);
-    LL_LAUNCHED();
+    std::vector<InstState*> sp(cur->ninst);
+    for (int k = 0; k < cur->ninst; ++k) sp[k] = &state[idx[k]];
+    // a sub-batch of one instance would only move its rows; stop compacting there
+    if (cur->prm.precision == LL_MIXED_FP32) batch_gcr<float, float>(cur, rtol, sp, compact && cur->ninst > 1);
+    else batch_gcr<double, double>(cur, rtol, sp, compact && cur->ninst > 1);
+    std::vector<int> sub;
+    for (int k = 0; k < cur->ninst; ++k) {
+      ll_mg_hierarchy* H = cur->inst[k];
+      double* xo = x[idx[k]];
+      if (sp[k]->done == 2) {  // zero right-hand side: the solution is zero
+        LL_CU(cudaMemsetAsync(xo, 0, 3 * H->g.n * sizeof(double), s));
+      } else {
+        kb_union_out<double, double><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(H->g, H->nat_of_slot,
+                                                                           *cur->rmap[k][0], cur->xw, xo);
+        LL_LAUNCHED();
+      }
+      if (sp[k]->paused) {
+        sp[k]->paused = false;
+        sub.push_back(idx[k]);
+      }
+    }
+    LL_CU(cudaStreamSynchronize(s));
+    if (sub.empty()) break;
+    cur = batch_child(B, sub);
+    idx = sub;
   }
-  LL_CU(cudaStreamSynchronize(s));
-  return rc;
+  int worst = LL_OK;
+  for (int i = 0; i < ni; ++i) {
+    if (iters) iters[i] = state[i].total;
+    if (relres) relres[i] = state[i].relres;
+    if (status) status[i] = state[i].st;
+    if (state[i].st == LL_BREAKDOWN) worst = LL_BREAKDOWN;
+    else if (state[i].st == LL_NOT_CONVERGED && worst == LL_OK) worst = LL_NOT_CONVERGED;
+  }
+  return worst;
 }
 
 int batch_create(int count, const double* const* m, const double* alpha, const double* dt, const double* h,
@@ -602,16 +690,8 @@ int batch_create(int count, const double* const* m, const double* alpha, const d
     B->ninst = count;
     B->user = (cudaStream_t)stream;
     LL_CU(cudaEventCreateWithFlags(&B->entry_ev, cudaEventDisableTiming));
-    B->U = new ll_mg_hierarchy();
+    batch_build(B);
     ll_mg_hierarchy* U = B->U;
-    U->prm = B->prm;
-    U->union_mode = true;
-    U->tail_first = -1;
-    U->user = B->user;
-    LL_CU(cudaStreamCreateWithFlags(&U->s, cudaStreamNonBlocking));
-    LL_CU(cudaEventCreateWithFlags(&U->entry_ev, cudaEventDisableTiming));
-    const char* ng = getenv("LLMG_NO_GRAPHS");
-    U->use_graphs = !(ng && ng[0] == '1');
     batch_enter(B);
     LL_CU(cudaStreamSynchronize(U->s));  // the callers' fields are ready
     ll_mg_params ip = B->prm;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstddef>
+#include <map>
 #include <new>
 #include <type_traits>
 
@@ -1611,6 +1612,7 @@ int ll_mg_batch_update(ll_mg_batch* B, const double* const* m_tilde, const doubl
       numeric(H, m_tilde[i]);
     }
     batch_refresh(B);
+    for (auto& c : B->children) batch_refresh(c.second);  // sub-batches share the instances
     return LL_OK;
   } catch (Status st) {
     return st.code;
@@ -1640,6 +1642,8 @@ int ll_mg_batch_level_colours(const ll_mg_batch* B, int level) {
   if (!B || level < 0 || level >= B->U->nlev) return -1;
   return B->U->lev[level].ncol;
 }
+int ll_mg_batch_subbatches(const ll_mg_batch* B) { return B ? (int)B->children.size() : 0; }
+
 int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i) {
   if (!B || i < 0 || i >= B->ninst) return -1;
   return B->inst[i]->nlev;

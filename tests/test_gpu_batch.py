@@ -127,6 +127,25 @@ def test_update_matches_fresh_batch():
         assert np.array_equal(a, b)  # same arithmetic in the same order
 
 
+def test_compaction_is_invisible(monkeypatch):
+    """Compacting the still-iterating instances into sub-batches at restart
+    boundaries changes nothing: iterations, residuals and solutions are
+    bit-identical to the lockstep solve of the whole batch."""
+    cases = SMALL + [dict(c, alpha=c["alpha"] * 0.3, dt=c["dt"] * 3) for c in SMALL[:3]]
+    ms, B = _batch(cases, rtol=1e-12)
+    monkeypatch.setenv("LLMG_BATCH_NO_COMPACT", "1")
+    st1, its1, rrs1, sts1, xs1 = _solve(B, ms, cases)
+    assert B.subbatches == 0
+    monkeypatch.delenv("LLMG_BATCH_NO_COMPACT")
+    st2, its2, rrs2, sts2, xs2 = _solve(B, ms, cases)
+    assert B.subbatches >= 1
+    assert its1 == its2 and sts1 == sts2 and rrs1 == rrs2
+    for a, b in zip(xs1, xs2):
+        assert np.array_equal(a, b)
+    st3, its3, rrs3, sts3, xs3 = _solve(B, ms, cases)  # the cached sub-batches again
+    assert its3 == its2 and all(np.array_equal(a, b) for a, b in zip(xs3, xs2))
+
+
 def test_zero_rhs_instance_and_guess():
     ms, B = _batch(SMALL[:3], rtol=1e-10)
     rhs = [_t(ms[0] / SMALL[0]["dt"]), torch.zeros(3 * int(np.prod(SMALL[1]["grid"])), dtype=torch.float64,
