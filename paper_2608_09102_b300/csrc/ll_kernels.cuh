@@ -119,53 +119,61 @@ __global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, 
 // ---------------------------------------------------------------------------
 // numeric Galerkin products (Eq. galerkin), accumulated in float64
 // ---------------------------------------------------------------------------
-// level 1: A_1(I,J) = delta_IJ |G_I|/dt I + sum_{k in G_I} w_kJ Chat_k
-__global__ void k_galerkin_l1(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                              const int* __restrict__ sptr, const int* __restrict__ sidx, const int* __restrict__ sw,
-                              const int* __restrict__ mptr, long n2, const double* __restrict__ chat64, double inv_dt,
-                              double* __restrict__ val, double* __restrict__ dinv64, int* __restrict__ bad) {
+// row of every block of a BSR level
+__global__ void k_block_rows(int n, const int* __restrict__ rowptr, int* __restrict__ prow) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
-  for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) {
-    double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
-      long k = sidx[q];
-      double w = (double)sw[q];
-      for (int e = 0; e < 9; ++e) a[e] += w * chat64[e * n2 + k];
-    }
-    if (col[p] == I) {
-      double sz = (double)(mptr[I + 1] - mptr[I]) * inv_dt;
-      a[0] += sz;
-      a[4] += sz;
-      a[8] += sz;
-      double o[9];
-      if (!inv3(a, o)) atomicExch(bad, 1);
-      for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
-    }
-    for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
+  for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) prow[p] = I;
+}
+
+// One thread per coarse block: neighbouring threads write neighbouring
+// blocks (coalesced stores).  Each block sums its slot list in a fixed order.
+// level 1: A_1(I,J) = delta_IJ |G_I|/dt I + sum_{k in G_I} w_kJ Chat_k
+__global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
+                                  const int* __restrict__ sptr, const int* __restrict__ sidx,
+                                  const int* __restrict__ sw, const int* __restrict__ mptr, long n2,
+                                  const double* __restrict__ chat64, double inv_dt, double* __restrict__ val,
+                                  double* __restrict__ dinv64, int* __restrict__ bad) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnzb) return;
+  int I = prow[p];
+  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
+    long k = sidx[q];
+    double w = (double)sw[q];
+    for (int e = 0; e < 9; ++e) a[e] += w * chat64[e * n2 + k];
   }
+  if (col[p] == I) {
+    double sz = (double)(mptr[I + 1] - mptr[I]) * inv_dt;
+    a[0] += sz;
+    a[4] += sz;
+    a[8] += sz;
+    double o[9];
+    if (!inv3(a, o)) atomicExch(bad, 1);
+    for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
+  }
+  for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
 }
 
 // levels >= 2: sum of the fine blocks of each coarse slot
-__global__ void k_galerkin_bsr(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                               const int* __restrict__ sptr, const int* __restrict__ sidx,
-                               const double* __restrict__ fval, double* __restrict__ val, double* __restrict__ dinv64,
-                               int* __restrict__ bad) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= n) return;
-  for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) {
-    double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
-      const double* f = fval + 9 * (long)sidx[q];
-      for (int e = 0; e < 9; ++e) a[e] += f[e];
-    }
-    if (col[p] == I) {
-      double o[9];
-      if (!inv3(a, o)) atomicExch(bad, 1);
-      for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
-    }
-    for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
+__global__ void k_galerkin_bsr_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
+                                   const int* __restrict__ sptr, const int* __restrict__ sidx,
+                                   const double* __restrict__ fval, double* __restrict__ val,
+                                   double* __restrict__ dinv64, int* __restrict__ bad) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnzb) return;
+  int I = prow[p];
+  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
+    const double* f = fval + 9 * (long)sidx[q];
+    for (int e = 0; e < 9; ++e) a[e] += f[e];
   }
+  if (col[p] == I) {
+    double o[9];
+    if (!inv3(a, o)) atomicExch(bad, 1);
+    for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
+  }
+  for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
 }
 
 template <typename T>

@@ -35,6 +35,7 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   std::vector<int> cs;
   // below: new numbering
   DBuf<int> rowptr, col, diag;      // BSR pattern
+  DBuf<int> prow;                   // row of each block
   DBuf<int> sptr, sidx, sw;         // Galerkin slot map from the finer level
   DBuf<int> mptr, mem;              // members in the finer level (level 1: red-black slots)
   DBuf<int> mptr0, mem0;            // level 1: colour-0 slots only
@@ -314,6 +315,9 @@ void symbolic(ll_mg_hierarchy* H) {
     DevGraph gn;
     permute_graph(C.graph, C.n2o, C.o2n, gn, s);
     bsr_pattern(gn, C.rowptr, C.col, C.diag, C.nnzb, s);
+    C.prow.alloc(C.nnzb);
+    k_block_rows<<<cdiv(C.n, kBlock), kBlock, 0, s>>>(C.n, C.rowptr, C.prow);
+    LL_LAUNCHED();
     LL_CU(cudaStreamSynchronize(s));
   }
   CLevel& L1 = H->lev[1];
@@ -636,11 +640,11 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
   for (int l = 1; l < H->nlev; ++l) {
     CLevel& C = H->lev[l];
     if (l == 1)
-      k_galerkin_l1<<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.rowptr, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
-                                                   H->chat64, inv_dt, C.val64, C.dinv64, H->flag);
+      k_galerkin_l1_blk<<<cdiv(C.nnzb, 128), 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr,
+                                                          H->n2, H->chat64, inv_dt, C.val64, C.dinv64, H->flag);
     else
-      k_galerkin_bsr<<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.rowptr, C.col, C.sptr, C.sidx, H->lev[l - 1].val64,
-                                                    C.val64, C.dinv64, H->flag);
+      k_galerkin_bsr_blk<<<cdiv(C.nnzb, 128), 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx,
+                                                           H->lev[l - 1].val64, C.val64, C.dinv64, H->flag);
     LL_LAUNCHED();
     if (mixed) {
       if (H->prm.precision == LL_MIXED_BF16)
