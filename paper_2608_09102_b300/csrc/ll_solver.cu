@@ -627,7 +627,10 @@ __global__ void k_cellmajor_to_rb(GridGeom g, const int* __restrict__ nat, const
 // ---------------------------------------------------------------------------
 // numeric setup (every time step)
 // ---------------------------------------------------------------------------
-void numeric(ll_mg_hierarchy* H, const double* m) {
+// Numeric setup for m~ = m (coefficients, Galerkin levels, coarsest inverse),
+// queued on the hierarchy's stream without waiting; numeric_check() then
+// reads the two failure flags.  A batch queues every instance first.
+void numeric_launch(ll_mg_hierarchy* H, const double* m) {
   LL_PROF(LL_KIND_NUMERIC);
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
@@ -659,7 +662,6 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
       LL_LAUNCHED();
     }
   }
-  check_flag(H, LL_SINGULAR_COARSE);
   // coarsest dense LU
   int N = H->ncoarse3;
   if (H->nlev == 1) {
@@ -673,10 +675,21 @@ void numeric(ll_mg_hierarchy* H, const double* m) {
   LL_LAUNCHED();
   k_lu_inverse<<<cdiv(N, 128), 128, 0, s>>>(N, H->lu, H->perm, H->ainv);
   LL_LAUNCHED();
-  int st = 0;
-  LL_CU(cudaMemcpyAsync(&st, H->lu_status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  LL_CU(cudaStreamSynchronize(s));
-  if (st) throw Status{LL_SINGULAR_COARSE};
+}
+
+// singular diagonal block (level 0 or a Galerkin level) or singular coarsest
+// matrix: LL_SINGULAR_COARSE
+void numeric_check(ll_mg_hierarchy* H) {
+  int v[2] = {0, 0};
+  LL_CU(cudaMemcpyAsync(&v[0], H->flag.p, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+  LL_CU(cudaMemcpyAsync(&v[1], H->lu_status.p, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+  LL_CU(cudaStreamSynchronize(H->s));
+  if (v[0] || v[1]) throw Status{LL_SINGULAR_COARSE};
+}
+
+void numeric(ll_mg_hierarchy* H, const double* m) {
+  numeric_launch(H, m);
+  numeric_check(H);
 }
 
 // ---------------------------------------------------------------------------
@@ -1625,12 +1638,13 @@ int ll_mg_batch_update(ll_mg_batch* B, const double* const* m_tilde, const doubl
   try {
     batch_enter(B);
     LL_CU(cudaStreamSynchronize(B->U->s));
-    for (int i = 0; i < B->ninst; ++i) {
+    for (int i = 0; i < B->ninst; ++i) {  // queue every instance (own streams), then check
       ll_mg_hierarchy* H = B->inst[i];
       H->alpha = alpha[i];
       H->dt = dt[i];
-      numeric(H, m_tilde[i]);
+      numeric_launch(H, m_tilde[i]);
     }
+    for (auto* H : B->inst) numeric_check(H);
     batch_refresh(B);
     for (auto& c : B->children) batch_refresh(c.second);  // sub-batches share the instances
     return LL_OK;
