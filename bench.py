@@ -167,6 +167,29 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# replicas: every rank solves its own copy of the workload (the solve does
+# not shard); the job's time is the slowest rank's
+# ---------------------------------------------------------------------------
+def max_over_ranks(v: float, device) -> float:
+    """Maximum of v over the ranks of the default process group (v itself
+    when there is none)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank in at most `seconds` (the maximum over ranks)."""
+    return units_per_rank * world / seconds
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 # kinds whose arithmetic is float64 whatever the V-cycle precision
@@ -279,10 +302,7 @@ def run_ours(args):
     launches = ll.launch_count() - launches0
     dom_ms, dom_launches, dom_flops, dom_bytes = prof_read(KIND_NAMES.index(dominant))
     prof_start(0)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e_steps = max(1, min(args.steps, 10))
@@ -292,11 +312,11 @@ def run_ours(args):
     for _ in range(e2e_steps):
         H.step(mh, 1)  # copies host -> device, steps, copies back
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - te
+    e2e_s = max_over_ranks(time.perf_counter() - te, dev)
 
     if rank != 0:
         return
-    value = UNKNOWNS * args.steps * world / (elapsed_ms * 1e-3)
+    value = replica_throughput(UNKNOWNS * args.steps, world, elapsed_ms * 1e-3)
     peaks, peak_src = measured_peaks()
     roof = roofline(dominant, dom_ms, dom_launches, dom_flops, dom_bytes, args.precision, peaks, peak_src)
     if dominant == "bsr_smooth" and args.precision == "fp64" and roof.get("bytes_per_launch"):
@@ -324,8 +344,9 @@ def run_ours(args):
                                                               peak_src).items()
                                        if kk in ("bound", "achieved", "unit", "frac", "hbm_gbs", "tflops")}
                                    for k in KIND_NAMES if breakdown[k][1] > 0},
-        "e2e": {"value": UNKNOWNS * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": UNKNOWNS * 8,
-                "d2h_bytes_per_step": UNKNOWNS * 8, "steps": e2e_steps},
+        "e2e": {"value": replica_throughput(UNKNOWNS * e2e_steps, world, e2e_s), "unit": UNIT,
+                "h2d_bytes_per_step": UNKNOWNS * 8 * world, "d2h_bytes_per_step": UNKNOWNS * 8 * world,
+                "steps": e2e_steps},
     }
     if not args.no_cpu_baseline:
         s, p = oracle_sample(3)
