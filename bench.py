@@ -192,6 +192,9 @@ def replica_throughput(units_per_rank: float, world: int, seconds: float) -> flo
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# kinds that make up the V-cycle preconditioner
+VCYCLE_KINDS = ("l0_smooth", "l0_restrict", "bsr_smooth", "bsr_other", "coarsest", "coarse_tail")
+
 # kinds whose arithmetic is float64 whatever the V-cycle precision
 FP64_KINDS = {"outer_apply", "gcr_vector", "coarsest", "numeric"}
 
@@ -339,6 +342,10 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "kernel_breakdown_warmup_ms": {k: round(v[0], 3) for k, v in breakdown.items()},
+        # the V-cycle's kernels together (algorithmic bytes over their event time, warm-up steps)
+        "vcycle_hbm_gbs": (sum(breakdown[k][3] for k in VCYCLE_KINDS)
+                           / max(sum(breakdown[k][0] for k in VCYCLE_KINDS), 1e-9) / 1e6),
+        "numeric_setup_ms_per_step": breakdown["numeric"][0] / max(args.warmup, 1),
         "kernel_roofline_warmup": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                        for kk, vv in roofline(k, *breakdown[k], args.precision, peaks,
                                                               peak_src).items()
