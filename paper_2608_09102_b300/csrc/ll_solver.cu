@@ -246,6 +246,14 @@ void launch_k(ll_mg_hierarchy* H, void (*k)(KP...), long grid, int block, A... a
 template <typename T> constexpr int lanes();
 template <> constexpr int lanes<double>() { return kRowLanes; }
 template <> constexpr int lanes<float>() { return 2 * kRowLanes; }
+// A launch over fewer rows than this fills only part of the GPU and lasts as
+// long as one row's chain of dependent loads; 8 lanes per row then halve the
+// chain in float64 too (issue slots are not the limit there).
+constexpr int kWideLaneRows = 20000;
+template <typename T>
+bool wide_lanes(long rows) {
+  return lanes<T>() >= 8 || rows < kWideLaneRows;
+}
 constexpr int kDotChunk = 8;
 // Coarse-level kernels use small blocks: a colour class of a small level then
 // spreads over many SMs instead of queueing on the float64 units of one.
@@ -724,9 +732,14 @@ void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e, bool timed = true
   double f = 0, by = 0;
   if (timed) class_work<T, TM, MODE>(L, t, f, by);
   ProfScope prof_scope_(H, timed ? LL_KIND_BSR_SMOOTH : LL_NUM_KINDS, f, by);
-  launch_k(H, kb_sweep<T, TM, lanes<T>(), MODE>, cdiv((long)(r1 - r0) * lanes<T>(), kCoarseBlock),
-           kCoarseBlock, r0, r1, (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col,
-           (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
+  if (wide_lanes<T>(r1 - r0))
+    launch_k(H, kb_sweep<T, TM, 8, MODE>, cdiv((long)(r1 - r0) * 8, kCoarseBlock), kCoarseBlock, r0, r1,
+             (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(),
+             (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
+  else
+    launch_k(H, kb_sweep<T, TM, kRowLanes, MODE>, cdiv((long)(r1 - r0) * kRowLanes, kCoarseBlock), kCoarseBlock,
+             r0, r1, (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(),
+             (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
 }
 
 // one full plain block-GS sweep of level l (colours ascending or descending)
