@@ -22,6 +22,9 @@ namespace llmg {
 
 constexpr int kTailThreads = 256;  // per CTA
 constexpr int kTailUnroll = 4;  // blocks per lane loaded before the products
+// levels below this many rows use 8 lanes per row: their classes leave most
+// of the cluster's threads idle, and wider rows shorten each phase's chain
+constexpr int kTailWideRows = 4096;
 constexpr int kTailMaxColours = 64;
 
 template <typename T, typename TM>
@@ -186,7 +189,10 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const TailArgs<T, 
   long nthreads = (long)gridDim.x * blockDim.x;  // the grid is one cluster
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   tail_prefetch(A, tid, nthreads);
-  for (int l = A.first; l < A.solo_first && l < A.last; ++l) tail_down<T, TM, G>(A, l, tid, nthreads, ClusterPhase());
+  for (int l = A.first; l < A.solo_first && l < A.last; ++l) {
+    if (A.L[l].n < kTailWideRows) tail_down<T, TM, 8>(A, l, tid, nthreads, ClusterPhase());
+    else tail_down<T, TM, G>(A, l, tid, nthreads, ClusterPhase());
+  }
   if (A.solo_first >= A.last) {
     tail_coarsest<T, TM>(A, tid, nthreads, ClusterPhase());
   } else {
@@ -198,8 +204,10 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const TailArgs<T, 
     }
     tail_sync();  // the first CTA's results, visible to the cluster
   }
-  for (int l = (A.solo_first < A.last ? A.solo_first : A.last) - 1; l >= A.first; --l)
-    tail_up<T, TM, G>(A, l, tid, nthreads, ClusterPhase());
+  for (int l = (A.solo_first < A.last ? A.solo_first : A.last) - 1; l >= A.first; --l) {
+    if (A.L[l].n < kTailWideRows) tail_up<T, TM, 8>(A, l, tid, nthreads, ClusterPhase());
+    else tail_up<T, TM, G>(A, l, tid, nthreads, ClusterPhase());
+  }
 }
 
 }  // namespace llmg
