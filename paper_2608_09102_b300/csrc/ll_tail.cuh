@@ -183,8 +183,10 @@ __device__ void tail_prefetch(const TailArgs<T, TM>& A, long tid, long nthreads)
 // hundred rows: there a phase is latency, and the first CTA runs them alone
 // with CTA barriers, which cost far less than cluster-wide ones, while the
 // other CTAs wait at the next cluster barrier.
+// One CTA per SM by construction (one cluster of CTAs on distinct SMs), so the
+// compiler may use the whole register file (avoids spills in float32).
 template <typename T, typename TM, int G>
-__global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const TailArgs<T, TM>* __restrict__ args) {
+__global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(const TailArgs<T, TM>* __restrict__ args) {
   const TailArgs<T, TM>& A = *args;
   long nthreads = (long)gridDim.x * blockDim.x;  // the grid is one cluster
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
