@@ -869,7 +869,9 @@ __device__ __forceinline__ void block_reduce_store(double* v, double* partial, i
 }
 
 // out[q] = sum of partial[q][0..kRedBlocks), fixed order
-__global__ void k_finish(const double* __restrict__ partial, double* __restrict__ out) {
+__global__ void k_finish(const double* __restrict__ partial, double* __restrict__ out,
+                         const double* __restrict__ gate = nullptr) {
+  if (gate && *gate == 0.0) return;
   __shared__ double sh[kBlock];
   int q = blockIdx.x;
   double a = 0;
@@ -1001,25 +1003,41 @@ __global__ void __launch_bounds__(256) kg_residual(GridGeom g, const double* __r
   block_reduce_store<2>(acc, partial, 2);
 }
 
-// partial dots d_i = C_i . v for i in [i0, i0 + cnt), cnt <= NV
-template <int NV>
+// A gated kernel does nothing when *gate == 0 (the whole grid returns at
+// once): the second Gram-Schmidt pass, decided on the device, inside a
+// captured graph.  gate == nullptr: always run.
+__device__ __forceinline__ bool gated_off(const double* gate) { return gate && *gate == 0.0; }
+
+// partial dots d_i = C_i . v for i in [i0, i0 + cnt), cnt <= NV; SELF adds
+// v . v as value cnt
+template <int NV, bool SELF = false>
 __global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restrict__ C, int i0, int cnt,
-                                                   const double* __restrict__ v, double* __restrict__ partial) {
-  double acc[NV];
+                                                   const double* __restrict__ v, double* __restrict__ partial,
+                                                   const double* __restrict__ gate = nullptr) {
+  if (gated_off(gate)) return;
+  double acc[NV + 1];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) acc[q] = 0;
+  for (int q = 0; q <= NV; ++q) acc[q] = 0;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double vt = v[t];
 #pragma unroll
     for (int q = 0; q < NV; ++q)
       if (q < cnt) acc[q] += C[(long)(i0 + q) * n + t] * vt;
+    if (SELF) acc[NV] += vt * vt;
   }
-  block_reduce_store<NV>(acc, partial, cnt);
+  if (SELF) {  // v . v goes to row cnt (static indices keep acc in registers)
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q == cnt) acc[q] = acc[NV];
+  }
+  block_reduce_store<NV + 1>(acc, partial, cnt + (SELF ? 1 : 0));
 }
 
 // v -= sum_{i<j} coef[i] C_i  (coef on the device)
 __global__ void __launch_bounds__(256) kg_multiaxpy(long n, double* __restrict__ v, const double* __restrict__ C,
-                                                    int j, const double* __restrict__ coef) {
+                                                    int j, const double* __restrict__ coef,
+                                                    const double* __restrict__ gate = nullptr) {
+  if (gated_off(gate)) return;
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= n) return;
   double a = v[t];
@@ -1089,7 +1107,8 @@ __global__ void k_from_rb(GridGeom g, const int* __restrict__ nat_of_slot, const
 // ---------------------------------------------------------------------------
 struct GcrScal {
   double rn2, bn2, cc, cr;         // reduction results (read by the host)
-  double gjj, rcoef, pad0, pad1;   // gamma_jj, alpha_j s_j
+  double gjj, rcoef;               // gamma_jj, alpha_j s_j
+  double cn2, pass2;               // |c|^2 before the projection; 1: run the second pass
   double d[kMaxRestart];           // dots of the current vector with C'_i
   double coef[kMaxRestart];        // projection coefficients of the update
   double gam[kMaxRestart * kMaxRestart];  // Gamma, row-major
@@ -1099,13 +1118,21 @@ struct GcrScal {
 // Gram-Schmidt coefficients from the dots d_i = C'_i . c (C'_i unnormalised,
 // c_i = s_i C'_i): gamma_i = s_i d_i is added to Gamma_ij and the update
 // c -= gamma_i c_i uses coef_i = gamma_i s_i.
-__global__ void k_gs_coef(GcrScal* S, int j, int first) {
+// After the first pass, the second is needed only when the projection removed
+// more than half of |c|^2 (|c - P c| < |c|/sqrt 2): below that, rounding
+// in the first pass can have left components along the c_i that a second
+// pass removes ("twice is enough", Kahan-Parlett).  pass2 is set to 0 or 1.
+__global__ void k_gs_coef(GcrScal* S, int j, int first, const double* __restrict__ gate = nullptr) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (gate && *gate == 0.0) return;
+  double proj = 0;
   for (int i = 0; i < j; ++i) {
     double gm = S->s[i] * S->d[i];
     S->gam[i * kMaxRestart + j] = first ? gm : S->gam[i * kMaxRestart + j] + gm;
     S->coef[i] = gm * S->s[i];
+    proj += gm * gm;
   }
+  if (first) S->pass2 = (S->cn2 - proj < 0.5 * S->cn2) ? 1.0 : 0.0;
 }
 // gamma_jj = |c|, s_j = 1/gamma_jj, alpha_j = c_j . r = s_j (c . r)
 __global__ void k_norm_coef(GcrScal* S, int j) {

@@ -1055,26 +1055,42 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
     kg_apply<T><<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);  // step 2
     LL_LAUNCHED();
   }
-  // step 3: classical Gram-Schmidt applied twice (the same projection as the
-  // modified Gram-Schmidt loop of Algorithm 1), then step 4's |c|^2 and c.r
+  // step 3: classical Gram-Schmidt, the same projection as the modified
+  // Gram-Schmidt loop of Algorithm 1 in exact arithmetic.  A second pass
+  // corrects the first pass's rounding; it runs only when the first removed
+  // more than half of |c|^2 (k_gs_coef sets the device flag pass2 that gates
+  // the second pass's kernels).  Then step 4's |c|^2 and c.r.
   for (int pass = 0; pass < 2 && j > 0; ++pass) {
+    const double* gate = pass == 0 ? nullptr : &S->pass2;
     for (int i0 = 0; i0 < j; i0 += kDotChunk) {
       int cnt = std::min(kDotChunk, j - i0);
+      bool self = pass == 0 && i0 == 0;  // |c|^2 before the projection, with the first dots
       {
         LL_PROFW(LL_KIND_GCR_VECTOR, 2.0 * cnt * n3, 8.0 * (cnt + 1) * n3);
-        kg_multidot<kDotChunk><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
+        if (self)
+          kg_multidot<kDotChunk, true><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
+        else
+          kg_multidot<kDotChunk, false><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial, gate);
         LL_LAUNCHED();
       }
-      finish(H, cnt, S->d + i0);
+      {
+        LL_PROF(LL_KIND_GCR_VECTOR);
+        k_finish<<<cnt, kBlock, 0, s>>>(H->partial, S->d + i0, gate);
+        LL_LAUNCHED();
+        if (self) {
+          k_finish<<<1, kBlock, 0, s>>>(H->partial + (size_t)cnt * kRedBlocks, &S->cn2);
+          LL_LAUNCHED();
+        }
+      }
     }
     {
       LL_PROF(LL_KIND_GCR_VECTOR);
-      k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0);
+      k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0, gate);
       LL_LAUNCHED();
     }
     {
       LL_PROFW(LL_KIND_GCR_VECTOR, 2.0 * j * n3, 8.0 * (j + 2) * n3);
-      kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef);
+      kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef, gate);
       LL_LAUNCHED();
     }
   }
