@@ -71,6 +71,7 @@ namespace {
 constexpr long kChunkElems = 3 * 2048;  // elements of one GCR chunk (one block)
 constexpr int kFieldRn2 = 0, kFieldBn2 = 1, kFieldCc = 2;
 constexpr int kFieldD = (int)(offsetof(GcrScal, d) / sizeof(double));
+constexpr int kFieldCn2 = (int)(offsetof(GcrScal, cn2) / sizeof(double));
 
 void batch_enter(ll_mg_batch* B) {
   LL_CU(cudaEventRecord(B->entry_ev, B->user));
@@ -316,7 +317,7 @@ void batch_allocate(ll_mg_batch* B) {
   LL_CU(cudaMemcpyAsync(B->chunks.p, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, U->s));
   B->iptr.alloc(ip.size());
   LL_CU(cudaMemcpyAsync(B->iptr.p, ip.data(), ip.size() * sizeof(int), cudaMemcpyHostToDevice, U->s));
-  B->partial.alloc((size_t)kDotChunk * B->nchunks);
+  B->partial.alloc((size_t)(kDotChunk + 1) * B->nchunks);  // dots plus |c|^2
   B->scal.alloc(ni);
   B->scal.zero(U->s);
   B->head.alloc(2 * ni);
@@ -376,8 +377,9 @@ void batch_refresh(ll_mg_batch* B) {
   else batch_values<double, double>(B);
 }
 
-void batch_finish(ll_mg_batch* B, int nvals, int field) {
-  kgb_finish<<<dim3(B->ninst, nvals), kBlock, 0, B->U->s>>>(B->partial, B->nchunks, B->iptr, B->scal, field);
+void batch_finish(ll_mg_batch* B, int nvals, int field, bool gated = false, int row0 = 0) {
+  kgb_finish<<<dim3(B->ninst, nvals), kBlock, 0, B->U->s>>>(B->partial.p + (size_t)row0 * B->nchunks, B->nchunks,
+                                                             B->iptr, B->scal, field, gated);
   LL_LAUNCHED();
 }
 
@@ -399,16 +401,23 @@ void batch_iteration_body(ll_mg_batch* B, int j) {
   LL_CU(cudaMemcpyAsync(zj, L0.x<T>(), n3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
   kgb_apply<T><<<cdiv(L0.n, kBlock), kBlock, 0, s>>>(L0.n, L0.rowptr, L0.col, L0.val64, zj, cj);  // step 2
   LL_LAUNCHED();
-  for (int pass = 0; pass < 2 && j > 0; ++pass) {  // step 3: CGS2
+  for (int pass = 0; pass < 2 && j > 0; ++pass) {  // step 3: CGS, second pass per instance when needed
+    const GcrScal* gate = pass == 0 ? nullptr : S;
     for (int i0 = 0; i0 < j; i0 += kDotChunk) {
       int cnt = std::min(kDotChunk, j - i0);
-      kgb_multidot<kDotChunk><<<nch, kBlock, 0, s>>>(B->chunks, nch, B->C, n3, i0, cnt, cj, B->partial);
+      bool self = pass == 0 && i0 == 0;
+      if (self)
+        kgb_multidot<kDotChunk, true><<<nch, kBlock, 0, s>>>(B->chunks, nch, B->C, n3, i0, cnt, cj, B->partial);
+      else
+        kgb_multidot<kDotChunk, false><<<nch, kBlock, 0, s>>>(B->chunks, nch, B->C, n3, i0, cnt, cj, B->partial,
+                                                              gate);
       LL_LAUNCHED();
-      batch_finish(B, cnt, kFieldD + i0);
+      batch_finish(B, cnt, kFieldD + i0, pass == 1);
+      if (self) batch_finish(B, 1, kFieldCn2, false, cnt);
     }
     kgb_gs_coef<<<cdiv(ni, 64), 64, 0, s>>>(S, ni, j, pass == 0);
     LL_LAUNCHED();
-    kgb_multiaxpy<<<nch, kBlock, 0, s>>>(B->chunks, cj, B->C, n3, j, S);
+    kgb_multiaxpy<<<nch, kBlock, 0, s>>>(B->chunks, cj, B->C, n3, j, S, gate);
     LL_LAUNCHED();
   }
   kgb_dot2<<<nch, kBlock, 0, s>>>(B->chunks, nch, cj, B->r, B->partial);  // step 4

@@ -374,9 +374,10 @@ __device__ __forceinline__ void chunk_reduce_store(double* v, double* partial, i
 
 // ((double*)&S[i])[field + q] = sum of partial[q][chunks of instance i]
 __global__ void kgb_finish(const double* __restrict__ partial, int nchunks, const int* __restrict__ iptr,
-                           GcrScal* __restrict__ S, int field) {
+                           GcrScal* __restrict__ S, int field, bool gated = false) {
   __shared__ double sh[kBlock];
   int i = blockIdx.x, q = blockIdx.y;
+  if (gated && S[i].pass2 == 0.0) return;
   double a = 0;
   for (int k = iptr[i] + threadIdx.x; k < iptr[i + 1]; k += kBlock) a += partial[(long)q * nchunks + k];
   sh[threadIdx.x] = a;
@@ -388,27 +389,42 @@ __global__ void kgb_finish(const double* __restrict__ partial, int nchunks, cons
   if (threadIdx.x == 0) reinterpret_cast<double*>(S + i)[field + q] = sh[0];
 }
 
-template <int NV>
+// gate: the second Gram-Schmidt pass of an instance runs only when its
+// pass2 flag is set (see k_gs_coef); gate == nullptr: always run
+__device__ __forceinline__ bool inst_off(const GcrScal* gate, int inst) { return gate && gate[inst].pass2 == 0.0; }
+
+// SELF adds v . v as value cnt (|c|^2 before the projection)
+template <int NV, bool SELF = false>
 __global__ void __launch_bounds__(256) kgb_multidot(const Chunk* __restrict__ ch, int nchunks,
                                                     const double* __restrict__ C, long n3, int i0, int cnt,
-                                                    const double* __restrict__ v, double* __restrict__ partial) {
+                                                    const double* __restrict__ v, double* __restrict__ partial,
+                                                    const GcrScal* __restrict__ gate = nullptr) {
   Chunk k = ch[blockIdx.x];
-  double acc[NV];
+  if (inst_off(gate, k.inst)) return;  // uniform per block: one chunk, one instance
+  double acc[NV + 1];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) acc[q] = 0;
+  for (int q = 0; q <= NV; ++q) acc[q] = 0;
   for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
     double vt = v[t];
 #pragma unroll
     for (int q = 0; q < NV; ++q)
       if (q < cnt) acc[q] += C[(long)(i0 + q) * n3 + t] * vt;
+    if (SELF) acc[NV] += vt * vt;
   }
-  chunk_reduce_store<NV>(acc, partial, cnt, nchunks);
+  if (SELF) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q == cnt) acc[q] = acc[NV];
+  }
+  chunk_reduce_store<NV + 1>(acc, partial, cnt + (SELF ? 1 : 0), nchunks);
 }
 
 __global__ void __launch_bounds__(256) kgb_multiaxpy(const Chunk* __restrict__ ch, double* __restrict__ v,
                                                      const double* __restrict__ C, long n3, int j,
-                                                     const GcrScal* __restrict__ S) {
+                                                     const GcrScal* __restrict__ S,
+                                                     const GcrScal* __restrict__ gate = nullptr) {
   Chunk k = ch[blockIdx.x];
+  if (inst_off(gate, k.inst)) return;
   const double* coef = S[k.inst].coef;
   for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
     double a = v[t];
@@ -512,11 +528,15 @@ __global__ void kgb_gs_coef(GcrScal* S, int ninst, int j, int first) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ninst) return;
   GcrScal& s = S[i];
+  if (!first && s.pass2 == 0.0) return;  // second pass not needed for this instance
+  double proj = 0;
   for (int q = 0; q < j; ++q) {
     double gm = s.s[q] * s.d[q];
     s.gam[q * kMaxRestart + j] = first ? gm : s.gam[q * kMaxRestart + j] + gm;
     s.coef[q] = gm * s.s[q];
+    proj += gm * gm;
   }
+  if (first) s.pass2 = (s.cn2 - proj < 0.5 * s.cn2) ? 1.0 : 0.0;
 }
 // as k_norm_coef; an instance that is not active keeps its residual
 __global__ void kgb_norm_coef(GcrScal* S, int ninst, int j, const int* __restrict__ act) {
