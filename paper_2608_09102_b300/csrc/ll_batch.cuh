@@ -407,10 +407,9 @@ void batch_iteration_body(ll_mg_batch* B, int j) {
       int cnt = std::min(kDotChunk, j - i0);
       bool self = pass == 0 && i0 == 0;
       if (self)
-        kgb_multidot<kDotChunk, true><<<nch, kBlock, 0, s>>>(B->chunks, nch, B->C, n3, i0, cnt, cj, B->partial);
+        launch_batch_multidot<kDotChunk, true>(cnt, s, nch, B->chunks, B->C, n3, i0, cj, B->partial);
       else
-        kgb_multidot<kDotChunk, false><<<nch, kBlock, 0, s>>>(B->chunks, nch, B->C, n3, i0, cnt, cj, B->partial,
-                                                              gate);
+        launch_batch_multidot<kDotChunk, false>(cnt, s, nch, B->chunks, B->C, n3, i0, cj, B->partial, gate);
       LL_LAUNCHED();
       batch_finish(B, cnt, kFieldD + i0, pass == 1);
       if (self) batch_finish(B, 1, kFieldCn2, false, cnt);

@@ -419,6 +419,19 @@ __global__ void __launch_bounds__(256) kgb_multidot(const Chunk* __restrict__ ch
   chunk_reduce_store<NV + 1>(acc, partial, cnt + (SELF ? 1 : 0), nchunks);
 }
 
+// kgb_multidot launched with NV = cnt (1 <= cnt <= NV), as launch_multidot
+template <int NV, bool SELF>
+void launch_batch_multidot(int cnt, cudaStream_t s, int nch, const Chunk* ch, const double* C, long n3, int i0,
+                           const double* v, double* partial, const GcrScal* gate = nullptr) {
+  if constexpr (NV > 1) {
+    if (cnt < NV) {
+      launch_batch_multidot<NV - 1, SELF>(cnt, s, nch, ch, C, n3, i0, v, partial, gate);
+      return;
+    }
+  }
+  kgb_multidot<NV, SELF><<<nch, kBlock, 0, s>>>(ch, nch, C, n3, i0, cnt, v, partial, gate);
+}
+
 __global__ void __launch_bounds__(256) kgb_multiaxpy(const Chunk* __restrict__ ch, double* __restrict__ v,
                                                      const double* __restrict__ C, long n3, int j,
                                                      const GcrScal* __restrict__ S,

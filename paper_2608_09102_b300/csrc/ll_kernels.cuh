@@ -1033,6 +1033,22 @@ __global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restr
   block_reduce_store<NV + 1>(acc, partial, cnt + (SELF ? 1 : 0));
 }
 
+// kg_multidot launched with NV = cnt (1 <= cnt <= NV).  The kernel is bound
+// by the float64 pipe, and with NV fixed at the chunk size every launch took
+// the time of a full chunk whatever cnt was: the masked-off fused
+// multiply-adds still cost pipe slots.
+template <int NV, bool SELF>
+void launch_multidot(int cnt, cudaStream_t s, long n, const double* C, int i0, const double* v, double* partial,
+                     const double* gate = nullptr) {
+  if constexpr (NV > 1) {
+    if (cnt < NV) {
+      launch_multidot<NV - 1, SELF>(cnt, s, n, C, i0, v, partial, gate);
+      return;
+    }
+  }
+  kg_multidot<NV, SELF><<<kRedBlocks, kBlock, 0, s>>>(n, C, i0, cnt, v, partial, gate);
+}
+
 // v -= sum_{i<j} coef[i] C_i  (coef on the device)
 __global__ void __launch_bounds__(256) kg_multiaxpy(long n, double* __restrict__ v, const double* __restrict__ C,
                                                     int j, const double* __restrict__ coef,

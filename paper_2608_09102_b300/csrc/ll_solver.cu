@@ -1072,9 +1072,9 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
       {
         LL_PROFW(LL_KIND_GCR_VECTOR, wk * 2.0 * cnt * n3, wk * 8.0 * (cnt + 1) * n3);
         if (self)
-          kg_multidot<kDotChunk, true><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial);
+          launch_multidot<kDotChunk, true>(cnt, s, n3, H->C, i0, cj, H->partial);
         else
-          kg_multidot<kDotChunk, false><<<kRedBlocks, kBlock, 0, s>>>(n3, H->C, i0, cnt, cj, H->partial, gate);
+          launch_multidot<kDotChunk, false>(cnt, s, n3, H->C, i0, cj, H->partial, gate);
         LL_LAUNCHED();
       }
       {
