@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # launches of the --grid 96 case, against the library's byte model for the
 # same launches (profiles/kb_sweep_96cube_fp64.md).  Scaled by the bytes a
 # launch processes to the traffic of a 128^3 launch.
-KB_SWEEP_TRAFFIC_RATIO = 9.667e6 / 9.293e6
+KB_SWEEP_TRAFFIC_RATIO = 9.679e6 / 9.293e6
 
 KIND_NAMES = ["l0_smooth", "l0_restrict", "outer_apply", "bsr_smooth", "bsr_other", "gcr_vector", "coarsest",
               "numeric", "coarse_tail"]

@@ -1,6 +1,7 @@
 // Device kernels of the numeric setup, the V-cycle and the GCR iteration.
 // Included by ll_solver.cu only.
 #pragma once
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <math.h>
@@ -658,6 +659,37 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
   }
 }
 
+// Slots of one lane in a row's lane-strided range of n block slots.
+template <int G>
+__device__ __forceinline__ int lane_slots(int n, int lane) {
+  return n > lane ? (n - lane + G - 1) / G : 0;
+}
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// The unroll a warp uses in row_msub / row_msub_off: the largest slot count of
+// its lanes, capped at U (0: no lane has a block).  With a fixed unroll, slots
+// that no lane of the warp has still issue their multiply-adds under
+// predication, and masked-off float64 instructions cost float64 pipe time as
+// if they ran; that pipe (2 multiply-adds per clock per SM here) sets the pace
+// of the float64 sweeps.  Every lane of the warp must call this.
+template <int U>
+__device__ __forceinline__ int warp_unroll(int n) {
+  int m = __reduce_max_sync(0xffffffffu, n);
+  return m < U ? m : U;
+}
+
+// f(std::integral_constant<int, UU>) with UU the smallest compiled unroll
+// >= u: the unrolls 1, 2 and 3 are compiled where bit 0, 1 and 2 of USET are
+// set, and U always.  u <= 0: nothing.
+template <int U, int USET, typename F>
+__device__ __forceinline__ void with_unroll(int u, F&& f) {
+  if (u <= 0) return;
+  if (USET > 0 && (USET & 1) && u == 1) f(std::integral_constant<int, cmin(U, 1)>{});
+  else if (USET > 0 && (USET & 2) && u <= 2) f(std::integral_constant<int, cmin(U, 2)>{});
+  else if (USET > 0 && (USET & 4) && u <= 3) f(std::integral_constant<int, cmin(U, 3)>{});
+  else f(std::integral_constant<int, U>{});
+}
+
 // Block Gauss-Seidel update of one row of a colour class, G lanes per row.
 // Coarse levels are renumbered so that each colour class is the contiguous
 // row range [r0, r1), colours ascending, and every row's blocks are sorted by
@@ -673,7 +705,7 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
 // three output components.  Every lane of the warp must call this (shuffles).
 // sweep_row with the row's block range already loaded: p0 = rowptr_I,
 // pd = diag_I, p1 = rowptr_{I+1}
-template <typename T, typename TM, int G, int MODE, int U = 4>
+template <typename T, typename TM, int G, int MODE, int U = 4, int USET = 7>
 __device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p0, int pd, int p1,
                                              const int* __restrict__ col, const TM* __restrict__ val,
                                              const T* __restrict__ dinv, const T* __restrict__ b,
@@ -681,10 +713,17 @@ __device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p
                                              const T* __restrict__ e) {
   static_assert(G >= 3, "one lane per output component");
   T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, d0 = 0, d1 = 0, d2 = 0;
-  if (active) {
-    if (MODE == 0) row_msub<T, TM, G, U, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-    else row_msub_off<T, TM, G, U, MODE == 2>(p0, pd, p1, lane, col, val, x, agg, e, a0, a1, a2);
-  }
+  // USET < 0: the fixed unroll U (the coarse tail, where the warp-uniform
+  // unroll measured slower: more copies of the loop in a kernel that already
+  // uses the full register budget)
+  int n = !active ? 0 : MODE == 0 ? lane_slots<G>(pd - p0, lane) : lane_slots<G>(p1 - p0 - 1, lane);
+  int u = USET < 0 ? (active ? U : 0) : warp_unroll<U>(n);
+  if (active)
+    with_unroll<U, USET>(u, [&](auto uc) {
+      constexpr int UU = decltype(uc)::value;
+      if (MODE == 0) row_msub<T, TM, G, UU, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
+      else row_msub_off<T, TM, G, UU, MODE == 2>(p0, pd, p1, lane, col, val, x, agg, e, a0, a1, a2);
+    });
   group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
   if (active && lane < 3) {
     b0 = b[3L * I]; b1 = b[3L * I + 1]; b2 = b[3L * I + 2];
@@ -694,7 +733,7 @@ __device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p
   }
 }
 
-template <typename T, typename TM, int G, int MODE, int U = 4>
+template <typename T, typename TM, int G, int MODE, int U = 4, int USET = 7>
 __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
                                           const int* __restrict__ diag, const int* __restrict__ col,
                                           const TM* __restrict__ val, const T* __restrict__ dinv,
@@ -706,7 +745,7 @@ __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const in
     pd = ro(diag + I);
     p1 = MODE == 0 ? 0 : ro(rowptr + I + 1);
   }
-  sweep_row_at<T, TM, G, MODE, U>(I, lane, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
+  sweep_row_at<T, TM, G, MODE, U, USET>(I, lane, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
 }
 
 
@@ -729,16 +768,19 @@ __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __res
 }
 
 // residual_row with the row's block range [p0, p1) already loaded
-template <typename T, typename TM, int G, bool SUFFIX, int U = 4>
+template <typename T, typename TM, int G, bool SUFFIX, int U = 4, int USET = 7>
 __device__ __forceinline__ void residual_row_at(int I, int lane, bool active, int p0, int p1,
                                                 const int* __restrict__ col, const TM* __restrict__ val,
                                                 const T* __restrict__ b, const T* __restrict__ x,
                                                 T* __restrict__ r) {
   static_assert(G >= 3, "one lane per output component");
   T a0 = 0, a1 = 0, a2 = 0, bc = 0;
+  int u = USET < 0 ? (active ? U : 0) : warp_unroll<U>(active ? lane_slots<G>(p1 - p0, lane) : 0);
   if (active) {
     if (!SUFFIX && lane < 3) bc = b[3L * I + lane];
-    row_msub<T, TM, G, U, false>(p0 + lane, p1, col, val, x, nullptr, nullptr, a0, a1, a2);
+    with_unroll<U, USET>(u, [&](auto uc) {
+      row_msub<T, TM, G, decltype(uc)::value, false>(p0 + lane, p1, col, val, x, nullptr, nullptr, a0, a1, a2);
+    });
   }
   group_sum3<G>(a0, a1, a2);
   if (active && lane < 3) r[3L * I + lane] = bc + (lane == 0 ? a0 : lane == 1 ? a1 : a2);
@@ -751,7 +793,7 @@ __device__ __forceinline__ void residual_row_at(int I, int lane, bool active, in
 // is only the part of the columns updated later:
 //   r_I = - sum_{J in higher colours} A_IJ x_J   (exact up to rounding),
 // half of the off-diagonal blocks and no b.
-template <typename T, typename TM, int G, bool SUFFIX = false, int U = 4>
+template <typename T, typename TM, int G, bool SUFFIX = false, int U = 4, int USET = 7>
 __device__ __forceinline__ void residual_row(int I, int lane, bool active, const int* __restrict__ rowptr,
                                              const int* __restrict__ diag, const int* __restrict__ col,
                                              const TM* __restrict__ val, const T* __restrict__ b,
@@ -761,7 +803,7 @@ __device__ __forceinline__ void residual_row(int I, int lane, bool active, const
     p0 = SUFFIX ? ro(diag + I) + 1 : ro(rowptr + I);
     p1 = ro(rowptr + I + 1);
   }
-  residual_row_at<T, TM, G, SUFFIX, U>(I, lane, active, p0, p1, col, val, b, x, r);
+  residual_row_at<T, TM, G, SUFFIX, U, USET>(I, lane, active, p0, p1, col, val, b, x, r);
 }
 
 template <typename T, typename TM, int G, bool SUFFIX>
@@ -898,8 +940,12 @@ __global__ void __launch_bounds__(256) kb_spmv(int n, const int* __restrict__ ro
   int lane = threadIdx.x % G;
   bool active = I < n;
   T a0 = 0, a1 = 0, a2 = 0;
+  int p0 = active ? rowptr[I] : 0, p1 = active ? rowptr[I + 1] : 0;
+  int u = warp_unroll<4>(active ? lane_slots<G>(p1 - p0, lane) : 0);
   if (active)
-    row_msub<T, TM, G, 4, false>(rowptr[I] + lane, rowptr[I + 1], col, val, x, nullptr, nullptr, a0, a1, a2);
+    with_unroll<4, 7>(u, [&](auto uc) {
+      row_msub<T, TM, G, decltype(uc)::value, false>(p0 + lane, p1, col, val, x, nullptr, nullptr, a0, a1, a2);
+    });
   group_sum3<G>(a0, a1, a2);
   if (active)
     for (int c = lane; c < 3; c += G) y[3L * I + c] = -(c == 0 ? a0 : c == 1 ? a1 : a2);

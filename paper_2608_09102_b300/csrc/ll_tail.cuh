@@ -21,7 +21,10 @@
 namespace llmg {
 
 constexpr int kTailThreads = 256;  // per CTA
-constexpr int kTailUnroll = 4;  // blocks per lane loaded before the products
+// blocks per lane loaded before the products, a fixed unroll here (the
+// per-class kernels choose a warp-uniform one)
+constexpr int kTailUnroll = 4;
+
 // levels below this many rows use 8 lanes per row: their classes leave most
 // of the cluster's threads idle, and wider rows shorten each phase's chain
 constexpr int kTailWideRows = 4096;
@@ -75,8 +78,8 @@ __device__ __forceinline__ void tail_sweep(const TailLevel<T, TM>& L, int t, con
   for (long base = 0; base < work; base += nthreads) {  // uniform trip count
     long g = base + tid;
     int I = r0 + (int)(g / G);
-    sweep_row<T, TM, G, MODE, kTailUnroll>(I, (int)(g % G), g < work, L.rowptr, L.diag, L.col, L.val, L.dinv, L.b,
-                                           L.x, L.agg, e);
+    sweep_row<T, TM, G, MODE, kTailUnroll, -1>(I, (int)(g % G), g < work, L.rowptr, L.diag, L.col, L.val, L.dinv,
+                                               L.b, L.x, L.agg, e);
   }
 }
 
@@ -101,11 +104,11 @@ __device__ __forceinline__ void tail_down(const TailArgs<T, TM>& A, int l, long 
   for (long base = 0; base < work; base += nthreads) {
     long g = base + tid;
     if (A.nu_pre == 1)  // right after one forward sweep: the higher colours' part only
-      residual_row<T, TM, G, true, kTailUnroll>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag, L.col,
-                                                L.val, L.b, L.x, L.r);
+      residual_row<T, TM, G, true, kTailUnroll, -1>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag,
+                                                    L.col, L.val, L.b, L.x, L.r);
     else
-      residual_row<T, TM, G, false, kTailUnroll>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag, L.col,
-                                                 L.val, L.b, L.x, L.r);
+      residual_row<T, TM, G, false, kTailUnroll, -1>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag,
+                                                     L.col, L.val, L.b, L.x, L.r);
   }
   sync();
   int init_end = (A.nu_pre >= 1 && l + 1 < A.last) ? N.cs[1] : 0;
