@@ -22,8 +22,12 @@ namespace llmg {
 
 constexpr int kTailThreads = 256;  // per CTA
 // blocks per lane loaded before the products, a fixed unroll here (the
-// per-class kernels choose a warp-uniform one)
-constexpr int kTailUnroll = 4;
+// per-class kernels choose a warp-uniform one).  Float64: 2, since slots past
+// a row's blocks still issue their multiply-adds under predication and the
+// float64 pipe is slow (unroll 4: 0.59 ms of tail per GCR iteration at 128^3,
+// unroll 2: 0.55 ms); float32 keeps 4 loads in flight per lane.
+template <typename T> constexpr int kTailUnroll = 4;
+template <> constexpr int kTailUnroll<double> = 2;
 
 // levels below this many rows use 8 lanes per row: their classes leave most
 // of the cluster's threads idle, and wider rows shorten each phase's chain
@@ -78,7 +82,7 @@ __device__ __forceinline__ void tail_sweep(const TailLevel<T, TM>& L, int t, con
   for (long base = 0; base < work; base += nthreads) {  // uniform trip count
     long g = base + tid;
     int I = r0 + (int)(g / G);
-    sweep_row<T, TM, G, MODE, kTailUnroll, -1>(I, (int)(g % G), g < work, L.rowptr, L.diag, L.col, L.val, L.dinv,
+    sweep_row<T, TM, G, MODE, kTailUnroll<T>, -1>(I, (int)(g % G), g < work, L.rowptr, L.diag, L.col, L.val, L.dinv,
                                                L.b, L.x, L.agg, e);
   }
 }
@@ -104,10 +108,10 @@ __device__ __forceinline__ void tail_down(const TailArgs<T, TM>& A, int l, long 
   for (long base = 0; base < work; base += nthreads) {
     long g = base + tid;
     if (A.nu_pre == 1)  // right after one forward sweep: the higher colours' part only
-      residual_row<T, TM, G, true, kTailUnroll, -1>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag,
+      residual_row<T, TM, G, true, kTailUnroll<T>, -1>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag,
                                                     L.col, L.val, L.b, L.x, L.r);
     else
-      residual_row<T, TM, G, false, kTailUnroll, -1>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag,
+      residual_row<T, TM, G, false, kTailUnroll<T>, -1>((int)(g / G), (int)(g % G), g < work, L.rowptr, L.diag,
                                                      L.col, L.val, L.b, L.x, L.r);
   }
   sync();
