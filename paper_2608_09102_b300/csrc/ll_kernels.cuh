@@ -29,6 +29,24 @@ __device__ __forceinline__ SlotPos slot_pos(const GridGeom& g, int c, long r) {
   return p;
 }
 
+// visit(slot) for each face neighbour (all of the other colour), in the order
+// of slot_neighbours; returns the count.  No index array: an array indexed
+// in a loop lives in local memory, and each neighbour's load would then wait
+// for the one before it.
+template <typename V>
+__device__ __forceinline__ int for_neighbours(const GridGeom& g, int c, const SlotPos& p, V&& visit) {
+  long base = (long)(1 - c) * g.nh;
+  long row = p.row * g.nxh;
+  int d = 0;
+  if (p.z > 0) visit(base + row - (long)g.ny * g.nxh + (p.x >> 1)), ++d;
+  if (p.y > 0) visit(base + row - g.nxh + (p.x >> 1)), ++d;
+  if (p.x > 0) visit(base + row + ((p.x - 1) >> 1)), ++d;
+  if (p.x < g.nx - 1) visit(base + row + ((p.x + 1) >> 1)), ++d;
+  if (p.y < g.ny - 1) visit(base + row + g.nxh + (p.x >> 1)), ++d;
+  if (p.z < g.nz - 1) visit(base + row + (long)g.ny * g.nxh + (p.x >> 1)), ++d;
+  return d;
+}
+
 // slots of the face neighbours (all of the other colour); returns the count
 __device__ __forceinline__ int slot_neighbours(const GridGeom& g, int c, const SlotPos& p, long* s) {
   long base = (long)(1 - c) * g.nh;
@@ -346,11 +364,8 @@ __global__ void __launch_bounds__(256) k0_smooth(GridGeom g, int c, const double
   if (!p.real) return;
   T v0 = (T)b[sl], v1 = (T)b[n2 + sl], v2 = (T)b[2 * n2 + sl];
   if (MODE != 0) {
-    long nb[6];
-    int d = slot_neighbours(g, c, p, nb);
     T s0 = 0, s1 = 0, s2 = 0;
-    for (int q = 0; q < d; ++q) {
-      long l = nb[q];
+    for_neighbours(g, c, p, [&](long l) {
       s0 += x[l];
       s1 += x[n2 + l];
       s2 += x[2 * n2 + l];
@@ -360,7 +375,7 @@ __global__ void __launch_bounds__(256) k0_smooth(GridGeom g, int c, const double
         s1 += e[a + 1];
         s2 += e[a + 2];
       }
-    }
+    });
     const T* C = chat + sl;
     T c0 = ld(C), c1 = ld(C + n2), c2 = ld(C + 2 * n2), c3 = ld(C + 3 * n2), c4 = ld(C + 4 * n2),
       c5 = ld(C + 5 * n2), c6 = ld(C + 6 * n2), c7 = ld(C + 7 * n2), c8 = ld(C + 8 * n2);
@@ -387,16 +402,13 @@ template <typename T, typename TX>
 __device__ __forceinline__ void slot_apply(const GridGeom& g, int c, long sl, const SlotPos& p, const TX* x,
                                            const T* chat, T inv_dt, T* y) {
   long n2 = 2 * g.nh;
-  long nb[6];
-  int d = slot_neighbours(g, c, p, nb);
   T x0 = (T)x[sl], x1 = (T)x[n2 + sl], x2 = (T)x[2 * n2 + sl];
   T s0 = 0, s1 = 0, s2 = 0;
-  for (int q = 0; q < d; ++q) {
-    long l = nb[q];
+  int d = for_neighbours(g, c, p, [&](long l) {
     s0 += (T)x[l];
     s1 += (T)x[n2 + l];
     s2 += (T)x[2 * n2 + l];
-  }
+  });
   T fd = (T)d;
   s0 -= fd * x0;
   s1 -= fd * x1;
@@ -412,16 +424,13 @@ template <typename T, typename TX>
 __device__ __forceinline__ void slot_residual(const GridGeom& g, int c, long sl, const SlotPos& p, const double* b,
                                               const TX* x, const T* chat, T inv_dt, T* r) {
   long n2 = 2 * g.nh;
-  long nb[6];
-  int d = slot_neighbours(g, c, p, nb);
   T x0 = (T)x[sl], x1 = (T)x[n2 + sl], x2 = (T)x[2 * n2 + sl];
   T s0 = 0, s1 = 0, s2 = 0;
-  for (int q = 0; q < d; ++q) {
-    long l = nb[q];
+  int d = for_neighbours(g, c, p, [&](long l) {
     s0 += (T)x[l];
     s1 += (T)x[n2 + l];
     s2 += (T)x[2 * n2 + l];
-  }
+  });
   T fd = (T)d;
   s0 = fma(-fd, x0, s0);
   s1 = fma(-fd, x1, s1);
@@ -453,15 +462,12 @@ template <typename T>
 __device__ __forceinline__ void slot_residual_after_sweep(const GridGeom& g, long sl, const SlotPos& p,
                                                           const T* x, const T* chat, T* r) {
   long n2 = 2 * g.nh;
-  long nb[6];
-  int d = slot_neighbours(g, 0, p, nb);
   T s0 = 0, s1 = 0, s2 = 0;
-  for (int q = 0; q < d; ++q) {
-    long l = nb[q];
+  for_neighbours(g, 0, p, [&](long l) {
     s0 += x[l];
     s1 += x[n2 + l];
     s2 += x[2 * n2 + l];
-  }
+  });
   const T* C = chat + sl;
   r[0] = -(ld(C) * s0 + ld(C + n2) * s1 + ld(C + 2 * n2) * s2);
   r[1] = -(ld(C + 3 * n2) * s0 + ld(C + 4 * n2) * s1 + ld(C + 5 * n2) * s2);
