@@ -549,13 +549,46 @@ __global__ void k_zero(long n, T* __restrict__ p) {
 // ---------------------------------------------------------------------------
 // coarse levels: 3x3 BSR, cell-major vectors; a group of G lanes per row
 // ---------------------------------------------------------------------------
+// Sums of a, b, c over the G lanes of each group, left in every lane of the
+// group; every lane of the warp must call it.  Float64, G = 4 or 8: the
+// first round leaves the partial sums of a and b in the lower half of the
+// group and those of c in the upper half, the later rounds halve the values
+// per lane again, and three shuffles gather the results.  That takes 4
+// float64 adds per lane instead of the butterfly's 3 log2(G), on a pipe that
+// retires 2 float64 operations per clock per SM here; the lanes are paired
+// as in the butterfly, so the sums are the same bit for bit.
 template <int G, typename T>
 __device__ __forceinline__ void group_sum3(T& a, T& b, T& c) {
+  constexpr unsigned kFull = 0xffffffffu;
+  if constexpr (std::is_same<T, double>::value && (G == 4 || G == 8)) {
+    int lane = threadIdx.x & 31, base = lane & ~(G - 1);
+    bool hi = lane & (G / 2);
+    double k0 = hi ? c : a, k1 = hi ? 0.0 : b;  // kept
+    double s0 = hi ? a : c, s1 = hi ? b : 0.0;  // sent to the partner half
+    k0 += __shfl_xor_sync(kFull, s0, G / 2);
+    k1 += __shfl_xor_sync(kFull, s1, G / 2);
+    if constexpr (G == 8) {
+      bool m = lane & 2;  // a (lanes 0, 1), b (2, 3), c (4, 5), zero (6, 7)
+      double kk = m ? k1 : k0, ss = m ? k0 : k1;
+      kk += __shfl_xor_sync(kFull, ss, 2);
+      kk += __shfl_xor_sync(kFull, kk, 1);
+      a = __shfl_sync(kFull, kk, base);
+      b = __shfl_sync(kFull, kk, base + 2);
+      c = __shfl_sync(kFull, kk, base + 4);
+    } else {  // a and b in lanes 0, 1; c in lanes 2, 3
+      k0 += __shfl_xor_sync(kFull, k0, 1);
+      k1 += __shfl_xor_sync(kFull, k1, 1);
+      a = __shfl_sync(kFull, k0, base);
+      b = __shfl_sync(kFull, k1, base);
+      c = __shfl_sync(kFull, k0, base + 2);
+    }
+  } else {
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+      c += __shfl_xor_sync(kFull, c, o);
+    }
   }
 }
 
