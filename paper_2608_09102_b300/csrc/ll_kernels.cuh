@@ -763,13 +763,13 @@ __device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p
       if (MODE == 0) row_msub<T, TM, G, UU, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
       else row_msub_off<T, TM, G, UU, MODE == 2>(p0, pd, p1, lane, col, val, x, agg, e, a0, a1, a2);
     });
-  group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
-  if (active && lane < 3) {
+  if (active && lane < 3) {  // issued before the group sum, whose latency hides theirs
     b0 = b[3L * I]; b1 = b[3L * I + 1]; b2 = b[3L * I + 2];
     const T* D = dinv + 9L * I + 3 * lane;
     d0 = ro(D); d1 = ro(D + 1); d2 = ro(D + 2);
-    x[3L * I + lane] = d0 * (b0 + a0) + d1 * (b1 + a1) + d2 * (b2 + a2);
   }
+  group_sum3<G>(a0, a1, a2);  // every lane of the group now holds -sum A v
+  if (active && lane < 3) x[3L * I + lane] = d0 * (b0 + a0) + d1 * (b1 + a1) + d2 * (b2 + a2);
 }
 
 template <typename T, typename TM, int G, int MODE, int U = 4, int USET = 7>
