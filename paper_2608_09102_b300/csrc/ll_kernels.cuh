@@ -1049,6 +1049,61 @@ __global__ void __launch_bounds__(256) kg_apply(GridGeom g, const TX* __restrict
   y[2 * n2 + sl] = v[2];
 }
 
+// Knuth's two-sum: s + e == a + b exactly (s the rounded sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// y = A x for a float32 x (the mixed path's outer product), with float64
+// products.  The stencil sum S - d x_k of float32 values is accumulated as an
+// unevaluated float32 pair hi + lo (two-sum per term, the rounding error of
+// d x_k by one fma), which carries it to about 1e-14 of the largest term;
+// then one float64 add per component.  This keeps the sums off the float64 pipe, which
+// bounds this kernel (the float64 sums were 18 of its 36 float64 operations
+// per cell).
+__global__ void __launch_bounds__(256) kg_apply_f32(GridGeom g, const float* __restrict__ x,
+                                                    const double* __restrict__ chat, double inv_dt,
+                                                    double* __restrict__ y) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n2 = 2 * g.nh;
+  if (sl >= n2) return;
+  int c = (int)(sl / g.nh);
+  SlotPos p = slot_pos(g, c, sl % g.nh);
+  if (!p.real) {
+    y[sl] = 0;
+    y[n2 + sl] = 0;
+    y[2 * n2 + sl] = 0;
+    return;
+  }
+  float x0 = x[sl], x1 = x[n2 + sl], x2 = x[2 * n2 + sl];
+  float h0 = 0, h1 = 0, h2 = 0, l0 = 0, l1 = 0, l2 = 0, e;
+  int d = for_neighbours(g, c, p, [&](long q) {
+    two_sum(h0, x[q], h0, e);
+    l0 += e;
+    two_sum(h1, x[n2 + q], h1, e);
+    l1 += e;
+    two_sum(h2, x[2 * n2 + q], h2, e);
+    l2 += e;
+  });
+  float fd = (float)d;
+  float p0 = -fd * x0, p1 = -fd * x1, p2 = -fd * x2;  // -d x_k = p + q exactly
+  float q0 = fmaf(-fd, x0, -p0), q1 = fmaf(-fd, x1, -p1), q2 = fmaf(-fd, x2, -p2);
+  two_sum(h0, p0, h0, e);
+  l0 += e + q0;
+  two_sum(h1, p1, h1, e);
+  l1 += e + q1;
+  two_sum(h2, p2, h2, e);
+  l2 += e + q2;
+  double s0 = (double)h0 + (double)l0, s1 = (double)h1 + (double)l1, s2 = (double)h2 + (double)l2;
+  double z0 = x0, z1 = x1, z2 = x2;
+  const double* C = chat + sl;
+  y[sl] = z0 * inv_dt + ld(C) * s0 + ld(C + n2) * s1 + ld(C + 2 * n2) * s2;
+  y[n2 + sl] = z1 * inv_dt + ld(C + 3 * n2) * s0 + ld(C + 4 * n2) * s1 + ld(C + 5 * n2) * s2;
+  y[2 * n2 + sl] = z2 * inv_dt + ld(C + 6 * n2) * s0 + ld(C + 7 * n2) * s1 + ld(C + 8 * n2) * s2;
+}
+
 // y = r on the colour-0 slots [0, Nh): the product A z there when z leaves a
 // block Gauss-Seidel sweep whose last half-sweep updated colour 0 with its
 // (colour-1) neighbours final -- then D_k z_k = r_k - C^_k sum_j z_j, so

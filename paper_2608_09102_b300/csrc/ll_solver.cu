@@ -99,7 +99,6 @@ struct ll_mg_hierarchy {
   DBuf<int> perm, lu_status, flag;
   // GCR workspace (red-black layout, 3*n2 doubles per vector)
   DBuf<double> Z64, C, r, xw, bw, partial;
-  DBuf<double> zd;  // mixed path: float64 copy of z_j for the outer product
   DBuf<float> Z32;
   DBuf<GcrScal> scal;
   DBuf<double> kscal;  // K-cycle scalars, 8 per level
@@ -399,7 +398,6 @@ void allocate(ll_mg_hierarchy* H) {
   long n3 = H->n3;
   if (mixed) {
     H->Z32.alloc((size_t)m * n3);
-    H->zd.alloc(n3);
   } else {
     H->Z64.alloc((size_t)m * n3);
   }
@@ -1043,12 +1041,10 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
     kg_apply<T><<<cdiv(g.nh, kBlock), kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj, g.nh);
     LL_LAUNCHED();
   } else if (!std::is_same<T, double>::value) {
-    // mixed path: widen z once (a float64 conversion per value instead of
-    // one per stencil read), then the float64 product
-    LL_PROFW(LL_KIND_OUTER_APPLY, 45.0 * g.n, 132.0 * g.n);
-    k_convert<T, double><<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, zj, H->zd);
-    LL_LAUNCHED();
-    kg_apply<double><<<nbs, kBlock, 0, s>>>(g, H->zd, H->chat64, 1.0 / H->dt, cj);  // step 2
+    // mixed path: the float64 product of the float32 z (stencil sums as
+    // float32 pairs, see kg_apply_f32)
+    LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 108.0 * g.n);
+    kg_apply_f32<<<nbs, kBlock, 0, s>>>(g, (const float*)zj, H->chat64, 1.0 / H->dt, cj);  // step 2
     LL_LAUNCHED();
   } else {
     LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 120.0 * g.n);
