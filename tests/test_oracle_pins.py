@@ -525,3 +525,34 @@ def test_kcycle_reduces_iterations():
         assert st == oracle.OK
         its.append(it)
     assert its[1] < its[0], its
+
+
+# --------------------------------------------------------------------------
+# known limit: i.i.d. random unit vectors at dt/h^2 = 6.55
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("alpha", [0.01, 0.1, 1.0])
+def test_random_unit_vectors_limit_of_the_vcycle(alpha):
+    """The 256 x 256 x 128 workload's field and dt/h^2 on a 16 x 16 x 8 grid.
+    The system is well posed for every alpha: plain GCR reaches 1e-8.  The
+    V-cycle-preconditioned GCR converges for alpha = 1 and stagnates for
+    alpha <= 0.1, where the symmetric part of the level-1 Galerkin operator
+    has a large share of negative eigenvalues (2 % for alpha = 1, over 25 %
+    below)."""
+    grid, h = (16, 16, 8), 1.0 / 16
+    dt = 6.5536 * h * h
+    m = inputs.random_sphere(*grid, seed=0).reshape(-1)
+    b = m / dt
+    plain = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(prec=1, maxit=3000, rtol=1e-8))
+    x, st, it, rr = plain.solve(b)
+    assert st == oracle.OK and rr < 1e-8
+    H = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-8, maxit=60))
+    x, st, it, rr = H.solve(b)
+    A1 = H.matrix(1).toarray()
+    neg = np.mean(np.linalg.eigvalsh(0.5 * (A1 + A1.T)) < 0)
+    if alpha == 1.0:
+        assert st == oracle.OK and it <= 40
+        assert neg < 0.05
+    else:
+        assert st == oracle.NOT_CONVERGED and rr > 0.5
+        assert neg > 0.25
