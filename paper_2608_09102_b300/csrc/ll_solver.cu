@@ -1032,19 +1032,19 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   T* zj = H->Z<T>() + (size_t)j * n3;
   double* cj = H->C.p + (size_t)j * n3;
   vcycle<T, TM>(H, H->r, zj);                                                       // step 1
-  if (std::is_same<T, double>::value && H->nlev > 1 && H->prm.nu_post >= 1) {
+  if constexpr (!std::is_same<T, double>::value) {
+    // mixed path: the float64 product of the float32 z (stencil sums as
+    // float32 pairs, see kg_apply_f32)
+    LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 108.0 * g.n);
+    kg_apply_f32<<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);  // step 2
+    LL_LAUNCHED();
+  } else if (H->nlev > 1 && H->prm.nu_post >= 1) {
     // step 2, c = A z: the V-cycle's last half-sweep solved the colour-0 rows
     // of A z = r exactly (float64 path), so only colour 1 needs the product
     LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * H->l0_cells[1], 120.0 * H->l0_cells[1] + 48.0 * H->l0_cells[0]);
     kg_copy_colour0<<<cdiv(g.nh, kBlock), kBlock, 0, s>>>(g, H->r, cj);
     LL_LAUNCHED();
     kg_apply<T><<<cdiv(g.nh, kBlock), kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj, g.nh);
-    LL_LAUNCHED();
-  } else if (!std::is_same<T, double>::value) {
-    // mixed path: the float64 product of the float32 z (stencil sums as
-    // float32 pairs, see kg_apply_f32)
-    LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 108.0 * g.n);
-    kg_apply_f32<<<nbs, kBlock, 0, s>>>(g, (const float*)zj, H->chat64, 1.0 / H->dt, cj);  // step 2
     LL_LAUNCHED();
   } else {
     LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 120.0 * g.n);
