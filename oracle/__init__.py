@@ -97,9 +97,15 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+    if _lib is None:
+        _lib = bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def bind(lib):
+    """Declare the argument and result types of the oracle's exports on a
+    loaded copy of the library (the tests also bind copies with a planted
+    mistake, to show that the pins catch it)."""
     vp, i, d, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint32
     sig = {
         "orc_setup": (vp, [i, i, i, d, d, d, _dp, ctypes.POINTER(_Params)]),
@@ -138,7 +144,6 @@ def _load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
     return lib
 
 

@@ -11,6 +11,9 @@ used to pin the oracle to something other than itself.
   DCT-II diagonalisation of the Neumann Laplacian.
 * ``manufactured``: an exact smooth unit field and the forcing that makes it
   solve the damped LL equation, for the time-convergence pin.
+* ``block_gs_sweep``, ``vcycle_dense``: the block Gauss-Seidel sweep and the
+  V-cycle of Sec. 3 on dense matrices, with Boolean prolongations made from
+  the aggregate maps (``boolean_prolongation``, ``galerkin_levels``).
 """
 from __future__ import annotations
 
@@ -138,3 +141,82 @@ class Manufactured:
         c1 = np.cross(me, lm, axis=0)
         c2 = np.cross(me, c1, axis=0)
         return (dt_m + c1 + self.alpha * c2)[:, None]
+
+
+# --------------------------------------------------------------------------
+# smoother and V-cycle (Sec. 3), written from their textbook definitions on
+# dense matrices: an independent restatement of what the oracle's gs_sweep
+# and vcycle compute
+# --------------------------------------------------------------------------
+
+def boolean_prolongation(agg, nc: int) -> np.ndarray:
+    """Dense Boolean prolongation of Eq. (Pagg) for a component-major vector:
+    P[(c, k), (c, agg[k])] = 1, i.e. I_3 (x) P_cell."""
+    agg = np.asarray(agg)
+    n = agg.size
+    p = np.zeros((n, nc))
+    p[np.arange(n), agg] = 1.0
+    return np.kron(np.eye(3), p)
+
+
+def galerkin_levels(A0: np.ndarray, aggs) -> list:
+    """Level operators A_{l+1} = P_l^T A_l P_l (Eq. galerkin) as dense
+    products, from the level-0 operator and the aggregate maps."""
+    ops, ps = [np.asarray(A0)], []
+    for agg in aggs:
+        nc = int(np.max(agg)) + 1
+        P = boolean_prolongation(agg, nc)
+        ps.append(P)
+        ops.append(P.T @ ops[-1] @ P)
+    return ops, ps
+
+
+def block_gs_sweep(A: np.ndarray, colours, b, x, forward: bool = True) -> np.ndarray:
+    """One block Gauss-Seidel sweep on a component-major system A (3n x 3n).
+
+    The cells are visited colour class by colour class, ascending colours
+    for a forward sweep and descending for a backward one.  A cell k takes
+    the exact solution of its own 3x3 equation,
+        x_k <- D_k^{-1} (b_k - sum_{j != k} A_kj x_j),
+    D_k = A_kk its diagonal block, with every other cell's current value.
+    Cells of one colour share no off-diagonal block (checked), so updating
+    a class all at once is the same as visiting its cells one by one."""
+    colours = np.asarray(colours)
+    n = colours.size
+    x = np.array(x, np.float64, copy=True)
+    b = np.asarray(b, np.float64)
+    classes = sorted(set(colours.tolist()), reverse=not forward)
+    for c in classes:
+        cells = np.flatnonzero(colours == c)
+        rows = np.concatenate([cells, n + cells, 2 * n + cells])
+        owner = np.tile(cells, 3)
+        assert not np.any(A[np.ix_(rows, rows)][owner[:, None] != owner[None, :]]), "cells of one colour are coupled"
+        s = b[rows] - A[rows] @ x  # every cell's residual with the old values
+        new = np.empty(rows.size)
+        for i, k in enumerate(cells):
+            mine = np.array([i, cells.size + i, 2 * cells.size + i])
+            own = rows[mine]
+            d = A[np.ix_(own, own)]
+            # add back the cell's own diagonal-block term, then solve with it
+            new[mine] = np.linalg.solve(d, s[mine] + d @ x[own])
+        x[rows] = new
+    return x
+
+
+def vcycle_dense(ops, ps, colours, b, nu_pre: int = 1, nu_post: int = 1, level: int = 0) -> np.ndarray:
+    """One V(nu_pre, nu_post) cycle for ops[level] x = b from x = 0 (Sec. 3):
+    forward block-GS sweeps, residual, restriction P^T, the same cycle on the
+    next level from a zero guess, prolongation x += P e, backward sweeps; an
+    exact (dense) solve on the last level."""
+    A = ops[level]
+    if level == len(ops) - 1:
+        return np.linalg.solve(A, b)
+    x = np.zeros_like(np.asarray(b, np.float64))
+    for _ in range(nu_pre):
+        x = block_gs_sweep(A, colours[level], b, x, True)
+    r = b - A @ x
+    e = vcycle_dense(ops, ps, colours, ps[level].T @ r, nu_pre, nu_post, level + 1)
+    x = x + ps[level] @ e
+    for _ in range(nu_post):
+        x = block_gs_sweep(A, colours[level], b, x, False)
+    return x

@@ -380,18 +380,23 @@ def test_zero_rhs_and_breakdown_free_statuses():
 # iteration counts and time stepping (Sec. 4)
 # --------------------------------------------------------------------------
 
-def test_iteration_counts_stay_bounded_under_refinement():
+@pytest.mark.parametrize("grids", [[(n, n, 1) for n in (32, 64, 128, 256)],
+                                   [(n, n, n) for n in (16, 32, 64)]], ids=["2d", "3d"])
+def test_iteration_counts_stay_bounded_under_refinement(grids):
     """Mesh-independent convergence (the paper's claim for the aggregation
-    solver), qualitatively: fixed dt/h^2, growing grids."""
+    solver, abstract and Tables 4-13): at fixed dt/h^2 = 8.19 the iteration
+    count to 1e-8 grows by at most 30 % from the coarsest to the finest grid
+    (2-D 32^2 -> 256^2, 3-D 16^3 -> 64^3; measured 26 -> 33 and 34 -> 42)."""
     its = []
-    for n in (32, 64, 128):
-        m = inputs.vortex(n, n, 1, seed=0).reshape(-1)
+    for g in grids:
+        n = g[0]
+        m = inputs.vortex(*g, seed=0).reshape(-1)
         dt = 8.19 / n ** 2
-        H = oracle.Hierarchy((n, n, 1), 1 / n, 0.02, dt, m, oracle.Params(rtol=1e-8))
+        H = oracle.Hierarchy(g, 1 / n, 0.02, dt, m, oracle.Params(rtol=1e-8))
         _, st, it, _ = H.solve(m / dt, m)
         assert st == oracle.OK
         its.append(it)
-    assert its[-1] <= its[0] + 10, its
+    assert max(its) <= 1.3 * its[0], its
 
 
 def test_projection_leaves_iteration_counts_unchanged():
