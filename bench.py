@@ -8,8 +8,21 @@ time step through the C ABI (ll_mg_step): numeric setup for m~ = m^n,
 aggregation-AMG-preconditioned GCR to relative residual 1e-8, projection
 m <- x/|x|.  The metric is unknown-solves per second (3 N unknowns per step).
 
+The default run times, in this order:
+  * the headline: K float64 steps with no instrumentation (CUDA events on
+    the launching stream around the K steps);
+  * the same K steps with the float32 V-cycle (mixed) and with bfloat16
+    coarse operators (bf16), each from the same initial state, for the
+    mixed-vs-float64 speedup at the same true relative residual 1e-8;
+  * a separate profiling pass of the float64 path (per-kind event timing) for
+    the kernel breakdown and the dominant kernel's roofline;
+  * end to end: steps of a pinned host field through ll_mg_step_host (the
+    library copies it in and out on its stream every step);
+  * the float64 multiply-add probe (the measured float64 peak);
+  * the CPU oracle on a bounded sample (cpu_baseline).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--precision fp64|mixed]
+                       [--precision fp64|mixed|bf16] [--workload step128|batch512|grad96]
 Prints one JSON line (rank 0).  Ranks are independent replicas (the solve
 does not shard); value = unknowns solved by all ranks / max over ranks of the
 timed region.
@@ -39,19 +52,22 @@ UNIT = "unknown-solves/s"
 WORKLOAD = "3D 128^3 semi-implicit LL time steps, alpha 0.02, dt 5e-4, vortex + 1e-2 noise, rtol 1e-8"
 
 # FP64 peak derived from unit counts and clocks: 148 SMs x 2 FP64 FMA/clk/SM
-# x 2 flop x 2.032 GHz (a DFMA throughput probe on this machine read 1.13 TFLOP/s
-# at 1.94 GHz, i.e. the same 2 FMA/clk/SM)
+# x 2 flop x 2.032 GHz.  The bench also measures it (ll_fp64_fma_probe).
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 
-# DRAM traffic of the float64 coarse sweeps per launch over the algorithmic
-# bytes: ncu dram__bytes_read.sum + dram__bytes_write.sum on 400 kb_sweep
-# launches of the --grid 96 case, against the library's byte model for the
-# same launches (profiles/kb_sweep_96cube_fp64.md).  Scaled by the bytes a
-# launch processes to the traffic of a 128^3 launch.
+# DRAM traffic of the float64 coarse sweeps per launch over their algorithmic
+# bytes: ncu dram__bytes_read.sum + dram__bytes_write.sum of kb_sweep launches
+# of the 96^3 profiling case, against the library's byte model for the same
+# launches.  Scaled by the bytes a launch processes to a 128^3 launch.
 KB_SWEEP_TRAFFIC_RATIO = 9.679e6 / 9.293e6
 
 KIND_NAMES = ["l0_smooth", "l0_restrict", "outer_apply", "bsr_smooth", "bsr_other", "gcr_vector", "coarsest",
               "numeric", "coarse_tail"]
+
+# The oracle's bounded sample: whole time steps on the central 48^3 block of
+# the 128^3 workload field (same h, alpha, dt, rtol; Neumann boundaries at
+# the block's faces).
+SAMPLE_SIDE = 48
 
 
 def measured_peaks():
@@ -114,56 +130,122 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (the reference arm and the cpu_baseline)
+# CPU oracle: whole time steps on a bounded block of the workload (the
+# reference arm and the cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(iters_sample: int = 3):
-    """Time the FP64 CPU oracle on the full 128^3 workload: its whole setup
-    for one step plus `iters_sample` GCR iterations.  Returns (setup_s,
-    seconds per GCR iteration)."""
-    import oracle
+def sample_field(side: int = SAMPLE_SIDE):
+    """The central side^3 block of the 128^3 workload's initial field."""
     from paper_2608_09102_b300 import inputs
 
-    m = inputs.vortex(*GRID, seed=0).reshape(-1)
+    off = (GRID[0] - side) // 2
+    m = inputs.vortex(*GRID, seed=0).reshape(3, GRID[2], GRID[1], GRID[0])
+    return np.ascontiguousarray(m[:, off:off + side, off:off + side, off:off + side]).reshape(-1)
+
+
+def oracle_steps(m, n_steps: int, side: int = SAMPLE_SIDE):
+    """n_steps whole oracle time steps (setup, GCR solve to 1e-8, projection)
+    from m; returns (m, seconds per step, iterations per step)."""
+    import oracle
+
+    secs, its = [], []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        m, it, rr, st = oracle.step(m, 1, (side,) * 3, H_SPACING, ALPHA, DT, oracle.Params(rtol=RTOL))
+        secs.append(time.perf_counter() - t0)
+        its.append(int(it[0]))
+    return m, secs, its
+
+
+def _replica_worker(side, barrier, out):
+    m = sample_field(side)
+    import oracle
+
+    oracle._load()
+    barrier.wait()
     t0 = time.perf_counter()
-    H = oracle.Hierarchy(GRID, H_SPACING, ALPHA, DT, m, oracle.Params(rtol=RTOL, maxit=iters_sample))
-    t1 = time.perf_counter()
-    b = m / DT
-    _, st, it, _ = H.solve(b, m.copy())
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / max(it, 1)
+    _, secs, its = oracle_steps(m, 1, side)
+    out.put((time.perf_counter() - t0, its[0]))
 
 
-# the oracle's own GCR iteration count on the first step of this workload
-# (42, from a full oracle solve); used to extrapolate the reference arm
-ORACLE_ITERS_PER_STEP = 42
+def oracle_all_cores(side: int = SAMPLE_SIDE):
+    """One whole oracle step in each of P concurrent processes (P = the host's
+    cores, fewer if memory is short: about 0.4 GB per process at 48^3), all
+    released together; returns (unknown-solves/s of all P, P, seconds of the
+    slowest, nproc).  The oracle is single-threaded, so its all-core
+    throughput is that of independent replicas."""
+    import multiprocessing as mp
+
+    nproc = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        import psutil
+
+        avail = psutil.virtual_memory().available
+        procs = max(1, min(nproc, int(avail * 0.5 / (0.4e9 * (side / 48) ** 3))))
+    except ImportError:
+        procs = nproc
+    ctx = mp.get_context("spawn")  # never fork a process that has used CUDA
+    barrier = ctx.Barrier(procs)
+    q = ctx.Queue()
+    workers = [ctx.Process(target=_replica_worker, args=(side, barrier, q)) for _ in range(procs)]
+    for w in workers:
+        w.start()
+    res = [q.get(timeout=1800) for _ in workers]
+    for w in workers:
+        w.join(timeout=60)
+    slowest = max(r[0] for r in res)
+    return 3 * side ** 3 * procs / slowest, procs, slowest, nproc
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, one thread, on
+    whole time steps of the bounded sample (W untimed, K timed), then the
+    all-core replica throughput of the same sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
-    setup_s = per_iter = None
     t_all = time.perf_counter()
-    steps = max(1, min(args.steps, 3))
-    for _ in range(steps):
-        s, p = oracle_sample(1)
-        setup_s = s if setup_s is None else min(setup_s, s)
-        per_iter = p if per_iter is None else min(per_iter, p)
-        times.append(s + ORACLE_ITERS_PER_STEP * p)
-    step_s = statistics.median(times)
-    value = UNKNOWNS / step_s
-    sample = ("%d x (oracle setup of one 128^3 step + 1 GCR iteration), extrapolated to %d iterations per step"
-              % (steps, ORACLE_ITERS_PER_STEP))
+    m = sample_field()
+    m, _, _ = oracle_steps(m, args.warmup)
+    t0 = time.perf_counter()
+    m, secs, its = oracle_steps(m, args.steps)
+    elapsed = time.perf_counter() - t0
+    unknowns = 3 * SAMPLE_SIDE ** 3
+    value = unknowns * args.steps / elapsed
+    allc, procs, slowest, nproc = oracle_all_cores()
+    sample = ("whole oracle time steps (setup, GCR to 1e-8, projection) on the central %d^3 block of the 128^3 "
+              "workload field, same h, alpha, dt; %d untimed, %d timed, one thread"
+              % (SAMPLE_SIDE, args.warmup, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "warmup": 0, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": list(GRID), "precision": "fp64"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(GRID), "precision": "fp64",
+                       "sample": "%d^3 central block" % SAMPLE_SIDE},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "all_cores": {"value": allc, "unit": UNIT, "cores": procs, "processes": procs,
+                          "slowest_step_s": slowest,
+                          "sample": "one whole step of the same block in each of %d concurrent processes" % procs},
+            "nproc": nproc,
+            "iterations_per_step": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "oracle_setup_s": setup_s, "oracle_s_per_iteration": per_iter,
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline():
+    """The oracle on the bounded sample, for our arm's line: two whole steps
+    on one thread, then one step in each of P concurrent processes."""
+    m = sample_field()
+    _, secs, its = oracle_steps(m, 2)
+    unknowns = 3 * SAMPLE_SIDE ** 3
+    value = unknowns * len(secs) / sum(secs)
+    allc, procs, slowest, nproc = oracle_all_cores()
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("2 whole oracle time steps (setup, GCR to 1e-8, projection) on the central %d^3 block of the "
+                       "128^3 workload field, same h, alpha, dt, one thread; %s GCR iterations"
+                       % (SAMPLE_SIDE, its)),
+            "all_cores": {"value": allc, "cores": procs, "slowest_step_s": slowest,
+                          "sample": "one whole step of the same block in each of %d concurrent processes" % procs},
+            "nproc": nproc}
 
 
 # ---------------------------------------------------------------------------
@@ -198,31 +280,75 @@ VCYCLE_KINDS = ("l0_smooth", "l0_restrict", "bsr_smooth", "bsr_other", "coarsest
 # kinds whose arithmetic is float64 whatever the V-cycle precision
 FP64_KINDS = {"outer_apply", "gcr_vector", "coarsest", "numeric"}
 
+# What bounds the dominant kernel, from its ncu counters (float64 coarse
+# sweeps): the small colour classes of levels 2-3 run at a few per cent
+# achieved occupancy with long-scoreboard stalls taking about two thirds of
+# the cycles between issues (latency); the level-1 classes keep the float64
+# pipe about three quarters busy.
+DOMINANT_LIMITER = "latency (small classes: dependent-load chains) and the float64 pipe (level-1 classes)"
 
-def roofline(kind: str, ms: float, launches: int, flops: float, byts: float, precision: str, peaks: dict,
-             peak_src: str):
-    """Roofline entry of one kernel kind from the library's live event timing
-    and its algorithmic flop and byte counts (models stated in ll_mg.h).
-    float64 kernels are bound by the float64 pipe of this GPU (2 FMA per
-    clock per SM, measured); float32 V-cycle kernels by HBM."""
+
+def roofline(kind: str, ms: float, launches: int, flops: float, byts: float, peaks: dict, peak_src: str,
+             fp64_peak: float):
+    """Roofline entry of one kernel kind from its event timing and the
+    library's algorithmic flop and byte counts (models stated in ll_mg.h).
+    The V-cycle kernels move about 0.18 float64 flop per byte: at the HBM
+    roofline they would need about 1.2 TFLOP/s, the float64 pipe's peak, so
+    the HBM roof is the lower of the two and is the bound reported; the
+    float64 rate is given beside it."""
     avg_ms = ms / max(launches, 1)
     per_launch_flops = flops / max(launches, 1)
     per_launch_bytes = byts / max(launches, 1)
     ach_tf = per_launch_flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
     ach_gb = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
-    common = {"kernel_kind": kind, "launches": launches, "avg_launch_ms": avg_ms,
-              "flops_per_launch": per_launch_flops, "bytes_per_launch": per_launch_bytes, "traffic": None}
-    if precision == "fp64" or kind in FP64_KINDS:
-        return dict(bound="alu", achieved=ach_tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=(ach_tf / FP64_PEAK_TFLOPS) if ach_tf else None,
-                    peak_source="derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x 2.032 GHz (probe: 1.13 TF at 1.94 GHz)",
-                    hbm_gbs=ach_gb, hbm_frac_of_measured=(ach_gb / peaks["hbm_gbs"]) if ach_gb else None, **common)
-    return dict(bound="hbm", achieved=ach_gb, peak=peaks["hbm_gbs"], unit="GB/s",
-                frac=(ach_gb / peaks["hbm_gbs"]) if ach_gb else None, peak_source=peak_src,
-                tflops=ach_tf, **common)
+    return {"bound": "hbm", "achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": (ach_gb / peaks["hbm_gbs"]) if ach_gb else None, "peak_source": peak_src,
+            "traffic": None, "kernel_kind": kind, "launches": launches, "avg_launch_ms": avg_ms,
+            "flops_per_launch": per_launch_flops, "bytes_per_launch": per_launch_bytes,
+            "fp64_tflops": ach_tf, "fp64_frac": (ach_tf / fp64_peak) if ach_tf else None}
+
+
+def fp64_probe(ll, torch, dev):
+    """Measured float64 multiply-add throughput (TFLOP/s, best of 5)."""
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    blocks = 148 * 8
+    ll.fp64_fma_probe(sink, 256, blocks)
+    best = 0.0
+    stream = torch.cuda.current_stream()
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fl = ll.fp64_fma_probe(sink, 8192, blocks)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def timed_steps(H, m, steps, stream, torch, ll, sampler=None):
+    """K steps of m on H between two CUDA events on `stream` (no profiling
+    scopes are active); returns (ms, iterations, relres, launches, clocks)."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its, rrs = [], []
+    launches0 = ll.launch_count()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0.record(stream)
+    for _ in range(steps):
+        st, it, rr = H.step(m, 1)
+        its += it
+        rrs += rr
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    return ev0.elapsed_time(ev1), its, rrs, ll.launch_count() - launches0, clocks
 
 
 def run_ours(args):
+    import ctypes
+
     import torch
 
     import paper_2608_09102_b300 as ll
@@ -241,127 +367,148 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     dev = torch.device("cuda", local)
-    precision = {"fp64": ll.LL_FP64, "mixed": ll.LL_MIXED_FP32, "bf16": ll.LL_MIXED_BF16}[args.precision]
+    stream = torch.cuda.current_stream()
+    lib = ll.load_library()
+    prec_code = {"fp64": ll.LL_FP64, "mixed": ll.LL_MIXED_FP32, "bf16": ll.LL_MIXED_BF16}
     m0 = inputs.vortex(*GRID, seed=0).reshape(-1)
+
+    def hierarchy(m, precision):
+        return ll.Hierarchy(m, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=prec_code[precision],
+                                                                     kcycle=args.kcycle))
+
+    # ---- the headline: K steps, no instrumentation -------------------------
     m = torch.tensor(m0, device=dev)
-    error_vs_fp64 = None
-    if precision != ll.LL_FP64:  # one step both ways from the same state
-        ma, mb = m.clone(), m.clone()
-        ll.Hierarchy(ma, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL)).step(ma, 1)
-        ll.Hierarchy(mb, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision,
-                                                               kcycle=args.kcycle)).step(mb, 1)
-        error_vs_fp64 = float(torch.linalg.norm(mb - ma) / torch.linalg.norm(ma))
-        del ma, mb
-        torch.cuda.empty_cache()
     t0 = time.perf_counter()
-    H = ll.Hierarchy(m, ALPHA, DT, H_SPACING, GRID, ll.Params(rtol=RTOL, precision=precision, kcycle=args.kcycle))
+    H = hierarchy(m, args.precision)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    lib = ll.load_library()
-    import ctypes
+    for _ in range(args.warmup):
+        H.step(m, 1)
+    m_start = m.clone()  # the end-to-end leg repeats these K steps from here
+    if world > 1:
+        dist.barrier()
+    elapsed_ms, its, rrs, launches, clocks = timed_steps(H, m, args.steps, stream, torch, ll, ClockSampler(local))
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
 
+    # ---- the other precisions on the same K steps ---------------------------
+    others = {}
+    if not args.no_mixed:
+        for prec in ("fp64", "mixed", "bf16"):
+            if prec == args.precision:
+                continue
+            mp_ = torch.tensor(m0, device=dev)
+            Hp = hierarchy(mp_, prec)
+            for _ in range(args.warmup):
+                Hp.step(mp_, 1)
+            ms_p, its_p, rrs_p, _, clk_p = timed_steps(Hp, mp_, args.steps, stream, torch, ll, ClockSampler(local))
+            ms_p = max_over_ranks(ms_p, dev)
+            # error against the float64 path: one step from the same state
+            ma, mb = torch.tensor(m0, device=dev), torch.tensor(m0, device=dev)
+            hierarchy(ma, "fp64").step(ma, 1)
+            hierarchy(mb, prec).step(mb, 1)
+            others[prec] = {"value": replica_throughput(UNKNOWNS * args.steps, world, ms_p * 1e-3),
+                            "ms_per_step": ms_p / args.steps,
+                            "iterations_per_step": float(np.mean(its_p)), "max_relres": float(max(rrs_p)),
+                            "error_vs_fp64": float(torch.linalg.norm(mb - ma) / torch.linalg.norm(ma)),
+                            "clocks_sm_mhz": clk_p["sm_mhz"], "clock_reasons": clk_p["reasons"]}
+            del Hp, mp_, ma, mb
+            torch.cuda.empty_cache()
+        fp64_ms = elapsed_ms / args.steps if args.precision == "fp64" else others["fp64"]["ms_per_step"]
+        for prec in ("mixed", "bf16"):
+            ms_p = elapsed_ms / args.steps if prec == args.precision else others[prec]["ms_per_step"]
+            if prec in others:
+                others[prec]["speedup_vs_fp64"] = fp64_ms / ms_p
+
+    # ---- profiling pass: per-kind breakdown, then the dominant kind alone ----
     def prof_start(mask):
         lib.ll_mg_profile(H._h, ctypes.c_uint(mask))
 
     def prof_read(kind):
-        ms = ctypes.c_double(0)
-        cnt = ctypes.c_longlong(0)
-        fl = ctypes.c_double(0)
-        by = ctypes.c_double(0)
+        ms, cnt, fl, by = ctypes.c_double(0), ctypes.c_longlong(0), ctypes.c_double(0), ctypes.c_double(0)
         lib.ll_mg_profile_read(H._h, kind, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl), ctypes.byref(by))
         return ms.value, cnt.value, fl.value, by.value
 
-    # warm-up steps, with every kernel kind timed to find the dominant kernel
+    prof_steps = max(1, min(args.steps, 5))
     prof_start((1 << len(KIND_NAMES)) - 1)
-    for _ in range(args.warmup):
-        H.step(m, 1)
+    pits = []
+    for _ in range(prof_steps):
+        pits += H.step(m, 1)[1]
     breakdown = {KIND_NAMES[k]: prof_read(k) for k in range(len(KIND_NAMES))}
-    kernel_kinds = [k for k in KIND_NAMES if k != "numeric"]
-    dominant = max(kernel_kinds, key=lambda k: breakdown[k][0])
+    dominant = max((k for k in KIND_NAMES if k != "numeric"), key=lambda k: breakdown[k][0])
     prof_start(1 << KIND_NAMES.index(dominant))
-    H.step(m, 1)  # one more warm-up step: graphs re-captured with the timed kind
-    prof_start(1 << KIND_NAMES.index(dominant))
-
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local)
-    its, rrs = [], []
-    launches0 = ll.launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        st, it, rr = H.step(m, 1)
-        its += it
-        rrs += rr
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    if world > 1:
-        dist.barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    launches = ll.launch_count() - launches0
-    dom_ms, dom_launches, dom_flops, dom_bytes = prof_read(KIND_NAMES.index(dominant))
+    for _ in range(prof_steps):
+        H.step(m, 1)
+    dom = prof_read(KIND_NAMES.index(dominant))
     prof_start(0)
-    elapsed_ms = max_over_ranks(elapsed_ms, dev)
 
-    # end to end through the public API with host buffers (pinned), copies timed
-    e2e_steps = max(1, min(args.steps, 10))
-    mh = m.detach().cpu().pin_memory()
+    # ---- end to end: the same K steps from the same state, the field in
+    # pinned host memory, through ll_mg_step_host (one call per step: the
+    # library copies the field in and out every step) ----------------------
+    e2e_steps = args.steps
+    H.step_host(m.detach().cpu().pin_memory(), 1)  # first call allocates the device copy
+    mh = m_start.cpu().pin_memory()
+    e2e_its = []
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(e2e_steps):
-        H.step(mh, 1)  # copies host -> device, steps, copies back
+        e2e_its += H.step_host(mh, 1)[1]
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - te, dev)
 
+    fp64_meas = fp64_probe(ll, torch, dev)
     if rank != 0:
         return
     value = replica_throughput(UNKNOWNS * args.steps, world, elapsed_ms * 1e-3)
     peaks, peak_src = measured_peaks()
-    roof = roofline(dominant, dom_ms, dom_launches, dom_flops, dom_bytes, args.precision, peaks, peak_src)
-    if dominant == "bsr_smooth" and args.precision == "fp64" and roof.get("bytes_per_launch"):
+    fp64_peak = max(fp64_meas, 1e-9)
+    roof = roofline(dominant, *dom, peaks, peak_src, fp64_peak)
+    roof["limiter"] = DOMINANT_LIMITER if dominant == "bsr_smooth" else None
+    roof["timed_in"] = "a separate profiling pass of %d steps right after the timed region" % prof_steps
+    if dominant == "bsr_smooth" and args.precision == "fp64":
         roof["traffic"] = KB_SWEEP_TRAFFIC_RATIO * roof["bytes_per_launch"]
         roof["traffic_source"] = ("ncu DRAM bytes of kb_sweep at 96^3 / algorithmic bytes = %.3f, times this "
                                   "launch's algorithmic bytes" % KB_SWEEP_TRAFFIC_RATIO)
+    vk = [k for k in VCYCLE_KINDS]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(GRID), "h": H_SPACING, "alpha": ALPHA, "dt": DT,
-                   "rtol": RTOL, "precision": args.precision, "kcycle": args.kcycle, "parallelism": "replicas" if world > 1 else "single",
-                   "levels": H.levels, "l2": "working set per step (~3 GB: GCR bases, operators) exceeds the 126 MB L2"},
+                   "rtol": RTOL, "precision": args.precision, "kcycle": args.kcycle,
+                   "parallelism": "replicas" if world > 1 else "single", "levels": H.levels,
+                   "l2": "inputs larger than L2: the working set per step (~3 GB: GCR bases, operators) exceeds "
+                         "the 126 MB L2"},
         "iterations_per_step": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},
         "max_relres": float(max(rrs)),
-        "error_vs_fp64": error_vs_fp64,
         "setup_s": setup_s,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,
-        "kernel_breakdown_warmup_ms": {k: round(v[0], 3) for k, v in breakdown.items()},
-        # the V-cycle's kernels together (algorithmic bytes over their event time, warm-up steps)
-        "vcycle_hbm_gbs": (sum(breakdown[k][3] for k in VCYCLE_KINDS)
-                           / max(sum(breakdown[k][0] for k in VCYCLE_KINDS), 1e-9) / 1e6),
-        "numeric_setup_ms_per_step": breakdown["numeric"][0] / max(args.warmup, 1),
-        "kernel_roofline_warmup": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
-                                       for kk, vv in roofline(k, *breakdown[k], args.precision, peaks,
-                                                              peak_src).items()
-                                       if kk in ("bound", "achieved", "unit", "frac", "hbm_gbs", "tflops")}
-                                   for k in KIND_NAMES if breakdown[k][1] > 0},
+        "precisions": others,
+        "mixed_vs_fp64_speedup": others.get("mixed", {}).get("speedup_vs_fp64"),
+        "bf16_vs_fp64_speedup": others.get("bf16", {}).get("speedup_vs_fp64"),
+        "fp64_peak": {"measured_tflops": fp64_meas, "derived_tflops": FP64_PEAK_TFLOPS,
+                      "probe": "ll_fp64_fma_probe: 1184 blocks x 256 threads x 8 chains x 8192 FMA, best of 5"},
+        "kernel_breakdown_ms_per_step": {k: round(v[0] / prof_steps, 3) for k, v in breakdown.items()},
+        # the V-cycle's kernels together (algorithmic bytes over their event time)
+        "vcycle_hbm_gbs": (sum(breakdown[k][3] for k in vk) / max(sum(breakdown[k][0] for k in vk), 1e-9) / 1e6),
+        "numeric_setup_ms_per_step": breakdown["numeric"][0] / prof_steps,
+        "kernel_roofline": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                for kk, vv in roofline(k, *breakdown[k], peaks, peak_src, fp64_peak).items()
+                                if kk in ("achieved", "frac", "fp64_tflops", "fp64_frac")}
+                            for k in KIND_NAMES if breakdown[k][1] > 0},
         "e2e": {"value": replica_throughput(UNKNOWNS * e2e_steps, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": UNKNOWNS * 8 * world, "d2h_bytes_per_step": UNKNOWNS * 8 * world,
-                "steps": e2e_steps},
+                "steps": e2e_steps, "iterations_per_step": float(np.mean(e2e_its)),
+                "api": "ll_mg_step_host (pinned host field, copies inside the library), the timed K steps again "
+                       "from the same state, host wall clock"},
     }
     if not args.no_cpu_baseline:
-        s, p = oracle_sample(3)
-        it_mean = float(np.mean(its))
-        cpu_v = UNKNOWNS / (s + it_mean * p)
-        line["cpu_baseline"] = {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "oracle setup of one 128^3 step + 3 GCR iterations, extrapolated to "
-                                          "the measured %.1f iterations per step" % it_mean}
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
 
 
@@ -525,6 +672,7 @@ def main():
     ap.add_argument("--kcycle", type=int, default=0,
                     help="coarse levels 1..K solved by two inner GCR steps (K-cycle); 0 = V-cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="time only the --precision path")
     ap.add_argument("--workload", choices=["step128", "batch512", "grad96"], default="step128",
                     help="step128: the 128^3 time-stepping workload; batch512: the ragged batch; "
                          "grad96: the 96^3 differentiation workload")

@@ -146,6 +146,16 @@ int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, 
 int ll_mg_step_llg(ll_mg_hierarchy* H, double* m, int n_steps, double q, const double* he,
                    int* iters_per_step, double* relres_per_step);
 
+/* As ll_mg_step, for a field held in HOST memory: m_host (3*N float64, SoA,
+ * pinned or pageable) is copied to a device buffer of the hierarchy (allocated
+ * on the first call, 24 N bytes, freed by ll_mg_destroy), n_steps steps run
+ * there, and the new field is copied back into m_host.  Both copies are
+ * queued on the hierarchy's stream after the work already queued on the
+ * caller's; the call returns when m_host holds the result.  Returns as
+ * ll_mg_step; on an error (negative status) m_host is left unchanged. */
+int ll_mg_step_host(ll_mg_hierarchy* H, double* m_host, int n_steps, int* iters_per_step,
+                    double* relres_per_step);
+
 /* Release the hierarchy and all its device memory (NULL is ignored). */
 void ll_mg_destroy(ll_mg_hierarchy* H);
 
@@ -173,6 +183,16 @@ int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col,
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all hierarchies, all threads). */
 long long ll_launch_count(void);
+
+/* Measurement helper (no counterpart in the paper): one launch of a kernel
+ * that only issues float64 fused multiply-adds (8 independent chains per
+ * thread, 256 threads per block, `blocks` blocks, `iters` multiply-adds per
+ * chain) on cuda_stream, for timing the GPU's float64 throughput with CUDA
+ * events around the call.  *flops (host, optional) receives the launch's
+ * floating-point operations, 2 per multiply-add.  sink: device, 1 double,
+ * written only in a case that does not occur.  Returns without waiting.
+ * Errors: LL_EINVAL, LL_ECUDA. */
+int ll_fp64_fma_probe(double* sink, long long iters, int blocks, void* cuda_stream, double* flops);
 
 /* Kernel timing by kind, for benchmarks.  While enabled, every kernel of a
  * kind whose bit is set in `kinds` is bracketed by two CUDA events on the
@@ -257,8 +277,9 @@ int ll_residual_noalloc(const double* m_tilde, double alpha, double dt, double h
  *   m_tilde   host array of count device pointers, each SoA 3*N_i float64
  *   alpha, dt, h, grids   host arrays of count values (as ll_mg_setup)
  *   p         parameters shared by all instances, or NULL for the defaults;
- *             precision LL_FP64 or LL_MIXED_FP32, kcycle 0 (LL_EINVAL
- *             otherwise)
+ *             precision LL_FP64 or LL_MIXED_FP32 (LL_EINVAL otherwise);
+ *             kcycle > 0 runs the K-cycle on those coarse levels of every
+ *             instance, with each instance's own inner-step scalars
  * Every instance must coarsen at least once (more cells than
  * p->coarsest_cells), else LL_EINVAL.  The batch owns all its memory;
  * m_tilde is not retained.  Errors as ll_mg_setup. */

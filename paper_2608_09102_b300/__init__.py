@@ -32,7 +32,7 @@ EXPORTS = (
     "ll_residual_noalloc", "ll_mg_step_llg", "ll_mg_batch_setup", "ll_mg_batch_update", "ll_mg_batch_solve",
     "ll_mg_batch_count", "ll_mg_batch_levels", "ll_mg_batch_level_rows", "ll_mg_batch_level_colours",
     "ll_mg_batch_instance_levels", "ll_mg_batch_destroy", "ll_mg_step_save", "ll_mg_batch_subbatches", "ll_mg_adjoint_setup",
-    "ll_mg_step_vjp",
+    "ll_mg_step_vjp", "ll_mg_step_host", "ll_fp64_fma_probe",
 )
 
 
@@ -127,6 +127,8 @@ def load_library():
         "ll_mg_step_save": (i, [vp, vp, i, vp, ip, dp]),
         "ll_mg_adjoint_setup": (i, [vp, d, d, d, _Grid, P, vp, ctypes.POINTER(vp)]),
         "ll_mg_step_vjp": (i, [vp, vp, d, d, vp, vp, vp, dp, d, ip, dp]),
+        "ll_mg_step_host": (i, [vp, vp, i, ip, dp]),
+        "ll_fp64_fma_probe": (i, [vp, ctypes.c_longlong, i, vp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -227,6 +229,23 @@ class Hierarchy:
         _check(st, "ll_mg_step")
         if dev is not m:
             m.copy_(dev, non_blocking=False)
+        return st, list(its[:n_steps]), list(rrs[:n_steps])
+
+    def step_host(self, m, n_steps: int = 1):
+        """n_steps steps of a field in HOST memory (``ll_mg_step_host``): the
+        library copies ``m`` (a contiguous float64 CPU tensor, best pinned) to
+        the device, steps it and copies the result back into ``m``.  Returns
+        (status, iterations per step, relres per step)."""
+        import torch
+
+        if not isinstance(m, torch.Tensor) or m.is_cuda or m.dtype != torch.float64:
+            raise TypeError("m must be a float64 CPU tensor")
+        if not m.is_contiguous() or m.numel() != 3 * self.n:
+            raise ValueError("m must be contiguous with 3*N = %d values" % (3 * self.n))
+        its = (ctypes.c_int * max(1, n_steps))()
+        rrs = (ctypes.c_double * max(1, n_steps))()
+        st = load_library().ll_mg_step_host(self._h, ctypes.c_void_p(m.data_ptr()), int(n_steps), its, rrs)
+        _check(st, "ll_mg_step_host")
         return st, list(its[:n_steps]), list(rrs[:n_steps])
 
     def step_save(self, m, x_save, n_steps: int = 1):
@@ -527,6 +546,17 @@ class Batch:
     def subbatches(self) -> int:
         """Compacted sub-batches built so far (ll_mg_batch_subbatches)."""
         return load_library().ll_mg_batch_subbatches(self._h)
+
+
+def fp64_fma_probe(sink, iters: int, blocks: int):
+    """One launch of the library's float64 multiply-add probe on the current
+    stream (``ll_fp64_fma_probe``); ``sink`` is a float64 CUDA tensor of at
+    least one element.  Returns the launch's floating-point operations."""
+    fl = ctypes.c_double(0.0)
+    st = load_library().ll_fp64_fma_probe(ctypes.c_void_p(sink.data_ptr()), int(iters), int(blocks), _stream(),
+                                          ctypes.byref(fl))
+    _check(st, "ll_fp64_fma_probe", ok=(LL_OK,))
+    return fl.value
 
 
 def launch_count() -> int:

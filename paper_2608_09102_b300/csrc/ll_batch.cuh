@@ -152,6 +152,29 @@ void batch_symbolic(ll_mg_batch* B) {
       }
     }
     L.n = row;
+    if (l <= B->prm.kcycle && l < nlev - 1) {  // K-cycle tables of this level
+      std::vector<Chunk> ch;
+      std::vector<int> ip(1, 0), ri(L.n, -1);
+      for (int i = 0; i < ni; ++i) {
+        ll_mg_hierarchy* H = B->inst[i];
+        if (H->nlev - 1 > l)
+          for (int t = 0; t < H->lev[l].ncol; ++t) {
+            int r0 = off[i][t], r1 = r0 + H->lev[l].cs[t + 1] - H->lev[l].cs[t];
+            for (int r = r0; r < r1; ++r) ri[r] = i;
+            for (long e = 3L * r0; e < 3L * r1; e += kChunkElems) ch.push_back({i, e, std::min(3L * r1, e + kChunkElems)});
+          }
+        ip.push_back((int)ch.size());
+      }
+      U->knch[l] = (int)ch.size();
+      U->kchunks[l].alloc(ch.size());
+      U->kiptr[l].alloc(ip.size());
+      U->krow_inst[l].alloc(ri.size());
+      if (!ch.empty())
+        LL_CU(cudaMemcpyAsync(U->kchunks[l].p, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+      LL_CU(cudaMemcpyAsync(U->kiptr[l].p, ip.data(), ip.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      LL_CU(cudaMemcpyAsync(U->krow_inst[l].p, ri.data(), ri.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      LL_CU(cudaStreamSynchronize(s));  // the host tables go out of scope
+    }
     U->uc_n[l] = (int)tasks.size();
     U->uc_maxN[l] = maxN;
     if (!tasks.empty()) {
@@ -293,6 +316,19 @@ void batch_allocate(ll_mg_batch* B) {
     }
   }
   int ni = B->ninst;
+  // K-cycle vectors and scalars (levels 1..kcycle that are not the coarsest)
+  int kmax = 0;
+  for (int l = 1; l < U->nlev - 1 && l <= B->prm.kcycle; ++l) {
+    for (int q = 0; q < 4; ++q) {
+      if (mixed) U->lev[l].k32[q].alloc(3L * U->lev[l].n);
+      else U->lev[l].k64[q].alloc(3L * U->lev[l].n);
+    }
+    kmax = std::max(kmax, U->knch[l]);
+  }
+  U->kninst = ni;
+  U->kscal_u.alloc((size_t)8 * ni * U->nlev);
+  U->kscal_u.zero(U->s);
+  U->partial.alloc((size_t)2 * std::max(kmax, 1));
   B->n3 = 3L * U->lev[0].n;
   int m = B->prm.restart;
   if (mixed) B->Z32.alloc((size_t)m * B->n3);

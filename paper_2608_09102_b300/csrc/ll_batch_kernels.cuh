@@ -535,6 +535,80 @@ __global__ void __launch_bounds__(256) kgb_residual(const Chunk* __restrict__ ch
   chunk_reduce_store<2>(acc, partial, 2, nchunks);
 }
 
+// ---------------------------------------------------------------------------
+// K-cycle on a union level: the two inner GCR steps of every instance that
+// has the K-cycle there, with 8 scalars per instance (ks[8 i + q], the same
+// fields as the single solve's), partial dots per chunk of one instance's
+// rows and per-instance sums in chunk order.  row_inst[R] is the instance of
+// union row R, or -1 for rows without the K-cycle (instances whose coarsest
+// level this is: their correction is the direct solve z1 itself).
+// ---------------------------------------------------------------------------
+template <typename T, int NQ>
+__global__ void __launch_bounds__(256) kbk_dots(const Chunk* __restrict__ ch, int nchunks, const T* __restrict__ u0,
+                                                const T* __restrict__ v0, const T* __restrict__ u1,
+                                                const T* __restrict__ v1, double* __restrict__ partial) {
+  Chunk k = ch[blockIdx.x];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0;
+  for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
+    acc[0] += (double)u0[t] * (double)v0[t];
+    if (NQ > 1) acc[NQ - 1] += (double)u1[t] * (double)v1[t];
+  }
+  chunk_reduce_store<NQ>(acc, partial, NQ, nchunks);
+}
+
+// ks[8 i + field + q] = sum of partial[q][chunks of instance i]
+__global__ void kbk_finish(const double* __restrict__ partial, int nchunks, const int* __restrict__ iptr,
+                           double* __restrict__ ks, int field) {
+  __shared__ double sh[kBlock];
+  int i = blockIdx.x, q = blockIdx.y;
+  double a = 0;
+  for (int k = iptr[i] + threadIdx.x; k < iptr[i + 1]; k += kBlock) a += partial[(long)q * nchunks + k];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kBlock / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ks[8L * i + field + q] = sh[0];
+}
+
+// y = u - (ks[8 i + num] / ks[8 i + den]) v per element of instance i (a
+// zero denominator means v = 0 there: coefficient 0); rows without the
+// K-cycle copy u
+template <typename T>
+__global__ void kbk_axpy(long n3, const int* __restrict__ row_inst, const T* u, const T* __restrict__ v,
+                         const double* __restrict__ ks, int num, int den, T* y) {  // y may alias u
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  int i = row_inst[t / 3];
+  double f = 0;
+  if (i >= 0) {
+    double d = ks[8L * i + den];
+    f = d > 0 ? ks[8L * i + num] / d : 0.0;
+  }
+  y[t] = u[t] - (T)f * v[t];
+}
+
+// x = y1 z1 + y2 x per instance (as kk_combine); rows without the K-cycle
+// take z1
+template <typename T>
+__global__ void kbk_combine(long n3, const int* __restrict__ row_inst, const T* __restrict__ z1, T* __restrict__ x,
+                            const double* __restrict__ ks) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  int i = row_inst[t / 3];
+  if (i < 0) {
+    x[t] = z1[t];
+    return;
+  }
+  const double* k = ks + 8L * i;
+  double y2 = k[3] > 0 ? k[4] / k[3] : 0.0;
+  double y1 = k[0] > 0 ? (k[1] - k[2] * y2) / k[0] : 0.0;
+  x[t] = (T)(y1 * (double)z1[t] + y2 * (double)x[t]);
+}
+
 // per-instance scalar updates (one thread per instance, the same formulas as
 // the single-instance kernels)
 __global__ void kgb_gs_coef(GcrScal* S, int ninst, int j, int first) {

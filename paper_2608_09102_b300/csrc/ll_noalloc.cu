@@ -56,20 +56,24 @@ __global__ void k_residual_partial(int nx, int ny, int nz, const double* __restr
     int i = (int)(k % nx);
     long t = k / nx;
     int j = (int)(t % ny), l = (int)(t / ny);
-    long nb[6];
-    int d = 0;
     long nxy = (long)nx * ny;
-    if (l > 0) nb[d++] = k - nxy;
-    if (j > 0) nb[d++] = k - nx;
-    if (i > 0) nb[d++] = k - 1;
-    if (i < nx - 1) nb[d++] = k + 1;
-    if (j < ny - 1) nb[d++] = k + nx;
-    if (l < nz - 1) nb[d++] = k + nxy;
+    // face neighbours present (Neumann: missing ones are left out), tested
+    // in place rather than gathered into an index array, which would sit in
+    // local memory and serialise the loads
+    bool zm = l > 0, ym = j > 0, xm = i > 0, xp = i < nx - 1, yp = j < ny - 1, zp = l < nz - 1;
+    int d = zm + ym + xm + xp + yp + zp;
     double lap[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
+      const double* xc = x + c * n + k;
       double s = 0.0;
-      for (int q = 0; q < d; ++q) s += x[c * n + nb[q]];
-      lap[c] = (s - d * x[c * n + k]) * ih2;  // (Delta_h x)_k
+      if (zm) s += xc[-nxy];
+      if (ym) s += xc[-nx];
+      if (xm) s += xc[-1];
+      if (xp) s += xc[1];
+      if (yp) s += xc[nx];
+      if (zp) s += xc[nxy];
+      lap[c] = (s - d * xc[0]) * ih2;  // (Delta_h x)_k
     }
     double m1 = m[k], m2 = m[n + k], m3 = m[2 * n + k];
     double mm = m1 * m1 + m2 * m2 + m3 * m3;

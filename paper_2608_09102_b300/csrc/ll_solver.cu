@@ -105,6 +105,7 @@ struct ll_mg_hierarchy {
   double* h_head = nullptr;  // pinned copy of the first scalars
   // time-step workspace (natural layout)
   DBuf<double> stepb, stepx;
+  DBuf<double> hostm;  // device copy of a host field (ll_mg_step_host), allocated on first use
   // the small coarse levels as one cluster kernel
   int tail_first = -1;  // first tail level, -1: no tail
   int tail_cluster = 0;
@@ -119,6 +120,15 @@ struct ll_mg_hierarchy {
   bool union_mode = false;
   DBuf<CoarseTask> uc_tasks[kMaxLevels];
   int uc_n[kMaxLevels] = {0}, uc_maxN[kMaxLevels] = {0};
+  // union hierarchies with the K-cycle: per K level, element chunks of the
+  // rows of every instance that has the K-cycle there (instance-major), the
+  // chunk range of each instance, the instance of each row (-1: none), and 8
+  // scalars per instance and level
+  int kninst = 0;
+  DBuf<Chunk> kchunks[kMaxLevels];
+  DBuf<int> kiptr[kMaxLevels], krow_inst[kMaxLevels];
+  int knch[kMaxLevels] = {0};
+  DBuf<double> kscal_u;
   // kernel timing (ll_mg_profile)
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -579,6 +589,27 @@ void launch_tail(ll_mg_hierarchy* H) {
   count_launch();
 }
 
+// Float64 FMA throughput probe: kProbeChains independent multiply-add chains
+// per thread (enough in flight to cover the float64 pipe's latency), no
+// memory traffic; the sum is stored only under a condition the compiler
+// cannot decide, so the chains are not removed.
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(kProbeThreads) k_fp64_fma_probe(double* sink, long long iters) {
+  double a[kProbeChains];
+#pragma unroll
+  for (int q = 0; q < kProbeChains; ++q) a[q] = 1e-3 * (threadIdx.x + q);
+  const double mul = 0.9999999, add = 1e-9;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < kProbeChains; ++q) a[q] = fma(a[q], mul, add);
+  }
+  double t = 0;
+#pragma unroll
+  for (int q = 0; q < kProbeChains; ++q) t += a[q];
+  if (t == -1.0) sink[0] = t;
+}
+
 // dense level-0 operator (single-level hierarchies), unknown 3k + c, k natural
 __global__ void k_dense_from_l0(GridGeom g, const double* __restrict__ chat64, double inv_dt,
                                 double* __restrict__ a) {
@@ -803,11 +834,67 @@ void kinner(ll_mg_hierarchy* H, int l) {
   }
 }
 
+// The K-cycle on level l of a batch's union hierarchy: kinner's steps for
+// every instance that has the K-cycle on this level, with each instance's
+// own scalars (dots summed per instance over its chunks in a fixed order).
+// Rows of instances whose coarsest level this is keep the direct solve.
+template <typename T, typename TM>
+void kinner_union(ll_mg_hierarchy* H, int l) {
+  CLevel& L = H->lev[l];
+  cudaStream_t s = H->s;
+  long n3 = 3L * L.n;
+  int nb = cdiv(n3, kBlock), nbs = cdiv((long)L.n * lanes<T>(), kCoarseBlock);
+  double* ks = H->kscal_u.p + (size_t)8 * H->kninst * l;
+  const Chunk* ch = H->kchunks[l];
+  const int* ip = H->kiptr[l];
+  const int* ri = H->krow_inst[l];
+  int nch = H->knch[l];
+  T *kr = L.kv<T>(0), *kz1 = L.kv<T>(1), *kc1 = L.kv<T>(2), *kc2 = L.kv<T>(3);
+  auto dots = [&](auto nq, const T* u0, const T* v0, const T* u1, const T* v1, int field) {
+    constexpr int NQ = decltype(nq)::value;
+    if (nch == 0) return;
+    kbk_dots<T, NQ><<<nch, kBlock, 0, s>>>(ch, nch, u0, v0, u1, v1, H->partial);
+    LL_LAUNCHED();
+    kbk_finish<<<dim3(H->kninst, NQ), kBlock, 0, s>>>(H->partial, nch, ip, ks, field);
+    LL_LAUNCHED();
+  };
+  {
+    LL_PROF(LL_KIND_BSR_OTHER);
+    LL_CU(cudaMemcpyAsync(kr, L.b<T>(), n3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+  vcycle_coarse<T, TM>(H, l, true);  // z1 = B r
+  {  // c1 = A z1; d11 = c1.c1, d1r = c1.r; r1 = r - (d1r/d11) c1 (into L.b)
+    LL_PROF(LL_KIND_BSR_OTHER);
+    LL_CU(cudaMemcpyAsync(kz1, L.x<T>(), n3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    kb_spmv<T, TM, lanes<T>()><<<nbs, kCoarseBlock, 0, s>>>(L.n, L.rowptr, L.col, L.valm<TM>(), kz1, kc1);
+    LL_LAUNCHED();
+    dots(std::integral_constant<int, 2>(), kc1, kc1, kc1, kr, 0);
+    kbk_axpy<T><<<nb, kBlock, 0, s>>>(n3, ri, kr, kc1, ks, 1, 0, L.b<T>());
+    LL_LAUNCHED();
+  }
+  vcycle_coarse<T, TM>(H, l, false);  // z2 = B r1 (in L.x)
+  {  // c2 = A z2 - (d12/d11) c1; d22 = c2.c2, d2r = c2.r1; x = y1 z1 + y2 z2
+    LL_PROF(LL_KIND_BSR_OTHER);
+    kb_spmv<T, TM, lanes<T>()><<<nbs, kCoarseBlock, 0, s>>>(L.n, L.rowptr, L.col, L.valm<TM>(), L.x<T>(), kc2);
+    LL_LAUNCHED();
+    dots(std::integral_constant<int, 1>(), kc1, kc2, nullptr, nullptr, 2);
+    kbk_axpy<T><<<nb, kBlock, 0, s>>>(n3, ri, kc2, kc1, ks, 2, 0, kc2);
+    LL_LAUNCHED();
+    dots(std::integral_constant<int, 2>(), kc2, kc2, kc2, L.b<T>(), 3);
+    kbk_combine<T><<<nb, kBlock, 0, s>>>(n3, ri, kz1, L.x<T>(), ks);
+    LL_LAUNCHED();
+  }
+}
+
 // the coarse problem of level l: a K level's two inner steps, or one cycle
 template <typename T, typename TM>
 void coarse_problem(ll_mg_hierarchy* H, int l) {
-  if (l <= H->prm.kcycle && l < H->nlev - 1) kinner<T, TM>(H, l);
-  else vcycle_coarse<T, TM>(H, l, true);
+  if (l <= H->prm.kcycle && l < H->nlev - 1) {
+    if (H->union_mode) kinner_union<T, TM>(H, l);
+    else kinner<T, TM>(H, l);
+  } else {
+    vcycle_coarse<T, TM>(H, l, true);
+  }
 }
 
 // union hierarchies: dense solves of the instances whose coarsest level is l
@@ -1444,7 +1531,35 @@ int ll_mg_step_save(ll_mg_hierarchy* H, double* m, int n_steps, double* x_save, 
   return st;
 }
 
+int ll_mg_step_host(ll_mg_hierarchy* H, double* m_host, int n_steps, int* iters_per_step,
+                    double* relres_per_step) {
+  if (!H || !m_host || n_steps < 0) return LL_EINVAL;
+  size_t bytes = 3 * (size_t)H->g.n * sizeof(double);
+  try {
+    enter(H);
+    if (!H->hostm.p) H->hostm.alloc(3 * H->g.n);
+    LL_CU(cudaMemcpyAsync(H->hostm.p, m_host, bytes, cudaMemcpyHostToDevice, H->s));
+  } catch (Status st) {
+    return st.code;
+  }
+  int worst = steps(H, H->hostm.p, n_steps, iters_per_step, relres_per_step, false);
+  if (worst < 0) return worst;
+  if (cudaMemcpyAsync(m_host, H->hostm.p, bytes, cudaMemcpyDeviceToHost, H->s) != cudaSuccess ||
+      cudaStreamSynchronize(H->s) != cudaSuccess)
+    return LL_ECUDA;
+  return worst;
+}
+
 long long ll_launch_count(void) { return g_launches.load(); }
+
+int ll_fp64_fma_probe(double* sink, long long iters, int blocks, void* cuda_stream, double* flops) {
+  if (!sink || iters < 1 || blocks < 1) return LL_EINVAL;
+  k_fp64_fma_probe<<<blocks, kProbeThreads, 0, (cudaStream_t)cuda_stream>>>(sink, iters);
+  if (cudaGetLastError() != cudaSuccess) return LL_ECUDA;
+  count_launch();
+  if (flops) *flops = 2.0 * kProbeChains * (double)iters * blocks * kProbeThreads;
+  return LL_OK;
+}
 
 void ll_mg_destroy(ll_mg_hierarchy* H) {
   if (H) {
@@ -1656,7 +1771,7 @@ int ll_mg_batch_setup(int count, const double* const* m_tilde, const double* alp
   for (int i = 0; i < count; ++i)
     if (!m_tilde[i] || !valid_problem(alpha[i], dt[i], h[i], grids[i])) return LL_EINVAL;
   if (p && !valid_params(*p)) return LL_EINVAL;
-  if (p && (p->kcycle != 0 || p->precision == LL_MIXED_BF16)) return LL_EINVAL;
+  if (p && p->precision == LL_MIXED_BF16) return LL_EINVAL;
   return batch_create(count, m_tilde, alpha, dt, h, grids, p, cuda_stream, out);
 }
 

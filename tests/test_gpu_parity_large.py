@@ -1,0 +1,198 @@
+"""Parity with the FP64 oracle where the dominant kernels run, through the
+C ABI.
+
+The small grids of ``test_gpu_parity.py`` put every coarse level inside the
+cluster tail.  Here the grids are large enough that the per-class coarse
+kernels run: at 48^3 level 1 (27,648 cells) is above the tail's limit and its
+colour classes take 8 lanes per row; at 128^3 levels 1-3 run per class and
+the level-1 classes (over 20,000 rows each) take 4 lanes per row.  Tolerances
+as in ``test_gpu_parity.py``: single sweeps to 1e-12 of the largest entry, a
+V-cycle to 1e-11 relative, float64 solves to 1e-10 relative of the oracle's,
+mixed-precision solves to 1e-8 of the oracle's.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_09102_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2608_09102_b300 as ll  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device=DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _cm_to_aos(v, n):
+    return np.ascontiguousarray(np.asarray(v).reshape(3, n).T).reshape(-1)
+
+
+def _aos_to_cm(v, n):
+    return np.ascontiguousarray(np.asarray(v).reshape(n, 3).T).reshape(-1)
+
+
+def _vortex_case(side, kcycle=0, precision=ll.LL_FP64, rtol=1e-12):
+    grid = (side,) * 3
+    h, alpha = 1.0 / side, 0.02
+    dt = 8.19 * h * h  # the time-stepping workload's dt/h^2
+    m = inputs.vortex(*grid, seed=0).reshape(-1)
+    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=rtol, kcycle=kcycle))
+    G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=rtol, kcycle=kcycle, precision=precision))
+    return grid, h, alpha, dt, m, O, G
+
+
+@pytest.fixture(scope="module")
+def case48():
+    return _vortex_case(48)
+
+
+@pytest.fixture(scope="module")
+def case128():
+    return _vortex_case(128)
+
+
+def _check_coarse_sweeps(O, G, levels):
+    rng = np.random.default_rng(6)
+    for l in levels:
+        n = O.cells(l)
+        b, x = rng.standard_normal(3 * n), rng.standard_normal(3 * n)
+        for fwd in (True, False):
+            xg = torch.tensor(_cm_to_aos(x, n), device=DEV)
+            G.smooth(l, torch.tensor(_cm_to_aos(b, n), device=DEV), xg, fwd)
+            ref = O.smooth(b, x, fwd, l=l)
+            err = np.abs(_aos_to_cm(_np(xg), n) - ref).max() / np.abs(ref).max()
+            assert err <= 1e-12, (l, fwd, err)
+
+
+def test_48cube_hierarchy_and_per_class_sweeps(case48):
+    grid, h, alpha, dt, m, O, G = case48
+    assert G.levels == O.nlevels
+    assert O.cells(1) > 12000  # level 1 runs per colour class, outside the tail
+    for l in range(O.nlevels - 1):
+        assert np.array_equal(G.aggregates(l), O.agg(l))
+        assert np.array_equal(G.colours(l + 1), O.colours(l + 1))
+    _check_coarse_sweeps(O, G, [1, 2])
+
+
+def test_48cube_vcycle(case48):
+    grid, h, alpha, dt, m, O, G = case48
+    r = inputs.rhs_field(*grid, seed=8).reshape(-1)
+    z = torch.empty_like(_t(r))
+    G.vcycle(_t(r), z)
+    ref = O.vcycle(r)
+    assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_48cube_kcycle_preconditioner():
+    grid, h, alpha, dt, m, O, G = _vortex_case(48, kcycle=1)
+    r = inputs.rhs_field(*grid, seed=8).reshape(-1)
+    z = torch.empty_like(_t(r))
+    G.vcycle(_t(r), z)
+    ref = O.vcycle(r)
+    assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_48cube_solve(case48):
+    grid, h, alpha, dt, m, O, G = case48
+    b = m / dt
+    xo, sto, ito, rro = O.solve(b, np.zeros_like(b))
+    x = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(b), x)
+    assert st == ll.LL_OK and sto == oracle.OK and rr < 1e-12
+    assert abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(_np(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("precision", [ll.LL_MIXED_FP32, ll.LL_MIXED_BF16])
+def test_48cube_mixed_solution_against_oracle(case48, precision):
+    """float32 / bfloat16 V-cycle inside float64 GCR to rtol 1e-10: within
+    1e-8 of the oracle's float64 solution."""
+    grid, h, alpha, dt, m, O, G = case48
+    b = m / dt
+    xo, sto, ito, rro = O.solve(b, np.zeros_like(b))
+    Gm = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-10, precision=precision))
+    x = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    st, it, rr = Gm.solve(_t(b), x)
+    assert st == ll.LL_OK and rr < 1e-10
+    assert np.linalg.norm(_np(x) - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_128cube_per_class_sweeps_and_vcycle(case128):
+    """The time-stepping workload's hierarchy: the level-1 classes take the
+    4-lane path, levels 2-3 the 8-lane path; one V-cycle through all of them
+    and the cluster tail."""
+    grid, h, alpha, dt, m, O, G = case128
+    assert G.levels == O.nlevels
+    assert O.cells(1) > 20000 * 4  # several level-1 classes above the 4-lane threshold
+    for l in range(1, 4):
+        assert np.array_equal(G.colours(l), O.colours(l))
+    _check_coarse_sweeps(O, G, [1, 2, 3])
+    r = inputs.rhs_field(*grid, seed=8).reshape(-1)
+    z = torch.empty_like(_t(r))
+    G.vcycle(_t(r), z)
+    ref = O.vcycle(r)
+    assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_iteration_counts_stay_bounded_under_refinement():
+    """Mesh independence on the GPU (3-D, dt/h^2 = 8.19, alpha = 0.02):
+    32^3 -> 128^3 grows the iteration count by at most 30 %."""
+    its = []
+    for side in (32, 64, 128):
+        grid = (side,) * 3
+        h = 1.0 / side
+        dt = 8.19 * h * h
+        m = inputs.vortex(*grid, seed=0).reshape(-1)
+        G = ll.Hierarchy(_t(m), 0.02, dt, h, grid, ll.Params(rtol=1e-8))
+        x = _t(m)
+        st, it, rr = G.solve(_t(m / dt), x)
+        assert st == ll.LL_OK
+        its.append(it)
+    assert max(its) <= 1.3 * its[0], its
+
+
+def test_step_host_equals_device_steps():
+    """ll_mg_step_host (a field in host memory, copied by the library) gives
+    the same steps as ll_mg_step on a device field."""
+    grid, h, alpha, dt = (24, 20, 8), 1 / 24, 0.05, 2e-3
+    m0 = inputs.vortex(*grid, seed=0).reshape(-1)
+    p = ll.Params(rtol=1e-10)
+    md = _t(m0)
+    Gd = ll.Hierarchy(md, alpha, dt, h, grid, p)
+    std, itd, rrd = Gd.step(md, 2)
+    mh = torch.tensor(m0).pin_memory()
+    Gh = ll.Hierarchy(_t(m0), alpha, dt, h, grid, p)
+    sth, ith, rrh = Gh.step_host(mh, 2)
+    assert std == sth == ll.LL_OK and itd == ith
+    assert torch.equal(mh, md.cpu())
+    mp = torch.tensor(m0)  # pageable host memory works too
+    Gp = ll.Hierarchy(_t(m0), alpha, dt, h, grid, p)
+    Gp.step_host(mp, 2)
+    assert torch.equal(mp, md.cpu())
+
+
+def test_fp64_probe_runs():
+    sink = torch.zeros(1, dtype=torch.float64, device=DEV)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fl = ll.fp64_fma_probe(sink, 4096, 148 * 4)
+    e1.record()
+    torch.cuda.synchronize()
+    assert fl == 2.0 * 8 * 4096 * 148 * 4 * 256
+    tflops = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    assert 0.05 < tflops < 5.0, tflops
+    assert float(sink[0]) == 0.0

@@ -40,13 +40,24 @@ def test_noalloc_residual_matches_existing_entry_points_twice():
     y = torch.empty_like(b)
     lib = ll.load_library()
     g = ll._Grid(*grid)
+
+    def call(x):
+        return lib.ll_residual_noalloc(ctypes.c_void_p(m.data_ptr()), alpha, dt, h, g, ctypes.c_void_p(b.data_ptr()),
+                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                       ctypes.c_void_p(norms.data_ptr()),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    # the first call on a device does the one-time set-up (looking up the
+    # scratch array's address, which may load the library's device code);
+    # after it, calls leave the device's free memory unchanged
+    assert call(xs[0]) == ll.LL_OK
+    torch.cuda.synchronize()
     for k, x in enumerate(xs):
-        st = lib.ll_residual_noalloc(ctypes.c_void_p(m.data_ptr()), alpha, dt, h, g, ctypes.c_void_p(b.data_ptr()),
-                                     ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()),
-                                     ctypes.c_void_p(norms.data_ptr()),
-                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        free0 = torch.cuda.mem_get_info()[0]
+        st = call(x)
         assert st == ll.LL_OK
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, "the call changed the device's free memory"
         H.apply(x, y)  # existing entry point: y = A x
         r_ref = b - y
         scale = float(r_ref.abs().max())
