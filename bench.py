@@ -537,8 +537,15 @@ def run_batch(args):
     dts = [s["dt"] for s in spec]
     ns = [int(np.prod(s["grid"])) for s in spec]
     params = ll.Params(rtol=RTOL, precision=precision, maxit=args.batch_maxit)
+    hs, grids = [s["h"] for s in spec], [s["grid"] for s in spec]
+    tune_s, tuned, per = None, 0, params
+    if not args.no_autotune:  # per class of instances: cycle and coarse-kernel shape (cache in a fresh file)
+        t0 = time.perf_counter()
+        with tempfile.TemporaryDirectory() as td:
+            per, tuned = ll.autotune(ms, alphas, dts, hs, grids, base=params, cache_path=os.path.join(td, "tune.txt"))
+        tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    B = ll.Batch(ms, alphas, dts, [s["h"] for s in spec], [s["grid"] for s in spec], params)
+    B = ll.Batch(ms, alphas, dts, hs, grids, per)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     rhs = [m / dt for m, dt in zip(ms, dts)]
@@ -598,6 +605,11 @@ def run_batch(args):
         "iterations": {"mean": float(np.mean(its)), "median": float(np.median(its)), "max": int(max(its)),
                        "lockstep": int(max(its))},
         "levels": B.levels, "setup_s": setup_s, "gpu_launches": int(launches), "clocks": clocks,
+        "autotune": None if args.no_autotune else {
+            "classes_tuned": tuned, "tune_s": tune_s, "groups": B.groups,
+            "choices": sorted({(p.nu_pre, p.nu_post, p.kcycle, p.coarse_lanes, p.coarse_block) for p in per}),
+            "key": "(grid, floor(log2(dt/h^2))); candidates V(1,1), V(2,2), K1+V(1,1), K1+V(2,2), K1+V(3,3), then lanes 8 "
+                   "and/or 128-thread blocks"},
         "e2e": {"value": solved * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "steps": e2e_steps},
     }
@@ -678,6 +690,7 @@ def main():
                          "grad96: the 96^3 differentiation workload")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--batch-maxit", type=int, default=300)
+    ap.add_argument("--no-autotune", action="store_true", help="batch512: one parameter set for every instance")
     ap.add_argument("--grid", type=int, default=128,
                     help="cube side of the step workload (default 128; smaller sides are profiling cases)")
     args = ap.parse_args()

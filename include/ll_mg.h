@@ -77,6 +77,10 @@ typedef struct ll_mg_params {
   int precision;       /* LL_FP64, LL_MIXED_FP32 or LL_MIXED_BF16     (LL_FP64) */
   int kcycle;          /* coarse levels 1..kcycle are solved by two inner
                           GCR steps (K-cycle, Sec. 3.1); 0: V-cycle   (0)    */
+  int coarse_lanes;    /* launch shape of the per-class coarse-level
+                          kernels: lanes per block row, 4 or 8; 0: by
+                          the level's size                            (0)    */
+  int coarse_block;    /* their threads per block, 32/64/128/256; 0: 64 (0)  */
 } ll_mg_params;
 
 typedef struct ll_mg_hierarchy ll_mg_hierarchy; /* opaque, library-owned */
@@ -320,6 +324,56 @@ int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i);
  * off. */
 int ll_mg_batch_subbatches(const ll_mg_batch* B);
 void ll_mg_batch_destroy(ll_mg_batch* B);
+
+/* ---- batches with per-instance parameters, and their autotuner -------------
+ * The paper tunes nothing; these calls exist because the instances of a
+ * ragged batch differ widely in how hard they are (dt/h^2 from 0.01 to
+ * several hundred, alpha from 0.005 to 1): a cycle that suits most of them
+ * stagnates on some, and a stronger one costs the rest time.
+ *
+ * ll_mg_batch_setup_groups: as ll_mg_batch_setup, with one parameter set per
+ * instance (p: host array of count ll_mg_params).  Instances with equal
+ * parameters form a group, one batch each; update and solve run the groups
+ * concurrently (one host thread and one CUDA stream per group) and give
+ * per-instance results as ll_mg_batch_solve.  With a single distinct
+ * parameter set this is ll_mg_batch_setup.  The introspection calls above
+ * return -1 for the levels of a batch of several groups. */
+int ll_mg_batch_setup_groups(int count, const double* const* m_tilde, const double* alpha, const double* dt,
+                             const double* h, const ll_grid* grids, const ll_mg_params* p, void* cuda_stream,
+                             ll_mg_batch** out);
+/* number of groups (1 for a batch made by ll_mg_batch_setup) and the group
+ * of instance i */
+int ll_mg_batch_groups(const ll_mg_batch* B);
+int ll_mg_batch_instance_group(const ll_mg_batch* B, int i);
+
+/* Autotuner.  Instances are classed by (precision, grid nx ny nz, octave of
+ * dt/h^2 = floor(log2(dt/h^2))).  For every class not yet in the cache, the
+ * class's (up to) 3 instances with the smallest alpha are solved as one
+ * batch (rhs = m/dt from the guess m, base's rtol, at most 300 iterations)
+ * with each candidate cycle -- V(1,1), V(2,2), each with the K-cycle on
+ * level 1, and V(3,3) with it -- then, for the best cycle, with the coarse kernels' launch shapes
+ * (lanes 8 and/or 128 threads per block); the best converges the most
+ * instances, then takes the least time (the second of two solves).
+ *   m_tilde, alpha, dt, h, grids  as ll_mg_batch_setup (device fields)
+ *   base        parameters of everything not tuned (NULL: defaults);
+ *               precision LL_FP64 or LL_MIXED_FP32
+ *   cache_path  text file of earlier choices, read first and rewritten with
+ *               the new ones (NULL: no cache)
+ *   chosen      host output, count ll_mg_params: base with the choice of the
+ *               instance's class (pass it to ll_mg_batch_setup_groups)
+ *   keys_tuned  host output (optional): classes timed by this call
+ * Errors: LL_EINVAL (bad argument, or the cache cannot be written),
+ * LL_ENOMEM, LL_ECUDA. */
+int ll_mg_batch_autotune(int count, const double* const* m_tilde, const double* alpha, const double* dt,
+                         const double* h, const ll_grid* grids, const ll_mg_params* base, const char* cache_path,
+                         void* cuda_stream, ll_mg_params* chosen, int* keys_tuned);
+/* Host-only helpers of the autotuner's cache (no device work): the octave
+ * floor(log2(dt/h^2)) of a class (INT_MIN for bad input), and the cached
+ * choice for one instance: p is read (its precision selects the class) and,
+ * when the cache holds the class, overwritten with base p plus the choice;
+ * returns 1 (found), 0 (not found) or LL_EINVAL. */
+int ll_mg_tune_octave(double dt, double h);
+int ll_mg_tune_lookup(const char* cache_path, ll_grid grid, double dt, double h, ll_mg_params* p);
 
 /* ---- differentiation of the time step (adjoint) ----------------------------
  * A loss L on a later state depends on m^n through every step

@@ -32,7 +32,8 @@ EXPORTS = (
     "ll_residual_noalloc", "ll_mg_step_llg", "ll_mg_batch_setup", "ll_mg_batch_update", "ll_mg_batch_solve",
     "ll_mg_batch_count", "ll_mg_batch_levels", "ll_mg_batch_level_rows", "ll_mg_batch_level_colours",
     "ll_mg_batch_instance_levels", "ll_mg_batch_destroy", "ll_mg_step_save", "ll_mg_batch_subbatches", "ll_mg_adjoint_setup",
-    "ll_mg_step_vjp", "ll_mg_step_host", "ll_fp64_fma_probe",
+    "ll_mg_step_vjp", "ll_mg_step_host", "ll_fp64_fma_probe", "ll_mg_batch_setup_groups", "ll_mg_batch_groups",
+    "ll_mg_batch_instance_group", "ll_mg_batch_autotune", "ll_mg_tune_octave", "ll_mg_tune_lookup",
 )
 
 
@@ -51,7 +52,8 @@ class _Params(ctypes.Structure):
         ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
         ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("coarsest_cells", ctypes.c_int),
         ("max_levels", ctypes.c_int), ("rounds", ctypes.c_int), ("seed", ctypes.c_uint),
-        ("precision", ctypes.c_int), ("kcycle", ctypes.c_int),
+        ("precision", ctypes.c_int), ("kcycle", ctypes.c_int), ("coarse_lanes", ctypes.c_int),
+        ("coarse_block", ctypes.c_int),
     ]
 
 
@@ -70,10 +72,18 @@ class Params:
     seed: int = 0
     precision: int = LL_FP64
     kcycle: int = 0
+    coarse_lanes: int = 0
+    coarse_block: int = 0
 
     def _c(self) -> _Params:
         return _Params(self.rtol, self.maxit, self.restart, self.nu_pre, self.nu_post, self.coarsest_cells,
-                       self.max_levels, self.rounds, self.seed & 0xFFFFFFFF, self.precision, self.kcycle)
+                       self.max_levels, self.rounds, self.seed & 0xFFFFFFFF, self.precision, self.kcycle,
+                       self.coarse_lanes, self.coarse_block)
+
+    @classmethod
+    def _from_c(cls, c: "_Params") -> "Params":
+        return cls(c.rtol, c.maxit, c.restart, c.nu_pre, c.nu_post, c.coarsest_cells, c.max_levels, c.rounds,
+                   c.seed, c.precision, c.kcycle, c.coarse_lanes, c.coarse_block)
 
 
 _lib = None
@@ -129,6 +139,12 @@ def load_library():
         "ll_mg_step_vjp": (i, [vp, vp, d, d, vp, vp, vp, dp, d, ip, dp]),
         "ll_mg_step_host": (i, [vp, vp, i, ip, dp]),
         "ll_fp64_fma_probe": (i, [vp, ctypes.c_longlong, i, vp, dp]),
+        "ll_mg_batch_setup_groups": (i, [i, vp, vp, vp, vp, vp, P, vp, ctypes.POINTER(vp)]),
+        "ll_mg_batch_groups": (i, [vp]),
+        "ll_mg_batch_instance_group": (i, [vp, i]),
+        "ll_mg_batch_autotune": (i, [i, vp, vp, vp, vp, vp, P, ctypes.c_char_p, vp, P, ip]),
+        "ll_mg_tune_octave": (i, [d, d]),
+        "ll_mg_tune_lookup": (i, [ctypes.c_char_p, _Grid, d, d, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -145,8 +161,7 @@ def status_string(status: int) -> str:
 def default_params() -> Params:
     c = _Params()
     load_library().ll_mg_default_params(ctypes.byref(c))
-    return Params(c.rtol, c.maxit, c.restart, c.nu_pre, c.nu_post, c.coarsest_cells, c.max_levels, c.rounds,
-                  c.seed, c.precision, c.kcycle)
+    return Params._from_c(c)
 
 
 def _grid(grid) -> _Grid:
@@ -485,19 +500,33 @@ def _ptrs(tensors, ns, name):
 
 class Batch:
     """Independent instances solved together (``ll_mg_batch_setup``): one
-    hierarchy per instance, concatenated level by level, GCR in lockstep."""
+    hierarchy per instance, concatenated level by level, GCR in lockstep.
 
-    def __init__(self, m_tildes, alphas, dts, hs, grids, params: Params | None = None):
+    ``params`` is one Params for every instance, or a list of one Params per
+    instance (``ll_mg_batch_setup_groups``: instances with equal parameters
+    form a group, and the groups run concurrently), e.g. the list
+    ``autotune`` returns."""
+
+    def __init__(self, m_tildes, alphas, dts, hs, grids, params=None):
         lib = load_library()
         self.count = len(m_tildes)
         gs = [_grid(g) for g in grids]
         self.grids = [(g.nx, g.ny, g.nz) for g in gs]
         self.ns = [g.nx * g.ny * g.nz for g in gs]
-        self.params = params or Params()
-        self._cp = self.params._c()
         garr = (_Grid * self.count)(*gs)
         dv = lambda v: (ctypes.c_double * self.count)(*[float(a) for a in v])  # noqa: E731
         self._h = ctypes.c_void_p()
+        if isinstance(params, (list, tuple)):
+            if len(params) != self.count:
+                raise ValueError("one Params per instance")
+            self.params = list(params)
+            self._cp = (_Params * self.count)(*[q._c() for q in self.params])
+            st = lib.ll_mg_batch_setup_groups(self.count, _ptrs(m_tildes, self.ns, "m_tilde"), dv(alphas), dv(dts),
+                                              dv(hs), garr, self._cp, _stream(), ctypes.byref(self._h))
+            _check(st, "ll_mg_batch_setup_groups", ok=(LL_OK,))
+            return
+        self.params = params or Params()
+        self._cp = self.params._c()
         st = lib.ll_mg_batch_setup(self.count, _ptrs(m_tildes, self.ns, "m_tilde"), dv(alphas), dv(dts), dv(hs),
                                    garr, ctypes.byref(self._cp), _stream(), ctypes.byref(self._h))
         _check(st, "ll_mg_batch_setup", ok=(LL_OK,))
@@ -546,6 +575,49 @@ class Batch:
     def subbatches(self) -> int:
         """Compacted sub-batches built so far (ll_mg_batch_subbatches)."""
         return load_library().ll_mg_batch_subbatches(self._h)
+
+    @property
+    def groups(self) -> int:
+        """Groups of equal parameters (1 for a single parameter set)."""
+        return load_library().ll_mg_batch_groups(self._h)
+
+    def instance_group(self, i: int) -> int:
+        return load_library().ll_mg_batch_instance_group(self._h, i)
+
+
+def autotune(m_tildes, alphas, dts, hs, grids, base: Params | None = None, cache_path: str | None = None):
+    """Per-class choice of cycle and coarse-kernel launch shape for a batch
+    (``ll_mg_batch_autotune``); returns (one Params per instance, classes
+    timed by this call)."""
+    lib = load_library()
+    count = len(m_tildes)
+    gs = [_grid(g) for g in grids]
+    ns = [g.nx * g.ny * g.nz for g in gs]
+    garr = (_Grid * count)(*gs)
+    dv = lambda v: (ctypes.c_double * count)(*[float(a) for a in v])  # noqa: E731
+    bp = (base or Params())._c()
+    out = (_Params * count)()
+    tuned = ctypes.c_int(0)
+    st = lib.ll_mg_batch_autotune(count, _ptrs(m_tildes, ns, "m_tilde"), dv(alphas), dv(dts), dv(hs), garr,
+                                  ctypes.byref(bp), cache_path.encode() if cache_path else None, _stream(), out,
+                                  ctypes.byref(tuned))
+    _check(st, "ll_mg_batch_autotune", ok=(LL_OK,))
+    return [Params._from_c(out[k]) for k in range(count)], tuned.value
+
+
+def tune_octave(dt: float, h: float) -> int:
+    """The autotuner's class octave floor(log2(dt/h^2)) (host only)."""
+    return int(load_library().ll_mg_tune_octave(float(dt), float(h)))
+
+
+def tune_lookup(cache_path: str, grid, dt: float, h: float, base: Params | None = None):
+    """The autotuner's cached choice for one instance (host only): base
+    with the choice applied, or None when the cache does not hold its class."""
+    c = (base or Params())._c()
+    st = load_library().ll_mg_tune_lookup(cache_path.encode(), _grid(grid), float(dt), float(h), ctypes.byref(c))
+    if st < 0:
+        raise LLError(st, "ll_mg_tune_lookup")
+    return Params._from_c(c) if st == 1 else None
 
 
 def fp64_fma_probe(sink, iters: int, blocks: int):

@@ -1,0 +1,215 @@
+// Autotuner of batched solves (ll_mg_batch_autotune): per class of instances
+// -- same grid, same octave of dt/h^2, same precision -- the smoothing sweeps
+// and cycle (V(1,1), V(2,2), either with the K-cycle on level 1, and V(3,3)
+// with it) and the
+// launch shape of the per-class coarse kernels (lanes per block row, threads
+// per block), chosen by timing solves of that class's hardest instances
+// (smallest alpha).  Choices are kept in a plain-text cache file and reused.
+//
+// Included by ll_solver.cu after the batched solver.
+#pragma once
+
+#include <stdio.h>
+
+#include <chrono>
+#include <string>
+
+namespace {
+
+struct TuneKey {
+  int precision, nx, ny, nz, oct;
+  bool operator<(const TuneKey& o) const {
+    if (precision != o.precision) return precision < o.precision;
+    if (nx != o.nx) return nx < o.nx;
+    if (ny != o.ny) return ny < o.ny;
+    if (nz != o.nz) return nz < o.nz;
+    return oct < o.oct;
+  }
+};
+
+struct TuneChoice {
+  int nu_pre = 1, nu_post = 1, kcycle = 0, lanes = 0, block = 0;
+  double ms = 0;  // time of the representatives' solve with this choice
+};
+
+// the octave of dt/h^2: floor(log2(dt / h^2))
+int tune_octave(double dt, double h) { return (int)floor(log2(dt / (h * h))); }
+
+TuneKey tune_key(int precision, ll_grid g, double dt, double h) {
+  return {precision, g.nx, g.ny, g.nz, tune_octave(dt, h)};
+}
+
+const char* kTuneTag = "llmg-tune-v1";
+
+// cache file: one line per class,
+//   llmg-tune-v1 precision nx ny nz octave nu_pre nu_post kcycle lanes block ms
+// other lines are ignored
+std::map<TuneKey, TuneChoice> tune_read(const char* path) {
+  std::map<TuneKey, TuneChoice> c;
+  if (!path) return c;
+  FILE* f = fopen(path, "r");
+  if (!f) return c;
+  char line[512];
+  while (fgets(line, sizeof line, f)) {
+    char tag[32];
+    TuneKey k;
+    TuneChoice v;
+    if (sscanf(line, "%31s %d %d %d %d %d %d %d %d %d %d %lf", tag, &k.precision, &k.nx, &k.ny, &k.nz, &k.oct,
+               &v.nu_pre, &v.nu_post, &v.kcycle, &v.lanes, &v.block, &v.ms) != 12)
+      continue;
+    if (strcmp(tag, kTuneTag) != 0) continue;
+    ll_mg_params t;
+    ll_mg_default_params(&t);
+    t.nu_pre = v.nu_pre;
+    t.nu_post = v.nu_post;
+    t.kcycle = v.kcycle;
+    t.coarse_lanes = v.lanes;
+    t.coarse_block = v.block;
+    if (!valid_params(t)) continue;
+    c[k] = v;
+  }
+  fclose(f);
+  return c;
+}
+
+// write the whole cache (to a temporary file, then renamed over the old one)
+bool tune_write(const char* path, const std::map<TuneKey, TuneChoice>& c) {
+  std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  fprintf(f, "# batch autotuner choices: %s precision nx ny nz octave(dt/h^2) nu_pre nu_post kcycle lanes block ms\n",
+          kTuneTag);
+  for (auto& e : c)
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %.6g\n", kTuneTag, e.first.precision, e.first.nx, e.first.ny,
+            e.first.nz, e.first.oct, e.second.nu_pre, e.second.nu_post, e.second.kcycle, e.second.lanes,
+            e.second.block, e.second.ms);
+  bool ok = fclose(f) == 0;
+  return ok && rename(tmp.c_str(), path) == 0;
+}
+
+ll_mg_params tune_apply(const ll_mg_params& base, const TuneChoice& v) {
+  ll_mg_params p = base;
+  p.nu_pre = v.nu_pre;
+  p.nu_post = v.nu_post;
+  p.kcycle = v.kcycle;
+  p.coarse_lanes = v.lanes;
+  p.coarse_block = v.block;
+  return p;
+}
+
+// Solve the representatives' step systems (rhs = m/dt from the guess m)
+// with parameters p as one batch: a first solve (which captures the
+// iteration graphs), then the timed one.  Returns the number that converged
+// and the milliseconds of the timed solve.
+std::pair<int, double> tune_eval(const std::vector<int>& reps, const double* const* m, const double* alpha,
+                                 const double* dt, const double* h, const ll_grid* grids, const ll_mg_params& p,
+                                 void* stream) {
+  int n = (int)reps.size();
+  std::vector<const double*> mr;
+  std::vector<double> ar, dr, hr;
+  std::vector<ll_grid> gr;
+  for (int i : reps) {
+    mr.push_back(m[i]);
+    ar.push_back(alpha[i]);
+    dr.push_back(dt[i]);
+    hr.push_back(h[i]);
+    gr.push_back(grids[i]);
+  }
+  ll_mg_batch* B = nullptr;
+  int rc = batch_create(n, mr.data(), ar.data(), dr.data(), hr.data(), gr.data(), &p, stream, &B);
+  if (rc != LL_OK) throw Status{rc};
+  std::unique_ptr<ll_mg_batch> own(B);
+  std::vector<std::unique_ptr<DBuf<double>>> rhs, x;
+  std::vector<const double*> rp;
+  std::vector<double*> xp;
+  cudaStream_t s = B->U->s;
+  for (int k = 0; k < n; ++k) {
+    long n3 = 3L * gr[k].nx * gr[k].ny * gr[k].nz;
+    rhs.emplace_back(new DBuf<double>());
+    x.emplace_back(new DBuf<double>());
+    rhs[k]->alloc(n3);
+    x[k]->alloc(n3);
+    rp.push_back(rhs[k]->p);
+    xp.push_back(x[k]->p);
+  }
+  std::vector<int> st(n);
+  double ms = 0;
+  for (int rep = 0; rep < 2; ++rep) {
+    for (int k = 0; k < n; ++k) {
+      long n3 = 3L * gr[k].nx * gr[k].ny * gr[k].nz;
+      k_scale<<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, mr[k], 1.0 / dr[k], rhs[k]->p);
+      LL_LAUNCHED();
+      LL_CU(cudaMemcpyAsync(xp[k], mr[k], n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    LL_CU(cudaStreamSynchronize(s));
+    auto t0 = std::chrono::steady_clock::now();
+    batch_solve(B, rp.data(), xp.data(), p.rtol, nullptr, nullptr, st.data());
+    ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  int conv = 0;
+  for (int v : st) conv += v == LL_OK;
+  return {conv, ms};
+}
+
+// better = more converged, then faster
+bool tune_better(std::pair<int, double> a, std::pair<int, double> b) {
+  return a.first != b.first ? a.first > b.first : a.second < b.second;
+}
+
+constexpr int kTuneReps = 3;  // representatives per class (its smallest alphas)
+
+int autotune(int count, const double* const* m, const double* alpha, const double* dt, const double* h,
+             const ll_grid* grids, const ll_mg_params& base, const char* cache_path, void* stream,
+             ll_mg_params* chosen, int* keys_tuned) {
+  std::map<TuneKey, TuneChoice> cache = tune_read(cache_path);
+  std::map<TuneKey, std::vector<int>> members;
+  for (int i = 0; i < count; ++i) members[tune_key(base.precision, grids[i], dt[i], h[i])].push_back(i);
+  int tuned = 0;
+  ll_mg_params b = base;
+  b.maxit = std::min(b.maxit, 300);
+  for (auto& e : members) {
+    if (cache.count(e.first)) continue;
+    std::vector<int> reps = e.second;
+    std::stable_sort(reps.begin(), reps.end(), [&](int a, int c) { return alpha[a] < alpha[c]; });
+    if ((int)reps.size() > kTuneReps) reps.resize(kTuneReps);
+    std::sort(reps.begin(), reps.end());
+    // the cycle: smoothing sweeps and the K-cycle on level 1
+    TuneChoice best;
+    std::pair<int, double> bestv{-1, 0.0};
+    const int cycles[5][3] = {{1, 1, 0}, {2, 2, 0}, {1, 1, 1}, {2, 2, 1}, {3, 3, 1}};
+    for (auto& c : cycles) {
+      TuneChoice v;
+      v.nu_pre = c[0];
+      v.nu_post = c[1];
+      v.kcycle = c[2];
+      auto r = tune_eval(reps, m, alpha, dt, h, grids, tune_apply(b, v), stream);
+      if (tune_better(r, bestv)) {
+        bestv = r;
+        best = v;
+        best.ms = r.second;
+      }
+    }
+    // the launch shape of the coarse kernels, for that cycle
+    const int shapes[3][2] = {{8, 0}, {0, 128}, {8, 128}};
+    TuneChoice cyc = best;
+    for (auto& sh : shapes) {
+      TuneChoice v = cyc;
+      v.lanes = sh[0];
+      v.block = sh[1];
+      auto r = tune_eval(reps, m, alpha, dt, h, grids, tune_apply(b, v), stream);
+      if (r.first == bestv.first && r.second < bestv.second) {
+        bestv = r;
+        best = v;
+        best.ms = r.second;
+      }
+    }
+    cache[e.first] = best;
+    ++tuned;
+  }
+  if (cache_path && tuned > 0 && !tune_write(cache_path, cache)) throw Status{LL_EINVAL};
+  for (int i = 0; i < count; ++i) chosen[i] = tune_apply(base, cache[tune_key(base.precision, grids[i], dt[i], h[i])]);
+  if (keys_tuned) *keys_tuned = tuned;
+  return LL_OK;
+}
+
+}  // namespace

@@ -46,7 +46,12 @@ struct ll_mg_batch {
   int* h_flags = nullptr;    // pinned staging of act / jdone
   cudaGraphExec_t graphs[llmg::kMaxRestart] = {nullptr};
   long long graph_kernels[llmg::kMaxRestart] = {0};
+  // a batch of groups (ll_mg_batch_setup_groups): each group is a batch of
+  // its own, with its own parameters; this batch then has no union (U null)
+  std::vector<ll_mg_batch*> groups;
+  std::vector<std::vector<int>> gidx;  // instances of each group, ascending
   ~ll_mg_batch() {
+    for (auto* g : groups) delete g;
     if (U && U->s) cudaStreamSynchronize(U->s);
     for (auto& g : graphs)
       if (g) cudaGraphExecDestroy(g);
@@ -74,6 +79,10 @@ constexpr int kFieldD = (int)(offsetof(GcrScal, d) / sizeof(double));
 constexpr int kFieldCn2 = (int)(offsetof(GcrScal, cn2) / sizeof(double));
 
 void batch_enter(ll_mg_batch* B) {
+  if (!B->U) {  // a batch of groups: each group waits for the caller's stream
+    for (auto* g : B->groups) batch_enter(g);
+    return;
+  }
   LL_CU(cudaEventRecord(B->entry_ev, B->user));
   LL_CU(cudaStreamWaitEvent(B->U->s, B->entry_ev, 0));
 }
@@ -758,6 +767,88 @@ int batch_create(int count, const double* const* m, const double* alpha, const d
     delete B;
     return LL_ENOMEM;
   }
+}
+
+// ---------------------------------------------------------------------------
+// batches of groups: instances with different parameters (the autotuner's
+// choice per class of instances) are split into groups of equal parameters;
+// each group is a batch of its own, and the groups are solved concurrently,
+// one host thread and one stream per group.
+// ---------------------------------------------------------------------------
+bool same_params(const ll_mg_params& a, const ll_mg_params& b) {
+  return a.rtol == b.rtol && a.maxit == b.maxit && a.restart == b.restart && a.nu_pre == b.nu_pre &&
+         a.nu_post == b.nu_post && a.coarsest_cells == b.coarsest_cells && a.max_levels == b.max_levels &&
+         a.rounds == b.rounds && a.seed == b.seed && a.precision == b.precision && a.kcycle == b.kcycle &&
+         a.coarse_lanes == b.coarse_lanes && a.coarse_block == b.coarse_block;
+}
+
+int batch_create_groups(int count, const double* const* m, const double* alpha, const double* dt, const double* h,
+                        const ll_grid* grids, const ll_mg_params* p, void* stream, ll_mg_batch** out) {
+  std::vector<int> gof(count, -1);
+  std::vector<ll_mg_params> gp;
+  std::vector<std::vector<int>> gidx;
+  for (int i = 0; i < count; ++i) {
+    int g = 0;
+    while (g < (int)gp.size() && !same_params(gp[g], p[i])) ++g;
+    if (g == (int)gp.size()) {
+      gp.push_back(p[i]);
+      gidx.emplace_back();
+    }
+    gidx[g].push_back(i);
+  }
+  if (gp.size() == 1) return batch_create(count, m, alpha, dt, h, grids, &gp[0], stream, out);
+  ll_mg_batch* B = new ll_mg_batch();
+  B->prm = gp[0];
+  B->ninst = count;
+  B->user = (cudaStream_t)stream;
+  B->gidx = gidx;
+  for (size_t g = 0; g < gp.size(); ++g) {
+    std::vector<const double*> mg;
+    std::vector<double> ag, dg, hg;
+    std::vector<ll_grid> gg;
+    for (int i : gidx[g]) {
+      mg.push_back(m[i]);
+      ag.push_back(alpha[i]);
+      dg.push_back(dt[i]);
+      hg.push_back(h[i]);
+      gg.push_back(grids[i]);
+    }
+    ll_mg_batch* G = nullptr;
+    int rc = batch_create((int)gidx[g].size(), mg.data(), ag.data(), dg.data(), hg.data(), gg.data(), &gp[g],
+                          stream, &G);
+    if (rc != LL_OK) {
+      delete B;
+      return rc;
+    }
+    B->groups.push_back(G);
+  }
+  *out = B;
+  return LL_OK;
+}
+
+// run fn(group, its instance indices) for every group, one host thread per
+// group; returns the first failure (negative status) or the worst outcome
+template <typename F>
+int for_groups(ll_mg_batch* B, F fn) {
+  int ng = (int)B->groups.size();
+  std::vector<int> rc(ng, LL_OK);
+  std::vector<std::thread> th;
+  for (int g = 0; g < ng; ++g)
+    th.emplace_back([&, g]() {
+      try {
+        rc[g] = fn(B->groups[g], B->gidx[g]);
+      } catch (Status st) {
+        rc[g] = st.code;
+      } catch (std::bad_alloc&) {
+        rc[g] = LL_ENOMEM;
+      }
+    });
+  for (auto& t : th) t.join();
+  int worst = LL_OK;
+  for (int r : rc)
+    if (r < 0) return r;
+  for (int r : rc) worst = std::max(worst, r);
+  return worst;
 }
 
 }  // namespace

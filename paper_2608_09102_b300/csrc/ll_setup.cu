@@ -454,8 +454,34 @@ int aggregate_level(const DevGraph& g, int rounds, uint32_t seed, int* agg, cuda
 }
 
 // ---------------------------------------------------------------------------
-// Jones-Plassmann colouring with hash priorities
+// Colouring of an aggregated level: Jones-Plassmann rounds with priority
+// (degree, node_key, index), then kRecolourPasses passes of iterated greedy
+// recolouring (the classes visited from the highest colour down, each node
+// taking the smallest colour unused by the neighbours already recoloured)
 // ---------------------------------------------------------------------------
+constexpr int kRecolourPasses = 4;
+
+// does node j take precedence over node i in the rounds?
+__device__ __forceinline__ bool node_beats(const int* __restrict__ rp, int j, int i, uint32_t seed) {
+  int dj = rp[j + 1] - rp[j], di = rp[i + 1] - rp[i];
+  if (dj != di) return dj > di;
+  uint32_t hj = node_key((uint32_t)j, seed), hi = node_key((uint32_t)i, seed);
+  if (hj != hi) return hj > hi;
+  return j > i;
+}
+
+// smallest colour below 128 not in the two bit masks; -1 if none
+__device__ __forceinline__ int first_free(unsigned long long used0, unsigned long long used1) {
+  if (~used0) return __ffsll((long long)~used0) - 1;
+  if (~used1) return 64 + __ffsll((long long)~used1) - 1;
+  return -1;
+}
+
+__device__ __forceinline__ void mark_used(int cj, unsigned long long& used0, unsigned long long& used1) {
+  if (cj >= 0 && cj < 64) used0 |= 1ull << cj;
+  else if (cj >= 64 && cj < 128) used1 |= 1ull << (cj - 64);
+}
+
 __global__ void k_colour_round(int n, const int* __restrict__ rp, const int* __restrict__ col, uint32_t seed,
                                const int* __restrict__ cin, int* __restrict__ cout, int* __restrict__ left,
                                int* __restrict__ overflow) {
@@ -466,18 +492,14 @@ __global__ void k_colour_round(int n, const int* __restrict__ rp, const int* __r
     cout[i] = ci;
     return;
   }
-  uint32_t hi = node_key((uint32_t)i, seed);
   bool wins = true;
   unsigned long long used0 = 0, used1 = 0;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
     int j = col[p], cj = cin[j];
     if (cj < 0) {
-      uint32_t hj = node_key((uint32_t)j, seed);
-      if (hj > hi || (hj == hi && j > i)) wins = false;
-    } else if (cj < 64) {
-      used0 |= 1ull << cj;
-    } else if (cj < 128) {
-      used1 |= 1ull << (cj - 64);
+      if (node_beats(rp, j, i, seed)) wins = false;
+    } else {
+      mark_used(cj, used0, used1);
     }
   }
   if (!wins) {
@@ -485,14 +507,38 @@ __global__ void k_colour_round(int n, const int* __restrict__ rp, const int* __r
     atomicAdd(left, 1);
     return;
   }
-  int c;
-  if (~used0) c = __ffsll((long long)~used0) - 1;
-  else if (~used1) c = 64 + __ffsll((long long)~used1) - 1;
-  else {
+  int c = first_free(used0, used1);
+  if (c < 0) {
     c = 0;
     *overflow = 1;
   }
   cout[i] = c;
+}
+
+// one class of a recolouring pass: the nodes of old colour c take the
+// smallest colour unused by their already recoloured neighbours (cnew >= 0)
+__global__ void k_recolour_class(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const int* __restrict__ cold, int c, int* __restrict__ cnew,
+                                 int* __restrict__ overflow) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cold[i] != c) return;
+  unsigned long long used0 = 0, used1 = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) mark_used(cnew[col[p]], used0, used1);
+  int k = first_free(used0, used1);
+  if (k < 0) {
+    k = 0;
+    *overflow = 1;
+  }
+  cnew[i] = k;
+}
+
+static int max_colour(const int* colour, int n, cudaStream_t s) {
+  std::vector<int> h(n);
+  LL_CU(cudaMemcpyAsync(h.data(), colour, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  LL_CU(cudaStreamSynchronize(s));
+  int mx = -1;
+  for (int v : h) mx = std::max(mx, v);
+  return mx;
 }
 
 // returns the number of colours, or -1 when more than kMaxColours are needed
@@ -514,15 +560,21 @@ int colour_graph(const DevGraph& g, uint32_t seed, int* colour, cudaStream_t s) 
     std::swap(a, b);
     if (read_int(left, s) == 0) break;
   }
-  if (a != colour) LL_CU(cudaMemcpyAsync(colour, a, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
   if (read_int(ovf, s)) return -1;
-  // number of colours = max + 1
-  std::vector<int> h(n);
-  LL_CU(cudaMemcpyAsync(h.data(), colour, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  int ncol = max_colour(a, n, s) + 1;
+  for (int pass = 0; pass < kRecolourPasses; ++pass) {
+    fill(b, -1, n, s);
+    for (int c = ncol - 1; c >= 0; --c) {
+      k_recolour_class<<<nb, kBlock, 0, s>>>(n, g.rowptr, g.col, a, c, b, ovf);
+      LL_LAUNCHED();
+    }
+    std::swap(a, b);
+    if (read_int(ovf, s)) return -1;
+    ncol = max_colour(a, n, s) + 1;
+  }
+  if (a != colour) LL_CU(cudaMemcpyAsync(colour, a, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
   LL_CU(cudaStreamSynchronize(s));
-  int mx = -1;
-  for (int v : h) mx = std::max(mx, v);
-  return mx + 1;
+  return ncol;
 }
 
 // Row-work key of a coarse row: the number of kRowLanes-wide block slots its

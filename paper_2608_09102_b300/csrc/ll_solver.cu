@@ -1,5 +1,6 @@
 // Hierarchy, numeric setup, V-cycle, GCR and the C ABI of the sm_103a
 // aggregation-multigrid solver (see include/ll_mg.h for the contract).
+#include <limits.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -7,6 +8,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <map>
+#include <memory>
 #include <new>
 #include <type_traits>
 
@@ -17,6 +19,7 @@
 #include "ll_batch_kernels.cuh"
 
 #include <atomic>
+#include <thread>
 
 namespace llmg {
 
@@ -741,6 +744,21 @@ void coarse_solve(ll_mg_hierarchy* H, const T* b, T* x) {
   LL_LAUNCHED();
 }
 
+// Launch shape of the per-class coarse kernels: the parameters' coarse_lanes
+// and coarse_block when set (the batch autotuner's choice), else the
+// defaults above.
+inline int coarse_block(const ll_mg_hierarchy* H) {
+  return H->prm.coarse_block > 0 ? H->prm.coarse_block : kCoarseBlock;
+}
+template <typename T>
+int sweep_lanes(const ll_mg_hierarchy* H, long rows) {
+  return H->prm.coarse_lanes > 0 ? H->prm.coarse_lanes : (wide_lanes<T>(rows) ? 8 : kRowLanes);
+}
+template <typename T>
+int residual_lanes(const ll_mg_hierarchy* H) {
+  return H->prm.coarse_lanes > 0 ? H->prm.coarse_lanes : lanes<T>();
+}
+
 // one colour class of level l: rows [cs[t], cs[t+1])
 // work model of one class sweep
 template <typename T, typename TM, int MODE>
@@ -761,13 +779,14 @@ void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e, bool timed = true
   double f = 0, by = 0;
   if (timed) class_work<T, TM, MODE>(L, t, f, by);
   ProfScope prof_scope_(H, timed ? LL_KIND_BSR_SMOOTH : LL_NUM_KINDS, f, by);
-  if (wide_lanes<T>(r1 - r0))
-    launch_k(H, kb_sweep<T, TM, 8, MODE>, cdiv((long)(r1 - r0) * 8, kCoarseBlock), kCoarseBlock, r0, r1,
-             (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(),
-             (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
+  int blk = coarse_block(H);
+  if (sweep_lanes<T>(H, r1 - r0) == 8)
+    launch_k(H, kb_sweep<T, TM, 8, MODE>, cdiv((long)(r1 - r0) * 8, blk), blk, r0, r1, (const int*)L.rowptr,
+             (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(),
+             (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
   else
-    launch_k(H, kb_sweep<T, TM, kRowLanes, MODE>, cdiv((long)(r1 - r0) * kRowLanes, kCoarseBlock), kCoarseBlock,
-             r0, r1, (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(),
+    launch_k(H, kb_sweep<T, TM, kRowLanes, MODE>, cdiv((long)(r1 - r0) * kRowLanes, blk), blk, r0, r1,
+             (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(),
              (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(), (const int*)L.agg, e);
 }
 
@@ -954,17 +973,23 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
              sweep_bytes(rblk, skip_from, (int)sizeof(T), (int)sizeof(TM)));
     int init_end = (nu_pre >= 1 && l + 1 < H->nlev - 1) ? N.cs[1] : 0;
     if (skip_from > 0) {
-      int nbr = cdiv((long)skip_from * lanes<T>(), kCoarseBlock);
-      if (nu_pre == 1)  // right after one forward sweep: the higher colours' part only
-        launch_k(H, kb_residual<T, TM, lanes<T>(), true>, nbr, kCoarseBlock, skip_from, (const int*)L.rowptr,
-                 (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.b<T>(),
-                 (const T*)L.x<T>(), L.r<T>());
-      else
-        launch_k(H, kb_residual<T, TM, lanes<T>(), false>, nbr, kCoarseBlock, skip_from, (const int*)L.rowptr,
-                 (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.b<T>(),
-                 (const T*)L.x<T>(), L.r<T>());
+      int blk = coarse_block(H), G = residual_lanes<T>(H);
+      auto go = [&](auto gc, auto suffix) {
+        constexpr int GG = decltype(gc)::value;
+        launch_k(H, kb_residual<T, TM, GG, decltype(suffix)::value>, cdiv((long)skip_from * GG, blk), blk,
+                 skip_from, (const int*)L.rowptr, (const int*)L.diag, (const int*)L.col, (const TM*)L.valm<TM>(),
+                 (const T*)L.b<T>(), (const T*)L.x<T>(), L.r<T>());
+      };
+      // right after one forward sweep: the higher colours' part only
+      if (nu_pre == 1) {
+        if (G == 8) go(std::integral_constant<int, 8>(), std::true_type());
+        else go(std::integral_constant<int, kRowLanes>(), std::true_type());
+      } else {
+        if (G == 8) go(std::integral_constant<int, 8>(), std::false_type());
+        else go(std::integral_constant<int, kRowLanes>(), std::false_type());
+      }
     }
-    launch_k(H, kb_restrict<T>, cdiv(N.n, kCoarseBlock), kCoarseBlock, N.n, (const int*)N.mptr,
+    launch_k(H, kb_restrict<T>, cdiv(N.n, coarse_block(H)), coarse_block(H), N.n, (const int*)N.mptr,
              (const int*)N.mem, skip_from, (const T*)L.r<T>(), N.b<T>(), init_end, (const T*)N.dinv<T>(), N.x<T>());
   }
   if (H->union_mode) union_coarse<T>(H, l);  // rows past the colour classes
@@ -1339,7 +1364,10 @@ bool valid_params(const ll_mg_params& p) {
          p.nu_pre <= 16 && p.nu_post >= 0 && p.nu_post <= 16 && p.coarsest_cells >= 1 && p.max_levels >= 1 &&
          p.max_levels <= kMaxLevels && p.rounds >= 1 &&
          (p.precision == LL_FP64 || p.precision == LL_MIXED_FP32 || p.precision == LL_MIXED_BF16) &&
-         p.kcycle >= 0 && p.kcycle <= kMaxLevels;
+         p.kcycle >= 0 && p.kcycle <= kMaxLevels &&
+         (p.coarse_lanes == 0 || p.coarse_lanes == kRowLanes || p.coarse_lanes == 8) &&
+         (p.coarse_block == 0 || p.coarse_block == 32 || p.coarse_block == 64 || p.coarse_block == 128 ||
+          p.coarse_block == 256);
 }
 
 int create(const double* m, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p, void* stream,
@@ -1386,6 +1414,7 @@ int create(const double* m, double alpha, double dt, double h, ll_grid grid, con
 }  // namespace
 
 #include "ll_batch.cuh"
+#include "ll_autotune.cuh"
 
 // ===========================================================================
 // C ABI
@@ -1405,6 +1434,8 @@ void ll_mg_default_params(ll_mg_params* p) {
   p->seed = 0;
   p->precision = LL_FP64;
   p->kcycle = 0;
+  p->coarse_lanes = 0;
+  p->coarse_block = 0;
 }
 
 static bool valid_problem(double alpha, double dt, double h, ll_grid grid) {
@@ -1779,6 +1810,17 @@ int ll_mg_batch_update(ll_mg_batch* B, const double* const* m_tilde, const doubl
   if (!B || !m_tilde || !alpha || !dt) return LL_EINVAL;
   for (int i = 0; i < B->ninst; ++i)
     if (!m_tilde[i] || !(dt[i] > 0) || !(alpha[i] >= 0) || !isfinite(dt[i]) || !isfinite(alpha[i])) return LL_EINVAL;
+  if (!B->groups.empty())
+    return for_groups(B, [&](ll_mg_batch* G, const std::vector<int>& idx) {
+      std::vector<const double*> mg;
+      std::vector<double> ag, dg;
+      for (int i : idx) {
+        mg.push_back(m_tilde[i]);
+        ag.push_back(alpha[i]);
+        dg.push_back(dt[i]);
+      }
+      return ll_mg_batch_update(G, mg.data(), ag.data(), dg.data());
+    });
   try {
     batch_enter(B);
     LL_CU(cudaStreamSynchronize(B->U->s));
@@ -1802,6 +1844,37 @@ int ll_mg_batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x
   if (!B || !rhs || !x) return LL_EINVAL;
   for (int i = 0; i < B->ninst; ++i)
     if (!rhs[i] || !x[i]) return LL_EINVAL;
+  if (!B->groups.empty()) {
+    std::vector<int> its(B->ninst, 0), sts(B->ninst, LL_NOT_CONVERGED);
+    std::vector<double> rrs(B->ninst, 0.0);
+    int rc = for_groups(B, [&](ll_mg_batch* G, const std::vector<int>& idx) {
+      std::vector<const double*> rg;
+      std::vector<double*> xg;
+      std::vector<int> ig(idx.size()), sg(idx.size());
+      std::vector<double> qg(idx.size());
+      for (int i : idx) {
+        rg.push_back(rhs[i]);
+        xg.push_back(x[i]);
+      }
+      int r = ll_mg_batch_solve(G, rg.data(), xg.data(), rtol, ig.data(), qg.data(), sg.data());
+      for (size_t k = 0; k < idx.size(); ++k) {
+        its[idx[k]] = ig[k];
+        rrs[idx[k]] = qg[k];
+        sts[idx[k]] = sg[k];
+      }
+      return r;
+    });
+    if (rc < 0) return rc;
+    if (iterations) std::copy(its.begin(), its.end(), iterations);
+    if (rel_residual) std::copy(rrs.begin(), rrs.end(), rel_residual);
+    if (status) std::copy(sts.begin(), sts.end(), status);
+    int worst = LL_OK;
+    for (int st : sts) {
+      if (st == LL_BREAKDOWN) worst = LL_BREAKDOWN;
+      else if (st == LL_NOT_CONVERGED && worst == LL_OK) worst = LL_NOT_CONVERGED;
+    }
+    return worst;
+  }
   try {
     batch_enter(B);
     return batch_solve(B, rhs, x, rtol, iterations, rel_residual, status);
@@ -1811,20 +1884,88 @@ int ll_mg_batch_solve(ll_mg_batch* B, const double* const* rhs, double* const* x
 }
 
 int ll_mg_batch_count(const ll_mg_batch* B) { return B ? B->ninst : 0; }
-int ll_mg_batch_levels(const ll_mg_batch* B) { return B ? B->U->nlev : 0; }
+int ll_mg_batch_levels(const ll_mg_batch* B) { return B && B->U ? B->U->nlev : -1; }
 long long ll_mg_batch_level_rows(const ll_mg_batch* B, int level) {
-  if (!B || level < 0 || level >= B->U->nlev) return -1;
+  if (!B || !B->U || level < 0 || level >= B->U->nlev) return -1;
   return B->U->lev[level].n;
 }
 int ll_mg_batch_level_colours(const ll_mg_batch* B, int level) {
-  if (!B || level < 0 || level >= B->U->nlev) return -1;
+  if (!B || !B->U || level < 0 || level >= B->U->nlev) return -1;
   return B->U->lev[level].ncol;
 }
-int ll_mg_batch_subbatches(const ll_mg_batch* B) { return B ? (int)B->children.size() : 0; }
+int ll_mg_batch_subbatches(const ll_mg_batch* B) {
+  if (!B) return 0;
+  int n = (int)B->children.size();
+  for (auto* g : B->groups) n += ll_mg_batch_subbatches(g);
+  return n;
+}
 
 int ll_mg_batch_instance_levels(const ll_mg_batch* B, int i) {
   if (!B || i < 0 || i >= B->ninst) return -1;
+  for (size_t g = 0; g < B->groups.size(); ++g)
+    for (size_t k = 0; k < B->gidx[g].size(); ++k)
+      if (B->gidx[g][k] == i) return ll_mg_batch_instance_levels(B->groups[g], (int)k);
   return B->inst[i]->nlev;
+}
+
+int ll_mg_batch_groups(const ll_mg_batch* B) { return B ? std::max(1, (int)B->groups.size()) : 0; }
+
+int ll_mg_batch_instance_group(const ll_mg_batch* B, int i) {
+  if (!B || i < 0 || i >= B->ninst) return -1;
+  for (size_t g = 0; g < B->groups.size(); ++g)
+    for (int k : B->gidx[g])
+      if (k == i) return (int)g;
+  return 0;
+}
+
+int ll_mg_batch_autotune(int count, const double* const* m_tilde, const double* alpha, const double* dt,
+                         const double* h, const ll_grid* grids, const ll_mg_params* base, const char* cache_path,
+                         void* cuda_stream, ll_mg_params* chosen, int* keys_tuned) {
+  if (count < 1 || !m_tilde || !alpha || !dt || !h || !grids || !chosen) return LL_EINVAL;
+  ll_mg_params b;
+  ll_mg_default_params(&b);
+  if (base) b = *base;
+  if (!valid_params(b) || b.precision == LL_MIXED_BF16) return LL_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!m_tilde[i] || !valid_problem(alpha[i], dt[i], h[i], grids[i])) return LL_EINVAL;
+  try {
+    return autotune(count, m_tilde, alpha, dt, h, grids, b, cache_path, cuda_stream, chosen, keys_tuned);
+  } catch (Status st) {
+    return st.code;
+  } catch (std::bad_alloc&) {
+    return LL_ENOMEM;
+  }
+}
+
+int ll_mg_tune_octave(double dt, double h) {
+  if (!(dt > 0) || !(h > 0) || !isfinite(dt) || !isfinite(h)) return INT_MIN;
+  return tune_octave(dt, h);
+}
+
+int ll_mg_tune_lookup(const char* cache_path, ll_grid grid, double dt, double h, ll_mg_params* p) {
+  if (!cache_path || !p || !(dt > 0) || !(h > 0)) return LL_EINVAL;
+  auto c = tune_read(cache_path);
+  auto it = c.find(tune_key(p->precision, grid, dt, h));
+  if (it == c.end()) return 0;
+  *p = tune_apply(*p, it->second);
+  return 1;
+}
+
+int ll_mg_batch_setup_groups(int count, const double* const* m_tilde, const double* alpha, const double* dt,
+                             const double* h, const ll_grid* grids, const ll_mg_params* p, void* cuda_stream,
+                             ll_mg_batch** out) {
+  if (count < 1 || !m_tilde || !alpha || !dt || !h || !grids || !p || !out) return LL_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!m_tilde[i] || !valid_problem(alpha[i], dt[i], h[i], grids[i])) return LL_EINVAL;
+    if (!valid_params(p[i]) || p[i].precision == LL_MIXED_BF16) return LL_EINVAL;
+  }
+  try {
+    return batch_create_groups(count, m_tilde, alpha, dt, h, grids, p, cuda_stream, out);
+  } catch (Status st) {
+    return st.code;
+  } catch (std::bad_alloc&) {
+    return LL_ENOMEM;
+  }
 }
 
 void ll_mg_batch_destroy(ll_mg_batch* B) { delete B; }

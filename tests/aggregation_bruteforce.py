@@ -108,19 +108,33 @@ def aggregate(adj, rounds=32, seed=0):
     return [rank[a] for a in comp], len(order)
 
 
-def colour(adj, seed=0):
+def colour(adj, seed=0, passes=4):
+    """Jones-Plassmann rounds with priority (degree, vertex hash, index), then
+    `passes` passes of iterated greedy recolouring, classes visited from the
+    highest colour down."""
     n = len(adj)
     col = [-1] * n
-    prio = [(vertex_hash(i, seed), i) for i in range(n)]
+    prio = [(len(adj[i]), vertex_hash(i, seed), i) for i in range(n)]
+
+    def smallest_free(i, c):
+        used = {c[j] for j in adj[i] if c[j] >= 0}
+        k = 0
+        while k in used:
+            k += 1
+        return k
+
     while any(c < 0 for c in col):
         snap = list(col)
         for i in range(n):
             if snap[i] >= 0:
                 continue
             if all(snap[j] >= 0 or prio[j] < prio[i] for j in adj[i]):
-                used = {snap[j] for j in adj[i] if snap[j] >= 0}
-                c = 0
-                while c in used:
-                    c += 1
-                col[i] = c
+                col[i] = smallest_free(i, snap)
+    for _ in range(passes):
+        new = [-1] * n
+        for c in range(max(col), -1, -1):
+            for i in range(n):
+                if col[i] == c:
+                    new[i] = smallest_free(i, new)
+        col = new
     return col

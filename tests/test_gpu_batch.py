@@ -46,11 +46,11 @@ def _t(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device=DEV)
 
 
-def _batch(cases, precision=ll.LL_FP64, rtol=1e-12, cc=CC, seed=0):
+def _batch(cases, precision=ll.LL_FP64, rtol=1e-12, cc=CC, seed=0, kcycle=0):
     ms = [_field(c.get("kind", "smooth"), c["grid"], seed + k) for k, c in enumerate(cases)]
     B = ll.Batch([_t(m) for m in ms], [c["alpha"] for c in cases], [c["dt"] for c in cases],
                  [c["h"] for c in cases], [c["grid"] for c in cases],
-                 ll.Params(rtol=rtol, coarsest_cells=cc, precision=precision))
+                 ll.Params(rtol=rtol, coarsest_cells=cc, precision=precision, kcycle=kcycle))
     return ms, B
 
 
@@ -164,7 +164,7 @@ def test_invalid_batches():
     ms = [_t(_field("smooth", c["grid"], k)) for k, c in enumerate(SMALL[:2])]
     args = ([c["alpha"] for c in SMALL[:2]], [c["dt"] for c in SMALL[:2]], [c["h"] for c in SMALL[:2]],
             [c["grid"] for c in SMALL[:2]])
-    for p in (ll.Params(kcycle=1, coarsest_cells=CC), ll.Params(precision=ll.LL_MIXED_BF16, coarsest_cells=CC)):
+    for p in (ll.Params(coarse_lanes=5, coarsest_cells=CC), ll.Params(precision=ll.LL_MIXED_BF16, coarsest_cells=CC)):
         with pytest.raises(ll.LLError):
             ll.Batch(ms, *args, params=p)
     with pytest.raises(ll.LLError):  # the 16x16 instance cannot coarsen below 1000 cells
@@ -195,4 +195,118 @@ def test_ragged_batch_sampled_against_oracle():
         xo, sto, ito, rro = O.solve(b, np.zeros_like(b))
         assert sto == oracle.OK and abs(its[k] - ito) <= 1
         # both stop at relres < 1e-8: the solutions agree to the stopping level
+        assert np.linalg.norm(xs[k] - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+# ---------------------------------------------------------------------------
+# the K-cycle in a batch, per-instance parameters (groups), the autotuner
+# ---------------------------------------------------------------------------
+
+def _oracle_solve(c, m, **kw):
+    O = oracle.Hierarchy(c["grid"], c["h"], c["alpha"], c["dt"], m, oracle.Params(**kw))
+    b = m / c["dt"]
+    return O.solve(b, np.zeros_like(b))
+
+
+@pytest.mark.parametrize("kcycle", [1, 2])
+def test_kcycle_batch_matches_oracle_per_instance(kcycle):
+    """The K-cycle on levels 1..kcycle of every instance, with each
+    instance's own inner-step scalars: the oracle's K-cycle solve per
+    instance (1e-10, iterations within one)."""
+    ms, B = _batch(SMALL, kcycle=kcycle)
+    st, its, rrs, sts, xs = _solve(B, ms, SMALL)
+    assert st == ll.LL_OK
+    for k, c in enumerate(SMALL):
+        xo, sto, ito, rro = _oracle_solve(c, ms[k], rtol=1e-12, coarsest_cells=CC, kcycle=kcycle)
+        assert sto == oracle.OK and rrs[k] < 1e-12
+        assert abs(its[k] - ito) <= 1, (k, its[k], ito)
+        assert np.linalg.norm(xs[k] - xo) <= 1e-10 * np.linalg.norm(xo), k
+
+
+def test_kcycle_mixed_batch():
+    ms, B64 = _batch(SMALL, rtol=1e-12, kcycle=1)
+    _, B32 = _batch(SMALL, precision=ll.LL_MIXED_FP32, rtol=1e-10, kcycle=1)
+    _, _, _, _, x64 = _solve(B64, ms, SMALL)
+    st, its, rrs, sts, x32 = _solve(B32, ms, SMALL)
+    assert st == ll.LL_OK and max(rrs) < 1e-10
+    for a, b in zip(x32, x64):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
+
+
+# instances of the 512-instance recipe (seed 0) where V(1,1) stagnates
+# (48^2, alpha 0.012, dt/h^2 18.9; 48^2, alpha 0.005, dt/h^2 14.6) and two
+# where it converges (64^2, dt/h^2 14.6 and 37.3)
+HARD = [229, 232, 211, 37]
+
+
+def _recipe(idx):
+    spec = inputs.batch_instances(512, seed=0)
+    cases = [{"grid": spec[k]["grid"], "h": spec[k]["h"], "alpha": spec[k]["alpha"], "dt": spec[k]["dt"]}
+             for k in idx]
+    ms = [inputs.smooth_field(*spec[k]["grid"], seed=spec[k]["seed"]).reshape(-1) for k in idx]
+    return cases, ms
+
+
+def _solve_from_guess(B, ms, cases, rtol=0.0):
+    rhs = [_t(m / c["dt"]) for m, c in zip(ms, cases)]
+    xs = [_t(m) for m in ms]
+    st, its, rrs, sts = B.solve(rhs, xs, rtol)
+    return st, its, rrs, sts, [x.cpu().numpy() for x in xs]
+
+
+def test_groups_run_each_instance_with_its_parameters():
+    """Per-instance parameters: instances with equal parameters share a
+    group; every instance matches the oracle solve with its own cycle."""
+    cycles = [dict(), dict(nu_pre=2, nu_post=2), dict(kcycle=1), dict(kcycle=1, nu_pre=2, nu_post=2)]
+    per = [cycles[k % 4] for k in range(len(SMALL))]
+    ms = [_field(c.get("kind", "smooth"), c["grid"], k) for k, c in enumerate(SMALL)]
+    args = ([_t(m) for m in ms], [c["alpha"] for c in SMALL], [c["dt"] for c in SMALL], [c["h"] for c in SMALL],
+            [c["grid"] for c in SMALL])
+    B = ll.Batch(*args, params=[ll.Params(rtol=1e-12, coarsest_cells=CC, **kw) for kw in per])
+    assert B.groups == 4
+    assert [B.instance_group(k) for k in range(len(SMALL))] == [k % 4 for k in range(len(SMALL))]
+    st, its, rrs, sts, xs = _solve(B, ms, SMALL)
+    assert st == ll.LL_OK
+    for k, c in enumerate(SMALL):
+        xo, sto, ito, rro = _oracle_solve(c, ms[k], rtol=1e-12, coarsest_cells=CC, **per[k])
+        assert sto == oracle.OK and abs(its[k] - ito) <= 1, (k, its[k], ito)
+        assert np.linalg.norm(xs[k] - xo) <= 1e-10 * np.linalg.norm(xo), k
+    # a single parameter set gives a plain batch
+    assert ll.Batch(*args, params=[ll.Params(coarsest_cells=CC)] * len(SMALL)).groups == 1
+
+
+def test_autotuner_rescues_the_stagnating_instances(tmp_path):
+    """The autotuner times each class's candidates on its instances: the
+    classes where V(1,1) stagnates get a cycle that converges, choices go to
+    the cache and are reused, and the tuned batch converges everywhere with
+    each instance matching the oracle run with its chosen cycle."""
+    cases, ms = _recipe(HARD)
+    args = ([_t(m) for m in ms], [c["alpha"] for c in cases], [c["dt"] for c in cases], [c["h"] for c in cases],
+            [c["grid"] for c in cases])
+    base = ll.Params(rtol=1e-8, maxit=300)
+    plain = ll.Batch(*args, params=base)
+    st, its, rrs, sts, xs = _solve_from_guess(plain, ms, cases)
+    assert sts[0] == ll.LL_NOT_CONVERGED and sts[1] != ll.LL_OK  # V(1,1) stagnates on the first two
+    cache = str(tmp_path / "tune.txt")
+    chosen, tuned = ll.autotune(*args, base=base, cache_path=cache)
+    assert tuned == 4
+    lines = [ln for ln in open(cache) if ln.startswith("llmg-tune-v1")]
+    assert len(lines) == 4
+    for k in (0, 1):
+        assert (chosen[k].nu_pre, chosen[k].kcycle) != (1, 0)
+    for p in chosen:
+        assert (p.rtol, p.maxit) == (base.rtol, base.maxit)
+    again, tuned2 = ll.autotune(*args, base=base, cache_path=cache)
+    assert tuned2 == 0 and again == chosen
+    for k, c in enumerate(cases):
+        assert ll.tune_lookup(cache, c["grid"], c["dt"], c["h"], base) == chosen[k]
+    B = ll.Batch(*args, params=chosen)
+    st, its, rrs, sts, xs = _solve_from_guess(B, ms, cases)
+    assert st == ll.LL_OK and all(r < 1e-8 for r in rrs)
+    for k, c in enumerate(cases):
+        p = chosen[k]
+        O = oracle.Hierarchy(c["grid"], c["h"], c["alpha"], c["dt"], ms[k],
+                             oracle.Params(rtol=1e-8, maxit=300, nu_pre=p.nu_pre, nu_post=p.nu_post, kcycle=p.kcycle))
+        xo, sto, ito, rro = O.solve(ms[k] / c["dt"], ms[k].copy())
+        assert sto == oracle.OK and abs(its[k] - ito) <= 1, (k, its[k], ito)
         assert np.linalg.norm(xs[k] - xo) <= 1e-6 * np.linalg.norm(xo)
