@@ -540,10 +540,41 @@ static csr_t prolongation(int n, int nc, const int *agg) {
 /* ------------------------------------------------------------------------ */
 
 /* Reading: on the grid the two colours are the parity of x+y+z (the 5/7-point
- * cell graph is bipartite).  On aggregated levels a Jones-Plassmann colouring:
- * in each round every uncoloured node whose priority (vertex_hash, then the
- * larger index) beats all its uncoloured neighbours takes the smallest colour
- * unused by its neighbours; those nodes form an independent set. */
+ * cell graph is bipartite).  On aggregated levels (the paper fixes no order
+ * of the Gauss-Seidel unknowns, Sec. 3) a colouring in two stages:
+ *  1. Jones-Plassmann rounds: every uncoloured node whose priority beats all
+ *     its uncoloured neighbours takes the smallest colour unused by its
+ *     neighbours (those nodes form an independent set).  Priority: the larger
+ *     degree (number of neighbours), then the larger vertex_hash, then the
+ *     larger index.
+ *  2. kRecolourPasses passes of iterated greedy recolouring: the classes of
+ *     the current colouring are visited from the highest colour to the
+ *     lowest, and each node takes the smallest colour unused by the
+ *     neighbours already visited in this pass.  Nodes of one class are not
+ *     adjacent, so the order inside a class does not matter, and a pass never
+ *     needs more colours than the colouring it starts from. */
+enum { kRecolourPasses = 4 };
+
+static int node_beats(const graph_t *g, int j, int i, uint32_t seed) {
+  int dj = g->rowptr[j + 1] - g->rowptr[j], di = g->rowptr[i + 1] - g->rowptr[i];
+  if (dj != di) return dj > di;
+  uint32_t hj = vertex_hash((uint32_t)j, seed), hi = vertex_hash((uint32_t)i, seed);
+  if (hj != hi) return hj > hi;
+  return j > i;
+}
+
+/* smallest colour not taken by a neighbour of i (colours < 0 are free) */
+static int first_free(const graph_t *g, int i, const int *c, char *used, int maxdeg) {
+  memset(used, 0, (size_t)maxdeg + 2);
+  for (int p = g->rowptr[i]; p < g->rowptr[i + 1]; ++p) {
+    int cj = c[g->col[p]];
+    if (cj >= 0 && cj <= maxdeg) used[cj] = 1;
+  }
+  int k = 0;
+  while (used[k]) ++k;
+  return k;
+}
+
 static int colour_graph(const graph_t *g, uint32_t seed, int *colour) {
   int n = g->n, ncol = 0;
   int *snap = (int *)xmalloc((size_t)n * sizeof(int));
@@ -553,33 +584,35 @@ static int colour_graph(const graph_t *g, uint32_t seed, int *colour) {
   for (int i = 0; i < n; ++i)
     if (g->rowptr[i + 1] - g->rowptr[i] > maxdeg) maxdeg = g->rowptr[i + 1] - g->rowptr[i];
   char *used = (char *)xcalloc((size_t)maxdeg + 2, 1);
-  while (left > 0) {
+  while (left > 0) { /* stage 1 */
     memcpy(snap, colour, (size_t)n * sizeof(int));
     for (int i = 0; i < n; ++i) {
       if (snap[i] >= 0) continue;
-      uint32_t hi = vertex_hash((uint32_t)i, seed);
       int wins = 1;
       for (int p = g->rowptr[i]; p < g->rowptr[i + 1]; ++p) {
         int j = g->col[p];
-        if (snap[j] >= 0) continue;
-        uint32_t hj = vertex_hash((uint32_t)j, seed);
-        if (hj > hi || (hj == hi && j > i)) {
+        if (snap[j] < 0 && node_beats(g, j, i, seed)) {
           wins = 0;
           break;
         }
       }
       if (!wins) continue;
-      memset(used, 0, (size_t)maxdeg + 2);
-      for (int p = g->rowptr[i]; p < g->rowptr[i + 1]; ++p) {
-        int cj = snap[g->col[p]];
-        if (cj >= 0 && cj <= maxdeg) used[cj] = 1;
-      }
-      int c = 0;
-      while (used[c]) ++c;
-      colour[i] = c;
-      if (c + 1 > ncol) ncol = c + 1;
+      colour[i] = first_free(g, i, snap, used, maxdeg);
+      if (colour[i] + 1 > ncol) ncol = colour[i] + 1;
       --left;
     }
+  }
+  for (int pass = 0; pass < kRecolourPasses; ++pass) { /* stage 2 */
+    for (int i = 0; i < n; ++i) snap[i] = -1;
+    int nnew = 0;
+    for (int c = ncol - 1; c >= 0; --c)
+      for (int i = 0; i < n; ++i) {
+        if (colour[i] != c) continue;
+        snap[i] = first_free(g, i, snap, used, maxdeg);
+        if (snap[i] + 1 > nnew) nnew = snap[i] + 1;
+      }
+    memcpy(colour, snap, (size_t)n * sizeof(int));
+    ncol = nnew;
   }
   free(snap);
   free(used);
