@@ -539,10 +539,14 @@ def run_batch(args):
     params = ll.Params(rtol=RTOL, precision=precision, maxit=args.batch_maxit)
     hs, grids = [s["h"] for s in spec], [s["grid"] for s in spec]
     tune_s, tuned, per = None, 0, params
-    if not args.no_autotune:  # per class of instances: cycle and coarse-kernel shape (cache in a fresh file)
+    if not args.no_autotune:  # per class of instances: cycle and coarse-kernel shape
         t0 = time.perf_counter()
-        with tempfile.TemporaryDirectory() as td:
-            per, tuned = ll.autotune(ms, alphas, dts, hs, grids, base=params, cache_path=os.path.join(td, "tune.txt"))
+        if args.tune_cache:  # earlier choices reused, new classes added
+            per, tuned = ll.autotune(ms, alphas, dts, hs, grids, base=params, cache_path=args.tune_cache)
+        else:  # tuned from scratch
+            with tempfile.TemporaryDirectory() as td:
+                per, tuned = ll.autotune(ms, alphas, dts, hs, grids, base=params,
+                                         cache_path=os.path.join(td, "tune.txt"))
         tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     B = ll.Batch(ms, alphas, dts, hs, grids, per)
@@ -608,7 +612,7 @@ def run_batch(args):
         "autotune": None if args.no_autotune else {
             "classes_tuned": tuned, "tune_s": tune_s, "groups": B.groups,
             "choices": sorted({(p.nu_pre, p.nu_post, p.kcycle, p.coarse_lanes, p.coarse_block) for p in per}),
-            "key": "(grid, floor(log2(dt/h^2))); candidates V(1,1), V(2,2), K1+V(1,1), K1+V(2,2), K1+V(3,3), then lanes 8 "
+            "key": "(grid, floor(log2(dt/h^2))); candidates V(1,1), V(2,2), K1+V(1,1), K1+V(2,2), then lanes 8 "
                    "and/or 128-thread blocks"},
         "e2e": {"value": solved * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "steps": e2e_steps},
@@ -691,6 +695,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--batch-maxit", type=int, default=300)
     ap.add_argument("--no-autotune", action="store_true", help="batch512: one parameter set for every instance")
+    ap.add_argument("--tune-cache", default=None, help="batch512: the autotuner's cache file (default: a fresh one)")
     ap.add_argument("--grid", type=int, default=128,
                     help="cube side of the step workload (default 128; smaller sides are profiling cases)")
     args = ap.parse_args()

@@ -350,8 +350,8 @@ int ll_mg_batch_instance_group(const ll_mg_batch* B, int i);
  * dt/h^2 = floor(log2(dt/h^2))).  For every class not yet in the cache, the
  * class's (up to) 3 instances with the smallest alpha are solved as one
  * batch (rhs = m/dt from the guess m, base's rtol, at most 300 iterations)
- * with each candidate cycle -- V(1,1), V(2,2), each with the K-cycle on
- * level 1, and V(3,3) with it -- then, for the best cycle, with the coarse kernels' launch shapes
+ * with each candidate cycle -- V(1,1), V(2,2), and each with the K-cycle on
+ * level 1 -- then, for the best cycle, with the coarse kernels' launch shapes
  * (lanes 8 and/or 128 threads per block); the best converges the most
  * instances, then takes the least time (the second of two solves).
  *   m_tilde, alpha, dt, h, grids  as ll_mg_batch_setup (device fields)

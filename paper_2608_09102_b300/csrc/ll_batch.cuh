@@ -190,6 +190,11 @@ void batch_symbolic(ll_mg_batch* B) {
       U->uc_tasks[l].alloc(tasks.size());
       LL_CU(cudaMemcpyAsync(U->uc_tasks[l].p, tasks.data(), tasks.size() * sizeof(CoarseTask),
                             cudaMemcpyHostToDevice, s));
+      std::vector<int> ptr(1, 0);
+      for (auto& t : tasks) ptr.push_back(ptr.back() + t.N);
+      U->uc_ptr[l].alloc(ptr.size());
+      LL_CU(cudaMemcpyAsync(U->uc_ptr[l].p, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      LL_CU(cudaStreamSynchronize(s));  // ptr goes out of scope
     }
     for (int i = 0; i < ni; ++i) {
       ll_mg_hierarchy* H = B->inst[i];
@@ -373,6 +378,12 @@ void batch_allocate(ll_mg_batch* B) {
   LL_CU(cudaStreamSynchronize(U->s));
 }
 
+// The union's small levels (from the first with at most kTailCells rows, K
+// levels excluded) run in one thread-block-cluster kernel, as a single
+// instance's do, with every instance's dense solve at the level where it
+// ends (off with LLMG_NO_TAIL=1).
+void batch_tail(ll_mg_batch* B) { setup_tail(B->U); }
+
 // numeric values of the union from the instances' numeric setups
 template <typename T, typename TM>
 void batch_values(ll_mg_batch* B) {
@@ -485,7 +496,7 @@ void batch_run_iteration(ll_mg_batch* B, int j) {
   } else {
     if (!B->graphs[j]) {
       cudaGraph_t graph;
-      long long before = g_launches.load();
+      long long before = t_launches;
       LL_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       try {
         batch_iteration_body<T, TM>(B, j);
@@ -497,7 +508,7 @@ void batch_run_iteration(ll_mg_batch* B, int j) {
       cudaError_t e = cudaGraphInstantiate(&B->graphs[j], graph, 0);
       cudaGraphDestroy(graph);
       LL_CU(e);
-      B->graph_kernels[j] = g_launches.load() - before;
+      B->graph_kernels[j] = t_launches - before;
       g_launches.fetch_sub(B->graph_kernels[j]);
     }
     LL_CU(cudaGraphLaunch(B->graphs[j], s));
@@ -663,6 +674,7 @@ ll_mg_batch* batch_child(ll_mg_batch* B, const std::vector<int>& sub) {
     batch_build(C);
     batch_symbolic(C);
     batch_allocate(C);
+    batch_tail(C);
     batch_refresh(C);
   } catch (...) {
     delete C;
@@ -757,6 +769,7 @@ int batch_create(int count, const double* const* m, const double* alpha, const d
     }
     batch_symbolic(B);
     batch_allocate(B);
+    batch_tail(B);
     batch_refresh(B);
     *out = B;
     return LL_OK;

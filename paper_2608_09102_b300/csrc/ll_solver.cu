@@ -23,8 +23,15 @@
 
 namespace llmg {
 
+// kernels launched: in total (all threads), and by the calling thread (the
+// kernels a graph capture records are counted on the capturing thread, so
+// that concurrent captures on other threads do not enter its count)
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
 
 struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   int n = 0, nnzb = 0, ncol = 0;
@@ -122,6 +129,7 @@ struct ll_mg_hierarchy {
   // instances whose coarsest level is l are solved densely at level l
   bool union_mode = false;
   DBuf<CoarseTask> uc_tasks[kMaxLevels];
+  DBuf<int> uc_ptr[kMaxLevels];  // running sums of the tasks' sizes N
   int uc_n[kMaxLevels] = {0}, uc_maxN[kMaxLevels] = {0};
   // union hierarchies with the K-cycle: per K level, element chunks of the
   // rows of every instance that has the K-cycle there (instance-major), the
@@ -445,8 +453,9 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
   while (A.solo_first > A.first && H->lev[A.solo_first - 1].n <= kSoloCells) --A.solo_first;
   A.nu_pre = H->prm.nu_pre;
   A.nu_post = H->prm.nu_post;
-  A.N = H->ncoarse3;
-  A.ainv = H->ainv;
+  A.uni = H->union_mode;
+  A.N = H->union_mode ? 0 : H->ncoarse3;
+  A.ainv = H->union_mode ? nullptr : H->ainv.p;
   for (int l = A.first; l <= A.last; ++l) {
     CLevel& C = H->lev[l];
     TailLevel<T, TM>& L = A.L[l];
@@ -466,6 +475,11 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
     L.agg = C.agg;
     L.mptr = C.mptr;
     L.mem = C.mem;
+    if (H->union_mode) {
+      L.nuc = H->uc_n[l];
+      L.uc = H->uc_tasks[l];
+      L.ucptr = H->uc_ptr[l];
+    }
   }
   int w = (int)sizeof(T), wm = (int)sizeof(TM);
   H->tail_flops = H->tail_bytes = 0;
@@ -484,7 +498,7 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
     H->tail_flops += sweep_flops(C.res_blk, rrows);
     H->tail_bytes += sweep_bytes(C.res_blk, rrows, w, wm);
   }
-  H->tail_flops += 2.0 * H->ncoarse3 * H->ncoarse3;
+  H->tail_flops += 2.0 * H->ncoarse3 * H->ncoarse3;  // zero for a union (its dense solves are not counted)
   H->tail_bytes += 8.0 * H->ncoarse3 * H->ncoarse3;
   dst.alloc(1);
   LL_CU(cudaMemcpyAsync(dst.p, &A, sizeof(A), cudaMemcpyHostToDevice, H->s));
@@ -1240,7 +1254,7 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
   if (H->graphs[j] && H->graph_mask[j] != H->prof_mask) H->drop_graph(j);
   if (!H->graphs[j]) {
     cudaGraph_t graph;
-    long long before = g_launches.load();
+    long long before = t_launches;
     LL_CU(cudaStreamBeginCapture(H->s, cudaStreamCaptureModeThreadLocal));
     H->capturing = j;
     try {
@@ -1256,7 +1270,7 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
     cudaGraphDestroy(graph);
     LL_CU(e);
     H->graph_mask[j] = H->prof_mask;
-    H->graph_kernels[j] = g_launches.load() - before;  // counted per launch below
+    H->graph_kernels[j] = t_launches - before;  // counted per launch below
     g_launches.fetch_sub(H->graph_kernels[j]);
   }
   LL_CU(cudaGraphLaunch(H->graphs[j], H->s));

@@ -129,8 +129,12 @@ def test_update_matches_fresh_batch():
 
 def test_compaction_is_invisible(monkeypatch):
     """Compacting the still-iterating instances into sub-batches at restart
-    boundaries changes nothing: iterations, residuals and solutions are
-    bit-identical to the lockstep solve of the whole batch."""
+    boundaries changes each instance's arithmetic by rounding only (a
+    sub-batch's smaller union may run a level in the cluster kernel that the
+    whole batch runs as per-class launches): same statuses, iterations within
+    one, solutions within 1e-10 and residuals within 1e-6 of the lockstep
+    solve of the whole batch; a second solve reuses the sub-batches and
+    repeats the first bit for bit."""
     cases = SMALL + [dict(c, alpha=c["alpha"] * 0.3, dt=c["dt"] * 3) for c in SMALL[:3]]
     ms, B = _batch(cases, rtol=1e-12)
     monkeypatch.setenv("LLMG_BATCH_NO_COMPACT", "1")
@@ -139,9 +143,12 @@ def test_compaction_is_invisible(monkeypatch):
     monkeypatch.delenv("LLMG_BATCH_NO_COMPACT")
     st2, its2, rrs2, sts2, xs2 = _solve(B, ms, cases)
     assert B.subbatches >= 1
-    assert its1 == its2 and sts1 == sts2 and rrs1 == rrs2
-    for a, b in zip(xs1, xs2):
-        assert np.array_equal(a, b)
+    assert sts1 == sts2
+    for k in range(len(cases)):
+        assert abs(its1[k] - its2[k]) <= 1, (k, its1[k], its2[k])
+        assert abs(rrs1[k] - rrs2[k]) <= 1e-6 * max(rrs1[k], 1e-12), (k, rrs1[k], rrs2[k])
+        if sts1[k] == ll.LL_OK:
+            assert np.linalg.norm(xs1[k] - xs2[k]) <= 1e-10 * np.linalg.norm(xs1[k]), k
     st3, its3, rrs3, sts3, xs3 = _solve(B, ms, cases)  # the cached sub-batches again
     assert its3 == its2 and all(np.array_equal(a, b) for a, b in zip(xs3, xs2))
 
@@ -312,3 +319,26 @@ def test_autotuner_rescues_the_stagnating_instances(tmp_path):
         xo, sto, ito, rro = O.solve(ms[k] / c["dt"], ms[k].copy())
         assert sto == oracle.OK and abs(its[k] - ito) <= 1, (k, its[k], ito)
         assert np.linalg.norm(xs[k] - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_union_tail_matches_per_class_launches(monkeypatch):
+    """The union's small levels in one cluster kernel (with every instance's
+    dense solve at its own coarsest level) against the same levels as
+    per-class launches: same iterations within one, solutions within 1e-10."""
+    spec = inputs.batch_instances(24, seed=5, sides=(32, 48, 64, 96))
+    cases = [{"grid": s["grid"], "h": s["h"], "alpha": s["alpha"], "dt": s["dt"]} for s in spec]
+    ms = [inputs.smooth_field(*s["grid"], seed=s["seed"]).reshape(-1) for s in spec]
+    args = ([_t(m) for m in ms], [c["alpha"] for c in cases], [c["dt"] for c in cases], [c["h"] for c in cases],
+            [c["grid"] for c in cases])
+    p = ll.Params(rtol=1e-12, maxit=400)
+    B = ll.Batch(*args, params=p)
+    monkeypatch.setenv("LLMG_NO_TAIL", "1")
+    N = ll.Batch(*args, params=p)
+    monkeypatch.delenv("LLMG_NO_TAIL")
+    st1, its1, rrs1, sts1, xs1 = _solve(B, ms, cases)
+    st2, its2, rrs2, sts2, xs2 = _solve(N, ms, cases)
+    assert sts1 == sts2
+    for k in range(len(cases)):
+        assert abs(its1[k] - its2[k]) <= 1, (k, its1[k], its2[k])
+        if sts1[k] == ll.LL_OK:
+            assert np.linalg.norm(xs1[k] - xs2[k]) <= 1e-10 * np.linalg.norm(xs2[k]), k
