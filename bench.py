@@ -56,10 +56,12 @@ WORKLOAD = "3D 128^3 semi-implicit LL time steps, alpha 0.02, dt 5e-4, vortex + 
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 
 # DRAM traffic of the float64 coarse sweeps per launch over their algorithmic
-# bytes: ncu dram__bytes_read.sum + dram__bytes_write.sum of kb_sweep launches
-# of the 96^3 profiling case, against the library's byte model for the same
-# launches.  Scaled by the bytes a launch processes to a 128^3 launch.
-KB_SWEEP_TRAFFIC_RATIO = 9.679e6 / 9.293e6
+# bytes: ncu dram__bytes_read.sum + dram__bytes_write.sum over 100 kb_sweep
+# launches (two V-cycles) of the 96^3 profiling case (1.109e7 B per launch),
+# against the library's byte model averaged over the same launch mix
+# (1.150e7 B per launch).  Scaled by the bytes a launch processes to a 128^3
+# launch.
+KB_SWEEP_TRAFFIC_RATIO = 1.1088e7 / 1.1495e7
 
 KIND_NAMES = ["l0_smooth", "l0_restrict", "outer_apply", "bsr_smooth", "bsr_other", "gcr_vector", "coarsest",
               "numeric", "coarse_tail"]
@@ -494,6 +496,8 @@ def run_ours(args):
         "fp64_peak": {"measured_tflops": fp64_meas, "derived_tflops": FP64_PEAK_TFLOPS,
                       "probe": "ll_fp64_fma_probe: 1184 blocks x 256 threads x 8 chains x 8192 FMA, best of 5"},
         "kernel_breakdown_ms_per_step": {k: round(v[0] / prof_steps, 3) for k, v in breakdown.items()},
+        "kernel_launches_per_iteration": {k: round(v[1] / max(sum(pits), 1), 2) for k, v in breakdown.items()},
+        "profiling_pass": {"steps": prof_steps, "iterations": int(sum(pits))},
         # the V-cycle's kernels together (algorithmic bytes over their event time)
         "vcycle_hbm_gbs": (sum(breakdown[k][3] for k in vk) / max(sum(breakdown[k][0] for k in vk), 1e-9) / 1e6),
         "numeric_setup_ms_per_step": breakdown["numeric"][0] / prof_steps,
