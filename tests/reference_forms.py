@@ -203,11 +203,14 @@ def block_gs_sweep(A: np.ndarray, colours, b, x, forward: bool = True) -> np.nda
     return x
 
 
-def vcycle_dense(ops, ps, colours, b, nu_pre: int = 1, nu_post: int = 1, level: int = 0) -> np.ndarray:
+def vcycle_dense(ops, ps, colours, b, nu_pre: int = 1, nu_post: int = 1, level: int = 0,
+                 kcycle: int = 0) -> np.ndarray:
     """One V(nu_pre, nu_post) cycle for ops[level] x = b from x = 0 (Sec. 3):
-    forward block-GS sweeps, residual, restriction P^T, the same cycle on the
-    next level from a zero guess, prolongation x += P e, backward sweeps; an
-    exact (dense) solve on the last level."""
+    forward block-GS sweeps, residual, restriction P^T, the coarse problem
+    from a zero guess, prolongation x += P e, backward sweeps; an exact
+    (dense) solve on the last level.  The coarse problem of levels
+    1..kcycle (never the last) is solved by kcycle_inner, else by the same
+    cycle one level down."""
     A = ops[level]
     if level == len(ops) - 1:
         return np.linalg.solve(A, b)
@@ -215,8 +218,33 @@ def vcycle_dense(ops, ps, colours, b, nu_pre: int = 1, nu_post: int = 1, level: 
     for _ in range(nu_pre):
         x = block_gs_sweep(A, colours[level], b, x, True)
     r = b - A @ x
-    e = vcycle_dense(ops, ps, colours, ps[level].T @ r, nu_pre, nu_post, level + 1)
+    bc = ps[level].T @ r
+    if level + 1 <= kcycle and level + 1 < len(ops) - 1:
+        e = kcycle_inner(ops, ps, colours, bc, nu_pre, nu_post, level + 1, kcycle)
+    else:
+        e = vcycle_dense(ops, ps, colours, bc, nu_pre, nu_post, level + 1, kcycle)
     x = x + ps[level] @ e
     for _ in range(nu_post):
         x = block_gs_sweep(A, colours[level], b, x, False)
     return x
+
+
+def kcycle_inner(ops, ps, colours, r, nu_pre: int, nu_post: int, level: int, kcycle: int) -> np.ndarray:
+    """The Krylov-accelerated coarse solve of Sec. 3.1 (reading: two steps of
+    Algorithm 1 on A e = r from e = 0, preconditioned by this level's cycle
+    B): the correction e in span{B r, B r1} that minimises |r - A e|, with
+    r1 = r - (c1.r) c1 the residual after the first step.  Written as the
+    least-squares solve over the two directions (not the oracle's Gram-Schmidt
+    recurrence); a direction whose image is zero is dropped."""
+    A = ops[level]
+    z1 = vcycle_dense(ops, ps, colours, r, nu_pre, nu_post, level, kcycle)
+    c1 = A @ z1
+    if not np.any(c1):
+        return np.zeros_like(r)
+    r1 = r - (c1 @ r) / (c1 @ c1) * c1
+    z2 = vcycle_dense(ops, ps, colours, r1, nu_pre, nu_post, level, kcycle)
+    W = np.column_stack([c1, A @ z2])
+    if not np.any(W[:, 1]) or np.linalg.matrix_rank(W) < 2:
+        return (c1 @ r) / (c1 @ c1) * z1
+    y, *_ = np.linalg.lstsq(W, r, rcond=None)
+    return y[0] * z1 + y[1] * z2

@@ -8,10 +8,14 @@ the colour vectors: none of the oracle's sparse matrices or loops.  The
 aggregates and colours themselves are pinned against a pure-Python
 restatement of the aggregation rule elsewhere.
 
-The last test plants plausible mistakes in a copy of the oracle (point
+The K-cycle of Sec. 3.1 (two GCR steps on a coarse level) is pinned the same
+way, against a least-squares statement of the two steps.
+
+The last tests plant plausible mistakes in a copy of the oracle (point
 instead of block Gauss-Seidel, the backward sweep in ascending colour order,
 a missing pre- or post-sweep, a non-zero coarse initial guess, a flipped
-residual sign) and checks that these pins catch every one of them.
+residual sign; one inner K-cycle step instead of two, no orthogonalisation
+of the second image) and check that these pins catch every one of them.
 """
 from __future__ import annotations
 
@@ -97,6 +101,21 @@ def test_vcycle_sweep_counts_match_restatement(nu):
     assert _vcycle_errors(H, ops, ps, cols, nu) <= 1e-12
 
 
+@pytest.mark.parametrize("k,kcycle", [(0, 1), (2, 1), (2, 2), (3, 20)])
+def test_kcycle_matches_restatement(k, kcycle):
+    """The K-cycle (Sec. 3.1, reading: two GCR steps on levels 1..kcycle)
+    against the least-squares restatement of the two steps."""
+    grid, h, alpha, dt, cc = GRIDS[k]
+    H, ops, ps, cols = _case(k, oracle.Params(coarsest_cells=cc, kcycle=kcycle))
+    r = np.random.default_rng(7).standard_normal(ops[0].shape[0])
+    ref = rf.vcycle_dense(ops, ps, cols, r, kcycle=kcycle)
+    got = H.vcycle(r)
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+    if kcycle == 1:  # and it is not the plain V-cycle
+        plain = rf.vcycle_dense(ops, ps, cols, r)
+        assert np.linalg.norm(plain - ref) > 1e-6 * np.linalg.norm(ref)
+
+
 # --------------------------------------------------------------------------
 # planted mistakes: each must make a pin fail
 # --------------------------------------------------------------------------
@@ -131,13 +150,24 @@ MUTATIONS = {
 }
 
 
+KC = "static void kinner("
+
+# mistakes in the K-cycle's two inner steps, caught by the K-cycle pin
+KMUTATIONS = {
+    # the second direction is dropped (one inner step)
+    "kcycle_one_step": (KC, "double y2 = g22 > 0 ? a2 / g22 : 0.0", "double y2 = 0.0"),
+    # the second image is not orthogonalised against the first
+    "kcycle_no_orthogonalisation": (KC, "c2[i] -= g12 * c1[i];", "c2[i] -= 0.0 * c1[i];"),
+}
+
+
 @pytest.fixture(scope="module")
 def mutant_dir(tmp_path_factory):
     return tmp_path_factory.mktemp("oracle_mutants")
 
 
 def _mutant(name, where):
-    head, old, new = MUTATIONS[name]
+    head, old, new = {**MUTATIONS, **KMUTATIONS}[name]
     src = open(os.path.join(os.path.dirname(oracle.__file__), "ll_oracle.c")).read()
     c = os.path.join(str(where), name + ".c")
     so = os.path.join(str(where), name + ".so")
@@ -168,3 +198,25 @@ def test_planted_mistakes_are_caught(name, mutant_dir):
     else:
         assert max(sweep) <= 1e-12, sweep
     assert min(cycle) > 1e-6, cycle
+
+
+@pytest.mark.parametrize("name", sorted(KMUTATIONS))
+def test_planted_kcycle_mistakes_are_caught(name, mutant_dir):
+    lib = _mutant(name, mutant_dir)
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        errs = []
+        for k in (0, 2):
+            grid, h, alpha, dt, cc = GRIDS[k]
+            H, ops, ps, cols = _case(k, oracle.Params(coarsest_cells=cc, kcycle=1))
+            r = np.random.default_rng(7).standard_normal(ops[0].shape[0])
+            ref = rf.vcycle_dense(ops, ps, cols, r, kcycle=1)
+            errs.append(np.linalg.norm(H.vcycle(r) - ref) / np.linalg.norm(ref))
+            H.__del__()
+    finally:
+        oracle._lib = saved
+    # far above the K-cycle pin's 1e-11 (the unorthogonalised second image
+    # is nearly orthogonal to the first already, so that mistake moves the
+    # result by a few 1e-8 only)
+    assert min(errs) > 1e-9, errs
