@@ -89,6 +89,59 @@ __device__ __forceinline__ T ld(const T* p) {
   return __ldg(p);
 }
 
+// float32 inverse of a 3x3 matrix (row-major) by cofactors
+__device__ __forceinline__ void inv3f(const float* a, float* o) {
+  float c00 = a[4] * a[8] - a[5] * a[7];
+  float c01 = a[5] * a[6] - a[3] * a[8];
+  float c02 = a[3] * a[7] - a[4] * a[6];
+  float id = 1.0f / (a[0] * c00 + a[1] * c01 + a[2] * c02);
+  o[0] = c00 * id;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  o[3] = c01 * id;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  o[6] = c02 * id;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+}
+
+// Level-0 coefficients of the float32 V-cycle formed in the kernels from m~
+// (12 bytes per slot) instead of read as C(m~)/h^2 and D^-1 (72 bytes): the
+// float32 level-0 kernels are bound by memory, not by float32 arithmetic.
+// m32 holds m~ per slot, SoA [3][2 Nh]; the numeric setup writes it (and
+// checks in float64 that every D is invertible).
+struct OnFly {
+  const float* m32;
+  float alpha, ih2, inv_dt;
+};
+// C(m~)/h^2 of slot sl, C(m) = [m]x + alpha (m m^T - |m|^2 I), row-major
+__device__ __forceinline__ void onfly_c(const OnFly& q, long sl, long n2, float* C) {
+  float m1 = ld(q.m32 + sl), m2 = ld(q.m32 + n2 + sl), m3 = ld(q.m32 + 2 * n2 + sl);
+  float s = m1 * m1 + m2 * m2 + m3 * m3, a = q.alpha;
+  C[0] = a * (m1 * m1 - s);
+  C[1] = -m3 + a * m1 * m2;
+  C[2] = m2 + a * m1 * m3;
+  C[3] = m3 + a * m2 * m1;
+  C[4] = a * (m2 * m2 - s);
+  C[5] = -m1 + a * m2 * m3;
+  C[6] = -m2 + a * m3 * m1;
+  C[7] = m1 + a * m3 * m2;
+  C[8] = a * (m3 * m3 - s);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) C[e] *= q.ih2;
+}
+// D^-1 = (I/dt - deg C(m~)/h^2)^-1 from C as onfly_c gives it
+__device__ __forceinline__ void onfly_dinv(const OnFly& q, const float* C, int deg, float* Di) {
+  float D[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) D[e] = -(float)deg * C[e];
+  D[0] += q.inv_dt;
+  D[4] += q.inv_dt;
+  D[8] += q.inv_dt;
+  inv3f(D, Di);
+}
+
 // ---------------------------------------------------------------------------
 // numeric setup, level 0: per slot C(m~)/h^2 and the inverse of the diagonal
 // block I/dt - deg C(m~)/h^2.  C(m) = [m]_x + alpha (m m^T - |m|^2 I)  (the
@@ -97,7 +150,7 @@ __device__ __forceinline__ T ld(const T* p) {
 template <typename T>
 __global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, double dt, double ih2,
                         double* __restrict__ chat64, T* __restrict__ chat, T* __restrict__ dinv,
-                        int* __restrict__ bad) {
+                        int* __restrict__ bad, float* __restrict__ m32 = nullptr) {
   long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long n2 = 2 * g.nh;
   if (sl >= n2) return;
@@ -131,7 +184,11 @@ __global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, 
   for (int e = 0; e < 9; ++e) {
     if (chat64) chat64[e * n2 + sl] = C[e];
     if (chat) chat[e * n2 + sl] = (T)C[e];
-    dinv[e * n2 + sl] = (T)Di[e];
+    if (dinv) dinv[e * n2 + sl] = (T)Di[e];
+  }
+  if (m32) {  // m~ per slot for the float32 kernels that form C and D^-1 themselves
+    long k = p.real ? p.x + (long)g.nx * (p.y + (long)g.ny * p.z) : 0;
+    for (int q = 0; q < 3; ++q) m32[q * n2 + sl] = p.real ? (float)m[q * g.n + k] : 0.0f;
   }
 }
 
@@ -472,6 +529,88 @@ __device__ __forceinline__ void slot_residual_after_sweep(const GridGeom& g, lon
   r[0] = -(ld(C) * s0 + ld(C + n2) * s1 + ld(C + 2 * n2) * s2);
   r[1] = -(ld(C + 3 * n2) * s0 + ld(C + 4 * n2) * s1 + ld(C + 5 * n2) * s2);
   r[2] = -(ld(C + 6 * n2) * s0 + ld(C + 7 * n2) * s1 + ld(C + 8 * n2) * s2);
+}
+
+// k0_smooth for the float32 V-cycle with the coefficients formed from m~
+// (OnFly); the same operations in the same order once C and D^-1 are formed
+template <int MODE>
+__global__ void __launch_bounds__(256) k0_smooth_onfly(GridGeom g, int c, const double* __restrict__ b,
+                                                       float* __restrict__ x, OnFly q,
+                                                       const int* __restrict__ agg, const float* __restrict__ e) {
+  long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= g.nh) return;
+  long n2 = 2 * g.nh;
+  long sl = (long)c * g.nh + r;
+  SlotPos p = slot_pos(g, c, r);
+  if (!p.real) return;
+  float v0 = (float)b[sl], v1 = (float)b[n2 + sl], v2 = (float)b[2 * n2 + sl];
+  float C[9];
+  onfly_c(q, sl, n2, C);
+  int deg = (p.x > 0) + (p.x < g.nx - 1) + (p.y > 0) + (p.y < g.ny - 1) + (p.z > 0) + (p.z < g.nz - 1);
+  if (MODE != 0) {
+    float s0 = 0, s1 = 0, s2 = 0;
+    for_neighbours(g, c, p, [&](long l) {
+      s0 += x[l];
+      s1 += x[n2 + l];
+      s2 += x[2 * n2 + l];
+      if (MODE == 2) {
+        long a = 3L * agg[l];
+        s0 += e[a];
+        s1 += e[a + 1];
+        s2 += e[a + 2];
+      }
+    });
+    v0 = fmaf(-C[0], s0, v0);
+    v0 = fmaf(-C[1], s1, v0);
+    v0 = fmaf(-C[2], s2, v0);
+    v1 = fmaf(-C[3], s0, v1);
+    v1 = fmaf(-C[4], s1, v1);
+    v1 = fmaf(-C[5], s2, v1);
+    v2 = fmaf(-C[6], s0, v2);
+    v2 = fmaf(-C[7], s1, v2);
+    v2 = fmaf(-C[8], s2, v2);
+  }
+  float D[9];
+  onfly_dinv(q, C, deg, D);
+  x[sl] = D[0] * v0 + D[1] * v1 + D[2] * v2;
+  x[n2 + sl] = D[3] * v0 + D[4] * v1 + D[5] * v2;
+  x[2 * n2 + sl] = D[6] * v0 + D[7] * v1 + D[8] * v2;
+}
+
+// k0_restrict<float, true> with C formed from m~ (OnFly)
+__global__ void k0_restrict_onfly(GridGeom g, const float* __restrict__ x, OnFly q, int nc,
+                                  const int* __restrict__ mptr, const int* __restrict__ mem, float* __restrict__ bc,
+                                  int init_end, const float* __restrict__ dinvc, float* __restrict__ xc,
+                                  const int* __restrict__ order) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  int I = order[t];
+  long n2 = 2 * g.nh;
+  float a0 = 0, a1 = 0, a2 = 0;
+  for (int qm = mptr[I]; qm < mptr[I + 1]; ++qm) {
+    long sl = mem[qm];
+    SlotPos p = slot_pos(g, 0, sl % g.nh);
+    float s0 = 0, s1 = 0, s2 = 0;
+    for_neighbours(g, 0, p, [&](long l) {
+      s0 += x[l];
+      s1 += x[n2 + l];
+      s2 += x[2 * n2 + l];
+    });
+    float C[9];
+    onfly_c(q, sl, n2, C);
+    a0 += -(C[0] * s0 + C[1] * s1 + C[2] * s2);
+    a1 += -(C[3] * s0 + C[4] * s1 + C[5] * s2);
+    a2 += -(C[6] * s0 + C[7] * s1 + C[8] * s2);
+  }
+  bc[3L * I] = a0;
+  bc[3L * I + 1] = a1;
+  bc[3L * I + 2] = a2;
+  if (I < init_end) {  // first colour of the next level's forward sweep
+    const float* D = dinvc + 9L * I;
+    xc[3L * I] = D[0] * a0 + D[1] * a1 + D[2] * a2;
+    xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
+    xc[3L * I + 2] = D[6] * a0 + D[7] * a1 + D[8] * a2;
+  }
 }
 
 // SHORT: one forward sweep preceded (the residual of slot_residual_after_sweep)

@@ -102,6 +102,7 @@ struct ll_mg_hierarchy {
   DBuf<int> agg_nat0, agg0, nat_of_slot;
   DBuf<double> chat64, dinv64;
   DBuf<float> chat32, dinv32;
+  DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
   CLevel lev[kMaxLevels];
   // coarsest dense LU and its inverse (column-major)
   int ncoarse3 = 0;
@@ -382,6 +383,7 @@ void allocate(ll_mg_hierarchy* H) {
   if (mixed) {
     H->chat32.alloc(9 * n2);
     H->dinv32.alloc(9 * n2);
+    H->m32.alloc(3 * n2);
   } else {
     H->dinv64.alloc(9 * n2);
   }
@@ -693,7 +695,8 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
   double ih2 = 1.0 / (H->h * H->h), inv_dt = 1.0 / H->dt;
   int nb = cdiv(H->n2, kBlock);
   if (mixed)
-    k0_coef<float><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, H->chat32, H->dinv32, H->flag);
+    k0_coef<float><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, H->chat32, H->dinv32, H->flag,
+                                         H->m32);
   else
     k0_coef<double><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, nullptr, H->dinv64, H->flag);
   LL_LAUNCHED();
@@ -1047,35 +1050,57 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   const T* dinv = H->dinv0<T>();
   T inv_dt = (T)(1.0 / H->dt);
   int nb = cdiv(g.nh, kBlock);
+  // float32 V-cycle: C and D^-1 formed in the kernels from m~ (OnFly)
+  OnFly q{H->m32.p, (float)H->alpha, (float)(1.0 / (H->h * H->h)), (float)(1.0 / H->dt)};
+  bool onfly = std::is_same<T, float>::value && H->m32.p;
+  auto half_sweep = [&](auto mode, int c, const int* agg, const T* e) {
+    constexpr int MODE = decltype(mode)::value;
+    if constexpr (std::is_same<T, float>::value) {
+      if (onfly) {
+        k0_smooth_onfly<MODE><<<nb, kBlock, 0, s>>>(g, c, r, z, q, agg, e);
+        return;
+      }
+    }
+    k0_smooth<T, MODE><<<nb, kBlock, 0, s>>>(g, c, r, z, chat, dinv, agg, e);
+  };
   if (H->prm.nu_pre >= 1) {
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 15.0 * H->l0_cells[0], (24 + 12 * (double)sizeof(T)) * H->l0_cells[0]);
-      k0_smooth<T, 0><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+      half_sweep(std::integral_constant<int, 0>(), 0, nullptr, nullptr);
       LL_LAUNCHED();
     }
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
-      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+      half_sweep(std::integral_constant<int, 1>(), 1, nullptr, nullptr);
       LL_LAUNCHED();
     }
     for (int sweep = 1; sweep < H->prm.nu_pre; ++sweep) {
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
-        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 0, nullptr, nullptr);
         LL_LAUNCHED();
       }
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
-        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 1, nullptr, nullptr);
         LL_LAUNCHED();
       }
     }
     int init_end = H->nlev > 2 ? L1.cs[1] : 0;  // level 1's first colour, unless it is the coarsest
     if (H->prm.nu_pre == 1) {  // right after one forward sweep: the neighbours' part only
       LL_PROFW(LL_KIND_L0_RESTRICT, 33.0 * H->l0_cells[0], (8 + 27.0 * sizeof(T)) * H->l0_cells[0]);
-      k0_restrict<T, true><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
-                                                                  L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
-                                                                  L1.o2n);
+      bool done = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (onfly) {
+          k0_restrict_onfly<<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, z, q, L1.n, L1.mptr0, L1.mem0, L1.b<T>(),
+                                                                  init_end, L1.dinv<T>(), L1.x<T>(), L1.o2n);
+          done = true;
+        }
+      }
+      if (!done)
+        k0_restrict<T, true><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
+                                                                    L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
+                                                                    L1.o2n);
     } else {
       LL_PROFW(LL_KIND_L0_RESTRICT, 48.0 * H->l0_cells[0], (24 + 15.0 * sizeof(T)) * H->l0_cells[0]);
       k0_restrict<T, false><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
@@ -1094,23 +1119,23 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   if (H->prm.nu_post >= 1) {
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 66.0 * H->l0_cells[1], (24 + 24.75 * (double)sizeof(T)) * H->l0_cells[1]);
-      k0_smooth<T, 2><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, H->agg0, L1.x<T>());
+      half_sweep(std::integral_constant<int, 2>(), 1, H->agg0, L1.x<T>());
       LL_LAUNCHED();
     }
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
-      k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+      half_sweep(std::integral_constant<int, 1>(), 0, nullptr, nullptr);
       LL_LAUNCHED();
     }
     for (int sweep = 1; sweep < H->prm.nu_post; ++sweep) {
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
-        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 1, r, z, chat, dinv, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 1, nullptr, nullptr);
         LL_LAUNCHED();
       }
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
-        k0_smooth<T, 1><<<nb, kBlock, 0, s>>>(g, 0, r, z, chat, dinv, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 0, nullptr, nullptr);
         LL_LAUNCHED();
       }
     }
