@@ -345,6 +345,98 @@ __global__ void k_lu_factor(int N, double* __restrict__ a, int* __restrict__ per
   }
 }
 
+// Coarsest levels of up to kLuSmemMax unknowns: the factorisation and the
+// inverse in one block, entirely in shared memory (the matrix and the
+// inverse's columns, 2 N^2 doubles), the same operations in the same order as
+// k_lu_factor followed by k_lu_inverse.  blockDim.x: a power of two >= N.
+constexpr int kLuSmemMax = 112;
+__global__ void k_lu_invert_smem(int N, const double* __restrict__ a, int* __restrict__ perm,
+                                 int* __restrict__ status, double* __restrict__ ainv) {
+  extern __shared__ double sm[];
+  double* A = sm;          // row-major N x N, factored in place
+  double* Y = sm + N * N;  // Y[k * N + j]: entry k of column j of the inverse
+  __shared__ double sval[128];
+  __shared__ int sidx[128];
+  __shared__ int sperm[kLuSmemMax];
+  __shared__ int piv, bad;
+  int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < N * N; e += nt) A[e] = a[e];
+  for (int i = t; i < N; i += nt) sperm[i] = i;
+  if (t == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    // pivot search: largest |a_ik|, ties to the lowest row
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + t; i < N; i += nt) {
+      double v = fabs(A[i * N + k]);
+      if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    sval[t] = bv;
+    sidx[t] = bi;
+    __syncthreads();
+    for (int o = nt / 2; o > 0; o >>= 1) {
+      if (t < o) {
+        double v2 = sval[t + o];
+        int i2 = sidx[t + o];
+        if (v2 > sval[t] || (v2 == sval[t] && i2 < sidx[t])) {
+          sval[t] = v2;
+          sidx[t] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (t == 0) {
+      piv = sidx[0];
+      if (!(sval[0] > 0.0)) bad = 1;
+    }
+    __syncthreads();
+    int p = piv;
+    if (p != k && p < N) {
+      for (int j = t; j < N; j += nt) {
+        double x = A[k * N + j];
+        A[k * N + j] = A[p * N + j];
+        A[p * N + j] = x;
+      }
+      if (t == 0) {
+        int x = sperm[k];
+        sperm[k] = sperm[p];
+        sperm[p] = x;
+      }
+    }
+    __syncthreads();
+    double akk = A[k * N + k];
+    for (int i = k + 1 + t; i < N; i += nt) A[i * N + k] /= akk;
+    __syncthreads();
+    int m = N - k - 1;
+    for (int e = t; e < m * m; e += nt) {
+      int i = k + 1 + e / m, j = k + 1 + e % m;
+      A[i * N + j] -= A[i * N + k] * A[k * N + j];
+    }
+    __syncthreads();
+  }
+  if (t < N) {  // column t of the inverse: L U y = P e_t
+    int j = t;
+    for (int i = 0; i < N; ++i) {  // forward, unit lower; (P e_j)_i = [perm_i == j]
+      double v = sperm[i] == j ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= A[i * N + k] * Y[k * N + j];
+      Y[i * N + j] = v;
+    }
+    for (int i = N - 1; i >= 0; --i) {  // backward
+      double v = Y[i * N + j];
+      for (int k = i + 1; k < N; ++k) v -= A[i * N + k] * Y[k * N + j];
+      Y[i * N + j] = v / A[i * N + i];
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < N * N; e += nt) ainv[e] = Y[(e % N) * N + e / N];  // column-major
+  for (int i = t; i < N; i += nt) perm[i] = sperm[i];
+  if (t == 0) *status = bad;
+}
+
 // Columns of the inverse from the LU factors: column j solves L U x = P e_j
 // (one thread per column, the column itself as workspace), stored
 // column-major: ainv[j*N + i] = (A^{-1})_ij.

@@ -281,7 +281,7 @@ constexpr int kDotChunk = 8;
 constexpr int kCoarseBlock = 64;
 // tail levels with at most this many cells run on one CTA (see k_coarse_tail)
 constexpr int kSoloCells = 200;
-constexpr int kTailCells = 12000;  // levels at or below this size run in the cluster tail
+constexpr int kTailCells = 5000;  // levels at or below this size run in the cluster tail
 constexpr int kMaxCoarsestCells = 2048;
 
 void check_flag(ll_mg_hierarchy* H, int code) {
@@ -728,10 +728,19 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
     k_dense_from_bsr<<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val64, H->lu);
   }
   LL_LAUNCHED();
-  k_lu_factor<<<1, 1024, 0, s>>>(N, H->lu, H->perm, H->lu_status);
-  LL_LAUNCHED();
-  k_lu_inverse<<<cdiv(N, 128), 128, 0, s>>>(N, H->lu, H->perm, H->ainv);
-  LL_LAUNCHED();
+  if (N <= kLuSmemMax) {  // factor and inverse in shared memory, one block
+    int nt = 32;
+    while (nt < N) nt *= 2;
+    size_t smem = 2 * sizeof(double) * N * N;
+    LL_CU(cudaFuncSetAttribute(k_lu_invert_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lu_invert_smem<<<1, nt, smem, s>>>(N, H->lu, H->perm, H->lu_status, H->ainv);
+    LL_LAUNCHED();
+  } else {
+    k_lu_factor<<<1, 1024, 0, s>>>(N, H->lu, H->perm, H->lu_status);
+    LL_LAUNCHED();
+    k_lu_inverse<<<cdiv(N, 128), 128, 0, s>>>(N, H->lu, H->perm, H->ainv);
+    LL_LAUNCHED();
+  }
 }
 
 // singular diagonal block (level 0 or a Galerkin level) or singular coarsest

@@ -3,9 +3,11 @@ C ABI.
 
 The small grids of ``test_gpu_parity.py`` put every coarse level inside the
 cluster tail.  Here the grids are large enough that the per-class coarse
-kernels run: at 48^3 level 1 (27,648 cells) is above the tail's limit and its
-colour classes take 8 lanes per row; at 128^3 levels 1-3 run per class and
-the level-1 classes (over 20,000 rows each) take 4 lanes per row.  Tolerances
+kernels run: at 48^3 levels 1 and 2 (27,598 and 6,842 cells) are above the
+tail's limit of 5,000 cells and their colour classes take 8 lanes per row,
+and the tail runs levels 3-4 on the whole cluster; at 128^3 levels 1-4 run
+per class and the level-1 classes (over 20,000 rows each) take 4 lanes per
+row.  Tolerances
 as in ``test_gpu_parity.py``: single sweeps to 1e-12 of the largest entry, a
 V-cycle to 1e-11 relative, float64 solves to 1e-10 relative of the oracle's,
 mixed-precision solves to 1e-8 of the oracle's.
@@ -81,7 +83,7 @@ def _check_coarse_sweeps(O, G, levels):
 def test_48cube_hierarchy_and_per_class_sweeps(case48):
     grid, h, alpha, dt, m, O, G = case48
     assert G.levels == O.nlevels
-    assert O.cells(1) > 12000  # level 1 runs per colour class, outside the tail
+    assert O.cells(1) > 5000  # level 1 runs per colour class, outside the tail
     for l in range(O.nlevels - 1):
         assert np.array_equal(G.aggregates(l), O.agg(l))
         assert np.array_equal(G.colours(l + 1), O.colours(l + 1))
@@ -133,14 +135,14 @@ def test_48cube_mixed_solution_against_oracle(case48, precision):
 
 def test_128cube_per_class_sweeps_and_vcycle(case128):
     """The time-stepping workload's hierarchy: the level-1 classes take the
-    4-lane path, levels 2-3 the 8-lane path; one V-cycle through all of them
+    4-lane path, levels 2-4 the 8-lane path; one V-cycle through all of them
     and the cluster tail."""
     grid, h, alpha, dt, m, O, G = case128
     assert G.levels == O.nlevels
     assert O.cells(1) > 20000 * 4  # several level-1 classes above the 4-lane threshold
-    for l in range(1, 4):
+    for l in range(1, 5):
         assert np.array_equal(G.colours(l), O.colours(l))
-    _check_coarse_sweeps(O, G, [1, 2, 3])
+    _check_coarse_sweeps(O, G, [1, 2, 3, 4])
     r = inputs.rhs_field(*grid, seed=8).reshape(-1)
     z = torch.empty_like(_t(r))
     G.vcycle(_t(r), z)
