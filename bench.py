@@ -12,8 +12,9 @@ The default run times, in this order:
   * the headline: K float64 steps with no instrumentation (CUDA events on
     the launching stream around the K steps);
   * the same K steps with the float32 V-cycle (mixed) and with bfloat16
-    coarse operators (bf16), each from the same initial state, for the
-    mixed-vs-float64 speedup at the same true relative residual 1e-8;
+    coarse operators (bf16, the mixed-precision configuration of the
+    workload list), each from the same initial state, for the mixed-vs-
+    float64 speedup at the same true relative residual 1e-8;
   * a separate profiling pass of the float64 path (per-kind event timing) for
     the kernel breakdown and the dominant kernel's roofline;
   * end to end: steps of a pinned host field through ll_mg_step_host (the
@@ -491,8 +492,11 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "precisions": others,
-        "mixed_vs_fp64_speedup": others.get("mixed", {}).get("speedup_vs_fp64"),
-        "bf16_vs_fp64_speedup": others.get("bf16", {}).get("speedup_vs_fp64"),
+        # the mixed-precision configuration as the workload list defines it: a
+        # float32 V-cycle with bfloat16 coarse-level operators in float64 GCR
+        "mixed_vs_fp64_speedup": others.get("bf16", {}).get("speedup_vs_fp64"),
+        "mixed_config": "bf16: float32 V-cycle, bfloat16 coarse-level operators, float64 GCR",
+        "fp32_vcycle_vs_fp64_speedup": others.get("mixed", {}).get("speedup_vs_fp64"),
         "fp64_peak": {"measured_tflops": fp64_meas, "derived_tflops": FP64_PEAK_TFLOPS,
                       "probe": "ll_fp64_fma_probe: 1184 blocks x 256 threads x 8 chains x 8192 FMA, best of 5"},
         "kernel_breakdown_ms_per_step": {k: round(v[0] / prof_steps, 3) for k, v in breakdown.items()},

@@ -345,16 +345,13 @@ __global__ void k_lu_factor(int N, double* __restrict__ a, int* __restrict__ per
   }
 }
 
-// Coarsest levels of up to kLuSmemMax unknowns: the factorisation and the
-// inverse in one block, entirely in shared memory (the matrix and the
-// inverse's columns, 2 N^2 doubles), the same operations in the same order as
-// k_lu_factor followed by k_lu_inverse.  blockDim.x: a power of two >= N.
-constexpr int kLuSmemMax = 112;
-__global__ void k_lu_invert_smem(int N, const double* __restrict__ a, int* __restrict__ perm,
-                                 int* __restrict__ status, double* __restrict__ ainv) {
-  extern __shared__ double sm[];
-  double* A = sm;          // row-major N x N, factored in place
-  double* Y = sm + N * N;  // Y[k * N + j]: entry k of column j of the inverse
+// Coarsest levels of up to kLuSmemMax unknowns: the factorisation in one
+// block in shared memory, the same operations in the same order as
+// k_lu_factor; the factors go back to a for k_lu_inverse_warp.
+// blockDim.x: a power of two >= N, at most 128.
+constexpr int kLuSmemMax = 128;
+__global__ void k_lu_factor_smem(int N, double* __restrict__ a, int* __restrict__ perm, int* __restrict__ status) {
+  extern __shared__ double A[];  // row-major N x N, factored in place
   __shared__ double sval[128];
   __shared__ int sidx[128];
   __shared__ int sperm[kLuSmemMax];
@@ -418,23 +415,35 @@ __global__ void k_lu_invert_smem(int N, const double* __restrict__ a, int* __res
     }
     __syncthreads();
   }
-  if (t < N) {  // column t of the inverse: L U y = P e_t
-    int j = t;
-    for (int i = 0; i < N; ++i) {  // forward, unit lower; (P e_j)_i = [perm_i == j]
-      double v = sperm[i] == j ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) v -= A[i * N + k] * Y[k * N + j];
-      Y[i * N + j] = v;
-    }
-    for (int i = N - 1; i >= 0; --i) {  // backward
-      double v = Y[i * N + j];
-      for (int k = i + 1; k < N; ++k) v -= A[i * N + k] * Y[k * N + j];
-      Y[i * N + j] = v / A[i * N + i];
-    }
-  }
-  __syncthreads();
-  for (int e = t; e < N * N; e += nt) ainv[e] = Y[(e % N) * N + e / N];  // column-major
+  for (int e = t; e < N * N; e += nt) a[e] = A[e];
   for (int i = t; i < N; i += nt) perm[i] = sperm[i];
   if (t == 0) *status = bad;
+}
+
+// Columns of the inverse from the LU factors, one warp per column j (grid of
+// N blocks of 32 threads): L U y = P e_j by forward and backward
+// substitution, each row's dot product split over the lanes and summed by
+// shuffles; y in shared memory.  Stored column-major: ainv[j*N + i].
+__global__ void __launch_bounds__(32) k_lu_inverse_warp(int N, const double* __restrict__ a,
+                                                        const int* __restrict__ perm, double* __restrict__ ainv) {
+  __shared__ double y[kLuSmemMax];
+  int j = blockIdx.x, lane = threadIdx.x;
+  if (j >= N) return;
+  for (int i = 0; i < N; ++i) {  // forward, unit lower; (P e_j)_i = [perm_i == j]
+    double v = 0.0;
+    for (int k = lane; k < i; k += 32) v += a[(long)i * N + k] * y[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) y[i] = (perm[i] == j ? 1.0 : 0.0) - v;
+    __syncwarp();
+  }
+  for (int i = N - 1; i >= 0; --i) {  // backward
+    double v = 0.0;
+    for (int k = i + 1 + lane; k < N; k += 32) v += a[(long)i * N + k] * y[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) y[i] = (y[i] - v) / a[(long)i * N + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < N; i += 32) ainv[(long)j * N + i] = y[i];
 }
 
 // Columns of the inverse from the LU factors: column j solves L U x = P e_j

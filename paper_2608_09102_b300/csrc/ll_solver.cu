@@ -728,12 +728,14 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
     k_dense_from_bsr<<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val64, H->lu);
   }
   LL_LAUNCHED();
-  if (N <= kLuSmemMax) {  // factor and inverse in shared memory, one block
+  if (N <= kLuSmemMax) {  // factor in shared memory (one block), then one warp per column of the inverse
     int nt = 32;
     while (nt < N) nt *= 2;
-    size_t smem = 2 * sizeof(double) * N * N;
-    LL_CU(cudaFuncSetAttribute(k_lu_invert_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lu_invert_smem<<<1, nt, smem, s>>>(N, H->lu, H->perm, H->lu_status, H->ainv);
+    size_t smem = sizeof(double) * N * N;
+    LL_CU(cudaFuncSetAttribute(k_lu_factor_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lu_factor_smem<<<1, nt, smem, s>>>(N, H->lu, H->perm, H->lu_status);
+    LL_LAUNCHED();
+    k_lu_inverse_warp<<<N, 32, 0, s>>>(N, H->lu, H->perm, H->ainv);
     LL_LAUNCHED();
   } else {
     k_lu_factor<<<1, 1024, 0, s>>>(N, H->lu, H->perm, H->lu_status);
