@@ -20,6 +20,9 @@ The default run times, in this order:
   * end to end: steps of a pinned host field through ll_mg_step_host (the
     library copies it in and out on its stream every step);
   * the float64 multiply-add probe (the measured float64 peak);
+  * one compact measurement of each other workload of the list
+    (other_workloads: the 64^2 solve, the 256^2 x 128 random-unit-vector
+    solves, the 512-instance batch, the 96^3 gradient);
   * the CPU oracle on a bounded sample (cpu_baseline).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -515,9 +518,114 @@ def run_ours(args):
                 "api": "ll_mg_step_host (pinned host field, copies inside the library), the timed K steps again "
                        "from the same state, host wall clock"},
     }
+    if not args.no_other_workloads:
+        line["other_workloads"] = other_workloads(ll, torch, inputs, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the other workloads of the list, measured compactly in the default run
+# ---------------------------------------------------------------------------
+TUNING_CACHE = os.path.join(ROOT, "paper_2608_09102_b300", "tuning", "batch512_mixed.txt")
+
+
+def _event_ms(torch, fn):
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def other_workloads(ll, torch, inputs, dev):
+    """One compact measurement of each other workload of the list (device
+    time by CUDA events on the current stream; every call synchronises):
+    the 64^2 solve against a dense-LU-sized problem, the 256^2 x 128 random
+    unit vectors with the mixed configuration (K-cycle on level 1), the
+    512-instance ragged batch with the autotuner's stored choices, and the
+    96^3 gradient."""
+    out = {}
+    # configuration 1: 2-D 64^2, alpha 0.1, dt 1e-3, one solve to 1e-10
+    g1 = (64, 64, 1)
+    m1 = torch.tensor(inputs.smooth_field(*g1, seed=0).reshape(-1), device=dev)
+    H1 = ll.Hierarchy(m1, 0.1, 1e-3, 1 / 64, g1, ll.Params(rtol=1e-10))
+    b1 = m1 / 1e-3
+    x1 = torch.zeros_like(b1)
+    H1.solve(b1, x1)
+    x1.zero_()
+    ms, (st, it, rr) = _event_ms(torch, lambda: H1.solve(b1, x1))
+    out["config1_64x64"] = {"ms_per_solve": ms, "iterations": it, "relres": rr, "status": st,
+                            "unknown_solves_per_s": 3 * 64 * 64 / (ms * 1e-3)}
+    # configuration 3: 256 x 256 x 128 random unit vectors, h 1/256, dt 1e-4
+    g3 = (256, 256, 128)
+    m3 = torch.tensor(inputs.random_sphere(*g3, seed=0).reshape(-1), device=dev)
+    b3 = m3 / 1e-4
+    c3 = {}
+    for alpha in (0.01, 0.1, 1.0):
+        H3 = ll.Hierarchy(m3, alpha, 1e-4, 1 / 256, g3, ll.Params(rtol=1e-8, kcycle=1, precision=ll.LL_MIXED_BF16))
+        x3 = torch.zeros_like(b3)
+        H3.solve(b3, x3)
+        x3.zero_()
+        ms, (st, it, rr) = _event_ms(torch, lambda: H3.solve(b3, x3))
+        c3["alpha_%g" % alpha] = {"ms_per_solve": ms, "iterations": it, "relres": rr, "status": st,
+                                  "unknown_solves_per_s": 3 * 256 * 256 * 128 / (ms * 1e-3)}
+        del H3, x3
+    out["config3_256x256x128_mixed_kcycle1"] = c3
+    del m3, b3
+    torch.cuda.empty_cache()
+    # configuration 4: the ragged batch, stored autotuner choices
+    spec = inputs.batch_instances(BATCH_COUNT, seed=0)
+    ms4 = [torch.tensor(inputs.smooth_field(*q["grid"], seed=q["seed"]).reshape(-1), device=dev) for q in spec]
+    al, dts = [q["alpha"] for q in spec], [q["dt"] for q in spec]
+    hs, grids = [q["h"] for q in spec], [q["grid"] for q in spec]
+    base = ll.Params(rtol=RTOL, precision=ll.LL_MIXED_FP32, maxit=300)
+    with tempfile.TemporaryDirectory() as td:  # a copy: the stored file is never rewritten
+        cache = os.path.join(td, "tune.txt")
+        with open(TUNING_CACHE) as f, open(cache, "w") as g:
+            g.write(f.read())
+        per, tuned = ll.autotune(ms4, al, dts, hs, grids, base=base, cache_path=cache)
+    B = ll.Batch(ms4, al, dts, hs, grids, per)
+    rhs = [m / d for m, d in zip(ms4, dts)]
+    xs = [torch.zeros_like(m) for m in ms4]
+
+    def bstep():
+        B.update(ms4, al, dts)
+        for x in xs:
+            x.zero_()
+        return B.solve(rhs, xs)
+
+    bstep()
+    ms, (st, its, rrs, sts) = _event_ms(torch, lambda: [bstep() for _ in range(2)][-1])
+    conv = sum(1 for v in sts if v == ll.LL_OK)
+    solved = 3 * sum(int(np.prod(q["grid"])) for q, v in zip(spec, sts) if v == ll.LL_OK)
+    out["config4_batch512_mixed_autotuned"] = {"ms_per_step": ms / 2, "converged": conv, "instances": len(spec),
+                                              "classes_tuned_now": tuned, "groups": B.groups,
+                                              "converged_unknown_solves_per_s": solved / (ms / 2 * 1e-3)}
+    del B, ms4, rhs, xs
+    torch.cuda.empty_cache()
+    # configuration 5: the 96^3 gradient (20 steps, checkpoints every 5)
+    g5, n5 = (96, 96, 96), 96 ** 3
+    m0 = torch.tensor(inputs.smooth_field(*g5, seed=0).reshape(-1), device=dev)
+    mt = torch.tensor(inputs.smooth_field(*g5, seed=1).reshape(-1), device=dev)
+
+    def grad():
+        m = m0.clone().requires_grad_(True)
+        a = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+        mN = ll.steps_autograd(m, a, 20, 1e-3, 1 / 96, g5, ll.Params(rtol=RTOL), checkpoint=5)
+        loss = 0.5 * torch.sum((mN - mt) ** 2)
+        loss.backward()
+        return float(loss.detach())
+
+    grad()
+    ms, loss = _event_ms(torch, grad)
+    out["config5_grad96_fp64"] = {"ms_per_gradient": ms, "loss": loss,
+                                  "unknown_solves_per_s": 60 * 3 * n5 / (ms * 1e-3)}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -697,6 +805,8 @@ def main():
                     help="coarse levels 1..K solved by two inner GCR steps (K-cycle); 0 = V-cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="time only the --precision path")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the compact measurements of the other workloads of the list")
     ap.add_argument("--workload", choices=["step128", "batch512", "grad96"], default="step128",
                     help="step128: the 128^3 time-stepping workload; batch512: the ragged batch; "
                          "grad96: the 96^3 differentiation workload")
