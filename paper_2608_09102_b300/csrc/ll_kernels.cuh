@@ -1028,7 +1028,14 @@ __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const in
 }
 
 
-template <typename T, typename TM, int G, int MODE>
+// PDL: launched as a programmatic dependent of the kernel before it (the
+// float32 sweeps, which are latency-bound): the row's block range is loaded
+// and its read-only operator data prefetched into L1 while that kernel may
+// still be finishing; griddepcontrol.wait then waits for its writes (x, b)
+// before the row reads them.  Nothing launched in the same graph or stream
+// writes the operator, whose values come from the numeric setup, which the
+// host waits for.
+template <typename T, typename TM, int G, int MODE, bool PDL = false>
 __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
                                                 const int* __restrict__ diag, const int* __restrict__ col,
                                                 const TM* __restrict__ val, const T* __restrict__ dinv,
@@ -1042,6 +1049,19 @@ __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __res
     p0 = ro(rowptr + I);
     pd = ro(diag + I);
     p1 = MODE == 0 ? 0 : ro(rowptr + I + 1);
+  }
+  if (PDL) {
+    if (active) {
+      int lane = threadIdx.x % G, pe = MODE == 0 ? pd : p1;
+      for (int q = p0 + lane; q < pe; q += G) {
+        const char* v = (const char*)(val + 9L * q);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(col + q));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(v));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(v + 9 * sizeof(TM) - 1));
+      }
+      if (lane < 3) asm volatile("prefetch.global.L1 [%0];" ::"l"(dinv + 9L * I + 3 * lane));
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
   }
   sweep_row_at<T, TM, G, MODE>(I, threadIdx.x % G, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
 }
