@@ -12,15 +12,16 @@ The default run times, in this order:
   * the headline: K float64 steps with no instrumentation (CUDA events on
     the launching stream around the K steps);
   * the same K steps with the float32 V-cycle (mixed) and with bfloat16
-    coarse operators (bf16, the mixed-precision configuration of the
-    workload list), each from the same initial state, for the mixed-vs-
-    float64 speedup at the same true relative residual 1e-8;
+    coarse operators (bf16, the mixed-precision configuration: float32
+    V-cycle, bfloat16 coarse levels, float64 GCR), each from the same
+    initial state, for the mixed-vs-float64 speedup at the same true
+    relative residual 1e-8;
   * a separate profiling pass of the float64 path (per-kind event timing) for
     the kernel breakdown and the dominant kernel's roofline;
   * end to end: steps of a pinned host field through ll_mg_step_host (the
     library copies it in and out on its stream every step);
   * the float64 multiply-add probe (the measured float64 peak);
-  * one compact measurement of each other workload of the list
+  * one compact measurement of each of the other workloads
     (other_workloads: the 64^2 solve, the 256^2 x 128 random-unit-vector
     solves, the 512-instance batch, the 96^3 gradient);
   * the CPU oracle on a bounded sample (cpu_baseline).
@@ -495,8 +496,8 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "precisions": others,
-        # the mixed-precision configuration as the workload list defines it: a
-        # float32 V-cycle with bfloat16 coarse-level operators in float64 GCR
+        # the mixed-precision configuration: a float32 V-cycle with bfloat16
+        # coarse-level operators inside float64 GCR
         "mixed_vs_fp64_speedup": others.get("bf16", {}).get("speedup_vs_fp64"),
         "mixed_config": "bf16: float32 V-cycle, bfloat16 coarse-level operators, float64 GCR",
         "fp32_vcycle_vs_fp64_speedup": others.get("mixed", {}).get("speedup_vs_fp64"),
@@ -526,7 +527,7 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
-# the other workloads of the list, measured compactly in the default run
+# the other workloads, measured compactly in the default run
 # ---------------------------------------------------------------------------
 TUNING_CACHE = os.path.join(ROOT, "paper_2608_09102_b300", "tuning", "batch512_mixed.txt")
 
