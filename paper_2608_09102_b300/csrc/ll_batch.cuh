@@ -762,7 +762,7 @@ int batch_create(int count, const double* const* m, const double* alpha, const d
     ll_mg_params ip = B->prm;
     for (int i = 0; i < count; ++i) {
       ll_mg_hierarchy* H = nullptr;
-      int rc = create(m[i], alpha[i], dt[i], h[i], grids[i], &ip, nullptr, &H);
+      int rc = create(m[i], alpha[i], dt[i], h[i], grids[i], &ip, nullptr, &H, false);
       if (rc != LL_OK) throw Status{rc};
       B->inst.push_back(H);
       if (H->nlev < 2) throw Status{LL_EINVAL};  // too small to coarsen: solve it alone

@@ -507,13 +507,10 @@ __global__ void k_lu_solve(int N, const double* __restrict__ a, const int* __res
 // Block Gauss-Seidel update of the cells of colour c:
 //   x_k = Dinv_k (b_k - Chat_k S_k),  S_k = sum of the neighbours' x.
 // mode 0: neighbours are zero (first half-sweep from x = 0);
-// mode 1: plain update;
-// mode 2: neighbours are read as x_l + e[agg(l)] (prolongation of the coarse
-//         correction folded into the first half-sweep after it).
+// mode 1: plain update.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k0_smooth(GridGeom g, int c, const double* __restrict__ b, T* __restrict__ x,
-                                                 const T* __restrict__ chat, const T* __restrict__ dinv,
-                                                 const int* __restrict__ agg, const T* __restrict__ e) {
+                                                 const T* __restrict__ chat, const T* __restrict__ dinv) {
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= g.nh) return;
   long n2 = 2 * g.nh;
@@ -527,12 +524,6 @@ __global__ void __launch_bounds__(256) k0_smooth(GridGeom g, int c, const double
       s0 += x[l];
       s1 += x[n2 + l];
       s2 += x[2 * n2 + l];
-      if (MODE == 2) {
-        long a = 3L * agg[l];
-        s0 += e[a];
-        s1 += e[a + 1];
-        s2 += e[a + 2];
-      }
     });
     const T* C = chat + sl;
     T c0 = ld(C), c1 = ld(C + n2), c2 = ld(C + 2 * n2), c3 = ld(C + 3 * n2), c4 = ld(C + 4 * n2),
@@ -636,8 +627,7 @@ __device__ __forceinline__ void slot_residual_after_sweep(const GridGeom& g, lon
 // (OnFly); the same operations in the same order once C and D^-1 are formed
 template <int MODE>
 __global__ void __launch_bounds__(256) k0_smooth_onfly(GridGeom g, int c, const double* __restrict__ b,
-                                                       float* __restrict__ x, OnFly q,
-                                                       const int* __restrict__ agg, const float* __restrict__ e) {
+                                                       float* __restrict__ x, OnFly q) {
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= g.nh) return;
   long n2 = 2 * g.nh;
@@ -654,12 +644,6 @@ __global__ void __launch_bounds__(256) k0_smooth_onfly(GridGeom g, int c, const 
       s0 += x[l];
       s1 += x[n2 + l];
       s2 += x[2 * n2 + l];
-      if (MODE == 2) {
-        long a = 3L * agg[l];
-        s0 += e[a];
-        s1 += e[a + 1];
-        s2 += e[a + 2];
-      }
     });
     v0 = fmaf(-C[0], s0, v0);
     v0 = fmaf(-C[1], s1, v0);
@@ -767,12 +751,14 @@ __global__ void k0_restrict_b(GridGeom g, const double* __restrict__ b, int nc, 
   bc[3L * I + 2] = a2;
 }
 
-// x_k += e[agg(k)] on all real slots (used when no post-smoothing follows)
+// x_k += e[agg(k)] on the real slots [first, first + count)
 template <typename T>
-__global__ void k0_prolong(GridGeom g, const int* __restrict__ agg, const T* __restrict__ e, T* __restrict__ x) {
-  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+__global__ void k0_prolong(GridGeom g, const int* __restrict__ agg, const T* __restrict__ e, T* __restrict__ x,
+                           long first, long count) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long n2 = 2 * g.nh;
-  if (sl >= n2) return;
+  if (i >= count) return;
+  long sl = first + i;
   int a = agg[sl];
   if (a < 0) return;
   x[sl] += e[3L * a];
@@ -867,12 +853,11 @@ __device__ __forceinline__ void block_msub(const TM* __restrict__ A, T v0, T v1,
 
 // a -= sum over the blocks p = p0, p0 + G, ... < p1 of A_p v_{col p}, with the
 // column indices of U blocks loaded first, then their x values, then the
-// products: three dependent memory round trips per U blocks instead of per
-// block.  PROL adds the coarse correction e[agg[J]] to every v.
-template <typename T, typename TM, int G, int U, bool PROL>
+// products: two dependent memory round trips per U blocks instead of per
+// block.
+template <typename T, typename TM, int G, int U>
 __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__ col, const TM* __restrict__ val,
-                                         const T* __restrict__ x, const int* __restrict__ agg,
-                                         const T* __restrict__ e, T& a0, T& a1, T& a2) {
+                                         const T* __restrict__ x, T& a0, T& a1, T& a2) {
   for (int base = p0; base < p1; base += G * U) {
     int J[U];
 #pragma unroll
@@ -884,12 +869,6 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
         v[u][0] = x[3L * J[u]];
         v[u][1] = x[3L * J[u] + 1];
         v[u][2] = x[3L * J[u] + 2];
-        if (PROL) {
-          long a = 3L * ro(agg + J[u]);
-          v[u][0] += e[a];
-          v[u][1] += e[a + 1];
-          v[u][2] += e[a + 2];
-        }
       }
     }
 #pragma unroll
@@ -901,12 +880,10 @@ __device__ __forceinline__ void row_msub(int p0, int p1, const int* __restrict__
 // a -= sum over the off-diagonal blocks of row [p0, p1) with diagonal pd, in
 // one lane-strided loop over the row's off-diagonal slots q (prefix then
 // suffix, the diagonal skipped): a row visits ceil((p1 - p0 - 1) / G) slots
-// instead of separate prefix and suffix loops.  PROL adds e[agg[J]] to the
-// prefix columns only.
-template <typename T, typename TM, int G, int U, bool PROL>
+// instead of separate prefix and suffix loops.
+template <typename T, typename TM, int G, int U>
 __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, const int* __restrict__ col,
-                                             const TM* __restrict__ val, const T* __restrict__ x,
-                                             const int* __restrict__ agg, const T* __restrict__ e, T& a0, T& a1,
+                                             const TM* __restrict__ val, const T* __restrict__ x, T& a0, T& a1,
                                              T& a2) {
   int npre = pd - p0, noff = p1 - p0 - 1;
   for (int base = lane; base < noff; base += G * U) {
@@ -924,12 +901,6 @@ __device__ __forceinline__ void row_msub_off(int p0, int pd, int p1, int lane, c
         v[u][0] = x[3L * J[u]];
         v[u][1] = x[3L * J[u] + 1];
         v[u][2] = x[3L * J[u] + 2];
-        if (PROL && base + u * G < npre) {
-          long a = 3L * ro(agg + J[u]);
-          v[u][0] += e[a];
-          v[u][1] += e[a + 1];
-          v[u][2] += e[a + 2];
-        }
       }
     }
 #pragma unroll
@@ -976,11 +947,9 @@ __device__ __forceinline__ void with_unroll(int u, F&& f) {
 // those of higher colours the suffix (diag_I, rowptr_{I+1}) (rows of one
 // colour are not coupled).  Hence
 //   MODE 0, forward sweep from x = 0: only the prefix (already updated) counts;
-//   MODE 1, plain sweep: prefix and suffix, all current;
-//   MODE 2, first backward sweep after the coarse correction e: the suffix
-//           was updated in this sweep, the prefix is read as x + e[agg] (the
-//           prolongation, never stored).
-// x_I = Dinv_I (b_I - sum_{J != I} A_IJ v_J); the lanes of a group share the
+//   MODE 1, plain sweep: prefix and suffix, all current (the coarse
+//           correction is added to x by a separate prolongation pass first).
+// x_I = Dinv_I (b_I - sum_{J != I} A_IJ x_J); the lanes of a group share the
 // three output components.  Every lane of the warp must call this (shuffles).
 // sweep_row with the row's block range already loaded: p0 = rowptr_I,
 // pd = diag_I, p1 = rowptr_{I+1}
@@ -988,9 +957,9 @@ template <typename T, typename TM, int G, int MODE, int U = 4, int USET = 7>
 __device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p0, int pd, int p1,
                                              const int* __restrict__ col, const TM* __restrict__ val,
                                              const T* __restrict__ dinv, const T* __restrict__ b,
-                                             T* __restrict__ x, const int* __restrict__ agg,
-                                             const T* __restrict__ e) {
+                                             T* __restrict__ x) {
   static_assert(G >= 3, "one lane per output component");
+  static_assert(MODE == 0 || MODE == 1, "sweep mode");
   T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, d0 = 0, d1 = 0, d2 = 0;
   // USET < 0: the fixed unroll U (the coarse tail, where the warp-uniform
   // unroll measured slower: more copies of the loop in a kernel that already
@@ -1000,8 +969,8 @@ __device__ __forceinline__ void sweep_row_at(int I, int lane, bool active, int p
   if (active)
     with_unroll<U, USET>(u, [&](auto uc) {
       constexpr int UU = decltype(uc)::value;
-      if (MODE == 0) row_msub<T, TM, G, UU, false>(p0 + lane, pd, col, val, x, agg, e, a0, a1, a2);  // prefix
-      else row_msub_off<T, TM, G, UU, MODE == 2>(p0, pd, p1, lane, col, val, x, agg, e, a0, a1, a2);
+      if (MODE == 0) row_msub<T, TM, G, UU>(p0 + lane, pd, col, val, x, a0, a1, a2);  // prefix
+      else row_msub_off<T, TM, G, UU>(p0, pd, p1, lane, col, val, x, a0, a1, a2);
     });
   if (active && lane < 3) {  // issued before the group sum, whose latency hides theirs
     b0 = b[3L * I]; b1 = b[3L * I + 1]; b2 = b[3L * I + 2];
@@ -1016,15 +985,14 @@ template <typename T, typename TM, int G, int MODE, int U = 4, int USET = 7>
 __device__ __forceinline__ void sweep_row(int I, int lane, bool active, const int* __restrict__ rowptr,
                                           const int* __restrict__ diag, const int* __restrict__ col,
                                           const TM* __restrict__ val, const T* __restrict__ dinv,
-                                          const T* __restrict__ b, T* __restrict__ x, const int* __restrict__ agg,
-                                          const T* __restrict__ e) {
+                                          const T* __restrict__ b, T* __restrict__ x) {
   int p0 = 0, pd = 0, p1 = 0;
   if (active) {
     p0 = ro(rowptr + I);
     pd = ro(diag + I);
     p1 = MODE == 0 ? 0 : ro(rowptr + I + 1);
   }
-  sweep_row_at<T, TM, G, MODE, U, USET>(I, lane, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
+  sweep_row_at<T, TM, G, MODE, U, USET>(I, lane, active, p0, pd, p1, col, val, dinv, b, x);
 }
 
 
@@ -1039,8 +1007,7 @@ template <typename T, typename TM, int G, int MODE, bool PDL = false>
 __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __restrict__ rowptr,
                                                 const int* __restrict__ diag, const int* __restrict__ col,
                                                 const TM* __restrict__ val, const T* __restrict__ dinv,
-                                                const T* __restrict__ b, T* __restrict__ x,
-                                                const int* __restrict__ agg, const T* __restrict__ e) {
+                                                const T* __restrict__ b, T* __restrict__ x) {
   long gt = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int I = r0 + (int)(gt / G);
   bool active = I < r1;
@@ -1063,7 +1030,166 @@ __global__ void __launch_bounds__(256) kb_sweep(int r0, int r1, const int* __res
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
   }
-  sweep_row_at<T, TM, G, MODE>(I, threadIdx.x % G, active, p0, pd, p1, col, val, dinv, b, x, agg, e);
+  sweep_row_at<T, TM, G, MODE>(I, threadIdx.x % G, active, p0, pd, p1, col, val, dinv, b, x);
+}
+
+// ---- SELL-32 form of a float64 coarse level (large colour classes) -------
+// Chunk c holds the rows [32c, 32c + 32) of the level; slot group g = soff[c]
+// + s holds the s-th off-diagonal block of each of the chunk's rows (prefix,
+// i.e. lower colours, first, then the suffix, each by ascending column):
+// column at scol[32 g + lane], entry k of the block at sval[(9 g + k) 32 +
+// lane], so a warp reads each entry of 32 rows' blocks as 256 contiguous
+// bytes.  A chunk has as many slot groups as its longest row has
+// off-diagonal blocks; shorter rows' slots hold column -1.
+constexpr int kSell = 32;
+
+// slot groups of each chunk: its longest row's off-diagonal block count
+__global__ void k_sell_width(int n, const int* __restrict__ rowptr, int* __restrict__ width) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c * kSell >= n) return;
+  int w = 0;
+  for (int I = c * kSell; I < min(n, (c + 1) * kSell); ++I) w = max(w, rowptr[I + 1] - rowptr[I] - 1);
+  width[c] = w;
+}
+
+// chunk of each slot group
+__global__ void k_sell_groups(int nch, const int* __restrict__ soff, int* __restrict__ sgc) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nch) return;
+  for (int g = soff[c]; g < soff[c + 1]; ++g) sgc[g] = c;
+}
+
+// BSR block position of slot (g, lane), or -1 for a padding slot
+__device__ __forceinline__ long sell_block(long g, int lane, int n, const int* __restrict__ sgc,
+                                           const int* __restrict__ soff, const int* __restrict__ rowptr,
+                                           const int* __restrict__ diag) {
+  int c = sgc[g];
+  int I = c * kSell + lane, s = (int)(g - soff[c]);
+  if (I >= n) return -1;
+  int p0 = rowptr[I], pd = diag[I];
+  if (s >= rowptr[I + 1] - p0 - 1) return -1;
+  return p0 + s + (s >= pd - p0 ? 1 : 0);
+}
+
+// columns of the slots (symbolic setup), one thread per slot
+__global__ void k_sell_cols(long groups, int n, const int* __restrict__ sgc, const int* __restrict__ soff,
+                            const int* __restrict__ rowptr, const int* __restrict__ diag, const int* __restrict__ col,
+                            int* __restrict__ scol) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= groups * kSell) return;
+  long p = sell_block(t / kSell, (int)(t % kSell), n, sgc, soff, rowptr, diag);
+  scol[t] = p < 0 ? -1 : col[p];
+}
+
+// block values of the slots (numeric setup, after the Galerkin product),
+// one thread per slot: reads its block's 72 bytes, writes 9 coalesced rows
+__global__ void k_sell_values(long groups, int n, const int* __restrict__ sgc, const int* __restrict__ soff,
+                              const int* __restrict__ rowptr, const int* __restrict__ diag,
+                              const double* __restrict__ val, double* __restrict__ sval) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= groups * kSell) return;
+  long g = t / kSell;
+  int lane = (int)(t % kSell);
+  long p = sell_block(g, lane, n, sgc, soff, rowptr, diag);
+  double* dst = sval + 9 * g * kSell + lane;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dst[k * kSell] = p < 0 ? 0.0 : val[9 * p + k];
+}
+
+// Block Gauss-Seidel update of the rows [r0, r1) of one colour class of a
+// SELL-32 float64 level, modes 0 (forward sweep from zero: prefix only) and 1
+// (plain sweep) of sweep_row_at, with G = 1, 2 or 4 lanes per row.  The
+// float64 pipe (2 multiply-adds per clock per SM here) bounds the large
+// classes, and masked-off float64 instructions cost it as much as live ones:
+// with one lane per row there is no group sum and no idle slot, since rows
+// within a class are ordered by their exact prefix and off-diagonal counts
+// and the 32 rows of a chunk visit nearly the same number of slots.  Two
+// lanes per row shorten each row's chain of loads for the longer full rows.
+// U slots per lane are loaded before their multiply-adds, and the next
+// slots' columns are in flight during them.
+template <int MODE, int G, int U>
+__global__ void __launch_bounds__(128) ks_sweep(int r0, int r1, const int* __restrict__ rowptr,
+                                                const int* __restrict__ diag, const int* __restrict__ soff,
+                                                const int* __restrict__ scol, const double* __restrict__ sval,
+                                                const double* __restrict__ dinv, const double* __restrict__ b,
+                                                double* __restrict__ x) {
+  static_assert(G == 1 || G == 2 || G == 4, "lanes per row");
+  static_assert(MODE == 0 || MODE == 1, "the prolongation is a separate pass on these levels");
+  // warp w covers rows [(w % G) 32/G, +32/G) of chunk w / G, counted from the
+  // class's first chunk; lane L takes row L / G of those and the slots h,
+  // h + G, h + 2G, ... with h = L % G
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int w = (int)(t / 32), L = (int)(t % 32), h = L % G;
+  int crow = (w % G) * (32 / G) + L / G;
+  int I = (r0 & ~(kSell - 1)) + (w / G) * kSell + crow;
+  bool active = I >= r0 && I < r1;
+  if (G == 1 && !active) return;  // no shuffles below when G == 1
+  int n = 0;
+  long g0 = 0;
+  if (active) {
+    int p0 = ro(rowptr + I);
+    n = MODE == 0 ? ro(diag + I) - p0 : ro(rowptr + I + 1) - p0 - 1;
+    g0 = ro(soff + I / kSell);
+  }
+  const int* cp = scol + g0 * kSell + crow;
+  const double* vp = sval + 9 * g0 * kSell + crow;
+  double a0 = 0, a1 = 0, a2 = 0;
+  // columns of the lane's slots j, ..., j + U - 1 (-1 past the row's end)
+  auto cols = [&](int j, int (&J)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int q = G * (j + u) + h;
+      J[u] = q < n ? ro(cp + (long)q * kSell) : -1;
+    }
+  };
+  int Jn[U];
+  cols(0, Jn);
+  for (int j = 0; G * j + h < n; j += U) {
+    int J[U];
+    double v[U][3], A[U][9];
+#pragma unroll
+    for (int u = 0; u < U; ++u) J[u] = Jn[u];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (J[u] >= 0) {
+        v[u][0] = x[3L * J[u]];
+        v[u][1] = x[3L * J[u] + 1];
+        v[u][2] = x[3L * J[u] + 2];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (J[u] >= 0) {
+        long q = G * (j + u) + h;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) A[u][k] = ro(vp + (9 * q + k) * kSell);
+      }
+    cols(j + U, Jn);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (J[u] >= 0) {
+        a0 = fma(-A[u][0], v[u][0], a0);
+        a0 = fma(-A[u][1], v[u][1], a0);
+        a0 = fma(-A[u][2], v[u][2], a0);
+        a1 = fma(-A[u][3], v[u][0], a1);
+        a1 = fma(-A[u][4], v[u][1], a1);
+        a1 = fma(-A[u][5], v[u][2], a1);
+        a2 = fma(-A[u][6], v[u][0], a2);
+        a2 = fma(-A[u][7], v[u][1], a2);
+        a2 = fma(-A[u][8], v[u][2], a2);
+      }
+  }
+#pragma unroll
+  for (int m = G / 2; m >= 1; m /= 2) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, m);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, m);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, m);
+  }
+  if (!active || h != 0) return;
+  double t0 = b[3L * I] + a0, t1 = b[3L * I + 1] + a1, t2 = b[3L * I + 2] + a2;
+  const double* D = dinv + 9L * I;
+  x[3L * I] = ro(D) * t0 + ro(D + 1) * t1 + ro(D + 2) * t2;
+  x[3L * I + 1] = ro(D + 3) * t0 + ro(D + 4) * t1 + ro(D + 5) * t2;
+  x[3L * I + 2] = ro(D + 6) * t0 + ro(D + 7) * t1 + ro(D + 8) * t2;
 }
 
 // residual_row with the row's block range [p0, p1) already loaded
@@ -1078,7 +1204,7 @@ __device__ __forceinline__ void residual_row_at(int I, int lane, bool active, in
   if (active) {
     if (!SUFFIX && lane < 3) bc = b[3L * I + lane];
     with_unroll<U, USET>(u, [&](auto uc) {
-      row_msub<T, TM, G, decltype(uc)::value, false>(p0 + lane, p1, col, val, x, nullptr, nullptr, a0, a1, a2);
+      row_msub<T, TM, G, decltype(uc)::value>(p0 + lane, p1, col, val, x, a0, a1, a2);
     });
   }
   group_sum3<G>(a0, a1, a2);
@@ -1243,7 +1369,7 @@ __global__ void __launch_bounds__(256) kb_spmv(int n, const int* __restrict__ ro
   int u = warp_unroll<4>(active ? lane_slots<G>(p1 - p0, lane) : 0);
   if (active)
     with_unroll<4, 7>(u, [&](auto uc) {
-      row_msub<T, TM, G, decltype(uc)::value, false>(p0 + lane, p1, col, val, x, nullptr, nullptr, a0, a1, a2);
+      row_msub<T, TM, G, decltype(uc)::value>(p0 + lane, p1, col, val, x, a0, a1, a2);
     });
   group_sum3<G>(a0, a1, a2);
   if (active)

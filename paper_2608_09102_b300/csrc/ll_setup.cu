@@ -577,78 +577,88 @@ int colour_graph(const DevGraph& g, uint32_t seed, int* colour, cudaStream_t s) 
   return ncol;
 }
 
-// Row-work key of a coarse row: the number of kRowLanes-wide block slots its
-// forward sweep visits (neighbours of lower colour) and its backward sweep
-// visits (all neighbours), 16 x ceil(pre / lanes) + ceil(deg / lanes), each
-// capped at 15.  Rows of one colour class are ordered by this key, so the
-// rows that share a warp in the sweeps need the same number of slots and few
-// float64 lanes idle.
+// Row-work key of a coarse row, by which the rows of one colour class are
+// ordered so that the rows sharing a warp in the sweeps need the same number
+// of block slots and few float64 lanes idle:
+//  * bucketed (the per-class kernels with kRowLanes or 8 lanes per row):
+//    16 x ceil(pre / kRowLanes) + ceil(deg / kRowLanes), each capped at 15;
+//  * exact (the one-row-per-thread SELL-32 sweeps, where a chunk of 32 rows
+//    visits as many slots as its longest row): 32 x min(pre, 31) + min(deg, 31);
+// pre = neighbours of lower colour (the forward sweep's blocks), deg = all
+// neighbours (the backward sweep's).
 __global__ void k_row_work_keys(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                const int* __restrict__ colour, int* __restrict__ key) {
+                                const int* __restrict__ colour, int exact, int* __restrict__ key) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int pre = 0, deg = rp[i + 1] - rp[i];
   for (int p = rp[i]; p < rp[i + 1]; ++p) pre += colour[ci[p]] < colour[i];
+  if (exact) {
+    key[i] = 32 * min(pre, 31) + min(deg, 31);
+    return;
+  }
   int sp = min((pre + kRowLanes - 1) / kRowLanes, 15), sd = min((deg + kRowLanes - 1) / kRowLanes, 15);
   key[i] = 16 * sp + sd;
 }
 
-void row_work_keys(const DevGraph& g, const int* colour, DBuf<int>& key, cudaStream_t s) {
+void row_work_keys(const DevGraph& g, const int* colour, bool exact, DBuf<int>& key, cudaStream_t s) {
   key.alloc(g.n);
-  k_row_work_keys<<<cdiv(g.n, kBlock), kBlock, 0, s>>>(g.n, g.rowptr, g.col, colour, key);
+  k_row_work_keys<<<cdiv(g.n, kBlock), kBlock, 0, s>>>(g.n, g.rowptr, g.col, colour, exact ? 1 : 0, key);
   LL_LAUNCHED();
 }
 
-__global__ void k_class_hist(int n, const int* __restrict__ colour, const int* __restrict__ key, int nkeys,
-                             int* __restrict__ hist) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicAdd(&hist[colour[i] * nkeys + key[i]], 1);  // counts only: order-independent
+// Stable counting sort of the rows by bucket b = colour * nkeys + key, in
+// tiles of kSortTile rows: counts per (bucket, tile), one exclusive scan in
+// bucket-major order, then every row goes to its bucket's offset for its tile
+// plus its rank among the earlier rows of its tile in the same bucket.
+constexpr int kSortTile = 1024;
+__global__ void k_tile_counts(int n, const int* __restrict__ colour, const int* __restrict__ key, int nkeys,
+                              int ntiles, int* __restrict__ cnt) {
+  int i = blockIdx.x * kSortTile + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[(long)(colour[i] * nkeys + key[i]) * ntiles + blockIdx.x], 1);  // counts only
 }
-__global__ void k_eq_flag(int n, const int* __restrict__ v, int c, const int* __restrict__ key, int k,
-                          int* __restrict__ flag) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) flag[i] = (v[i] == c && key[i] == k) ? 1 : 0;
+__global__ void __launch_bounds__(kSortTile) k_tile_scatter(int n, const int* __restrict__ colour,
+                                                            const int* __restrict__ key, int nkeys, int ntiles,
+                                                            const int* __restrict__ off, int* __restrict__ out) {
+  __shared__ int bk[kSortTile];
+  int i = blockIdx.x * kSortTile + threadIdx.x;
+  int b = i < n ? colour[i] * nkeys + key[i] : -1;
+  bk[threadIdx.x] = b;
+  __syncthreads();
+  if (i >= n) return;
+  int rank = 0;
+  for (int j = 0; j < (int)threadIdx.x; ++j) rank += bk[j] == b;
+  out[off[(long)b * ntiles + blockIdx.x] + rank] = i;
 }
-__global__ void k_scatter_class(int n, const int* __restrict__ flag, const int* __restrict__ pos, int base,
-                                int* __restrict__ out) {
+__global__ void k_colour_counts(int n, const int* __restrict__ colour, int* __restrict__ cnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && flag[i]) out[base + pos[i]] = i;
+  if (i < n) atomicAdd(&cnt[colour[i]], 1);  // counts only: order-independent
 }
 
-// rows of each colour, crow[cptr[c] .. cptr[c+1]), ordered by (key, index):
-// a stable, deterministic bucket order built from one scan per non-empty
-// (colour, key) bucket
+// rows of each colour, crow[cptr[c] .. cptr[c+1]), ordered by (key, index)
 void colour_classes(int n, const int* colour, int ncol, const int* key, int nkeys, DBuf<int>& cptr, DBuf<int>& crow,
                     std::vector<int>& h_cptr, cudaStream_t s) {
-  DBuf<int> flag, pos, hist;
-  flag.alloc(n);
-  pos.alloc(n + 1);
+  int ntiles = cdiv(n, kSortTile);
+  long nb = (long)ncol * nkeys * ntiles;
+  if (nb >= (1L << 31) - 1) throw Status{LL_ELIMIT};
+  DBuf<int> cnt, off, ccnt;
+  cnt.alloc(nb);
+  off.alloc(nb + 1);
+  ccnt.alloc(ncol);
   crow.alloc(n);
-  hist.alloc((long)ncol * nkeys);
-  LL_CU(cudaMemsetAsync(hist.p, 0, (size_t)ncol * nkeys * sizeof(int), s));
-  int nb = cdiv(n, kBlock);
-  k_class_hist<<<nb, kBlock, 0, s>>>(n, colour, key, nkeys, hist);
+  cnt.zero(s);
+  ccnt.zero(s);
+  k_tile_counts<<<ntiles, kSortTile, 0, s>>>(n, colour, key, nkeys, ntiles, cnt);
   LL_LAUNCHED();
-  std::vector<int> h_hist((size_t)ncol * nkeys);
-  LL_CU(cudaMemcpyAsync(h_hist.data(), hist.p, h_hist.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (exclusive_scan(cnt, off, (int)nb, s) != n) throw Status{LL_ECUDA};
+  k_tile_scatter<<<ntiles, kSortTile, 0, s>>>(n, colour, key, nkeys, ntiles, off, crow);
+  LL_LAUNCHED();
+  k_colour_counts<<<cdiv(n, kBlock), kBlock, 0, s>>>(n, colour, ccnt);
+  LL_LAUNCHED();
+  std::vector<int> h_cnt(ncol);
+  LL_CU(cudaMemcpyAsync(h_cnt.data(), ccnt.p, ncol * sizeof(int), cudaMemcpyDeviceToHost, s));
   LL_CU(cudaStreamSynchronize(s));
   h_cptr.assign(ncol + 1, 0);
-  int base = 0;
-  for (int c = 0; c < ncol; ++c) {
-    for (int k = 0; k < nkeys; ++k) {
-      int cnt = h_hist[(size_t)c * nkeys + k];
-      if (cnt == 0) continue;
-      k_eq_flag<<<nb, kBlock, 0, s>>>(n, colour, c, key, k, flag);
-      LL_LAUNCHED();
-      int got = exclusive_scan(flag, pos, n, s);
-      if (got != cnt) throw Status{LL_ECUDA};
-      k_scatter_class<<<nb, kBlock, 0, s>>>(n, flag, pos, base, crow);
-      LL_LAUNCHED();
-      base += cnt;
-    }
-    h_cptr[c + 1] = base;
-  }
-  LL_CU(cudaStreamSynchronize(s));
+  for (int c = 0; c < ncol; ++c) h_cptr[c + 1] = h_cptr[c] + h_cnt[c];
   cptr.alloc(ncol + 1);
   LL_CU(cudaMemcpyAsync(cptr.p, h_cptr.data(), (ncol + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   LL_CU(cudaStreamSynchronize(s));

@@ -13,8 +13,9 @@ void contract_graph(const DevGraph& g, const int* map, int nc, const int* mptr, 
                     cudaStream_t s);
 int aggregate_level(const DevGraph& g, int rounds, uint32_t seed, int* agg, cudaStream_t s);
 int colour_graph(const DevGraph& g, uint32_t seed, int* colour, cudaStream_t s);
-constexpr int kRowKeys = 256;  // distinct row-work keys (see row_work_keys)
-void row_work_keys(const DevGraph& g, const int* colour, DBuf<int>& key, cudaStream_t s);
+constexpr int kRowKeys = 256;        // distinct bucketed row-work keys (see row_work_keys)
+constexpr int kRowKeysExact = 1024;  // distinct exact row-work keys
+void row_work_keys(const DevGraph& g, const int* colour, bool exact, DBuf<int>& key, cudaStream_t s);
 void colour_classes(int n, const int* colour, int ncol, const int* key, int nkeys, DBuf<int>& cptr, DBuf<int>& crow,
                     std::vector<int>& h_cptr, cudaStream_t s);
 void bsr_pattern(const DevGraph& g, DBuf<int>& rowptr, DBuf<int>& col, DBuf<int>& diag, int& nnzb, cudaStream_t s);

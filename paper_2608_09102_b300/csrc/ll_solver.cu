@@ -54,6 +54,13 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   std::vector<long long> pre_blk, off_blk;  // per colour class: prefix / off-diagonal blocks
   long long res_blk = 0;                    // blocks the residual reads (rows before the last colour)
   DBuf<double> val64, dinv64;
+  // SELL-32 copy of the off-diagonal blocks (float64 levels whose colour
+  // classes are large; the layout is described at ks_sweep)
+  bool sell = false;
+  long sgroups = 0;        // slot groups
+  DBuf<int> soff, sgc;     // slot-group offset of each chunk; chunk of each slot group
+  DBuf<int> scol;          // column of each slot (-1: padding)
+  DBuf<double> sval;       // block entries of each slot
   DBuf<float> val32, dinv32;
   DBuf<__nv_bfloat16> val16;        // bfloat16 storage of the operator (LL_MIXED_BF16)
   DBuf<double> x64, b64, r64;
@@ -103,6 +110,7 @@ struct ll_mg_hierarchy {
   DBuf<double> chat64, dinv64;
   DBuf<float> chat32, dinv32;
   DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
+  bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
   CLevel lev[kMaxLevels];
   // coarsest dense LU and its inverse (column-major)
   int ncoarse3 = 0;
@@ -288,6 +296,24 @@ template <> constexpr int lanes<float>() { return 2 * kRowLanes; }
 // long as one row's chain of dependent loads; 8 lanes per row then halve the
 // chain in float64 too (issue slots are not the limit there).
 constexpr int kWideLaneRows = 20000;
+// SELL-32 sweeps: float64 levels whose average colour class has at least
+// kSellLevelClass rows keep a SELL-32 copy, and their classes of at least
+// kSellMinRows rows sweep on it with 1, 2 or 4 lanes per row (sell_lanes)
+constexpr int kSellLevelClass = 20000;
+constexpr int kSellMinRows = 20000;
+constexpr int kSellRows1 = 40000, kSellRows2 = 8000;
+constexpr int kSellBlock = 128;
+constexpr int kSellUnroll = 2;
+// lanes per row of a SELL-32 sweep of a class of `rows` rows: few lanes keep
+// the float64 pipe busy with useful multiply-adds (no idle slots, no group
+// sum); more lanes shorten each row's chain where the class is too small to
+// fill the GPU with one-lane rows
+template <int MODE>
+int sell_lanes(long rows) {
+  if (rows >= kSellRows1) return MODE == 0 ? 1 : 2;
+  if (rows >= kSellRows2) return 2;
+  return 4;
+}
 template <typename T>
 bool wide_lanes(long rows) {
   return lanes<T>() >= 8 || rows < kWideLaneRows;
@@ -306,6 +332,28 @@ void check_flag(ll_mg_hierarchy* H, int code) {
   LL_CU(cudaMemcpyAsync(&v, H->flag.p, sizeof(int), cudaMemcpyDeviceToHost, H->s));
   LL_CU(cudaStreamSynchronize(H->s));
   if (v) throw Status{code};
+}
+
+// SELL-32 pattern of a level from its BSR pattern (see ks_sweep): chunk
+// widths, their offsets, the chunk of each slot group, the slots' columns
+void sell_build(CLevel& C, cudaStream_t s) {
+  int nch = cdiv(C.n, kSell);
+  DBuf<int> w;
+  w.alloc(nch);
+  k_sell_width<<<cdiv(nch, kBlock), kBlock, 0, s>>>(C.n, C.rowptr, w);
+  LL_LAUNCHED();
+  C.soff.alloc(nch + 1);
+  C.sgroups = exclusive_scan(w, C.soff, nch, s);
+  C.sgc.alloc(C.sgroups);
+  k_sell_groups<<<cdiv(nch, kBlock), kBlock, 0, s>>>(nch, C.soff, C.sgc);
+  LL_LAUNCHED();
+  C.scol.alloc(C.sgroups * kSell);
+  if (C.sgroups > 0) {
+    k_sell_cols<<<cdiv(C.sgroups * kSell, kBlock), kBlock, 0, s>>>(C.sgroups, C.n, C.sgc, C.soff, C.rowptr, C.diag,
+                                                                   C.col, C.scol);
+    LL_LAUNCHED();
+  }
+  LL_CU(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------------------
@@ -339,10 +387,12 @@ void symbolic(ll_mg_hierarchy* H) {
     C.colour.alloc(nc);
     C.ncol = colour_graph(C.graph, p.seed, C.colour, s);
     if (C.ncol < 0) throw Status{LL_ELIMIT};
+    // the SELL-32 sweeps where the average colour class is large
+    C.sell = H->sell_ok && (long)nc >= (long)kSellLevelClass * C.ncol;
     {
       DBuf<int> cptr, key;
-      row_work_keys(C.graph, C.colour, key, s);
-      colour_classes(nc, C.colour, C.ncol, key, kRowKeys, cptr, C.n2o, C.cs, s);
+      row_work_keys(C.graph, C.colour, C.sell, key, s);
+      colour_classes(nc, C.colour, C.ncol, key, C.sell ? kRowKeysExact : kRowKeys, cptr, C.n2o, C.cs, s);
     }
     C.o2n.alloc(nc);
     invert_perm(nc, C.n2o, C.o2n, s);
@@ -390,6 +440,8 @@ void symbolic(ll_mg_hierarchy* H) {
     build_members(F.n, F.agg, C.n, C.mptr, C.mem, s);
     slot_map_bsr(F.n, F.rowptr, F.col, F.agg, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, s);
   }
+  for (int l = 1; l < H->nlev; ++l)
+    if (H->lev[l].sell) sell_build(H->lev[l], s);
   LL_CU(cudaStreamSynchronize(s));
 }
 
@@ -419,6 +471,7 @@ void allocate(ll_mg_hierarchy* H) {
       C.x64.alloc(3L * C.n);
       C.b64.alloc(3L * C.n);
       C.r64.alloc(3L * C.n);
+      if (C.sell) C.sval.alloc(9L * kSell * C.sgroups);
     }
   }
   for (int l = 1; l < H->nlev - 1 && l <= H->prm.kcycle; ++l)
@@ -726,6 +779,11 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
       k_galerkin_bsr_blk<<<cdiv(C.nnzb, 128), 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx,
                                                            H->lev[l - 1].val64, C.val64, C.dinv64, H->flag);
     LL_LAUNCHED();
+    if (C.sell && C.sgroups > 0) {
+      k_sell_values<<<cdiv(C.sgroups * kSell, kBlock), kBlock, 0, s>>>(C.sgroups, C.n, C.sgc, C.soff, C.rowptr,
+                                                                        C.diag, C.val64, C.sval);
+      LL_LAUNCHED();
+    }
     if (mixed) {
       if (H->prm.precision == LL_MIXED_BF16)
         k_cast<__nv_bfloat16><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val16);
@@ -817,13 +875,29 @@ void class_work(const CLevel& L, int t, double& flops, double& bytes) {
 // one colour class of level l: rows [cs[t], cs[t+1]); timed on its own
 // unless the caller times a group of classes (timed = false)
 template <typename T, typename TM, int MODE>
-void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e, bool timed = true) {
+void sweep_class(ll_mg_hierarchy* H, int l, int t, bool timed = true) {
   CLevel& L = H->lev[l];
   int r0 = L.cs[t], r1 = L.cs[t + 1];
   if (r1 <= r0) return;
   double f = 0, by = 0;
   if (timed) class_work<T, TM, MODE>(L, t, f, by);
   ProfScope prof_scope_(H, timed ? LL_KIND_BSR_SMOOTH : LL_NUM_KINDS, f, by);
+  if constexpr (std::is_same<T, double>::value && std::is_same<TM, double>::value) {
+    if (L.sell && r1 - r0 >= kSellMinRows) {  // on the SELL-32 copy
+      long rows = cdiv((long)(r1 - (r0 & ~(kSell - 1))), kSell) * kSell;  // whole chunks
+      auto go = [&](auto kern, int G) {
+        launch_k(H, kern, cdiv(rows * G, kSellBlock), kSellBlock, r0, r1, (const int*)L.rowptr, (const int*)L.diag,
+                 (const int*)L.soff, (const int*)L.scol, (const double*)L.sval, (const double*)L.dinv64,
+                 (const double*)L.b64, L.x64.p);
+      };
+      switch (sell_lanes<MODE>(r1 - r0)) {
+        case 1: go(ks_sweep<MODE, 1, kSellUnroll>, 1); break;
+        case 2: go(ks_sweep<MODE, 2, kSellUnroll>, 2); break;
+        default: go(ks_sweep<MODE, 4, kSellUnroll>, 4); break;
+      }
+      return;
+    }
+  }
   int blk = coarse_block(H);
   // the float32 sweeps overlap their start with the kernel before them (PDL);
   // measured: float32 step -1.8 %, float64 no gain (its large classes are
@@ -832,12 +906,10 @@ void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e, bool timed = true
   auto go = [&](auto kern, int G) {
     if (pdl)
       launch_pdl(H, kern, cdiv((long)(r1 - r0) * G, blk), blk, r0, r1, (const int*)L.rowptr, (const int*)L.diag,
-                 (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(),
-                 (const int*)L.agg, e);
+                 (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>());
     else
       launch_k(H, kern, cdiv((long)(r1 - r0) * G, blk), blk, r0, r1, (const int*)L.rowptr, (const int*)L.diag,
-               (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>(),
-               (const int*)L.agg, e);
+               (const int*)L.col, (const TM*)L.valm<TM>(), (const T*)L.dinv<T>(), (const T*)L.b<T>(), L.x<T>());
   };
   if (sweep_lanes<T>(H, r1 - r0) == 8) go(kb_sweep<T, TM, 8, MODE, pdl>, 8);
   else go(kb_sweep<T, TM, kRowLanes, MODE, pdl>, kRowLanes);
@@ -847,7 +919,7 @@ void sweep_class(ll_mg_hierarchy* H, int l, int t, const T* e, bool timed = true
 template <typename T, typename TM>
 void smooth_level(ll_mg_hierarchy* H, int l, bool forward) {
   CLevel& L = H->lev[l];
-  for (int k = 0; k < L.ncol; ++k) sweep_class<T, TM, 1>(H, l, forward ? k : L.ncol - 1 - k, nullptr);
+  for (int k = 0; k < L.ncol; ++k) sweep_class<T, TM, 1>(H, l, forward ? k : L.ncol - 1 - k);
 }
 
 // V-cycle below level 0.  On entry b_l holds the restricted residual and,
@@ -1015,8 +1087,8 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
     }
     LL_PROFN(LL_KIND_BSR_SMOOTH, f, by, nl);
     for (int t = t0; t < K; ++t) {
-      if (sweep == 0) sweep_class<T, TM, 0>(H, l, t, nullptr, false);
-      else sweep_class<T, TM, 1>(H, l, t, nullptr, false);
+      if (sweep == 0) sweep_class<T, TM, 0>(H, l, t, false);
+      else sweep_class<T, TM, 1>(H, l, t, false);
     }
   }
   {
@@ -1047,8 +1119,13 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
   }
   if (H->union_mode) union_coarse<T>(H, l);  // rows past the colour classes
   coarse_problem<T, TM>(H, l + 1);
-  if (nu_post == 0) {
-    LL_PROF(LL_KIND_BSR_OTHER);
+  // the correction x += P e in one pass, then plain sweeps: on this part a
+  // prolongation fused into the first backward sweep (x + e formed for every
+  // block that reads a lower colour) measured 5 % slower per float64 step
+  // (float64 adds per block, one more dependent gather in each row's chain)
+  {
+    int w = (int)sizeof(T);
+    LL_PROFW(LL_KIND_BSR_OTHER, 3.0 * L.n, (4.0 + 9.0 * w) * L.n);
     kb_prolong<T><<<cdiv(L.n, kBlock), kBlock, 0, s>>>(L.n, L.agg, N.x<T>(), L.x<T>());
     LL_LAUNCHED();
   }
@@ -1056,15 +1133,11 @@ void vcycle_coarse(ll_mg_hierarchy* H, int l, bool init0_done) {
     double f = 0, by = 0;
     int nl = 0;
     for (int t = 0; t < K; ++t) {
-      if (sweep == 0) class_work<T, TM, 2>(L, t, f, by);
-      else class_work<T, TM, 1>(L, t, f, by);
+      class_work<T, TM, 1>(L, t, f, by);
       nl += L.cs[t + 1] > L.cs[t];
     }
     LL_PROFN(LL_KIND_BSR_SMOOTH, f, by, nl);
-    for (int k = 0; k < K; ++k) {
-      if (sweep == 0) sweep_class<T, TM, 2>(H, l, K - 1 - k, N.x<T>(), false);
-      else sweep_class<T, TM, 1>(H, l, K - 1 - k, nullptr, false);
-    }
+    for (int k = 0; k < K; ++k) sweep_class<T, TM, 1>(H, l, K - 1 - k, false);
   }
 }
 
@@ -1089,36 +1162,36 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   // float32 V-cycle: C and D^-1 formed in the kernels from m~ (OnFly)
   OnFly q{H->m32.p, (float)H->alpha, (float)(1.0 / (H->h * H->h)), (float)(1.0 / H->dt)};
   bool onfly = std::is_same<T, float>::value && H->m32.p;
-  auto half_sweep = [&](auto mode, int c, const int* agg, const T* e) {
+  auto half_sweep = [&](auto mode, int c) {
     constexpr int MODE = decltype(mode)::value;
     if constexpr (std::is_same<T, float>::value) {
       if (onfly) {
-        k0_smooth_onfly<MODE><<<nb, kBlock, 0, s>>>(g, c, r, z, q, agg, e);
+        k0_smooth_onfly<MODE><<<nb, kBlock, 0, s>>>(g, c, r, z, q);
         return;
       }
     }
-    k0_smooth<T, MODE><<<nb, kBlock, 0, s>>>(g, c, r, z, chat, dinv, agg, e);
+    k0_smooth<T, MODE><<<nb, kBlock, 0, s>>>(g, c, r, z, chat, dinv);
   };
   if (H->prm.nu_pre >= 1) {
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 15.0 * H->l0_cells[0], (24 + 12 * (double)sizeof(T)) * H->l0_cells[0]);
-      half_sweep(std::integral_constant<int, 0>(), 0, nullptr, nullptr);
+      half_sweep(std::integral_constant<int, 0>(), 0);
       LL_LAUNCHED();
     }
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
-      half_sweep(std::integral_constant<int, 1>(), 1, nullptr, nullptr);
+      half_sweep(std::integral_constant<int, 1>(), 1);
       LL_LAUNCHED();
     }
     for (int sweep = 1; sweep < H->prm.nu_pre; ++sweep) {
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
-        half_sweep(std::integral_constant<int, 1>(), 0, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 0);
         LL_LAUNCHED();
       }
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
-        half_sweep(std::integral_constant<int, 1>(), 1, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 1);
         LL_LAUNCHED();
       }
     }
@@ -1153,31 +1226,40 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
   }
   coarse_problem<T, TM>(H, 1);
   if (H->prm.nu_post >= 1) {
+    // the correction on the colour-0 slots only (the colour-1 half-sweep
+    // reads them; colour 1's own x and then colour 0's are overwritten),
+    // then a plain half-sweep: measured 1.2 % faster per float64 step than
+    // the prolongation folded into the half-sweep's neighbour sums
     {
-      LL_PROFW(LL_KIND_L0_SMOOTH, 66.0 * H->l0_cells[1], (24 + 24.75 * (double)sizeof(T)) * H->l0_cells[1]);
-      half_sweep(std::integral_constant<int, 2>(), 1, H->agg0, L1.x<T>());
+      LL_PROFW(LL_KIND_L0_SMOOTH, 3.0 * H->l0_cells[0], (4 + 9.0 * sizeof(T)) * H->l0_cells[0]);
+      k0_prolong<T><<<cdiv(g.nh, kBlock), kBlock, 0, s>>>(g, H->agg0, L1.x<T>(), z, 0L, g.nh);
+      LL_LAUNCHED();
+    }
+    {
+      LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
+      half_sweep(std::integral_constant<int, 1>(), 1);
       LL_LAUNCHED();
     }
     {
       LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
-      half_sweep(std::integral_constant<int, 1>(), 0, nullptr, nullptr);
+      half_sweep(std::integral_constant<int, 1>(), 0);
       LL_LAUNCHED();
     }
     for (int sweep = 1; sweep < H->prm.nu_post; ++sweep) {
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[1], (24 + 24 * (double)sizeof(T)) * H->l0_cells[1]);
-        half_sweep(std::integral_constant<int, 1>(), 1, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 1);
         LL_LAUNCHED();
       }
       {
         LL_PROFW(LL_KIND_L0_SMOOTH, 48.0 * H->l0_cells[0], (24 + 24 * (double)sizeof(T)) * H->l0_cells[0]);
-        half_sweep(std::integral_constant<int, 1>(), 0, nullptr, nullptr);
+        half_sweep(std::integral_constant<int, 1>(), 0);
         LL_LAUNCHED();
       }
     }
   } else {
     LL_PROF(LL_KIND_L0_RESTRICT);
-    k0_prolong<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->agg0, L1.x<T>(), z);
+    k0_prolong<T><<<cdiv(H->n2, kBlock), kBlock, 0, s>>>(g, H->agg0, L1.x<T>(), z, 0L, H->n2);
     LL_LAUNCHED();
   }
 }
@@ -1214,7 +1296,7 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   cudaStream_t s = H->s;
   const GridGeom& g = H->g;
   long n3 = H->n3;
-  int nbs = cdiv(H->n2, kBlock), nbv = cdiv(n3, kBlock);
+  int nbs = cdiv(H->n2, kBlock);
   GcrScal* S = H->scal.p;
   T* zj = H->Z<T>() + (size_t)j * n3;
   double* cj = H->C.p + (size_t)j * n3;
@@ -1277,7 +1359,7 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
     }
     {
       LL_PROFW(LL_KIND_GCR_VECTOR, wk * 2.0 * j * n3, wk * 8.0 * (j + 2) * n3);
-      kg_multiaxpy<<<nbv, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef, gate);
+      kg_multiaxpy<<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, cj, H->C, j, S->coef, gate);
       LL_LAUNCHED();
     }
   }
@@ -1445,8 +1527,10 @@ bool valid_params(const ll_mg_params& p) {
           p.coarse_block == 256);
 }
 
+// standalone = false: an instance of a batch, solved only through the batch's
+// union hierarchy (no SELL-32 copies)
 int create(const double* m, double alpha, double dt, double h, ll_grid grid, const ll_mg_params* p, void* stream,
-           ll_mg_hierarchy** out) {
+           ll_mg_hierarchy** out, bool standalone = true) {
   ll_mg_hierarchy* H = nullptr;
   try {
     H = new ll_mg_hierarchy();
@@ -1470,6 +1554,7 @@ int create(const double* m, double alpha, double dt, double h, ll_grid grid, con
     g.n = (long)grid.nx * grid.ny * grid.nz;
     H->n2 = 2 * g.nh;
     H->n3 = 3 * H->n2;
+    H->sell_ok = standalone && H->prm.precision == LL_FP64 && H->prm.coarse_lanes == 0 && H->prm.coarse_block == 0;
     symbolic(H);
     allocate(H);
     setup_counts(H);
@@ -1844,7 +1929,7 @@ int ll_mg_smooth(ll_mg_hierarchy* H, int l, const double* b, double* x, int forw
       LL_LAUNCHED();
       for (int t = 0; t < 2; ++t) {
         int c = forward ? t : 1 - t;
-        k0_smooth<double, 1><<<nb, kBlock, 0, s>>>(g, c, H->bw, H->xw.p, H->chat64, H->dinv64, nullptr, nullptr);
+        k0_smooth<double, 1><<<nb, kBlock, 0, s>>>(g, c, H->bw, H->xw.p, H->chat64, H->dinv64);
         LL_LAUNCHED();
       }
       k_from_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, H->xw, x);
