@@ -150,7 +150,8 @@ __device__ __forceinline__ void onfly_dinv(const OnFly& q, const float* C, int d
 template <typename T>
 __global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, double dt, double ih2,
                         double* __restrict__ chat64, T* __restrict__ chat, T* __restrict__ dinv,
-                        int* __restrict__ bad, float* __restrict__ m32 = nullptr) {
+                        int* __restrict__ bad, float* __restrict__ m32 = nullptr,
+                        float* __restrict__ chat_lo = nullptr) {
   long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long n2 = 2 * g.nh;
   if (sl >= n2) return;
@@ -185,6 +186,8 @@ __global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, 
     if (chat64) chat64[e * n2 + sl] = C[e];
     if (chat) chat[e * n2 + sl] = (T)C[e];
     if (dinv) dinv[e * n2 + sl] = (T)Di[e];
+    // C = chat + chat_lo to about 2^-48 (chat = C rounded to float32)
+    if (chat_lo) chat_lo[e * n2 + sl] = (float)(C[e] - (double)(float)C[e]);
   }
   if (m32) {  // m~ per slot for the float32 kernels that form C and D^-1 themselves
     long k = p.real ? p.x + (long)g.nx * (p.y + (long)g.ny * p.z) : 0;
@@ -1442,16 +1445,37 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bp)) + (b - bp);
 }
 
-// y = A x for a float32 x (the mixed path's outer product), with float64
-// products.  The stencil sum S - d x_k of float32 values is accumulated as an
-// unevaluated float32 pair hi + lo (two-sum per term, the rounding error of
-// d x_k by one fma), which carries it to about 1e-14 of the largest term;
-// then one float64 add per component.  This keeps the sums off the float64 pipe, which
-// bounds this kernel (the float64 sums were 18 of its 36 float64 operations
-// per cell).
-__global__ void __launch_bounds__(256) kg_apply_f32(GridGeom g, const float* __restrict__ x,
-                                                    const double* __restrict__ chat, double inv_dt,
-                                                    double* __restrict__ y) {
+// Float32-pair ("double-float") arithmetic for kg_apply_ff: a value is the
+// unevaluated sum hi + lo of two float32.  two_prod is exact (fma); the pair
+// product drops lo * lo; the pair sum renormalises with two_sum.  Each
+// operation carries about 2^-48 of the operands' magnitude.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+// (sh, sl) += (ah, al) * (bh, bl)
+__device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float p, e, t;
+  two_prod(ah, bh, p, e);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  two_sum(sh, p, sh, t);
+  sl += t + e;
+}
+
+// y = A x for a float32 x (the mixed path's outer product, step 2 of each GCR
+// iteration).  The stencil sum S - d x_k of float32 values is accumulated as
+// a float32 pair (two-sum per term, the rounding error of d x_k by one fma),
+// and x_k / dt + C^_k (S - d x_k) in float32-pair arithmetic, with C^ held
+// as the pair (chat, chat_lo) written by the numeric setup and 1/dt as
+// (idt, idt_lo): about 1e-14 of the largest term, against 1e-16 for float64
+// products.  Only the last add of each component and its two widenings are
+// float64: the float64 pipe (1/64 of the float32 rate here) bounded the
+// float64-product version of this kernel (24 float64 operations per cell,
+// conversions included; now 9).  (Widening with integer bit operations
+// instead of the conversions measured slower.)
+__global__ void __launch_bounds__(256) kg_apply_ff(GridGeom g, const float* __restrict__ x,
+                                                   const float* __restrict__ chat, const float* __restrict__ chat_lo,
+                                                   float idt, float idt_lo, double* __restrict__ y) {
   long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long n2 = 2 * g.nh;
   if (sl >= n2) return;
@@ -1482,12 +1506,23 @@ __global__ void __launch_bounds__(256) kg_apply_f32(GridGeom g, const float* __r
   l1 += e + q1;
   two_sum(h2, p2, h2, e);
   l2 += e + q2;
-  double s0 = (double)h0 + (double)l0, s1 = (double)h1 + (double)l1, s2 = (double)h2 + (double)l2;
-  double z0 = x0, z1 = x1, z2 = x2;
-  const double* C = chat + sl;
-  y[sl] = z0 * inv_dt + ld(C) * s0 + ld(C + n2) * s1 + ld(C + 2 * n2) * s2;
-  y[n2 + sl] = z1 * inv_dt + ld(C + 3 * n2) * s0 + ld(C + 4 * n2) * s1 + ld(C + 5 * n2) * s2;
-  y[2 * n2 + sl] = z2 * inv_dt + ld(C + 6 * n2) * s0 + ld(C + 7 * n2) * s1 + ld(C + 8 * n2) * s2;
+  float s0, s1, s2;  // the sums renormalised as pairs (s, l)
+  two_sum(h0, l0, s0, l0);
+  two_sum(h1, l1, s1, l1);
+  two_sum(h2, l2, s2, l2);
+  const float* Ch = chat + sl;
+  const float* Cl = chat_lo + sl;
+  float xs[3] = {x0, x1, x2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float yh, yl;
+    two_prod(xs[k], idt, yh, yl);
+    yl = fmaf(xs[k], idt_lo, yl);
+    ff_fma(ld(Ch + (3 * k) * n2), ld(Cl + (3 * k) * n2), s0, l0, yh, yl);
+    ff_fma(ld(Ch + (3 * k + 1) * n2), ld(Cl + (3 * k + 1) * n2), s1, l1, yh, yl);
+    ff_fma(ld(Ch + (3 * k + 2) * n2), ld(Cl + (3 * k + 2) * n2), s2, l2, yh, yl);
+    y[k * n2 + sl] = (double)yh + (double)yl;
+  }
 }
 
 // y = r on the colour-0 slots [0, Nh): the product A z there when z leaves a

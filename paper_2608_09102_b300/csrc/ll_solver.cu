@@ -109,6 +109,7 @@ struct ll_mg_hierarchy {
   DBuf<int> agg_nat0, agg0, nat_of_slot;
   DBuf<double> chat64, dinv64;
   DBuf<float> chat32, dinv32;
+  DBuf<float> chatlo;  // mixed: C^ - chat32 (the pair (chat32, chatlo) of kg_apply_ff)
   DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
   bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
   CLevel lev[kMaxLevels];
@@ -451,6 +452,7 @@ void allocate(ll_mg_hierarchy* H) {
   H->chat64.alloc(9 * n2);
   if (mixed) {
     H->chat32.alloc(9 * n2);
+    H->chatlo.alloc(9 * n2);
     H->dinv32.alloc(9 * n2);
     H->m32.alloc(3 * n2);
   } else {
@@ -766,7 +768,7 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
   int nb = cdiv(H->n2, kBlock);
   if (mixed)
     k0_coef<float><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, H->chat32, H->dinv32, H->flag,
-                                         H->m32);
+                                         H->m32, H->chatlo);
   else
     k0_coef<double><<<nb, kBlock, 0, s>>>(g, m, H->alpha, H->dt, ih2, H->chat64, nullptr, H->dinv64, H->flag);
   LL_LAUNCHED();
@@ -1302,10 +1304,12 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   double* cj = H->C.p + (size_t)j * n3;
   vcycle<T, TM>(H, H->r, zj);                                                       // step 1
   if constexpr (!std::is_same<T, double>::value) {
-    // mixed path: the float64 product of the float32 z (stencil sums as
-    // float32 pairs, see kg_apply_f32)
+    // mixed path: the product of the float32 z in float32-pair arithmetic
+    // (see kg_apply_ff), C^ as the pair (chat32, chatlo)
     LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * g.n, 108.0 * g.n);
-    kg_apply_f32<<<nbs, kBlock, 0, s>>>(g, zj, H->chat64, 1.0 / H->dt, cj);  // step 2
+    double idt = 1.0 / H->dt;
+    float idt_hi = (float)idt, idt_lo = (float)(idt - (double)idt_hi);
+    kg_apply_ff<<<nbs, kBlock, 0, s>>>(g, zj, H->chat32, H->chatlo, idt_hi, idt_lo, cj);  // step 2
     LL_LAUNCHED();
   } else if (H->nlev > 1 && H->prm.nu_post >= 1) {
     // step 2, c = A z: the V-cycle's last half-sweep solved the colour-0 rows
