@@ -11,11 +11,11 @@ m <- x/|x|.  The metric is unknown-solves per second (3 N unknowns per step).
 The default run times, in this order:
   * the headline: K float64 steps with no instrumentation (CUDA events on
     the launching stream around the K steps);
-  * the same K steps with the float32 V-cycle (mixed) and with bfloat16
-    coarse operators (bf16, the mixed-precision configuration: float32
-    V-cycle, bfloat16 coarse levels, float64 GCR), each from the same
-    initial state, for the mixed-vs-float64 speedup at the same true
-    relative residual 1e-8;
+  * the same K steps in float64, with the float32 V-cycle (mixed) and with
+    bfloat16 coarse operators (bf16, the mixed-precision configuration:
+    float32 V-cycle, bfloat16 coarse levels, float64 GCR), each from the same
+    initial state and one after another, for the mixed-vs-float64 speedup at
+    the same true relative residual 1e-8;
   * a separate profiling pass of the float64 path (per-kind event timing) for
     the kernel breakdown and the dominant kernel's roofline;
   * end to end: steps of a pinned host field through ll_mg_step_host (the
@@ -399,12 +399,16 @@ def run_ours(args):
         dist.barrier()
     elapsed_ms = max_over_ranks(elapsed_ms, dev)
 
-    # ---- the other precisions on the same K steps ---------------------------
+    # ---- the precisions side by side on the same K steps --------------------
+    # Every hierarchy set up after a second one in the same process runs about
+    # 2 % slower than the first (measured; not from allocations, streams,
+    # events, pinned memory or module loading), so the headline (the first
+    # hierarchy) is not compared with later ones: the three precisions are
+    # timed here one after another in the same process state, and the
+    # speed-ups divide these.
     others = {}
     if not args.no_mixed:
         for prec in ("fp64", "mixed", "bf16"):
-            if prec == args.precision:
-                continue
             mp_ = torch.tensor(m0, device=dev)
             Hp = hierarchy(mp_, prec)
             for _ in range(args.warmup):
@@ -422,11 +426,9 @@ def run_ours(args):
                             "clocks_sm_mhz": clk_p["sm_mhz"], "clock_reasons": clk_p["reasons"]}
             del Hp, mp_, ma, mb
             torch.cuda.empty_cache()
-        fp64_ms = elapsed_ms / args.steps if args.precision == "fp64" else others["fp64"]["ms_per_step"]
+        fp64_ms = others["fp64"]["ms_per_step"]
         for prec in ("mixed", "bf16"):
-            ms_p = elapsed_ms / args.steps if prec == args.precision else others[prec]["ms_per_step"]
-            if prec in others:
-                others[prec]["speedup_vs_fp64"] = fp64_ms / ms_p
+            others[prec]["speedup_vs_fp64"] = fp64_ms / others[prec]["ms_per_step"]
 
     # ---- profiling pass: per-kind breakdown, then the dominant kind alone ----
     def prof_start(mask):

@@ -393,10 +393,11 @@ __global__ void kgb_finish(const double* __restrict__ partial, int nchunks, cons
 // pass2 flag is set (see k_gs_coef); gate == nullptr: always run
 __device__ __forceinline__ bool inst_off(const GcrScal* gate, int inst) { return gate && gate[inst].pass2 == 0.0; }
 
-// SELF adds v . v as value cnt (|c|^2 before the projection)
+// dots with C_i for i in [i0, i0 + NV); SELF adds v . v as value NV (|c|^2
+// before the projection).  Compile-time indices only: acc stays in registers.
 template <int NV, bool SELF = false>
 __global__ void __launch_bounds__(256) kgb_multidot(const Chunk* __restrict__ ch, int nchunks,
-                                                    const double* __restrict__ C, long n3, int i0, int cnt,
+                                                    const double* __restrict__ C, long n3, int i0,
                                                     const double* __restrict__ v, double* __restrict__ partial,
                                                     const GcrScal* __restrict__ gate = nullptr) {
   Chunk k = ch[blockIdx.x];
@@ -407,16 +408,10 @@ __global__ void __launch_bounds__(256) kgb_multidot(const Chunk* __restrict__ ch
   for (long t = k.e0 + threadIdx.x; t < k.e1; t += blockDim.x) {
     double vt = v[t];
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-      if (q < cnt) acc[q] += C[(long)(i0 + q) * n3 + t] * vt;
+    for (int q = 0; q < NV; ++q) acc[q] += C[(long)(i0 + q) * n3 + t] * vt;
     if (SELF) acc[NV] += vt * vt;
   }
-  if (SELF) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-      if (q == cnt) acc[q] = acc[NV];
-  }
-  chunk_reduce_store<NV + 1>(acc, partial, cnt + (SELF ? 1 : 0), nchunks);
+  chunk_reduce_store<NV + 1>(acc, partial, NV + (SELF ? 1 : 0), nchunks);
 }
 
 // kgb_multidot launched with NV = cnt (1 <= cnt <= NV), as launch_multidot
@@ -429,7 +424,7 @@ void launch_batch_multidot(int cnt, cudaStream_t s, int nch, const Chunk* ch, co
       return;
     }
   }
-  kgb_multidot<NV, SELF><<<nch, kBlock, 0, s>>>(ch, nch, C, n3, i0, cnt, v, partial, gate);
+  kgb_multidot<NV, SELF><<<nch, kBlock, 0, s>>>(ch, nch, C, n3, i0, v, partial, gate);
 }
 
 __global__ void __launch_bounds__(256) kgb_multiaxpy(const Chunk* __restrict__ ch, double* __restrict__ v,

@@ -665,7 +665,10 @@ __global__ void __launch_bounds__(256) k0_smooth_onfly(GridGeom g, int c, const 
   x[2 * n2 + sl] = D[6] * v0 + D[7] * v1 + D[8] * v2;
 }
 
-// k0_restrict<float, true> with C formed from m~ (OnFly)
+// The float32 V-cycle's colour-0 residual right after one forward sweep
+// (slot_residual_after_sweep, C formed from m~) and its restriction in one
+// kernel, thread t taking aggregate order[t]; for I < init_end also the
+// first colour of the next level's forward sweep
 __global__ void k0_restrict_onfly(GridGeom g, const float* __restrict__ x, OnFly q, int nc,
                                   const int* __restrict__ mptr, const int* __restrict__ mem, float* __restrict__ bc,
                                   int init_end, const float* __restrict__ dinvc, float* __restrict__ xc,
@@ -701,8 +704,9 @@ __global__ void k0_restrict_onfly(GridGeom g, const float* __restrict__ x, OnFly
   }
 }
 
-// SHORT: one forward sweep preceded (the residual of slot_residual_after_sweep)
-template <typename T, bool SHORT>
+// Residual and restriction in one kernel (after nu_pre >= 2 sweeps):
+// bc_I = sum over the members k of aggregate I of b_k - (A x)_k
+template <typename T>
 __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* __restrict__ x,
                             const T* __restrict__ chat, T inv_dt, int nc, const int* __restrict__ mptr,
                             const int* __restrict__ mem, T* __restrict__ bc, int init_end,
@@ -718,8 +722,7 @@ __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* _
     int c = (int)(sl / g.nh);
     SlotPos p = slot_pos(g, c, sl % g.nh);
     T r[3];
-    if (SHORT) slot_residual_after_sweep<T>(g, sl, p, x, chat, r);
-    else slot_residual<T, T>(g, c, sl, p, b, x, chat, inv_dt, r);
+    slot_residual<T, T>(g, c, sl, p, b, x, chat, inv_dt, r);
     a0 += r[0];
     a1 += r[1];
     a2 += r[2];
@@ -728,6 +731,52 @@ __global__ void k0_restrict(GridGeom g, const double* __restrict__ b, const T* _
   bc[3L * I + 1] = a1;
   bc[3L * I + 2] = a2;
   if (I < init_end) {  // first colour of the next level's forward sweep
+    const T* D = dinvc + 9L * I;
+    xc[3L * I] = D[0] * a0 + D[1] * a1 + D[2] * a2;
+    xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
+    xc[3L * I + 2] = D[6] * a0 + D[7] * a1 + D[8] * a2;
+  }
+}
+
+// The residual of the colour-0 cells right after one forward sweep
+// (slot_residual_after_sweep), one thread per colour-0 slot, into the
+// colour-0 part r0 of a red-black vector (3 x nh, component-major): every
+// load is by slot, so the entry-major coefficients are read coalesced.
+template <typename T>
+__global__ void k0_residual_c0(GridGeom g, const T* __restrict__ x, const T* __restrict__ chat,
+                               T* __restrict__ r0) {
+  long sl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (sl >= g.nh) return;
+  SlotPos p = slot_pos(g, 0, sl);
+  T r[3] = {0, 0, 0};
+  if (p.real) slot_residual_after_sweep<T>(g, sl, p, x, chat, r);
+  r0[sl] = r[0];
+  r0[g.nh + sl] = r[1];
+  r0[2 * g.nh + sl] = r[2];
+}
+
+// restriction of that residual: bc_I = sum over the colour-0 members of
+// aggregate I (mptr0 / mem0); for I < init_end, xc_I = Dinvc_I bc_I (the
+// first colour of the next level's forward sweep).  Thread t takes aggregate
+// order[t], as k0_restrict.
+template <typename T>
+__global__ void k0_restrict_c0(GridGeom g, const T* __restrict__ r0, int nc, const int* __restrict__ mptr,
+                               const int* __restrict__ mem, T* __restrict__ bc, int init_end,
+                               const T* __restrict__ dinvc, T* __restrict__ xc, const int* __restrict__ order) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  int I = order[t];
+  T a0 = 0, a1 = 0, a2 = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+    long sl = mem[q];
+    a0 += r0[sl];
+    a1 += r0[g.nh + sl];
+    a2 += r0[2 * g.nh + sl];
+  }
+  bc[3L * I] = a0;
+  bc[3L * I + 1] = a1;
+  bc[3L * I + 2] = a2;
+  if (I < init_end) {
     const T* D = dinvc + 9L * I;
     xc[3L * I] = D[0] * a0 + D[1] * a1 + D[2] * a2;
     xc[3L * I + 1] = D[3] * a0 + D[4] * a1 + D[5] * a2;
@@ -1569,10 +1618,11 @@ __global__ void __launch_bounds__(256) kg_residual(GridGeom g, const double* __r
 // captured graph.  gate == nullptr: always run.
 __device__ __forceinline__ bool gated_off(const double* gate) { return gate && *gate == 0.0; }
 
-// partial dots d_i = C_i . v for i in [i0, i0 + cnt), cnt <= NV; SELF adds
-// v . v as value cnt
+// partial dots d_i = C_i . v for i in [i0, i0 + NV); SELF adds v . v as
+// value NV.  Every index into acc is a compile-time constant, so acc stays
+// in registers.
 template <int NV, bool SELF = false>
-__global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restrict__ C, int i0, int cnt,
+__global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restrict__ C, int i0,
                                                    const double* __restrict__ v, double* __restrict__ partial,
                                                    const double* __restrict__ gate = nullptr) {
   if (gated_off(gate)) return;
@@ -1582,16 +1632,10 @@ __global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restr
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double vt = v[t];
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-      if (q < cnt) acc[q] += C[(long)(i0 + q) * n + t] * vt;
+    for (int q = 0; q < NV; ++q) acc[q] += C[(long)(i0 + q) * n + t] * vt;
     if (SELF) acc[NV] += vt * vt;
   }
-  if (SELF) {  // v . v goes to row cnt (static indices keep acc in registers)
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-      if (q == cnt) acc[q] = acc[NV];
-  }
-  block_reduce_store<NV + 1>(acc, partial, cnt + (SELF ? 1 : 0));
+  block_reduce_store<NV + 1>(acc, partial, NV + (SELF ? 1 : 0));
 }
 
 // kg_multidot launched with NV = cnt (1 <= cnt <= NV).  The kernel is bound
@@ -1607,7 +1651,7 @@ void launch_multidot(int cnt, cudaStream_t s, long n, const double* C, int i0, c
       return;
     }
   }
-  kg_multidot<NV, SELF><<<kRedBlocks, kBlock, 0, s>>>(n, C, i0, cnt, v, partial, gate);
+  kg_multidot<NV, SELF><<<kRedBlocks, kBlock, 0, s>>>(n, C, i0, v, partial, gate);
 }
 
 // v -= sum_{i<j} coef[i] C_i  (coef on the device)

@@ -111,6 +111,7 @@ struct ll_mg_hierarchy {
   DBuf<float> chat32, dinv32;
   DBuf<float> chatlo;  // mixed: C^ - chat32 (the pair (chat32, chatlo) of kg_apply_ff)
   DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
+  DBuf<double> r0tmp64;  // colour-0 residual of the level-0 restriction (float64 path)
   bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
   CLevel lev[kMaxLevels];
   // coarsest dense LU and its inverse (column-major)
@@ -457,6 +458,7 @@ void allocate(ll_mg_hierarchy* H) {
     H->m32.alloc(3 * n2);
   } else {
     H->dinv64.alloc(9 * n2);
+    if (H->nlev > 1) H->r0tmp64.alloc(3 * H->g.nh);
   }
   for (int l = 1; l < H->nlev; ++l) {
     CLevel& C = H->lev[l];
@@ -1200,21 +1202,22 @@ void vcycle(ll_mg_hierarchy* H, const double* r, T* z) {
     int init_end = H->nlev > 2 ? L1.cs[1] : 0;  // level 1's first colour, unless it is the coarsest
     if (H->prm.nu_pre == 1) {  // right after one forward sweep: the neighbours' part only
       LL_PROFW(LL_KIND_L0_RESTRICT, 33.0 * H->l0_cells[0], (8 + 27.0 * sizeof(T)) * H->l0_cells[0]);
-      bool done = false;
-      if constexpr (std::is_same<T, float>::value) {
-        if (onfly) {
-          k0_restrict_onfly<<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, z, q, L1.n, L1.mptr0, L1.mem0, L1.b<T>(),
-                                                                  init_end, L1.dinv<T>(), L1.x<T>(), L1.o2n);
-          done = true;
-        }
+      if constexpr (std::is_same<T, float>::value) {  // C formed from m~ in the kernel
+        k0_restrict_onfly<<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, z, q, L1.n, L1.mptr0, L1.mem0, L1.b<T>(),
+                                                                init_end, L1.dinv<T>(), L1.x<T>(), L1.o2n);
+      } else {
+        // the colour-0 residual in one pass by slot, then its restriction:
+        // measured 1.5 % faster per float64 step than one kernel per
+        // aggregate that gathers its members' coefficients
+        k0_residual_c0<T><<<cdiv(g.nh, kBlock), kBlock, 0, s>>>(g, z, chat, H->r0tmp64.p);
+        LL_LAUNCHED();
+        k0_restrict_c0<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, H->r0tmp64.p, L1.n, L1.mptr0, L1.mem0,
+                                                                 L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
+                                                                 L1.o2n);
       }
-      if (!done)
-        k0_restrict<T, true><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
-                                                                    L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
-                                                                    L1.o2n);
     } else {
       LL_PROFW(LL_KIND_L0_RESTRICT, 48.0 * H->l0_cells[0], (24 + 15.0 * sizeof(T)) * H->l0_cells[0]);
-      k0_restrict<T, false><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
+      k0_restrict<T><<<cdiv(L1.n, kBlock), kBlock, 0, s>>>(g, r, z, chat, inv_dt, L1.n, L1.mptr0, L1.mem0,
                                                                    L1.b<T>(), init_end, L1.dinv<T>(), L1.x<T>(),
                                                                    L1.o2n);
     }

@@ -99,6 +99,25 @@ def test_48cube_vcycle(case48):
     assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("nu", [(2, 2), (2, 1), (1, 2), (0, 1), (1, 0)])
+def test_48cube_vcycle_sweep_counts(nu):
+    """Other smoothing counts take other kernels on level 0 (the full
+    residual with the restriction after two forward sweeps, the restriction
+    of b alone without pre-sweeps, the prolongation alone without
+    post-sweeps) and on the per-class and tail levels."""
+    grid = (48,) * 3
+    h, alpha = 1.0 / 48, 0.02
+    dt = 8.19 * h * h
+    m = inputs.vortex(*grid, seed=0).reshape(-1)
+    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-12, nu_pre=nu[0], nu_post=nu[1]))
+    G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-12, nu_pre=nu[0], nu_post=nu[1]))
+    r = inputs.rhs_field(*grid, seed=8).reshape(-1)
+    z = torch.empty_like(_t(r))
+    G.vcycle(_t(r), z)
+    ref = O.vcycle(r)
+    assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
 def test_48cube_kcycle_preconditioner():
     grid, h, alpha, dt, m, O, G = _vortex_case(48, kcycle=1)
     r = inputs.rhs_field(*grid, seed=8).reshape(-1)
