@@ -61,12 +61,14 @@ WORKLOAD = "3D 128^3 semi-implicit LL time steps, alpha 0.02, dt 5e-4, vortex + 
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 
 # DRAM traffic of the float64 coarse sweeps per launch over their algorithmic
-# bytes: ncu dram__bytes_read.sum + dram__bytes_write.sum over 100 kb_sweep
-# launches (two V-cycles) of the 96^3 profiling case (1.109e7 B per launch),
-# against the library's byte model averaged over the same launch mix
-# (1.150e7 B per launch).  Scaled by the bytes a launch processes to a 128^3
-# launch.
-KB_SWEEP_TRAFFIC_RATIO = 1.1088e7 / 1.1495e7
+# bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, 96^3 profiling
+# case, three launches of each sweep kernel): the level-1 classes on the
+# SELL-32 copy (ks_sweep: 89.75 MB against 104.46 MB of the byte model,
+# 0.859) and small classes on BSR (kb_sweep: 5.22 MB against 5.26 MB, 0.992),
+# weighted by the model's bytes of one V-cycle's sweeps at 96^3 (424 MB on the
+# SELL-32 copy, 162 MB on BSR).  Scaled by the bytes a launch processes to a
+# 128^3 launch.
+KB_SWEEP_TRAFFIC_RATIO = (424.05 * 0.8592 + 162.25 * 0.9919) / (424.05 + 162.25)
 
 KIND_NAMES = ["l0_smooth", "l0_restrict", "outer_apply", "bsr_smooth", "bsr_other", "gcr_vector", "coarsest",
               "numeric", "coarse_tail"]
@@ -477,8 +479,9 @@ def run_ours(args):
     roof["timed_in"] = "a separate profiling pass of %d steps right after the timed region" % prof_steps
     if dominant == "bsr_smooth" and args.precision == "fp64":
         roof["traffic"] = KB_SWEEP_TRAFFIC_RATIO * roof["bytes_per_launch"]
-        roof["traffic_source"] = ("ncu DRAM bytes of kb_sweep at 96^3 / algorithmic bytes = %.3f, times this "
-                                  "launch's algorithmic bytes" % KB_SWEEP_TRAFFIC_RATIO)
+        roof["traffic_source"] = ("ncu DRAM bytes of ks_sweep and kb_sweep launches at 96^3 / algorithmic bytes, "
+                                  "weighted by a V-cycle's bytes = %.3f, times this launch's algorithmic bytes"
+                                  % KB_SWEEP_TRAFFIC_RATIO)
     vk = [k for k in VCYCLE_KINDS]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
