@@ -181,7 +181,8 @@ int ll_mg_level_colours(const ll_mg_hierarchy* H, int l, int* colour);
 int ll_mg_level_blocks(const ll_mg_hierarchy* H, int l);
 /* Copy the BSR operator of level l >= 1 to HOST buffers: rowptr (n+1),
  * col (nnzb), val (9*nnzb, each block row-major, component (r, c) at
- * 3r + c, cell-major unknowns).  Values are float64 whatever the storage. */
+ * 3r + c, cell-major unknowns).  Values are float64: a mixed-precision
+ * hierarchy's float32 Galerkin values (its V-cycle's operators) widened. */
 int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col, double* val);
 
 /* Number of CUDA kernels this library has launched since it was loaded

@@ -84,6 +84,26 @@ __host__ __device__ __forceinline__ bool inv3(const double* a, double* o) {
   return true;
 }
 
+// the same inverse in float32 (the mixed path's Galerkin levels)
+__device__ __forceinline__ bool inv3(const float* a, float* o) {
+  float c00 = a[4] * a[8] - a[5] * a[7];
+  float c01 = a[5] * a[6] - a[3] * a[8];
+  float c02 = a[3] * a[7] - a[4] * a[6];
+  float det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(det != 0.0f) || !isfinite(det)) return false;
+  float id = 1.0f / det;
+  o[0] = c00 * id;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  o[3] = c01 * id;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  o[6] = c02 * id;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) {
   return __ldg(p);
@@ -196,7 +216,10 @@ __global__ void k0_coef(GridGeom g, const double* __restrict__ m, double alpha, 
 }
 
 // ---------------------------------------------------------------------------
-// numeric Galerkin products (Eq. galerkin), accumulated in float64
+// numeric Galerkin products (Eq. galerkin), accumulated in T: float64 for the
+// float64 path, float32 for the mixed path's float32 preconditioner (its
+// coarse operators are stored in float32 or bfloat16 anyway; float64 sums
+// there cost the float64 pipe, which bounds these kernels)
 // ---------------------------------------------------------------------------
 // row of every block of a BSR level
 __global__ void k_block_rows(int n, const int* __restrict__ rowptr, int* __restrict__ prow) {
@@ -208,69 +231,67 @@ __global__ void k_block_rows(int n, const int* __restrict__ rowptr, int* __restr
 // One thread per coarse block: neighbouring threads write neighbouring
 // blocks (coalesced stores).  Each block sums its slot list in a fixed order.
 // level 1: A_1(I,J) = delta_IJ |G_I|/dt I + sum_{k in G_I} w_kJ Chat_k
+template <typename T>
 __global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
                                   const int* __restrict__ sptr, const int* __restrict__ sidx,
                                   const int* __restrict__ sw, const int* __restrict__ mptr, long n2,
-                                  const double* __restrict__ chat64, double inv_dt, double* __restrict__ val,
-                                  double* __restrict__ dinv64, int* __restrict__ bad) {
+                                  const T* __restrict__ chat, T inv_dt, T* __restrict__ val, T* __restrict__ dinv,
+                                  int* __restrict__ bad) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb) return;
   int I = prow[p];
-  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
     long k = sidx[q];
-    double w = (double)sw[q];
-    for (int e = 0; e < 9; ++e) a[e] += w * chat64[e * n2 + k];
+    T w = (T)sw[q];
+    for (int e = 0; e < 9; ++e) a[e] += w * chat[e * n2 + k];
   }
   if (col[p] == I) {
-    double sz = (double)(mptr[I + 1] - mptr[I]) * inv_dt;
+    T sz = (T)(mptr[I + 1] - mptr[I]) * inv_dt;
     a[0] += sz;
     a[4] += sz;
     a[8] += sz;
-    double o[9];
+    T o[9];
     if (!inv3(a, o)) atomicExch(bad, 1);
-    for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
+    for (int e = 0; e < 9; ++e) dinv[9 * (long)I + e] = o[e];
   }
   for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
 }
 
 // levels >= 2: sum of the fine blocks of each coarse slot
+template <typename T>
 __global__ void k_galerkin_bsr_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
                                    const int* __restrict__ sptr, const int* __restrict__ sidx,
-                                   const double* __restrict__ fval, double* __restrict__ val,
-                                   double* __restrict__ dinv64, int* __restrict__ bad) {
+                                   const T* __restrict__ fval, T* __restrict__ val, T* __restrict__ dinv,
+                                   int* __restrict__ bad) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb) return;
   int I = prow[p];
-  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
-    const double* f = fval + 9 * (long)sidx[q];
+    const T* f = fval + 9 * (long)sidx[q];
     for (int e = 0; e < 9; ++e) a[e] += f[e];
   }
   if (col[p] == I) {
-    double o[9];
+    T o[9];
     if (!inv3(a, o)) atomicExch(bad, 1);
-    for (int e = 0; e < 9; ++e) dinv64[9 * (long)I + e] = o[e];
+    for (int e = 0; e < 9; ++e) dinv[9 * (long)I + e] = o[e];
   }
   for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
 }
 
-template <typename T>
-__global__ void k_cast(long n, const double* __restrict__ in, T* __restrict__ out) {
+// float32 -> bfloat16 (round to nearest even)
+__global__ void k_cast_bf16(long n, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (T)in[i];
-}
-template <>
-__global__ void k_cast<__nv_bfloat16>(long n, const double* __restrict__ in, __nv_bfloat16* __restrict__ out) {
-  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = __double2bfloat16(in[i]);
+  if (i < n) out[i] = __float2bfloat16(in[i]);
 }
 
 // ---------------------------------------------------------------------------
 // coarsest level: dense LU with partial pivoting (one CTA), unknown 3I + c
 // ---------------------------------------------------------------------------
+template <typename TV>
 __global__ void k_dense_from_bsr(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                                 const double* __restrict__ val, double* __restrict__ a) {
+                                 const TV* __restrict__ val, double* __restrict__ a) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   int N = 3 * n;
@@ -279,7 +300,7 @@ __global__ void k_dense_from_bsr(int n, const int* __restrict__ rowptr, const in
   for (int p = rowptr[I]; p < rowptr[I + 1]; ++p) {
     int J = col[p];
     for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) a[(long)(3 * I + r) * N + 3 * J + c] = val[9 * (long)p + 3 * r + c];
+      for (int c = 0; c < 3; ++c) a[(long)(3 * I + r) * N + 3 * J + c] = (double)val[9 * (long)p + 3 * r + c];
   }
 }
 

@@ -462,16 +462,16 @@ void allocate(ll_mg_hierarchy* H) {
   }
   for (int l = 1; l < H->nlev; ++l) {
     CLevel& C = H->lev[l];
-    C.val64.alloc(9L * C.nnzb);
-    C.dinv64.alloc(9L * C.n);
-    if (mixed) {
+    if (mixed) {  // float32 Galerkin levels (bfloat16 copies of them for LL_MIXED_BF16)
+      C.val32.alloc(9L * C.nnzb);
       if (H->prm.precision == LL_MIXED_BF16) C.val16.alloc(9L * C.nnzb);
-      else C.val32.alloc(9L * C.nnzb);
       C.dinv32.alloc(9L * C.n);
       C.x32.alloc(3L * C.n);
       C.b32.alloc(3L * C.n);
       C.r32.alloc(3L * C.n);
     } else {
+      C.val64.alloc(9L * C.nnzb);
+      C.dinv64.alloc(9L * C.n);
       C.x64.alloc(3L * C.n);
       C.b64.alloc(3L * C.n);
       C.r64.alloc(3L * C.n);
@@ -776,25 +776,31 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
   LL_LAUNCHED();
   for (int l = 1; l < H->nlev; ++l) {
     CLevel& C = H->lev[l];
+    int nb = cdiv(C.nnzb, 128);
+    if (mixed) {  // the float32 preconditioner's levels in float32 from chat32
+      if (l == 1)
+        k_galerkin_l1_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
+                                                    H->chat32, (float)inv_dt, C.val32, C.dinv32, H->flag);
+      else
+        k_galerkin_bsr_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, H->lev[l - 1].val32,
+                                                     C.val32, C.dinv32, H->flag);
+      LL_LAUNCHED();
+      if (H->prm.precision == LL_MIXED_BF16) {
+        k_cast_bf16<<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val32, C.val16);
+        LL_LAUNCHED();
+      }
+      continue;
+    }
     if (l == 1)
-      k_galerkin_l1_blk<<<cdiv(C.nnzb, 128), 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr,
-                                                          H->n2, H->chat64, inv_dt, C.val64, C.dinv64, H->flag);
+      k_galerkin_l1_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
+                                                   H->chat64, inv_dt, C.val64, C.dinv64, H->flag);
     else
-      k_galerkin_bsr_blk<<<cdiv(C.nnzb, 128), 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx,
-                                                           H->lev[l - 1].val64, C.val64, C.dinv64, H->flag);
+      k_galerkin_bsr_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, H->lev[l - 1].val64,
+                                                    C.val64, C.dinv64, H->flag);
     LL_LAUNCHED();
     if (C.sell && C.sgroups > 0) {
       k_sell_values<<<cdiv(C.sgroups * kSell, kBlock), kBlock, 0, s>>>(C.sgroups, C.n, C.sgc, C.soff, C.rowptr,
                                                                         C.diag, C.val64, C.sval);
-      LL_LAUNCHED();
-    }
-    if (mixed) {
-      if (H->prm.precision == LL_MIXED_BF16)
-        k_cast<__nv_bfloat16><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val16);
-      else
-        k_cast<float><<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val64, C.val32);
-      LL_LAUNCHED();
-      k_cast<float><<<cdiv(9L * C.n, kBlock), kBlock, 0, s>>>(9L * C.n, C.dinv64, C.dinv32);
       LL_LAUNCHED();
     }
   }
@@ -804,7 +810,10 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
     k_dense_from_l0<<<cdiv(g.n, 64), 64, 0, s>>>(g, H->chat64, inv_dt, H->lu);
   } else {
     CLevel& C = H->lev[H->nlev - 1];
-    k_dense_from_bsr<<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val64, H->lu);
+    if (mixed)
+      k_dense_from_bsr<float><<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val32, H->lu);
+    else
+      k_dense_from_bsr<double><<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val64, H->lu);
   }
   LL_LAUNCHED();
   if (N <= kLuSmemMax) {  // factor in shared memory (one block), then one warp per column of the inverse
@@ -1822,11 +1831,17 @@ int ll_mg_level_operator(const ll_mg_hierarchy* H, int l, int* rowptr, int* col,
   // aggregation's numbering, columns ascending
   std::vector<int> rp(C.n + 1), cl(C.nnzb), n2o(C.n), o2n(C.n);
   std::vector<double> va(9L * C.nnzb);
+  std::vector<float> va32;
+  bool f32 = C.val64.p == nullptr;  // mixed hierarchy: the float32 Galerkin values
+  if (f32) va32.resize(9L * C.nnzb);
   if (cudaMemcpy(rp.data(), C.rowptr.p, (C.n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(cl.data(), C.col.p, C.nnzb * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(va.data(), C.val64.p, 9L * C.nnzb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      (f32 ? cudaMemcpy(va32.data(), C.val32.p, 9L * C.nnzb * sizeof(float), cudaMemcpyDeviceToHost)
+           : cudaMemcpy(va.data(), C.val64.p, 9L * C.nnzb * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
       cudaMemcpy(n2o.data(), C.n2o.p, C.n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LL_ECUDA;
+  if (f32)
+    for (size_t i = 0; i < va.size(); ++i) va[i] = va32[i];
   for (int r = 0; r < C.n; ++r) o2n[n2o[r]] = r;
   int q = 0;
   rowptr[0] = 0;
