@@ -103,6 +103,27 @@ def test_galerkin_operators(name):
         np.testing.assert_allclose(dense, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("precision", [ll.LL_MIXED_FP32, ll.LL_MIXED_BF16])
+@pytest.mark.parametrize("name", list(CASES))
+def test_galerkin_operators_float32(name, precision):
+    """The mixed hierarchies build their coarse operators in float32 (the
+    V-cycle's precision) from float32 coefficients: every level within
+    float32 rounding of the oracle's float64 product (a few roundings of
+    2^-24 per entry, growing with the level's sums)."""
+    grid, h, alpha, dt, m, O, G = _pair(name, precision=precision)
+    for l in range(1, O.nlevels):
+        n = O.cells(l)
+        rp, ci, val = G.operator(l)
+        dense = np.zeros((3 * n, 3 * n))
+        for I in range(n):
+            for p in range(rp[I], rp[I + 1]):
+                dense[3 * I:3 * I + 3, 3 * ci[p]:3 * ci[p] + 3] = val[p]
+        perm = np.array([c * n + I for I in range(n) for c in range(3)])
+        ref = O.matrix(l).toarray()[np.ix_(perm, perm)]
+        err = np.abs(dense - ref).max() / np.abs(ref).max()
+        assert err <= 1e-5, (l, err)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_operator_apply(name):
     grid, h, alpha, dt, m, O, G = _pair(name)
