@@ -121,8 +121,12 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
                 double* rel_residual);
 
 /* n_steps time steps of the semi-implicit scheme with projection (Sec. 4):
- * per step m~ = m, rhs = m/dt, solve from the guess m, then m <- x/|x| per
- * cell.  Aggregates are computed once; each step redoes the numeric setup.
+ * per step m~ = m, rhs = m/dt, solve (Algorithm 1) from the initial
+ * approximation u_0, then m <- x/|x| per cell.  u_0 = m for the first step,
+ * u_0 = 2 m^n - m^{n-1} (the linear extrapolation of the last two states)
+ * for the later ones; the stopping test ||r|| < rtol ||rhs|| is the same
+ * for any u_0.  Aggregates are computed once; each step redoes the numeric
+ * setup.
  *   m               device SoA 3*N float64, in/out (cells must be nonzero).
  *   iters_per_step  host, optional, n_steps ints.
  *   relres_per_step host, optional, n_steps doubles.
@@ -133,6 +137,9 @@ int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid g
 /* n_steps time steps on an existing hierarchy (same grid and parameters;
  * alpha and dt are the hierarchy's): per step the numeric setup is redone for
  * m~ = m, then solve and project as ll_step does.  Reuses the aggregates.
+ * The hierarchy keeps the state before its last step and its last output:
+ * when m is bit for bit that output (a continued integration), the first
+ * step of the call also starts from 2 m^n - m^{n-1}.
  *   m device SoA 3*N float64, in/out; iters/relres host, optional, n_steps.
  * Returns the worst status over the steps (errors stop early). */
 int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step);
@@ -145,7 +152,8 @@ int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, 
  * i.e. the same operator with Delta_h scaled by eps and the right-hand side
  * m^n/dt - C(m^n) f^n.  The exchange factor eps enters through the
  * hierarchy's spacing: set it up with h/sqrt(eps).  Then as ll_mg_step
- * (numeric setup per step, solve from the guess m^n, projection).
+ * (numeric setup per step, solve from the same initial approximations,
+ * projection).
  *   m  device SoA 3*N float64, in/out;  he  host, 3 doubles (NULL: zero). */
 int ll_mg_step_llg(ll_mg_hierarchy* H, double* m, int n_steps, double q, const double* he,
                    int* iters_per_step, double* relres_per_step);
@@ -385,7 +393,8 @@ int ll_mg_tune_lookup(const char* cache_path, ll_grid grid, double dt, double h,
  *
  * ll_mg_step_save: n_steps steps as ll_mg_step, also storing each step's
  * solution before the projection: x_save (device) receives n_steps vectors
- * of 3*N float64 (SoA), step k at offset 3*N*k.  Blocks until done. */
+ * of 3*N float64 (SoA), step k at offset 3*N*k.  Every solve starts from
+ * u_0 = m (the map whose gradient the calls below give).  Blocks until done. */
 int ll_mg_step_save(ll_mg_hierarchy* H, double* m, int n_steps, double* x_save, int* iters_per_step,
                     double* relres_per_step);
 /* A one-instance batch (see above) that solves with the transposed operator

@@ -1044,19 +1044,30 @@ done:
 /* time stepping with projection                                             */
 /* ------------------------------------------------------------------------ */
 
+/* The initial approximation u_0 of each step's solve (Algorithm 1 takes it
+ * as an input; the paper does not fix it for the time loop).  Reading: the
+ * first step of a call starts from m^n; each later step from the linear
+ * extrapolation of the last two states, u_0 = 2 m^n - m^{n-1}, which is
+ * O(dt^2) from the new solution where m^n is O(dt) from it.  prev holds
+ * m^{n-1} (NULL: no earlier state). */
+static void step_guess(int n3, const double *m, const double *prev, double *x) {
+  for (int i = 0; i < n3; ++i) x[i] = prev ? 2.0 * m[i] - prev[i] : m[i];
+}
+
 /* n_steps steps of the semi-implicit scheme: m~ = m^n, b = m^n/dt, solve
- * from the guess m^n, then m^{n+1} = x/|x| per cell when project != 0. */
+ * from the guess of step_guess, then m^{n+1} = x/|x| per cell when
+ * project != 0. */
 int orc_step(double *m, int n_steps, int nx, int ny, int nz, double h, double alpha, double dt,
              const orc_params *prm, int project, int *iters_per_step, double *relres_per_step) {
   int n = nx * ny * nz, worst = ORC_OK;
   double *b = (double *)xmalloc((size_t)3 * n * sizeof(double));
   double *x = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *prev = (double *)xmalloc((size_t)3 * n * sizeof(double));
   for (int s = 0; s < n_steps; ++s) {
     orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
-    for (int i = 0; i < 3 * n; ++i) {
-      b[i] = m[i] / dt;
-      x[i] = m[i];
-    }
+    for (int i = 0; i < 3 * n; ++i) b[i] = m[i] / dt;
+    step_guess(3 * n, m, s > 0 ? prev : NULL, x);
+    memcpy(prev, m, (size_t)3 * n * sizeof(double));
     int it = 0;
     double rr = 0.0;
     int st = orc_solve(H, b, x, prm->rtol, &it, &rr, NULL);
@@ -1074,6 +1085,7 @@ int orc_step(double *m, int n_steps, int nx, int ny, int nz, double h, double al
   }
   free(b);
   free(x);
+  free(prev);
   return worst;
 }
 
@@ -1088,6 +1100,7 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
   int n = nx * ny * nz, worst = ORC_OK;
   double *b = (double *)xmalloc((size_t)3 * n * sizeof(double));
   double *x = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *prev = (double *)xmalloc((size_t)3 * n * sizeof(double));
   for (int s = 0; s < n_steps; ++s) {
     orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
     for (int k = 0; k < n; ++k) {
@@ -1097,9 +1110,10 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
       for (int c = 0; c < 3; ++c) {
         double cf = C[c][0] * f[0] + C[c][1] * f[1] + C[c][2] * f[2];
         b[c * n + k] = mk[c] / dt - cf;
-        x[c * n + k] = mk[c];
       }
     }
+    step_guess(3 * n, m, s > 0 ? prev : NULL, x);
+    memcpy(prev, m, (size_t)3 * n * sizeof(double));
     int it = 0;
     double rr = 0.0;
     int st = orc_solve(H, b, x, prm->rtol, &it, &rr, NULL);
@@ -1117,6 +1131,7 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
   }
   free(b);
   free(x);
+  free(prev);
   return worst;
 }
 

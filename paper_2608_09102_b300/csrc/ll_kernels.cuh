@@ -1829,6 +1829,22 @@ __global__ void k_rhs_llg(long n, const double* __restrict__ m, double alpha, do
   b[2 * n + k] = m3 * inv_dt - c3;
 }
 
+// The initial approximation of a time step's solve (the same reading as the
+// oracle's step_guess): x = 2 m - prev, the linear extrapolation of the last
+// two states
+__global__ void k_step_guess(long n, const double* __restrict__ m, const double* __restrict__ prev,
+                             double* __restrict__ x) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 2.0 * m[i] - prev[i];
+}
+
+// *differ = 1 if a and b differ in any bit (a continued time integration is
+// recognised by the field passed in being the hierarchy's last output)
+__global__ void k_differ(long n, const double* __restrict__ a, const double* __restrict__ b, int* __restrict__ differ) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n && __double_as_longlong(a[i]) != __double_as_longlong(b[i])) *differ = 1;
+}
+
 // rhs = m / dt
 __global__ void k_scale(long n, const double* __restrict__ m, double inv_dt, double* __restrict__ b) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;

@@ -113,6 +113,12 @@ struct ll_mg_hierarchy {
   DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
   DBuf<double> r0tmp64;  // colour-0 residual of the level-0 restriction (float64 path)
   bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
+  // time-stepping history for the steps' initial approximations: the state
+  // before the last step (step_prev) and the last output (step_last), valid
+  // when step_hist is set
+  DBuf<double> step_prev, step_last;
+  DBuf<int> step_differ;
+  bool step_hist = false;
   CLevel lev[kMaxLevels];
   // coarsest dense LU and its inverse (column-major)
   int ncoarse3 = 0;
@@ -1654,12 +1660,37 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 
 // time steps on an existing hierarchy; fresh = numeric setup already done for
 // m; src = explicit source terms (q, he0, he1, he2) or NULL
+// Time steps of m in place.  The initial approximation of each solve:
+// 2 m^n - m^{n-1} when the state before m is known -- within a call from
+// its second step, and for the first step when m is bit for bit the last
+// output of the previous call on this hierarchy (a continued integration);
+// else m itself (the oracle's step_guess; not for x_save, the adjoint's
+// forward map, whose solves start from m).
 static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step,
                  bool fresh, const double* src = nullptr, double* x_save = nullptr) {
   int worst = LL_OK;
   double dt = H->dt;
   try {
     long n3 = 3 * H->g.n;
+    bool guess = x_save == nullptr;
+    bool have_prev = false;
+    if (guess) {
+      if (!H->step_prev.p) {
+        H->step_prev.alloc(n3);
+        H->step_last.alloc(n3);
+        H->step_differ.alloc(1);
+      }
+      if (H->step_hist && n_steps > 0) {
+        H->step_differ.zero(H->s);
+        k_differ<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, H->step_last, H->step_differ);
+        LL_LAUNCHED();
+        int differ = 1;
+        LL_CU(cudaMemcpyAsync(&differ, H->step_differ.p, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+        LL_CU(cudaStreamSynchronize(H->s));
+        have_prev = differ == 0;
+      }
+      H->step_hist = false;  // set again when every step of this call has completed
+    }
     for (int k = 0; k < n_steps; ++k) {
       if (k > 0 || !fresh) numeric(H, m);
       if (src)
@@ -1668,7 +1699,16 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
       else
         k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
       LL_LAUNCHED();
-      LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+      if (have_prev) {
+        k_step_guess<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, H->step_prev, H->stepx);
+        LL_LAUNCHED();
+      } else {
+        LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+      }
+      if (guess) {
+        LL_CU(cudaMemcpyAsync(H->step_prev.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+        have_prev = true;
+      }
       int it = 0;
       double rr = 0;
       int s2 = solve(H, H->stepb, H->stepx, H->prm.rtol, &it, &rr);
@@ -1683,8 +1723,13 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
       LL_LAUNCHED();
       check_flag(H, LL_BREAKDOWN);
     }
+    if (guess && n_steps > 0 && worst == LL_OK) {
+      LL_CU(cudaMemcpyAsync(H->step_last.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+      H->step_hist = true;
+    }
   } catch (Status e) {
     worst = e.code;
+    H->step_hist = false;
   }
   return worst;
 }
