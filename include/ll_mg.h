@@ -122,11 +122,12 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 
 /* n_steps time steps of the semi-implicit scheme with projection (Sec. 4):
  * per step m~ = m, rhs = m/dt, solve (Algorithm 1) from the initial
- * approximation u_0, then m <- x/|x| per cell.  u_0 = m for the first step,
- * u_0 = 2 m^n - m^{n-1} (the linear extrapolation of the last two states)
- * for the later ones; the stopping test ||r|| < rtol ||rhs|| is the same
- * for any u_0.  Aggregates are computed once; each step redoes the numeric
- * setup.
+ * approximation u_0, then m <- x/|x| per cell.  u_0 = m for the first step;
+ * for step k the polynomial extrapolation through m^n and the min(k, 3)
+ * states before it (2 m^n - m^{n-1}; 3 m^n - 3 m^{n-1} + m^{n-2};
+ * 4 m^n - 6 m^{n-1} + 4 m^{n-2} - m^{n-3}).  The stopping test
+ * ||r|| < rtol ||rhs|| is the same for any u_0.  Aggregates are computed
+ * once; each step redoes the numeric setup.
  *   m               device SoA 3*N float64, in/out (cells must be nonzero).
  *   iters_per_step  host, optional, n_steps ints.
  *   relres_per_step host, optional, n_steps doubles.
@@ -137,9 +138,9 @@ int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid g
 /* n_steps time steps on an existing hierarchy (same grid and parameters;
  * alpha and dt are the hierarchy's): per step the numeric setup is redone for
  * m~ = m, then solve and project as ll_step does.  Reuses the aggregates.
- * The hierarchy keeps the state before its last step and its last output:
- * when m is bit for bit that output (a continued integration), the first
- * step of the call also starts from 2 m^n - m^{n-1}.
+ * The hierarchy keeps up to three states before its last output and that
+ * output: when m is bit for bit that output (a continued integration), the
+ * call's first step also starts from the extrapolation.
  *   m device SoA 3*N float64, in/out; iters/relres host, optional, n_steps.
  * Returns the worst status over the steps (errors stop early). */
 int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step);

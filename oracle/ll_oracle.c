@@ -1046,12 +1046,29 @@ done:
 
 /* The initial approximation u_0 of each step's solve (Algorithm 1 takes it
  * as an input; the paper does not fix it for the time loop).  Reading: the
- * first step of a call starts from m^n; each later step from the linear
- * extrapolation of the last two states, u_0 = 2 m^n - m^{n-1}, which is
- * O(dt^2) from the new solution where m^n is O(dt) from it.  prev holds
- * m^{n-1} (NULL: no earlier state). */
-static void step_guess(int n3, const double *m, const double *prev, double *x) {
-  for (int i = 0; i < n3; ++i) x[i] = prev ? 2.0 * m[i] - prev[i] : m[i];
+ * polynomial extrapolation of the states through m^n and the k earlier ones
+ * this call has, k = min(steps so far, 3):
+ *   k = 0: m^n;  1: 2 m^n - m^{n-1};  2: 3 m^n - 3 m^{n-1} + m^{n-2};
+ *   3: 4 m^n - 6 m^{n-1} + 4 m^{n-2} - m^{n-3},
+ * which is O(dt^{k+1}) from the new solution where m^n is O(dt) from it.
+ * prev[j] holds m^{n-1-j}. */
+static void step_guess(int n3, int k, const double *m, double *const *prev, double *x) {
+  static const double c[4][4] = {{1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
+  for (int i = 0; i < n3; ++i) {
+    double v = c[k][0] * m[i];
+    for (int j = 0; j < k; ++j) v += c[k][j + 1] * prev[j][i];
+    x[i] = v;
+  }
+}
+
+/* push m^n onto the history (prev[0] newest); returns the new depth */
+static int step_push(int n3, int k, const double *m, double **prev) {
+  double *t = prev[2];
+  prev[2] = prev[1];
+  prev[1] = prev[0];
+  prev[0] = t;
+  memcpy(prev[0], m, (size_t)n3 * sizeof(double));
+  return k < 3 ? k + 1 : 3;
 }
 
 /* n_steps steps of the semi-implicit scheme: m~ = m^n, b = m^n/dt, solve
@@ -1062,12 +1079,14 @@ int orc_step(double *m, int n_steps, int nx, int ny, int nz, double h, double al
   int n = nx * ny * nz, worst = ORC_OK;
   double *b = (double *)xmalloc((size_t)3 * n * sizeof(double));
   double *x = (double *)xmalloc((size_t)3 * n * sizeof(double));
-  double *prev = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *prev[3];
+  for (int j = 0; j < 3; ++j) prev[j] = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  int depth = 0;
   for (int s = 0; s < n_steps; ++s) {
     orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
     for (int i = 0; i < 3 * n; ++i) b[i] = m[i] / dt;
-    step_guess(3 * n, m, s > 0 ? prev : NULL, x);
-    memcpy(prev, m, (size_t)3 * n * sizeof(double));
+    step_guess(3 * n, depth, m, prev, x);
+    depth = step_push(3 * n, depth, m, prev);
     int it = 0;
     double rr = 0.0;
     int st = orc_solve(H, b, x, prm->rtol, &it, &rr, NULL);
@@ -1085,7 +1104,7 @@ int orc_step(double *m, int n_steps, int nx, int ny, int nz, double h, double al
   }
   free(b);
   free(x);
-  free(prev);
+  for (int j = 0; j < 3; ++j) free(prev[j]);
   return worst;
 }
 
@@ -1100,7 +1119,9 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
   int n = nx * ny * nz, worst = ORC_OK;
   double *b = (double *)xmalloc((size_t)3 * n * sizeof(double));
   double *x = (double *)xmalloc((size_t)3 * n * sizeof(double));
-  double *prev = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *prev[3];
+  for (int j = 0; j < 3; ++j) prev[j] = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  int depth = 0;
   for (int s = 0; s < n_steps; ++s) {
     orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
     for (int k = 0; k < n; ++k) {
@@ -1112,8 +1133,8 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
         b[c * n + k] = mk[c] / dt - cf;
       }
     }
-    step_guess(3 * n, m, s > 0 ? prev : NULL, x);
-    memcpy(prev, m, (size_t)3 * n * sizeof(double));
+    step_guess(3 * n, depth, m, prev, x);
+    depth = step_push(3 * n, depth, m, prev);
     int it = 0;
     double rr = 0.0;
     int st = orc_solve(H, b, x, prm->rtol, &it, &rr, NULL);
@@ -1131,7 +1152,7 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
   }
   free(b);
   free(x);
-  free(prev);
+  for (int j = 0; j < 3; ++j) free(prev[j]);
   return worst;
 }
 

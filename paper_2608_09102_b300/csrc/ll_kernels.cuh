@@ -1830,12 +1830,19 @@ __global__ void k_rhs_llg(long n, const double* __restrict__ m, double alpha, do
 }
 
 // The initial approximation of a time step's solve (the same reading as the
-// oracle's step_guess): x = 2 m - prev, the linear extrapolation of the last
-// two states
-__global__ void k_step_guess(long n, const double* __restrict__ m, const double* __restrict__ prev,
+// oracle's step_guess): the polynomial extrapolation through m and the k
+// earlier states p1 (newest), p2, p3:  k = 1: 2 m - p1;  2: 3 m - 3 p1 + p2;
+// 3: 4 m - 6 p1 + 4 p2 - p3
+__global__ void k_step_guess(long n, int k, const double* __restrict__ m, const double* __restrict__ p1,
+                             const double* __restrict__ p2, const double* __restrict__ p3,
                              double* __restrict__ x) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i < n) x[i] = 2.0 * m[i] - prev[i];
+  if (i >= n) return;
+  double v;
+  if (k == 1) v = 2.0 * m[i] + -1.0 * p1[i];
+  else if (k == 2) v = 3.0 * m[i] + -3.0 * p1[i] + 1.0 * p2[i];
+  else v = 4.0 * m[i] + -6.0 * p1[i] + 4.0 * p2[i] + -1.0 * p3[i];
+  x[i] = v;
 }
 
 // *differ = 1 if a and b differ in any bit (a continued time integration is

@@ -113,11 +113,13 @@ struct ll_mg_hierarchy {
   DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
   DBuf<double> r0tmp64;  // colour-0 residual of the level-0 restriction (float64 path)
   bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
-  // time-stepping history for the steps' initial approximations: the state
-  // before the last step (step_prev) and the last output (step_last), valid
+  // time-stepping history for the steps' initial approximations: up to three
+  // states before the last output (step_h[(step_i + j) % 3] holds the j-th
+  // newest, j < step_depth) and the last output itself (step_last), valid
   // when step_hist is set
-  DBuf<double> step_prev, step_last;
+  DBuf<double> step_h[3], step_last;
   DBuf<int> step_differ;
+  int step_i = 0, step_depth = 0;
   bool step_hist = false;
   CLevel lev[kMaxLevels];
   // coarsest dense LU and its inverse (column-major)
@@ -1660,12 +1662,13 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 
 // time steps on an existing hierarchy; fresh = numeric setup already done for
 // m; src = explicit source terms (q, he0, he1, he2) or NULL
-// Time steps of m in place.  The initial approximation of each solve:
-// 2 m^n - m^{n-1} when the state before m is known -- within a call from
-// its second step, and for the first step when m is bit for bit the last
-// output of the previous call on this hierarchy (a continued integration);
-// else m itself (the oracle's step_guess; not for x_save, the adjoint's
-// forward map, whose solves start from m).
+// Time steps of m in place.  The initial approximation of each solve: the
+// polynomial extrapolation through m and the (up to three) states before it
+// that are known -- within a call from its second step, and from the first
+// step when m is bit for bit the last output of the previous call on this
+// hierarchy (a continued integration); else m itself (the oracle's
+// step_guess; not for x_save, the adjoint's forward map, whose solves start
+// from m).
 static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step,
                  bool fresh, const double* src = nullptr, double* x_save = nullptr) {
   int worst = LL_OK;
@@ -1673,10 +1676,10 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
   try {
     long n3 = 3 * H->g.n;
     bool guess = x_save == nullptr;
-    bool have_prev = false;
+    int depth = 0;  // earlier states known for the next step's guess
     if (guess) {
-      if (!H->step_prev.p) {
-        H->step_prev.alloc(n3);
+      if (!H->step_last.p) {
+        for (auto& b : H->step_h) b.alloc(n3);
         H->step_last.alloc(n3);
         H->step_differ.alloc(1);
       }
@@ -1687,10 +1690,11 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
         int differ = 1;
         LL_CU(cudaMemcpyAsync(&differ, H->step_differ.p, sizeof(int), cudaMemcpyDeviceToHost, H->s));
         LL_CU(cudaStreamSynchronize(H->s));
-        have_prev = differ == 0;
+        if (differ == 0) depth = H->step_depth;
       }
       H->step_hist = false;  // set again when every step of this call has completed
     }
+    auto hist = [&](int j) { return H->step_h[(H->step_i + j) % 3].p; };
     for (int k = 0; k < n_steps; ++k) {
       if (k > 0 || !fresh) numeric(H, m);
       if (src)
@@ -1699,15 +1703,17 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
       else
         k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
       LL_LAUNCHED();
-      if (have_prev) {
-        k_step_guess<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, H->step_prev, H->stepx);
+      if (depth > 0) {
+        k_step_guess<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, depth, m, hist(0), hist(1), hist(2), H->stepx);
         LL_LAUNCHED();
       } else {
         LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
       }
-      if (guess) {
-        LL_CU(cudaMemcpyAsync(H->step_prev.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
-        have_prev = true;
+      if (guess) {  // m^n becomes the newest earlier state (the oldest slot is reused)
+        H->step_i = (H->step_i + 2) % 3;
+        LL_CU(cudaMemcpyAsync(hist(0), m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+        depth = std::min(depth + 1, 3);
+        H->step_depth = depth;
       }
       int it = 0;
       double rr = 0;

@@ -564,27 +564,29 @@ def test_random_unit_vectors_limit_of_the_vcycle(alpha):
 
 
 def test_step_initial_approximation_is_the_extrapolated_state():
-    """Reading of the time loop (Algorithm 1 takes u_0 as an input): the first
-    step of a call starts from m^n, a later one from 2 m^n - m^{n-1}.  A
-    three-step call equals three explicit solves with those guesses, and the
-    extrapolated guess starts closer to the solution than m^n does."""
+    """Reading of the time loop (Algorithm 1 takes u_0 as an input): step k of
+    a call starts from the polynomial extrapolation through m^n and the
+    min(k, 3) states before it.  A five-step call equals five explicit solves
+    with those guesses, and each extrapolated guess starts closer to the
+    solution than m^n does."""
     n = 16
     grid, h, alpha, dt = (n, n, 1), 1 / n, 0.05, 2e-3
     m0 = inputs.smooth_field(*grid, seed=4).reshape(-1)
     p = oracle.Params(rtol=1e-12)
+    coef = {0: [1.0], 1: [2.0, -1.0], 2: [3.0, -3.0, 1.0], 3: [4.0, -6.0, 4.0, -1.0]}
     ms = [m0]
     gains = []
-    for k in range(3):
+    for k in range(5):
+        order = min(k, 3)
+        guess = sum(c * ms[-1 - j] for j, c in enumerate(coef[order]))
         H = oracle.Hierarchy(grid, h, alpha, dt, ms[-1], p)
-        b = ms[-1] / dt
-        guess = ms[-1].copy() if k == 0 else 2 * ms[-1] - ms[-2]
-        x, st, it, rr = H.solve(b, guess.copy())
+        x, st, it, rr = H.solve(ms[-1] / dt, guess.copy())
         assert st == oracle.OK
         if k > 0:
             gains.append(np.linalg.norm(x - guess) / np.linalg.norm(x - ms[-1]))
         v = x.reshape(3, -1)
         ms.append((v / np.linalg.norm(v, axis=0)).reshape(-1))
-    out, its, rrs, st = oracle.step(m0, 3, grid, h, alpha, dt, p)
+    out, its, rrs, st = oracle.step(m0, 5, grid, h, alpha, dt, p)
     assert st == oracle.OK
     assert np.abs(out - ms[-1]).max() <= 1e-13
     assert max(gains) < 0.5, gains
