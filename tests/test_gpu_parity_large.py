@@ -206,6 +206,36 @@ def test_step_host_equals_device_steps():
     assert torch.equal(mp, md.cpu())
 
 
+def test_continued_integration_keeps_the_extrapolation_history():
+    """Steps split over several calls equal the same steps in one call (the
+    field passed in is the hierarchy's last output, so the history of earlier
+    states carries over); a field that is not that output starts a fresh
+    history, as a new hierarchy would.  Against the oracle's one-call steps."""
+    grid, h, alpha, dt = (24, 20, 8), 1 / 24, 0.05, 2e-3
+    m0 = inputs.vortex(*grid, seed=0).reshape(-1)
+    p = ll.Params(rtol=1e-12)
+    ma = _t(m0)
+    Ga = ll.Hierarchy(ma, alpha, dt, h, grid, p)
+    sa, ita, _ = Ga.step(ma, 6)
+    mb = _t(m0)
+    Gb = ll.Hierarchy(mb, alpha, dt, h, grid, p)
+    itb = []
+    for k in (1, 2, 3):
+        st, its, _ = Gb.step(mb, k)
+        itb += its
+    assert torch.equal(ma, mb) and ita == itb
+    mo, ito, rro, sto = oracle.step(m0, 6, grid, h, alpha, dt, oracle.Params(rtol=1e-12))
+    assert np.abs(_np(ma) - mo).max() <= 1e-10
+    assert all(abs(a - b) <= 1 for a, b in zip(ita, ito)), (ita, ito)
+    # a field that is not the last output: no history (as on a fresh hierarchy)
+    mc = _t(m0)
+    st, itc, _ = Gb.step(mc, 2)
+    md = _t(m0)
+    Gd = ll.Hierarchy(md, alpha, dt, h, grid, p)
+    st, itd, _ = Gd.step(md, 2)
+    assert torch.equal(mc, md) and itc == itd
+
+
 def test_fp64_probe_runs():
     sink = torch.zeros(1, dtype=torch.float64, device=DEV)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
