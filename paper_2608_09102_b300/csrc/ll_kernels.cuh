@@ -3,6 +3,7 @@
 #pragma once
 #include <type_traits>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -230,13 +231,15 @@ __global__ void k_block_rows(int n, const int* __restrict__ rowptr, int* __restr
 
 // One thread per coarse block: neighbouring threads write neighbouring
 // blocks (coalesced stores).  Each block sums its slot list in a fixed order.
+// The diagonal blocks' inverses are a separate pass (k_block_dinv): inside
+// this kernel only about one lane in 13 holds a diagonal block, and the warp
+// would issue the inverse's float64 instructions for all 32 lanes.
 // level 1: A_1(I,J) = delta_IJ |G_I|/dt I + sum_{k in G_I} w_kJ Chat_k
 template <typename T>
 __global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
                                   const int* __restrict__ sptr, const int* __restrict__ sidx,
                                   const int* __restrict__ sw, const int* __restrict__ mptr, long n2,
-                                  const T* __restrict__ chat, T inv_dt, T* __restrict__ val, T* __restrict__ dinv,
-                                  int* __restrict__ bad) {
+                                  const T* __restrict__ chat, T inv_dt, T* __restrict__ val) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb) return;
   int I = prow[p];
@@ -251,33 +254,36 @@ __global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ prow, const 
     a[0] += sz;
     a[4] += sz;
     a[8] += sz;
-    T o[9];
-    if (!inv3(a, o)) atomicExch(bad, 1);
-    for (int e = 0; e < 9; ++e) dinv[9 * (long)I + e] = o[e];
   }
   for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
 }
 
 // levels >= 2: sum of the fine blocks of each coarse slot
 template <typename T>
-__global__ void k_galerkin_bsr_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
-                                   const int* __restrict__ sptr, const int* __restrict__ sidx,
-                                   const T* __restrict__ fval, T* __restrict__ val, T* __restrict__ dinv,
-                                   int* __restrict__ bad) {
+__global__ void k_galerkin_bsr_blk(int nnzb, const int* __restrict__ sptr, const int* __restrict__ sidx,
+                                   const T* __restrict__ fval, T* __restrict__ val) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb) return;
-  int I = prow[p];
   T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
     const T* f = fval + 9 * (long)sidx[q];
     for (int e = 0; e < 9; ++e) a[e] += f[e];
   }
-  if (col[p] == I) {
-    T o[9];
-    if (!inv3(a, o)) atomicExch(bad, 1);
-    for (int e = 0; e < 9; ++e) dinv[9 * (long)I + e] = o[e];
-  }
   for (int e = 0; e < 9; ++e) val[9 * (long)p + e] = a[e];
+}
+
+// inverse of every diagonal block of a Galerkin level, one thread per row;
+// a singular block sets *bad
+template <typename T>
+__global__ void k_block_dinv(int n, const int* __restrict__ diag, const T* __restrict__ val, T* __restrict__ dinv,
+                             int* __restrict__ bad) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  const T* d = val + 9 * (long)diag[I];
+  T a[9], o[9];
+  for (int e = 0; e < 9; ++e) a[e] = d[e];
+  if (!inv3(a, o)) atomicExch(bad, 1);
+  for (int e = 0; e < 9; ++e) dinv[9 * (long)I + e] = o[e];
 }
 
 // float32 -> bfloat16 (round to nearest even)
@@ -369,105 +375,122 @@ __global__ void k_lu_factor(int N, double* __restrict__ a, int* __restrict__ per
   }
 }
 
-// Coarsest levels of up to kLuSmemMax unknowns: the factorisation in one
-// block in shared memory, the same operations in the same order as
-// k_lu_factor; the factors go back to a for k_lu_inverse_warp.
-// blockDim.x: a power of two >= N, at most 128.
-constexpr int kLuSmemMax = 128;
-__global__ void k_lu_factor_smem(int N, double* __restrict__ a, int* __restrict__ perm, int* __restrict__ status) {
-  extern __shared__ double A[];  // row-major N x N, factored in place
-  __shared__ double sval[128];
-  __shared__ int sidx[128];
-  __shared__ int sperm[kLuSmemMax];
-  __shared__ int piv, bad;
-  int t = threadIdx.x, nt = blockDim.x;
-  for (int e = t; e < N * N; e += nt) A[e] = a[e];
-  for (int i = t; i < N; i += nt) sperm[i] = i;
-  if (t == 0) bad = 0;
-  __syncthreads();
+// Coarsest inverse for up to kGjMax unknowns: in-place Gauss-Jordan
+// elimination with partial pivoting on one thread-block cluster.  Column j of
+// the matrix lives in the shared memory of CTA j % P at local column j / P,
+// one warp per local column, lanes over rows.  Step k: the warp holding
+// column k finds the pivot row p (largest |a_ik| over i >= k, ties to the
+// lowest row, as in k_lu_factor), publishes p, column k with rows k and p
+// exchanged and the pivot's reciprocal in its CTA's shared memory, and sets
+// its own column to e_p.  After a cluster barrier every warp reads them
+// through distributed shared memory and applies the step to its column: rows
+// k and p exchanged, row k times the reciprocal, f_i times row k subtracted
+// from every other row i.
+// Column k then holds a column of the inverse with its rows in pivot order;
+// undoing the row exchanges in reverse order on the columns puts the inverse
+// in order.  N^3 multiply-adds spread over P SMs, one cluster barrier per
+// step.  The published column is double-buffered: the owner of step k + 2
+// writes the buffer of step k only after the barrier of step k + 1, which
+// every CTA reaches after its reads of step k.  a: row-major N x N; ainv:
+// column-major; *status = 1 on a zero or non-finite pivot.
+constexpr int kGjCluster = 8;
+constexpr int kGjMax = 256;               // at most 32 local columns (warps) per CTA
+constexpr int kGjRows = kGjMax / 32;      // rows per lane
+__global__ void __launch_bounds__(1024, 1) k_gj_inverse(int N, const double* __restrict__ a,
+                                                        double* __restrict__ ainv, int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int P = (int)cl.num_blocks(), r = (int)cl.block_rank();
+  const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  extern __shared__ double gj_sm[];
+  double* colv = gj_sm + (size_t)w * N;  // this warp's column
+  double* pub = gj_sm + (size_t)W * N;   // 2 x (N + 1): column k, then 1 / pivot
+  __shared__ int pubp[2];
+  __shared__ int pivs[kGjMax];
+  __shared__ int dest[kGjMax];
+  __shared__ int q[kGjMax];
+  const int j = w * P + r;
+  const bool have = j < N;
+  if (have)
+    for (int i = lane; i < N; i += 32) colv[i] = a[(long)i * N + j];
+  if (r == 0 && threadIdx.x == 0) *status = 0;
+  cl.sync();
   for (int k = 0; k < N; ++k) {
-    // pivot search: largest |a_ik|, ties to the lowest row
-    double bv = -1.0;
-    int bi = N;
-    for (int i = k + t; i < N; i += nt) {
-      double v = fabs(A[i * N + k]);
-      if (v > bv || (v == bv && i < bi)) {
-        bv = v;
-        bi = i;
-      }
-    }
-    sval[t] = bv;
-    sidx[t] = bi;
-    __syncthreads();
-    for (int o = nt / 2; o > 0; o >>= 1) {
-      if (t < o) {
-        double v2 = sval[t + o];
-        int i2 = sidx[t + o];
-        if (v2 > sval[t] || (v2 == sval[t] && i2 < sidx[t])) {
-          sval[t] = v2;
-          sidx[t] = i2;
+    const int buf = k & 1;
+    if (r == k % P && w == k / P) {
+      double bv = -1.0;
+      int bi = N;
+      for (int i = k + lane; i < N; i += 32) {  // rows ascending per lane: the first maximum
+        double v = fabs(colv[i]);
+        if (v > bv) {
+          bv = v;
+          bi = i;
         }
       }
-      __syncthreads();
-    }
-    if (t == 0) {
-      piv = sidx[0];
-      if (!(sval[0] > 0.0)) bad = 1;
-    }
-    __syncthreads();
-    int p = piv;
-    if (p != k && p < N) {
-      for (int j = t; j < N; j += nt) {
-        double x = A[k * N + j];
-        A[k * N + j] = A[p * N + j];
-        A[p * N + j] = x;
+      for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > bv || (v2 == bv && i2 < bi)) {
+          bv = v2;
+          bi = i2;
+        }
       }
-      if (t == 0) {
-        int x = sperm[k];
-        sperm[k] = sperm[p];
-        sperm[p] = x;
+      int p = bi;
+      if (!(bv > 0.0) || !isfinite(bv)) {
+        if (lane == 0) atomicExch(status, 1);
+        p = k;
       }
+      double* f = pub + buf * (N + 1);
+      for (int i = lane; i < N; i += 32) f[i] = colv[i == k ? p : (i == p ? k : i)];
+      if (lane == 0) {
+        f[N] = 1.0 / colv[p];
+        pubp[buf] = p;
+      }
+      __syncwarp();
+      for (int i = lane; i < N; i += 32) colv[i] = i == p ? 1.0 : 0.0;
     }
-    __syncthreads();
-    double akk = A[k * N + k];
-    for (int i = k + 1 + t; i < N; i += nt) A[i * N + k] /= akk;
-    __syncthreads();
-    int m = N - k - 1;
-    for (int e = t; e < m * m; e += nt) {
-      int i = k + 1 + e / m, j = k + 1 + e % m;
-      A[i * N + j] -= A[i * N + k] * A[k * N + j];
+    cl.sync();
+    const int o = k % P;
+    const double* f = cl.map_shared_rank(pub + buf * (N + 1), o);
+    const int p = *cl.map_shared_rank(&pubp[buf], o);
+    if (threadIdx.x == 0) pivs[k] = p;
+    if (have) {
+      // every remote load issued before the first use
+      double fr[kGjRows];
+#pragma unroll
+      for (int t = 0; t < kGjRows; ++t) fr[t] = lane + 32 * t < N ? f[lane + 32 * t] : 0.0;
+      double ip = f[N];
+      if (lane == 0 && p != k) {
+        double t = colv[k];
+        colv[k] = colv[p];
+        colv[p] = t;
+      }
+      __syncwarp();
+      double rk = colv[k] * ip;
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kGjRows; ++t) {
+        int i = lane + 32 * t;
+        if (i < N) colv[i] = i == k ? rk : colv[i] - fr[t] * rk;
+      }
+      __syncwarp();
     }
-    __syncthreads();
   }
-  for (int e = t; e < N * N; e += nt) a[e] = A[e];
-  for (int i = t; i < N; i += nt) perm[i] = sperm[i];
-  if (t == 0) *status = bad;
-}
-
-// Columns of the inverse from the LU factors, one warp per column j (grid of
-// N blocks of 32 threads): L U y = P e_j by forward and backward
-// substitution, each row's dot product split over the lanes and summed by
-// shuffles; y in shared memory.  Stored column-major: ainv[j*N + i].
-__global__ void __launch_bounds__(32) k_lu_inverse_warp(int N, const double* __restrict__ a,
-                                                        const int* __restrict__ perm, double* __restrict__ ainv) {
-  __shared__ double y[kLuSmemMax];
-  int j = blockIdx.x, lane = threadIdx.x;
-  if (j >= N) return;
-  for (int i = 0; i < N; ++i) {  // forward, unit lower; (P e_j)_i = [perm_i == j]
-    double v = 0.0;
-    for (int k = lane; k < i; k += 32) v += a[(long)i * N + k] * y[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) y[i] = (perm[i] == j ? 1.0 : 0.0) - v;
-    __syncwarp();
+  cl.sync();  // no CTA leaves while another may still read its published column
+  if (threadIdx.x == 0) {
+    // q[jj]: the column that ends as column jj of the inverse (the row
+    // exchanges undone on the columns in reverse order); dest: its inverse map
+    for (int jj = 0; jj < N; ++jj) q[jj] = jj;
+    for (int k = N - 1; k >= 0; --k) {
+      int t = q[k];
+      q[k] = q[pivs[k]];
+      q[pivs[k]] = t;
+    }
+    for (int jj = 0; jj < N; ++jj) dest[q[jj]] = jj;
   }
-  for (int i = N - 1; i >= 0; --i) {  // backward
-    double v = 0.0;
-    for (int k = i + 1 + lane; k < N; k += 32) v += a[(long)i * N + k] * y[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) y[i] = (y[i] - v) / a[(long)i * N + i];
-    __syncwarp();
-  }
-  for (int i = lane; i < N; i += 32) ainv[(long)j * N + i] = y[i];
+  __syncthreads();
+  if (have)
+    for (int i = lane; i < N; i += 32) ainv[(long)dest[j] * N + i] = colv[i];
 }
 
 // Columns of the inverse from the LU factors: column j solves L U x = P e_j
@@ -501,28 +524,6 @@ __global__ void kc_solve(int N, const double* __restrict__ ainv, const T* __rest
   double acc = 0.0;
   for (int j = 0; j < N; ++j) acc += ainv[(long)j * N + i] * sb[j];
   x[i] = (T)acc;
-}
-
-template <typename T>
-__global__ void k_lu_solve(int N, const double* __restrict__ a, const int* __restrict__ perm,
-                           const T* __restrict__ b, T* __restrict__ x) {
-  extern __shared__ double y[];
-  int t = threadIdx.x, nt = blockDim.x;
-  for (int i = t; i < N; i += nt) y[i] = (double)b[perm[i]];
-  __syncthreads();
-  for (int j = 0; j < N; ++j) {  // forward, unit lower
-    double yj = y[j];
-    for (int i = j + 1 + t; i < N; i += nt) y[i] -= a[(long)i * N + j] * yj;
-    __syncthreads();
-  }
-  for (int j = N - 1; j >= 0; --j) {  // backward
-    if (t == 0) y[j] /= a[(long)j * N + j];
-    __syncthreads();
-    double yj = y[j];
-    for (int i = t; i < j; i += nt) y[i] -= a[(long)i * N + j] * yj;
-    __syncthreads();
-  }
-  for (int i = t; i < N; i += nt) x[i] = (T)y[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -1639,24 +1640,29 @@ __global__ void __launch_bounds__(256) kg_residual(GridGeom g, const double* __r
 // captured graph.  gate == nullptr: always run.
 __device__ __forceinline__ bool gated_off(const double* gate) { return gate && *gate == 0.0; }
 
-// partial dots d_i = C_i . v for i in [i0, i0 + NV); SELF adds v . v as
-// value NV.  Every index into acc is a compile-time constant, so acc stays
-// in registers.
+// partial dots d_i = C_i . v for i in [i0, i0 + NV); SELF adds v . v and
+// v . r as values NV and NV + 1.  Every index into acc is a compile-time
+// constant, so acc stays in registers.
 template <int NV, bool SELF = false>
 __global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restrict__ C, int i0,
                                                    const double* __restrict__ v, double* __restrict__ partial,
-                                                   const double* __restrict__ gate = nullptr) {
+                                                   const double* __restrict__ gate = nullptr,
+                                                   const double* __restrict__ r = nullptr) {
   if (gated_off(gate)) return;
-  double acc[NV + 1];
+  constexpr int NQ = NV + (SELF ? 2 : 0);
+  double acc[NQ];
 #pragma unroll
-  for (int q = 0; q <= NV; ++q) acc[q] = 0;
+  for (int q = 0; q < NQ; ++q) acc[q] = 0;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double vt = v[t];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] += C[(long)(i0 + q) * n + t] * vt;
-    if (SELF) acc[NV] += vt * vt;
+    if constexpr (SELF) {
+      acc[NV] += vt * vt;
+      acc[NV + 1] += vt * r[t];
+    }
   }
-  block_reduce_store<NV + 1>(acc, partial, NV + (SELF ? 1 : 0));
+  block_reduce_store<NQ>(acc, partial, NQ);
 }
 
 // kg_multidot launched with NV = cnt (1 <= cnt <= NV).  The kernel is bound
@@ -1665,26 +1671,41 @@ __global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restr
 // multiply-adds still cost pipe slots.
 template <int NV, bool SELF>
 void launch_multidot(int cnt, cudaStream_t s, long n, const double* C, int i0, const double* v, double* partial,
-                     const double* gate = nullptr) {
+                     const double* gate = nullptr, const double* r = nullptr) {
   if constexpr (NV > 1) {
     if (cnt < NV) {
-      launch_multidot<NV - 1, SELF>(cnt, s, n, C, i0, v, partial, gate);
+      launch_multidot<NV - 1, SELF>(cnt, s, n, C, i0, v, partial, gate, r);
       return;
     }
   }
-  kg_multidot<NV, SELF><<<kRedBlocks, kBlock, 0, s>>>(n, C, i0, v, partial, gate);
+  kg_multidot<NV, SELF><<<kRedBlocks, kBlock, 0, s>>>(n, C, i0, v, partial, gate, r);
 }
 
-// v -= sum_{i<j} coef[i] C_i  (coef on the device)
-__global__ void __launch_bounds__(256) kg_multiaxpy(long n, double* __restrict__ v, const double* __restrict__ C,
-                                                    int j, const double* __restrict__ coef,
-                                                    const double* __restrict__ gate = nullptr) {
+// v -= sum_{i<j} coef[i] C_i (coef on the device); when *rnow != 0 the same
+// pass also takes the GCR step r -= rcoef v with the new v and stores the
+// partial sums of |r|^2
+__global__ void __launch_bounds__(256) kg_multiaxpy_r(long n, double* __restrict__ v, const double* __restrict__ C,
+                                                      int j, const double* __restrict__ coef,
+                                                      double* __restrict__ r, const double* __restrict__ rnow,
+                                                      const double* __restrict__ rcoef,
+                                                      double* __restrict__ partial,
+                                                      const double* __restrict__ gate = nullptr) {
   if (gated_off(gate)) return;
-  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  double a = v[t];
-  for (int i = 0; i < j; ++i) a -= coef[i] * C[(long)i * n + t];
-  v[t] = a;
+  const bool upd = *rnow != 0.0;
+  const double f = *rcoef;
+  double acc[1] = {0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    double a = v[t];
+#pragma unroll 4
+    for (int i = 0; i < j; ++i) a -= coef[i] * C[(long)i * n + t];
+    v[t] = a;
+    if (upd) {
+      double b = r[t] - f * a;
+      r[t] = b;
+      acc[0] += b * b;
+    }
+  }
+  if (upd) block_reduce_store<1>(acc, partial, 1);
 }
 
 // partial sums of |c|^2 and c.r
@@ -1755,15 +1776,38 @@ struct GcrScal {
   double coef[kMaxRestart];        // projection coefficients of the update
   double gam[kMaxRestart * kMaxRestart];  // Gamma, row-major
   double alpha[kMaxRestart], s[kMaxRestart], y[kMaxRestart];
+  double cq[2];                    // |c|^2 and c . r before the current projection pass
+  double rnow;                     // 1: the current pass's update also takes the GCR step
 };
+
+// gamma_jj = |c|, s_j = 1/gamma_jj, alpha_j = c_j . r = s_j (c . r)
+__device__ __forceinline__ void norm_coef(GcrScal* S, int j) {
+  double g = sqrt(S->cc);
+  S->gjj = g;
+  S->gam[j * kMaxRestart + j] = g;
+  double s = 1.0 / g;
+  S->s[j] = s;
+  S->alpha[j] = s * S->cr;
+  S->rcoef = S->alpha[j] * s;
+}
+__global__ void k_norm_coef(GcrScal* S, int j) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  norm_coef(S, j);
+}
 
 // Gram-Schmidt coefficients from the dots d_i = C'_i . c (C'_i unnormalised,
 // c_i = s_i C'_i): gamma_i = s_i d_i is added to Gamma_ij and the update
-// c -= gamma_i c_i uses coef_i = gamma_i s_i.
+// c -= gamma_i c_i uses coef_i = gamma_i s_i.  With the c_i orthonormal,
+// |c - P c|^2 = |c|^2 - sum gamma_i^2.
 // After the first pass, the second is needed only when the projection removed
 // more than half of |c|^2 (|c - P c| < |c|/sqrt 2): below that, rounding
 // in the first pass can have left components along the c_i that a second
 // pass removes ("twice is enough", Kahan-Parlett).  pass2 is set to 0 or 1.
+// The pass that ends the projection (the first when no second runs) also
+// takes step 4 here: |c - P c|^2 from the sum above (at least half of |c|^2
+// in the first pass; in the second, P c is at rounding level), and
+// (c - P c) . r = c . r, r being orthogonal to every earlier c_i; rnow = 1
+// makes the projection's update take step 5 in the same pass.
 __global__ void k_gs_coef(GcrScal* S, int j, int first, const double* __restrict__ gate = nullptr) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (gate && *gate == 0.0) return;
@@ -1774,18 +1818,18 @@ __global__ void k_gs_coef(GcrScal* S, int j, int first, const double* __restrict
     S->coef[i] = gm * S->s[i];
     proj += gm * gm;
   }
-  if (first) S->pass2 = (S->cn2 - proj < 0.5 * S->cn2) ? 1.0 : 0.0;
-}
-// gamma_jj = |c|, s_j = 1/gamma_jj, alpha_j = c_j . r = s_j (c . r)
-__global__ void k_norm_coef(GcrScal* S, int j) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double g = sqrt(S->cc);
-  S->gjj = g;
-  S->gam[j * kMaxRestart + j] = g;
-  double s = 1.0 / g;
-  S->s[j] = s;
-  S->alpha[j] = s * S->cr;
-  S->rcoef = S->alpha[j] * s;
+  double rem = S->cq[0] - proj;
+  bool last = true;
+  if (first) {
+    S->pass2 = rem < 0.5 * S->cq[0] ? 1.0 : 0.0;
+    last = S->pass2 == 0.0;
+  }
+  S->rnow = last ? 1.0 : 0.0;
+  if (last) {
+    S->cc = rem;
+    S->cr = S->cq[1];
+    norm_coef(S, j);
+  }
 }
 // y = Gamma^{-1} alpha (upper triangular)
 __global__ void k_backsub(GcrScal* S, int m) {

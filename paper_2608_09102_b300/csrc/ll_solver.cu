@@ -788,10 +788,11 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
     if (mixed) {  // the float32 preconditioner's levels in float32 from chat32
       if (l == 1)
         k_galerkin_l1_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
-                                                    H->chat32, (float)inv_dt, C.val32, C.dinv32, H->flag);
+                                                    H->chat32, (float)inv_dt, C.val32);
       else
-        k_galerkin_bsr_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, H->lev[l - 1].val32,
-                                                     C.val32, C.dinv32, H->flag);
+        k_galerkin_bsr_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.sptr, C.sidx, H->lev[l - 1].val32, C.val32);
+      LL_LAUNCHED();
+      k_block_dinv<float><<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.diag, C.val32, C.dinv32, H->flag);
       LL_LAUNCHED();
       if (H->prm.precision == LL_MIXED_BF16) {
         k_cast_bf16<<<cdiv(9L * C.nnzb, kBlock), kBlock, 0, s>>>(9L * C.nnzb, C.val32, C.val16);
@@ -801,10 +802,11 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
     }
     if (l == 1)
       k_galerkin_l1_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
-                                                   H->chat64, inv_dt, C.val64, C.dinv64, H->flag);
+                                                   H->chat64, inv_dt, C.val64);
     else
-      k_galerkin_bsr_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, H->lev[l - 1].val64,
-                                                    C.val64, C.dinv64, H->flag);
+      k_galerkin_bsr_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.sptr, C.sidx, H->lev[l - 1].val64, C.val64);
+    LL_LAUNCHED();
+    k_block_dinv<double><<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.diag, C.val64, C.dinv64, H->flag);
     LL_LAUNCHED();
     if (C.sell && C.sgroups > 0) {
       k_sell_values<<<cdiv(C.sgroups * kSell, kBlock), kBlock, 0, s>>>(C.sgroups, C.n, C.sgc, C.soff, C.rowptr,
@@ -824,14 +826,23 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
       k_dense_from_bsr<double><<<cdiv(C.n, 64), 64, 0, s>>>(C.n, C.rowptr, C.col, C.val64, H->lu);
   }
   LL_LAUNCHED();
-  if (N <= kLuSmemMax) {  // factor in shared memory (one block), then one warp per column of the inverse
-    int nt = 32;
-    while (nt < N) nt *= 2;
-    size_t smem = sizeof(double) * N * N;
-    LL_CU(cudaFuncSetAttribute(k_lu_factor_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lu_factor_smem<<<1, nt, smem, s>>>(N, H->lu, H->perm, H->lu_status);
-    LL_LAUNCHED();
-    k_lu_inverse_warp<<<N, 32, 0, s>>>(N, H->lu, H->perm, H->ainv);
+  if (N <= kGjMax) {  // Gauss-Jordan on one cluster, the columns spread over its CTAs
+    int W = cdiv(N, kGjCluster);
+    size_t smem = sizeof(double) * ((size_t)W * N + 2 * (N + 1));
+    LL_CU(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kGjCluster);
+    cfg.blockDim = dim3(32 * W);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = kGjCluster;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    LL_CU(cudaLaunchKernelEx(&cfg, k_gj_inverse, N, (const double*)H->lu.p, H->ainv.p, H->lu_status.p));
     LL_LAUNCHED();
   } else {
     k_lu_factor<<<1, 1024, 0, s>>>(N, H->lu, H->perm, H->lu_status);
@@ -1348,60 +1359,66 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   // Gram-Schmidt loop of Algorithm 1 in exact arithmetic.  A second pass
   // corrects the first pass's rounding; it runs only when the first removed
   // more than half of |c|^2 (k_gs_coef sets the device flag pass2 that gates
-  // the second pass's kernels).  Then step 4's |c|^2 and c.r.
-  for (int pass = 0; pass < 2 && j > 0; ++pass) {
-    const double* gate = pass == 0 ? nullptr : &S->pass2;
-    // The timing scopes count no work for the second pass: the host does not
-    // know whether it ran, and it mostly returns at once (the kind's rate is
-    // then a lower bound).
-    double wk = pass == 0 ? 1.0 : 0.0;
-    for (int i0 = 0; i0 < j; i0 += kDotChunk) {
-      int cnt = std::min(kDotChunk, j - i0);
-      bool self = pass == 0 && i0 == 0;  // |c|^2 before the projection, with the first dots
-      {
-        LL_PROFW(LL_KIND_GCR_VECTOR, wk * 2.0 * cnt * n3, wk * 8.0 * (cnt + 1) * n3);
-        if (self)
-          launch_multidot<kDotChunk, true>(cnt, s, n3, H->C, i0, cj, H->partial);
-        else
-          launch_multidot<kDotChunk, false>(cnt, s, n3, H->C, i0, cj, H->partial, gate);
-        LL_LAUNCHED();
+  // the second pass's kernels).  The dots of the pass that ends the
+  // projection also give step 4's |c|^2 and c.r, and its update takes step 5
+  // (r -= alpha_j c_j, |r|^2) in the same sweep over the vectors.
+  if (j > 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      const double* gate = pass == 0 ? nullptr : &S->pass2;
+      // The timing scopes count no work for the second pass: the host does not
+      // know whether it ran, and it mostly returns at once (the kind's rate is
+      // then a lower bound).
+      double wk = pass == 0 ? 1.0 : 0.0;
+      for (int i0 = 0; i0 < j; i0 += kDotChunk) {
+        int cnt = std::min(kDotChunk, j - i0);
+        bool self = i0 == 0;  // |c|^2 and c.r before the projection, with the first dots
+        {
+          LL_PROFW(LL_KIND_GCR_VECTOR, wk * 2.0 * (cnt + (self ? 2 : 0)) * n3, wk * 8.0 * (cnt + (self ? 2 : 1)) * n3);
+          if (self)
+            launch_multidot<kDotChunk, true>(cnt, s, n3, H->C, i0, cj, H->partial, gate, H->r);
+          else
+            launch_multidot<kDotChunk, false>(cnt, s, n3, H->C, i0, cj, H->partial, gate);
+          LL_LAUNCHED();
+        }
+        {
+          LL_PROF(LL_KIND_GCR_VECTOR);
+          k_finish<<<cnt, kBlock, 0, s>>>(H->partial, S->d + i0, gate);
+          LL_LAUNCHED();
+          if (self) {
+            k_finish<<<2, kBlock, 0, s>>>(H->partial + (size_t)cnt * kRedBlocks, S->cq, gate);
+            LL_LAUNCHED();
+          }
+        }
       }
       {
         LL_PROF(LL_KIND_GCR_VECTOR);
-        k_finish<<<cnt, kBlock, 0, s>>>(H->partial, S->d + i0, gate);
+        k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0, gate);
         LL_LAUNCHED();
-        if (self) {
-          k_finish<<<1, kBlock, 0, s>>>(H->partial + (size_t)cnt * kRedBlocks, &S->cn2);
-          LL_LAUNCHED();
-        }
+      }
+      {
+        LL_PROFW(LL_KIND_GCR_VECTOR, wk * 2.0 * (j + 2) * n3, wk * 8.0 * (j + 4) * n3);
+        kg_multiaxpy_r<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->C, j, S->coef, H->r, &S->rnow, &S->rcoef,
+                                                     H->partial, gate);
+        LL_LAUNCHED();
       }
     }
+  } else {
+    {
+      LL_PROFW(LL_KIND_GCR_VECTOR, 4.0 * n3, 16.0 * n3);
+      kg_dot2<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->r, H->partial);             // step 4
+      LL_LAUNCHED();
+    }
+    finish(H, 2, &S->cc);
     {
       LL_PROF(LL_KIND_GCR_VECTOR);
-      k_gs_coef<<<1, 1, 0, s>>>(S, j, pass == 0, gate);
+      k_norm_coef<<<1, 1, 0, s>>>(S, j);
       LL_LAUNCHED();
     }
     {
-      LL_PROFW(LL_KIND_GCR_VECTOR, wk * 2.0 * j * n3, wk * 8.0 * (j + 2) * n3);
-      kg_multiaxpy<<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, cj, H->C, j, S->coef, gate);
+      LL_PROFW(LL_KIND_GCR_VECTOR, 4.0 * n3, 24.0 * n3);
+      kg_rupdate<<<kRedBlocks, kBlock, 0, s>>>(n3, H->r, cj, &S->rcoef, H->partial); // step 5
       LL_LAUNCHED();
     }
-  }
-  {
-    LL_PROFW(LL_KIND_GCR_VECTOR, 4.0 * n3, 16.0 * n3);
-    kg_dot2<<<kRedBlocks, kBlock, 0, s>>>(n3, cj, H->r, H->partial);             // step 4
-    LL_LAUNCHED();
-  }
-  finish(H, 2, &S->cc);
-  {
-    LL_PROF(LL_KIND_GCR_VECTOR);
-    k_norm_coef<<<1, 1, 0, s>>>(S, j);
-    LL_LAUNCHED();
-  }
-  {
-    LL_PROFW(LL_KIND_GCR_VECTOR, 4.0 * n3, 24.0 * n3);
-    kg_rupdate<<<kRedBlocks, kBlock, 0, s>>>(n3, H->r, cj, &S->rcoef, H->partial); // step 5
-    LL_LAUNCHED();
   }
   finish(H, 1, &S->rn2);
 }
