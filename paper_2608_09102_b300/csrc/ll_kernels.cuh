@@ -230,18 +230,22 @@ __global__ void k_block_rows(int n, const int* __restrict__ rowptr, int* __restr
 }
 
 // One thread per coarse block: neighbouring threads write neighbouring
-// blocks (coalesced stores).  Each block sums its slot list in a fixed order.
+// blocks (coalesced stores), or, with perm, the blocks in the order perm (by
+// decreasing slot-list length, ties by index: the lanes of a warp sum lists
+// of about the same length).  Each block sums its slot list in a fixed order.
 // The diagonal blocks' inverses are a separate pass (k_block_dinv): inside
 // this kernel only about one lane in 13 holds a diagonal block, and the warp
 // would issue the inverse's float64 instructions for all 32 lanes.
 // level 1: A_1(I,J) = delta_IJ |G_I|/dt I + sum_{k in G_I} w_kJ Chat_k
 template <typename T>
-__global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ prow, const int* __restrict__ col,
-                                  const int* __restrict__ sptr, const int* __restrict__ sidx,
-                                  const int* __restrict__ sw, const int* __restrict__ mptr, long n2,
-                                  const T* __restrict__ chat, T inv_dt, T* __restrict__ val) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nnzb) return;
+__global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ perm, const int* __restrict__ prow,
+                                  const int* __restrict__ col, const int* __restrict__ sptr,
+                                  const int* __restrict__ sidx, const int* __restrict__ sw,
+                                  const int* __restrict__ mptr, long n2, const T* __restrict__ chat, T inv_dt,
+                                  T* __restrict__ val) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  int p = perm ? perm[t] : t;
   int I = prow[p];
   T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
@@ -260,10 +264,11 @@ __global__ void k_galerkin_l1_blk(int nnzb, const int* __restrict__ prow, const 
 
 // levels >= 2: sum of the fine blocks of each coarse slot
 template <typename T>
-__global__ void k_galerkin_bsr_blk(int nnzb, const int* __restrict__ sptr, const int* __restrict__ sidx,
-                                   const T* __restrict__ fval, T* __restrict__ val) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nnzb) return;
+__global__ void k_galerkin_bsr_blk(int nnzb, const int* __restrict__ perm, const int* __restrict__ sptr,
+                                   const int* __restrict__ sidx, const T* __restrict__ fval, T* __restrict__ val) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  int p = perm ? perm[t] : t;
   T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int q = sptr[p]; q < sptr[p + 1]; ++q) {
     const T* f = fval + 9 * (long)sidx[q];
@@ -376,26 +381,63 @@ __global__ void k_lu_factor(int N, double* __restrict__ a, int* __restrict__ per
 }
 
 // Coarsest inverse for up to kGjMax unknowns: in-place Gauss-Jordan
-// elimination with partial pivoting on one thread-block cluster.  Column j of
-// the matrix lives in the shared memory of CTA j % P at local column j / P,
-// one warp per local column, lanes over rows.  Step k: the warp holding
+// elimination with partial pivoting on one thread-block cluster of P CTAs.
+// Column j of the matrix lives in the shared memory of CTA j % P at local
+// column j / P, one warp per local column, lanes over rows.  The warp holding
 // column k finds the pivot row p (largest |a_ik| over i >= k, ties to the
 // lowest row, as in k_lu_factor), publishes p, column k with rows k and p
 // exchanged and the pivot's reciprocal in its CTA's shared memory, and sets
 // its own column to e_p.  After a cluster barrier every warp reads them
-// through distributed shared memory and applies the step to its column: rows
-// k and p exchanged, row k times the reciprocal, f_i times row k subtracted
-// from every other row i.
-// Column k then holds a column of the inverse with its rows in pivot order;
-// undoing the row exchanges in reverse order on the columns puts the inverse
-// in order.  N^3 multiply-adds spread over P SMs, one cluster barrier per
-// step.  The published column is double-buffered: the owner of step k + 2
-// writes the buffer of step k only after the barrier of step k + 1, which
-// every CTA reaches after its reads of step k.  a: row-major N x N; ainv:
-// column-major; *status = 1 on a zero or non-finite pivot.
-constexpr int kGjCluster = 8;
+// through distributed shared memory and applies step k to its column: rows k
+// and p exchanged, row k times the reciprocal, f_i times row k subtracted from
+// every other row i.  The warp holding column k + 1 publishes step k + 1 right
+// after its own update of step k, while the other warps are still updating,
+// so each step costs one barrier.  Column k then holds a column of the inverse
+// with its rows in pivot order; undoing the row exchanges in reverse order on
+// the columns puts the inverse in order.  N^3 multiply-adds spread over P SMs.
+// The published column is double-buffered: step k + 2 is published after the
+// barrier that ends step k's reads.  a: row-major N x N; ainv: column-major;
+// *status = 1 on a zero or non-finite pivot.
 constexpr int kGjMax = 256;               // at most 32 local columns (warps) per CTA
 constexpr int kGjRows = kGjMax / 32;      // rows per lane
+
+// pivot search and publication of step k by the warp holding column k
+__device__ __forceinline__ void gj_publish(int N, int k, double* colv, double* pub, int* pubp, int lane,
+                                           int* status) {
+  const int buf = k & 1;
+  double bv = -1.0;
+  int bi = N;
+  for (int i = k + lane; i < N; i += 32) {  // rows ascending per lane: the first maximum
+    double v = fabs(colv[i]);
+    if (v > bv) {
+      bv = v;
+      bi = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (v2 > bv || (v2 == bv && i2 < bi)) {
+      bv = v2;
+      bi = i2;
+    }
+  }
+  int p = bi;
+  if (!(bv > 0.0) || !isfinite(bv)) {
+    if (lane == 0) atomicExch(status, 1);
+    p = k;
+  }
+  double* f = pub + buf * (N + 1);
+  for (int i = lane; i < N; i += 32) f[i] = colv[i == k ? p : (i == p ? k : i)];
+  if (lane == 0) {
+    f[N] = 1.0 / colv[p];
+    pubp[buf] = p;
+  }
+  __syncwarp();
+  for (int i = lane; i < N; i += 32) colv[i] = i == p ? 1.0 : 0.0;
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(1024, 1) k_gj_inverse(int N, const double* __restrict__ a,
                                                         double* __restrict__ ainv, int* __restrict__ status) {
   namespace cg = cooperative_groups;
@@ -414,51 +456,23 @@ __global__ void __launch_bounds__(1024, 1) k_gj_inverse(int N, const double* __r
   if (have)
     for (int i = lane; i < N; i += 32) colv[i] = a[(long)i * N + j];
   if (r == 0 && threadIdx.x == 0) *status = 0;
+  cl.sync();  // status cleared before any pivot can set it
+  if (j == 0) gj_publish(N, 0, colv, pub, pubp, lane, status);
   cl.sync();
   for (int k = 0; k < N; ++k) {
-    const int buf = k & 1;
-    if (r == k % P && w == k / P) {
-      double bv = -1.0;
-      int bi = N;
-      for (int i = k + lane; i < N; i += 32) {  // rows ascending per lane: the first maximum
-        double v = fabs(colv[i]);
-        if (v > bv) {
-          bv = v;
-          bi = i;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-        int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (v2 > bv || (v2 == bv && i2 < bi)) {
-          bv = v2;
-          bi = i2;
-        }
-      }
-      int p = bi;
-      if (!(bv > 0.0) || !isfinite(bv)) {
-        if (lane == 0) atomicExch(status, 1);
-        p = k;
-      }
-      double* f = pub + buf * (N + 1);
-      for (int i = lane; i < N; i += 32) f[i] = colv[i == k ? p : (i == p ? k : i)];
-      if (lane == 0) {
-        f[N] = 1.0 / colv[p];
-        pubp[buf] = p;
-      }
-      __syncwarp();
-      for (int i = lane; i < N; i += 32) colv[i] = i == p ? 1.0 : 0.0;
-    }
-    cl.sync();
-    const int o = k % P;
+    const int buf = k & 1, o = k % P;
     const double* f = cl.map_shared_rank(pub + buf * (N + 1), o);
     const int p = *cl.map_shared_rank(&pubp[buf], o);
     if (threadIdx.x == 0) pivs[k] = p;
     if (have) {
-      // every remote load issued before the first use
+      // every remote load issued before the first use; row blocks past N
+      // skipped whole (a masked float64 instruction costs as much as a full one)
       double fr[kGjRows];
 #pragma unroll
-      for (int t = 0; t < kGjRows; ++t) fr[t] = lane + 32 * t < N ? f[lane + 32 * t] : 0.0;
+      for (int t = 0; t < kGjRows; ++t) {
+        if (32 * t >= N) break;
+        fr[t] = lane + 32 * t < N ? f[lane + 32 * t] : 0.0;
+      }
       double ip = f[N];
       if (lane == 0 && p != k) {
         double t = colv[k];
@@ -470,11 +484,14 @@ __global__ void __launch_bounds__(1024, 1) k_gj_inverse(int N, const double* __r
       __syncwarp();
 #pragma unroll
       for (int t = 0; t < kGjRows; ++t) {
+        if (32 * t >= N) break;
         int i = lane + 32 * t;
         if (i < N) colv[i] = i == k ? rk : colv[i] - fr[t] * rk;
       }
       __syncwarp();
+      if (j == k + 1) gj_publish(N, k + 1, colv, pub, pubp, lane, status);
     }
+    cl.sync();
   }
   cl.sync();  // no CTA leaves while another may still read its published column
   if (threadIdx.x == 0) {
@@ -1733,12 +1750,14 @@ __global__ void __launch_bounds__(256) kg_rupdate(long n, double* __restrict__ r
   block_reduce_store<1>(acc, partial, 1);
 }
 
-// x += sum_k y_k Z_k
+// x += sum_k y_k Z_k; mdev: m read from the device (a cycle run from one graph)
 template <typename TZ>
 __global__ void __launch_bounds__(256) kg_xupdate(long n, double* __restrict__ x, const TZ* __restrict__ Z, int m,
-                                                  const double* __restrict__ y) {
+                                                  const double* __restrict__ y,
+                                                  const double* __restrict__ mdev = nullptr) {
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= n) return;
+  if (mdev) m = (int)*mdev;
   double a = x[t];
   for (int k = 0; k < m; ++k) a += y[k] * (double)Z[(long)k * n + t];
   x[t] = a;
@@ -1778,6 +1797,10 @@ struct GcrScal {
   double alpha[kMaxRestart], s[kMaxRestart], y[kMaxRestart];
   double cq[2];                    // |c|^2 and c . r before the current projection pass
   double rnow;                     // 1: the current pass's update also takes the GCR step
+  // a GCR cycle run from one graph: iterations run, directions kept, 1 on a
+  // breakdown, 1 while active; the stopping tolerance
+  double cyc[4];
+  double rtol;
 };
 
 // gamma_jj = |c|, s_j = 1/gamma_jj, alpha_j = c_j . r = s_j (c . r)
@@ -1831,14 +1854,56 @@ __global__ void k_gs_coef(GcrScal* S, int j, int first, const double* __restrict
     norm_coef(S, j);
   }
 }
-// y = Gamma^{-1} alpha (upper triangular)
+// y = Gamma^{-1} alpha (upper triangular); m < 0: the directions kept by a
+// cycle run from one graph
 __global__ void k_backsub(GcrScal* S, int m) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (m < 0) m = (int)S->cyc[1];
   for (int i = m - 1; i >= 0; --i) {
     double a = S->alpha[i];
     for (int k = i + 1; k < m; ++k) a -= S->gam[i * kMaxRestart + k] * S->y[k];
     S->y[i] = a / S->gam[i * kMaxRestart + i];
   }
+}
+
+// A GCR cycle run from one CUDA graph: iteration j sits in a conditional
+// node, followed by k_gcr_check, which takes the host's tests on the device
+// and sets the condition of iteration j + 1.  k_gcr_cycle_begin (before the
+// graph) marks the cycle active.
+__global__ void k_gcr_cycle_begin(GcrScal* S, double rtol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  S->cyc[0] = 0;
+  S->cyc[1] = 0;
+  S->cyc[2] = 0;
+  S->cyc[3] = 1;
+  S->rtol = rtol;
+}
+// While the cycle is active, iteration j ran: a zero or non-finite gamma_jj
+// is a breakdown with j directions kept, a non-finite |r| one with j + 1, and
+// |r| < rtol |b| ends the cycle (step 6); the same tests, in the same
+// arithmetic, as the host's loop over single iterations.
+__global__ void k_gcr_check(GcrScal* S, int j, cudaGraphConditionalHandle next, int has_next) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bool act = S->cyc[3] != 0.0;
+  if (act) {
+    S->cyc[0] = j + 1;
+    double g = S->gjj;
+    if (!(g > 0.0) || !isfinite(g)) {
+      S->cyc[2] = 1;
+      act = false;
+    } else {
+      S->cyc[1] = j + 1;
+      double rj = sqrt(S->rn2);
+      if (!isfinite(rj)) {
+        S->cyc[2] = 1;
+        act = false;
+      } else if (rj < S->rtol * sqrt(S->bn2)) {
+        act = false;
+      }
+    }
+    S->cyc[3] = act ? 1.0 : 0.0;
+  }
+  if (has_next) cudaGraphSetConditional(next, act ? 1u : 0u);
 }
 
 // m <- x / |x| per cell (the projection step), natural SoA

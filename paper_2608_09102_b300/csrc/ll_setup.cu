@@ -664,6 +664,28 @@ void colour_classes(int n, const int* colour, int ncol, const int* key, int nkey
   LL_CU(cudaStreamSynchronize(s));
 }
 
+// The blocks of a Galerkin level in order of decreasing slot-list length
+// (ties by index): the Galerkin threads take them in this order, so that the
+// lanes of a warp sum lists of about the same length (the diagonal blocks'
+// lists are several times longer than the others').
+constexpr int kLenKeys = 64;
+__global__ void k_len_keys(int n, const int* __restrict__ sptr, int* __restrict__ key, int* __restrict__ zero) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int len = sptr[p + 1] - sptr[p];
+  key[p] = kLenKeys - 1 - (len < kLenKeys - 1 ? len : kLenKeys - 1);
+  zero[p] = 0;
+}
+void order_by_length(int n, const int* sptr, DBuf<int>& perm, cudaStream_t s) {
+  DBuf<int> key, zero, cptr;
+  key.alloc(n);
+  zero.alloc(n);
+  k_len_keys<<<cdiv(n, kBlock), kBlock, 0, s>>>(n, sptr, key, zero);
+  LL_LAUNCHED();
+  std::vector<int> h_cptr;
+  colour_classes(n, zero, 1, key, kLenKeys, cptr, perm, h_cptr, s);
+}
+
 // ---------------------------------------------------------------------------
 // BSR pattern of a coarse operator: graph neighbours plus the diagonal
 // ---------------------------------------------------------------------------

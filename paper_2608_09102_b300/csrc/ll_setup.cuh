@@ -18,6 +18,7 @@ constexpr int kRowKeysExact = 1024;  // distinct exact row-work keys
 void row_work_keys(const DevGraph& g, const int* colour, bool exact, DBuf<int>& key, cudaStream_t s);
 void colour_classes(int n, const int* colour, int ncol, const int* key, int nkeys, DBuf<int>& cptr, DBuf<int>& crow,
                     std::vector<int>& h_cptr, cudaStream_t s);
+void order_by_length(int n, const int* sptr, DBuf<int>& perm, cudaStream_t s);
 void bsr_pattern(const DevGraph& g, DBuf<int>& rowptr, DBuf<int>& col, DBuf<int>& diag, int& nnzb, cudaStream_t s);
 void slot_map_level1(const GridGeom& g, const int* agg_nat, const DevGraph& g1, const int* rowptr, const int* col,
                      int nnzb, DBuf<int>& sptr, DBuf<int>& sidx, DBuf<int>& sw, cudaStream_t s);

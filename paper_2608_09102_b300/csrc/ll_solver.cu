@@ -47,6 +47,7 @@ struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
   DBuf<int> rowptr, col, diag;      // BSR pattern
   DBuf<int> prow;                   // row of each block
   DBuf<int> sptr, sidx, sw;         // Galerkin slot map from the finer level
+  DBuf<int> gperm;                  // blocks by decreasing slot-list length (Galerkin thread order)
   DBuf<int> mptr, mem;              // members in the finer level (level 1: red-black slots)
   DBuf<int> mptr0, mem0;            // level 1: colour-0 slots only
   DBuf<int> agg;                    // this level -> next level
@@ -124,6 +125,7 @@ struct ll_mg_hierarchy {
   CLevel lev[kMaxLevels];
   // coarsest dense LU and its inverse (column-major)
   int ncoarse3 = 0;
+  int gj_cluster = 0;  // CTAs of the coarsest inverse's cluster (0: not chosen yet)
   DBuf<double> lu, ainv;
   DBuf<int> perm, lu_status, flag;
   // GCR workspace (red-black layout, 3*n2 doubles per vector)
@@ -191,6 +193,17 @@ struct ll_mg_hierarchy {
     int nl;  // kernel launches between b and e
   };
   std::vector<GPair> gpairs[kMaxRestart];
+  // a GCR cycle of m iterations as one graph (conditional nodes), by m
+  cudaGraphExec_t cycles[kMaxRestart + 1] = {nullptr};
+  long long cyc_body[kMaxRestart] = {0};  // kernels of iteration j in a cycle graph
+  long long cyc_tail = 0;                 // kernels after the cycle's last check
+  bool cyc_failed = false;                // the graphs could not be built: one graph per iteration
+  void drop_cycles() {
+    for (auto& c : cycles) {
+      if (c) cudaGraphExecDestroy(c);
+      c = nullptr;
+    }
+  }
   void drop_graph(int j) {
     if (graphs[j]) cudaGraphExecDestroy(graphs[j]);
     graphs[j] = nullptr;
@@ -203,6 +216,7 @@ struct ll_mg_hierarchy {
   ~ll_mg_hierarchy() {
     if (s) cudaStreamSynchronize(s);
     for (int j = 0; j < kMaxRestart; ++j) drop_graph(j);
+    drop_cycles();
     if (h_head) cudaFreeHost(h_head);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (entry_ev) cudaEventDestroy(entry_ev);
@@ -329,6 +343,7 @@ bool wide_lanes(long rows) {
   return lanes<T>() >= 8 || rows < kWideLaneRows;
 }
 constexpr int kDotChunk = 8;
+constexpr int kGalerkinSortBlocks = 200000;  // float64 Galerkin levels >= 2 with this many blocks: ordered threads
 // Coarse-level kernels use small blocks: a colour class of a small level then
 // spreads over many SMs instead of queueing on the float64 units of one.
 constexpr int kCoarseBlock = 64;
@@ -450,6 +465,14 @@ void symbolic(ll_mg_hierarchy* H) {
     build_members(F.n, F.agg, C.n, C.mptr, C.mem, s);
     slot_map_bsr(F.n, F.rowptr, F.col, F.agg, C.rowptr, C.col, C.nnzb, C.sptr, C.sidx, s);
   }
+  // float64 Galerkin products of the large levels >= 2 by slot-list length
+  // (level 2 at 128^3: 0.64 -> 0.35 ms); level 1 and the small levels keep
+  // the row order, whose loads share cache lines (level 1 sorted: 0.67 ->
+  // 1.01 ms), and so do float32 products, whose divergence costs little
+  if (H->prm.precision == LL_FP64)
+    for (int l = 2; l < H->nlev; ++l)
+      if (H->lev[l].nnzb >= kGalerkinSortBlocks)
+        order_by_length(H->lev[l].nnzb, H->lev[l].sptr, H->lev[l].gperm, s);
   for (int l = 1; l < H->nlev; ++l)
     if (H->lev[l].sell) sell_build(H->lev[l], s);
   LL_CU(cudaStreamSynchronize(s));
@@ -513,7 +536,7 @@ void allocate(ll_mg_hierarchy* H) {
   H->partial.alloc((size_t)(kMaxRestart + 2) * kRedBlocks);
   H->scal.alloc(1);
   H->scal.zero(H->s);
-  LL_CU(cudaMallocHost((void**)&H->h_head, 8 * sizeof(double)));
+  LL_CU(cudaMallocHost((void**)&H->h_head, 12 * sizeof(double)));  // 8 head scalars, then cyc
   H->stepb.alloc(3 * H->g.n);
   H->stepx.alloc(3 * H->g.n);
   if (H->nlev == 1) {
@@ -787,10 +810,10 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
     int nb = cdiv(C.nnzb, 128);
     if (mixed) {  // the float32 preconditioner's levels in float32 from chat32
       if (l == 1)
-        k_galerkin_l1_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
-                                                    H->chat32, (float)inv_dt, C.val32);
+        k_galerkin_l1_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.gperm, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr,
+                                                    H->n2, H->chat32, (float)inv_dt, C.val32);
       else
-        k_galerkin_bsr_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.sptr, C.sidx, H->lev[l - 1].val32, C.val32);
+        k_galerkin_bsr_blk<float><<<nb, 128, 0, s>>>(C.nnzb, C.gperm, C.sptr, C.sidx, H->lev[l - 1].val32, C.val32);
       LL_LAUNCHED();
       k_block_dinv<float><<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.diag, C.val32, C.dinv32, H->flag);
       LL_LAUNCHED();
@@ -801,10 +824,10 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
       continue;
     }
     if (l == 1)
-      k_galerkin_l1_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr, H->n2,
-                                                   H->chat64, inv_dt, C.val64);
+      k_galerkin_l1_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.gperm, C.prow, C.col, C.sptr, C.sidx, C.sw, C.mptr,
+                                                   H->n2, H->chat64, inv_dt, C.val64);
     else
-      k_galerkin_bsr_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.sptr, C.sidx, H->lev[l - 1].val64, C.val64);
+      k_galerkin_bsr_blk<double><<<nb, 128, 0, s>>>(C.nnzb, C.gperm, C.sptr, C.sidx, H->lev[l - 1].val64, C.val64);
     LL_LAUNCHED();
     k_block_dinv<double><<<cdiv(C.n, 128), 128, 0, s>>>(C.n, C.diag, C.val64, C.dinv64, H->flag);
     LL_LAUNCHED();
@@ -827,21 +850,36 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
   }
   LL_LAUNCHED();
   if (N <= kGjMax) {  // Gauss-Jordan on one cluster, the columns spread over its CTAs
-    int W = cdiv(N, kGjCluster);
-    size_t smem = sizeof(double) * ((size_t)W * N + 2 * (N + 1));
-    LL_CU(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kGjCluster);
-    cfg.blockDim = dim3(32 * W);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
+    // 16 CTAs where a cluster of that size can be scheduled, else 8
+    auto config = [&](int P, cudaLaunchConfig_t& cfg, cudaLaunchAttribute& at) {
+      int W = cdiv(N, P);
+      cfg = {};
+      cfg.gridDim = dim3(P);
+      cfg.blockDim = dim3(32 * W);
+      cfg.dynamicSmemBytes = sizeof(double) * ((size_t)W * N + 2 * (N + 1));
+      cfg.stream = s;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = P;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+    };
+    cudaLaunchConfig_t cfg;
     cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = kGjCluster;
-    at.val.clusterDim.y = 1;
-    at.val.clusterDim.z = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
+    if (H->gj_cluster == 0) {
+      H->gj_cluster = 8;
+      config(16, cfg, at);
+      int nclusters = 0;
+      if (cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+          cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)cfg.dynamicSmemBytes) == cudaSuccess &&
+          cudaOccupancyMaxActiveClusters(&nclusters, k_gj_inverse, &cfg) == cudaSuccess && nclusters > 0)
+        H->gj_cluster = 16;
+      cudaGetLastError();
+    }
+    config(H->gj_cluster, cfg, at);
+    LL_CU(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes));
     LL_CU(cudaLaunchKernelEx(&cfg, k_gj_inverse, N, (const double*)H->lu.p, H->ainv.p, H->lu_status.p));
     LL_LAUNCHED();
   } else {
@@ -1311,13 +1349,17 @@ void finish(ll_mg_hierarchy* H, int nvals, double* out) {
   LL_LAUNCHED();
 }
 
-void true_residual(ll_mg_hierarchy* H) {
+void true_residual_launch(ll_mg_hierarchy* H) {
   {
     LL_PROFW(LL_KIND_OUTER_APPLY, 42.0 * H->g.n, 144.0 * H->g.n);
     kg_residual<<<kRedBlocks, kBlock, 0, H->s>>>(H->g, H->bw, H->xw, H->chat64, 1.0 / H->dt, H->r, H->partial);
     LL_LAUNCHED();
   }
   finish(H, 2, &H->scal.p->rn2);
+}
+
+void true_residual(ll_mg_hierarchy* H) {
+  true_residual_launch(H);
   read_head(H);
 }
 
@@ -1423,6 +1465,15 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
   finish(H, 1, &S->rn2);
 }
 
+// the graphs hold 1/dt as a kernel argument: a new dt drops them
+void graphs_for_dt(ll_mg_hierarchy* H) {
+  if (H->graph_dt != H->dt) {
+    for (int q = 0; q < kMaxRestart; ++q) H->drop_graph(q);
+    H->drop_cycles();
+    H->graph_dt = H->dt;
+  }
+}
+
 // run iteration j, from a CUDA graph captured on first use (one launch
 // instead of a few hundred), then fold any graph-timed kernels into the totals
 template <typename T, typename TM>
@@ -1431,10 +1482,7 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
     iteration_body<T, TM>(H, j);
     return;
   }
-  if (H->graph_dt != H->dt) {
-    for (int q = 0; q < kMaxRestart; ++q) H->drop_graph(q);
-    H->graph_dt = H->dt;
-  }
+  graphs_for_dt(H);
   if (H->graphs[j] && H->graph_mask[j] != H->prof_mask) H->drop_graph(j);
   if (!H->graphs[j]) {
     cudaGraph_t graph;
@@ -1472,6 +1520,126 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
   }
 }
 
+// A GCR cycle of m iterations as one CUDA graph: conditional node j holds
+// iteration j, and the kernel k_gcr_check after it takes the host's tests on
+// the device and sets whether iteration j + 1 runs; after the last check,
+// y = Gamma^{-1} alpha, x += Z y and the true residual of the new x.  The host
+// then waits once per cycle instead of once per iteration.  Returns false
+// (and the solver keeps one graph per iteration) if the graph cannot be built.
+template <typename T, typename TM>
+bool build_cycle(ll_mg_hierarchy* H, int m) {
+  cudaStream_t s = H->s;
+  GcrScal* S = H->scal.p;
+  long n3 = H->n3;
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
+  std::vector<cudaGraphConditionalHandle> hs(m);
+  bool ok = true;
+  for (int j = 0; j < m && ok; ++j)
+    ok = cudaGraphConditionalHandleCreate(&hs[j], G, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNode_t prev = nullptr;
+  for (int j = 0; j < m && ok; ++j) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hs[j];
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t ifn = nullptr;
+    if (cudaGraphAddNode(&ifn, G, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    if (cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    long long before = t_launches;
+    H->capturing = j;
+    try {
+      iteration_body<T, TM>(H, j);
+    } catch (Status) {
+      ok = false;
+    }
+    H->capturing = -1;
+    cudaGraph_t body = nullptr;
+    if (cudaStreamEndCapture(s, &body) != cudaSuccess) ok = false;
+    H->cyc_body[j] = t_launches - before;  // counted per launch by run_cycle
+    g_launches.fetch_sub(H->cyc_body[j]);
+    if (!ok) break;
+    int jj = j, has_next = j + 1 < m ? 1 : 0;
+    cudaGraphConditionalHandle next = has_next ? hs[j + 1] : 0;
+    void* args[] = {&S, &jj, &next, &has_next};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_gcr_check;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    cudaGraphNode_t chk = nullptr;
+    if (cudaGraphAddKernelNode(&chk, G, &ifn, 1, &kp) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    prev = chk;
+  }
+  if (ok && cudaStreamBeginCaptureToGraph(s, G, &prev, nullptr, 1, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    long long before = t_launches;
+    try {
+      {
+        LL_PROF(LL_KIND_GCR_VECTOR);
+        k_backsub<<<1, 1, 0, s>>>(S, -1);
+        LL_LAUNCHED();
+      }
+      {
+        LL_PROF(LL_KIND_GCR_VECTOR);
+        kg_xupdate<T><<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, H->xw, H->Z<T>(), 0, S->y, &S->cyc[1]);
+        LL_LAUNCHED();
+      }
+      true_residual_launch(H);
+    } catch (Status) {
+      ok = false;
+    }
+    cudaGraph_t tail = nullptr;
+    if (cudaStreamEndCapture(s, &tail) != cudaSuccess) ok = false;
+    H->cyc_tail = t_launches - before;
+    g_launches.fetch_sub(H->cyc_tail);
+  } else {
+    ok = false;
+  }
+  if (ok) ok = cudaGraphInstantiate(&H->cycles[m], G, 0) == cudaSuccess;
+  cudaGraphDestroy(G);
+  if (!ok) {
+    cudaGetLastError();
+    H->cycles[m] = nullptr;
+  }
+  return ok;
+}
+
+// one cycle of at most m iterations from its graph; false: not available
+template <typename T, typename TM>
+bool run_cycle(ll_mg_hierarchy* H, int m, double rtol, int* iters, bool* broke) {
+  if (!H->use_graphs || H->cyc_failed || H->prof_mask != 0) return false;
+  graphs_for_dt(H);
+  if (!H->cycles[m] && !build_cycle<T, TM>(H, m)) {
+    H->cyc_failed = true;
+    return false;
+  }
+  cudaStream_t s = H->s;
+  k_gcr_cycle_begin<<<1, 1, 0, s>>>(H->scal.p, rtol);
+  LL_LAUNCHED();
+  LL_CU(cudaGraphLaunch(H->cycles[m], s));
+  LL_CU(cudaMemcpyAsync(H->h_head, H->scal.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LL_CU(cudaMemcpyAsync(H->h_head + 8, H->scal.p->cyc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LL_CU(cudaStreamSynchronize(s));
+  int it = (int)H->h_head[8];
+  long long nk = m + H->cyc_tail;
+  for (int j = 0; j < it; ++j) nk += H->cyc_body[j];
+  g_launches.fetch_add(nk);
+  *iters = it;
+  *broke = H->h_head[10] != 0.0;
+  return true;
+}
+
 template <typename T, typename TM>
 int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int* iters, double* relres) {
   cudaStream_t s = H->s;
@@ -1485,8 +1653,11 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
   GcrScal* S = H->scal.p;
   int total = 0, status = LL_NOT_CONVERGED;
   double bnorm = 0;
+  bool fresh = false;    // the head already holds the true residual of x (a cycle graph computed it)
+  bool current = false;  // the loop ended on the true residual of the final x
   for (;;) {
-    true_residual(H);
+    if (!fresh) true_residual(H);
+    fresh = false;
     double rn2 = H->h_head[0];
     bnorm = sqrt(H->h_head[1]);
     if (bnorm == 0.0) {
@@ -1501,10 +1672,27 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
     }
     if (sqrt(rn2) < rtol * bnorm) {
       status = LL_OK;
+      current = true;
       break;
     }
-    if (total >= H->prm.maxit) break;
+    if (total >= H->prm.maxit) {
+      current = true;
+      break;
+    }
     int m = std::min(H->prm.restart, H->prm.maxit - total);
+    {
+      int it = 0;
+      bool broke = false;
+      if (run_cycle<T, TM>(H, m, rtol, &it, &broke)) {
+        total += it;
+        if (broke) {
+          status = LL_BREAKDOWN;
+          break;
+        }
+        fresh = true;
+        continue;
+      }
+    }
     int jdone = 0;
     bool broke = false;
     for (int j = 0; j < m; ++j) {
@@ -1541,7 +1729,7 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
       break;
     }
   }
-  true_residual(H);
+  if (!current) true_residual(H);
   if (iters) *iters = total;
   if (relres) *relres = bnorm > 0 ? sqrt(H->h_head[0]) / bnorm : 0.0;
   k_from_rb<double, double><<<nbs, kBlock, 0, s>>>(g, H->nat_of_slot, H->xw, x_nat);
