@@ -1750,14 +1750,12 @@ __global__ void __launch_bounds__(256) kg_rupdate(long n, double* __restrict__ r
   block_reduce_store<1>(acc, partial, 1);
 }
 
-// x += sum_k y_k Z_k; mdev: m read from the device (a cycle run from one graph)
+// x += sum_k y_k Z_k
 template <typename TZ>
 __global__ void __launch_bounds__(256) kg_xupdate(long n, double* __restrict__ x, const TZ* __restrict__ Z, int m,
-                                                  const double* __restrict__ y,
-                                                  const double* __restrict__ mdev = nullptr) {
+                                                  const double* __restrict__ y) {
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  if (mdev) m = (int)*mdev;
   double a = x[t];
   for (int k = 0; k < m; ++k) a += y[k] * (double)Z[(long)k * n + t];
   x[t] = a;
@@ -1797,10 +1795,6 @@ struct GcrScal {
   double alpha[kMaxRestart], s[kMaxRestart], y[kMaxRestart];
   double cq[2];                    // |c|^2 and c . r before the current projection pass
   double rnow;                     // 1: the current pass's update also takes the GCR step
-  // a GCR cycle run from one graph: iterations run, directions kept, 1 on a
-  // breakdown, 1 while active; the stopping tolerance
-  double cyc[4];
-  double rtol;
 };
 
 // gamma_jj = |c|, s_j = 1/gamma_jj, alpha_j = c_j . r = s_j (c . r)
@@ -1854,56 +1848,14 @@ __global__ void k_gs_coef(GcrScal* S, int j, int first, const double* __restrict
     norm_coef(S, j);
   }
 }
-// y = Gamma^{-1} alpha (upper triangular); m < 0: the directions kept by a
-// cycle run from one graph
+// y = Gamma^{-1} alpha (upper triangular)
 __global__ void k_backsub(GcrScal* S, int m) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (m < 0) m = (int)S->cyc[1];
   for (int i = m - 1; i >= 0; --i) {
     double a = S->alpha[i];
     for (int k = i + 1; k < m; ++k) a -= S->gam[i * kMaxRestart + k] * S->y[k];
     S->y[i] = a / S->gam[i * kMaxRestart + i];
   }
-}
-
-// A GCR cycle run from one CUDA graph: iteration j sits in a conditional
-// node, followed by k_gcr_check, which takes the host's tests on the device
-// and sets the condition of iteration j + 1.  k_gcr_cycle_begin (before the
-// graph) marks the cycle active.
-__global__ void k_gcr_cycle_begin(GcrScal* S, double rtol) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  S->cyc[0] = 0;
-  S->cyc[1] = 0;
-  S->cyc[2] = 0;
-  S->cyc[3] = 1;
-  S->rtol = rtol;
-}
-// While the cycle is active, iteration j ran: a zero or non-finite gamma_jj
-// is a breakdown with j directions kept, a non-finite |r| one with j + 1, and
-// |r| < rtol |b| ends the cycle (step 6); the same tests, in the same
-// arithmetic, as the host's loop over single iterations.
-__global__ void k_gcr_check(GcrScal* S, int j, cudaGraphConditionalHandle next, int has_next) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  bool act = S->cyc[3] != 0.0;
-  if (act) {
-    S->cyc[0] = j + 1;
-    double g = S->gjj;
-    if (!(g > 0.0) || !isfinite(g)) {
-      S->cyc[2] = 1;
-      act = false;
-    } else {
-      S->cyc[1] = j + 1;
-      double rj = sqrt(S->rn2);
-      if (!isfinite(rj)) {
-        S->cyc[2] = 1;
-        act = false;
-      } else if (rj < S->rtol * sqrt(S->bn2)) {
-        act = false;
-      }
-    }
-    S->cyc[3] = act ? 1.0 : 0.0;
-  }
-  if (has_next) cudaGraphSetConditional(next, act ? 1u : 0u);
 }
 
 // m <- x / |x| per cell (the projection step), natural SoA

@@ -193,17 +193,6 @@ struct ll_mg_hierarchy {
     int nl;  // kernel launches between b and e
   };
   std::vector<GPair> gpairs[kMaxRestart];
-  // a GCR cycle of m iterations as one graph (conditional nodes), by m
-  cudaGraphExec_t cycles[kMaxRestart + 1] = {nullptr};
-  long long cyc_body[kMaxRestart] = {0};  // kernels of iteration j in a cycle graph
-  long long cyc_tail = 0;                 // kernels after the cycle's last check
-  bool cyc_failed = false;                // the graphs could not be built: one graph per iteration
-  void drop_cycles() {
-    for (auto& c : cycles) {
-      if (c) cudaGraphExecDestroy(c);
-      c = nullptr;
-    }
-  }
   void drop_graph(int j) {
     if (graphs[j]) cudaGraphExecDestroy(graphs[j]);
     graphs[j] = nullptr;
@@ -216,7 +205,6 @@ struct ll_mg_hierarchy {
   ~ll_mg_hierarchy() {
     if (s) cudaStreamSynchronize(s);
     for (int j = 0; j < kMaxRestart; ++j) drop_graph(j);
-    drop_cycles();
     if (h_head) cudaFreeHost(h_head);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (entry_ev) cudaEventDestroy(entry_ev);
@@ -536,7 +524,7 @@ void allocate(ll_mg_hierarchy* H) {
   H->partial.alloc((size_t)(kMaxRestart + 2) * kRedBlocks);
   H->scal.alloc(1);
   H->scal.zero(H->s);
-  LL_CU(cudaMallocHost((void**)&H->h_head, 12 * sizeof(double)));  // 8 head scalars, then cyc
+  LL_CU(cudaMallocHost((void**)&H->h_head, 8 * sizeof(double)));
   H->stepb.alloc(3 * H->g.n);
   H->stepx.alloc(3 * H->g.n);
   if (H->nlev == 1) {
@@ -1469,7 +1457,6 @@ void iteration_body(ll_mg_hierarchy* H, int j) {
 void graphs_for_dt(ll_mg_hierarchy* H) {
   if (H->graph_dt != H->dt) {
     for (int q = 0; q < kMaxRestart; ++q) H->drop_graph(q);
-    H->drop_cycles();
     H->graph_dt = H->dt;
   }
 }
@@ -1520,126 +1507,6 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
   }
 }
 
-// A GCR cycle of m iterations as one CUDA graph: conditional node j holds
-// iteration j, and the kernel k_gcr_check after it takes the host's tests on
-// the device and sets whether iteration j + 1 runs; after the last check,
-// y = Gamma^{-1} alpha, x += Z y and the true residual of the new x.  The host
-// then waits once per cycle instead of once per iteration.  Returns false
-// (and the solver keeps one graph per iteration) if the graph cannot be built.
-template <typename T, typename TM>
-bool build_cycle(ll_mg_hierarchy* H, int m) {
-  cudaStream_t s = H->s;
-  GcrScal* S = H->scal.p;
-  long n3 = H->n3;
-  cudaGraph_t G = nullptr;
-  if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
-  std::vector<cudaGraphConditionalHandle> hs(m);
-  bool ok = true;
-  for (int j = 0; j < m && ok; ++j)
-    ok = cudaGraphConditionalHandleCreate(&hs[j], G, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault) == cudaSuccess;
-  cudaGraphNode_t prev = nullptr;
-  for (int j = 0; j < m && ok; ++j) {
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hs[j];
-    cp.conditional.type = cudaGraphCondTypeIf;
-    cp.conditional.size = 1;
-    cudaGraphNode_t ifn = nullptr;
-    if (cudaGraphAddNode(&ifn, G, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp) != cudaSuccess) {
-      ok = false;
-      break;
-    }
-    if (cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      ok = false;
-      break;
-    }
-    long long before = t_launches;
-    H->capturing = j;
-    try {
-      iteration_body<T, TM>(H, j);
-    } catch (Status) {
-      ok = false;
-    }
-    H->capturing = -1;
-    cudaGraph_t body = nullptr;
-    if (cudaStreamEndCapture(s, &body) != cudaSuccess) ok = false;
-    H->cyc_body[j] = t_launches - before;  // counted per launch by run_cycle
-    g_launches.fetch_sub(H->cyc_body[j]);
-    if (!ok) break;
-    int jj = j, has_next = j + 1 < m ? 1 : 0;
-    cudaGraphConditionalHandle next = has_next ? hs[j + 1] : 0;
-    void* args[] = {&S, &jj, &next, &has_next};
-    cudaKernelNodeParams kp = {};
-    kp.func = (void*)k_gcr_check;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(1);
-    kp.kernelParams = args;
-    cudaGraphNode_t chk = nullptr;
-    if (cudaGraphAddKernelNode(&chk, G, &ifn, 1, &kp) != cudaSuccess) {
-      ok = false;
-      break;
-    }
-    prev = chk;
-  }
-  if (ok && cudaStreamBeginCaptureToGraph(s, G, &prev, nullptr, 1, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    long long before = t_launches;
-    try {
-      {
-        LL_PROF(LL_KIND_GCR_VECTOR);
-        k_backsub<<<1, 1, 0, s>>>(S, -1);
-        LL_LAUNCHED();
-      }
-      {
-        LL_PROF(LL_KIND_GCR_VECTOR);
-        kg_xupdate<T><<<cdiv(n3, kBlock), kBlock, 0, s>>>(n3, H->xw, H->Z<T>(), 0, S->y, &S->cyc[1]);
-        LL_LAUNCHED();
-      }
-      true_residual_launch(H);
-    } catch (Status) {
-      ok = false;
-    }
-    cudaGraph_t tail = nullptr;
-    if (cudaStreamEndCapture(s, &tail) != cudaSuccess) ok = false;
-    H->cyc_tail = t_launches - before;
-    g_launches.fetch_sub(H->cyc_tail);
-  } else {
-    ok = false;
-  }
-  if (ok) ok = cudaGraphInstantiate(&H->cycles[m], G, 0) == cudaSuccess;
-  cudaGraphDestroy(G);
-  if (!ok) {
-    cudaGetLastError();
-    H->cycles[m] = nullptr;
-  }
-  return ok;
-}
-
-// one cycle of at most m iterations from its graph; false: not available
-template <typename T, typename TM>
-bool run_cycle(ll_mg_hierarchy* H, int m, double rtol, int* iters, bool* broke) {
-  if (!H->use_graphs || H->cyc_failed || H->prof_mask != 0) return false;
-  graphs_for_dt(H);
-  if (!H->cycles[m] && !build_cycle<T, TM>(H, m)) {
-    H->cyc_failed = true;
-    return false;
-  }
-  cudaStream_t s = H->s;
-  k_gcr_cycle_begin<<<1, 1, 0, s>>>(H->scal.p, rtol);
-  LL_LAUNCHED();
-  LL_CU(cudaGraphLaunch(H->cycles[m], s));
-  LL_CU(cudaMemcpyAsync(H->h_head, H->scal.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  LL_CU(cudaMemcpyAsync(H->h_head + 8, H->scal.p->cyc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  LL_CU(cudaStreamSynchronize(s));
-  int it = (int)H->h_head[8];
-  long long nk = m + H->cyc_tail;
-  for (int j = 0; j < it; ++j) nk += H->cyc_body[j];
-  g_launches.fetch_add(nk);
-  *iters = it;
-  *broke = H->h_head[10] != 0.0;
-  return true;
-}
-
 template <typename T, typename TM>
 int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int* iters, double* relres) {
   cudaStream_t s = H->s;
@@ -1653,11 +1520,9 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
   GcrScal* S = H->scal.p;
   int total = 0, status = LL_NOT_CONVERGED;
   double bnorm = 0;
-  bool fresh = false;    // the head already holds the true residual of x (a cycle graph computed it)
   bool current = false;  // the loop ended on the true residual of the final x
   for (;;) {
-    if (!fresh) true_residual(H);
-    fresh = false;
+    true_residual(H);
     double rn2 = H->h_head[0];
     bnorm = sqrt(H->h_head[1]);
     if (bnorm == 0.0) {
@@ -1680,19 +1545,6 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
       break;
     }
     int m = std::min(H->prm.restart, H->prm.maxit - total);
-    {
-      int it = 0;
-      bool broke = false;
-      if (run_cycle<T, TM>(H, m, rtol, &it, &broke)) {
-        total += it;
-        if (broke) {
-          status = LL_BREAKDOWN;
-          break;
-        }
-        fresh = true;
-        continue;
-      }
-    }
     int jdone = 0;
     bool broke = false;
     for (int j = 0; j < m; ++j) {

@@ -218,14 +218,18 @@ def test_host_buffers_round_trip():
     assert torch.equal(mh, md.cpu())
 
 
-def test_single_level_problem_is_solved_directly():
-    grid = (4, 4, 1)
+@pytest.mark.parametrize("grid", [(4, 4, 1), (5, 4, 3), (9, 9, 1), (85, 1, 1), (86, 1, 1)])
+def test_single_level_problem_is_solved_directly(grid):
+    """One level: the preconditioner is the dense coarsest solve, so GCR
+    takes one iteration.  Up to 85 cells (255 unknowns) the inverse comes
+    from the cluster Gauss-Jordan kernel (16, 60, 81 and 85 cells: one to
+    sixteen columns per CTA), from 86 cells from the one-block LU."""
     m = inputs.smooth_field(*grid).reshape(-1)
-    O = oracle.Hierarchy(grid, 0.25, 0.1, 1e-2, m, oracle.Params(rtol=1e-13))
-    G = ll.Hierarchy(_t(m), 0.1, 1e-2, 0.25, grid, ll.Params(rtol=1e-13))
+    O = oracle.Hierarchy(grid, 0.25, 0.1, 1e-2, m, oracle.Params(rtol=1e-13, max_levels=1))
+    G = ll.Hierarchy(_t(m), 0.1, 1e-2, 0.25, grid, ll.Params(rtol=1e-13, max_levels=1))
     assert G.levels == O.nlevels == 1
     b = inputs.rhs_field(*grid).reshape(-1)
-    x = torch.zeros(48, dtype=torch.float64, device=DEV)
+    x = torch.zeros(m.size, dtype=torch.float64, device=DEV)
     st, it, rr = G.solve(_t(b), x)
     xo, _, ito, _ = O.solve(b)
     assert st == ll.LL_OK and it == ito == 1

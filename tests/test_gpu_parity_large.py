@@ -169,6 +169,61 @@ def test_128cube_per_class_sweeps_and_vcycle(case128):
     assert np.linalg.norm(_np(z) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+def test_128cube_ordered_galerkin_levels(case128):
+    """Levels 2 and 3 of the 128^3 hierarchy (over 200,000 blocks each) are
+    built with the Galerkin threads in slot-list-length order: every block
+    within 1e-12 of the oracle's P^T A P (compared as sparse matrices)."""
+    import scipy.sparse as sp
+
+    grid, h, alpha, dt, m, O, G = case128
+    for l in (2, 3):
+        n = O.cells(l)
+        rp, ci, val = G.operator(l)
+        assert rp[-1] >= 200000, (l, rp[-1])
+        bsr = sp.bsr_matrix((val, ci, rp), shape=(3 * n, 3 * n)).tocsr()
+        perm = np.array([3 * I + c for c in range(3) for I in range(n)])  # component-major -> cell-major
+        mine = bsr[perm][:, perm]
+        ref = O.matrix(l).tocsr()
+        diff = (mine - ref).tocsr()
+        scale = np.abs(ref.data).max()
+        assert (np.abs(diff.data).max() if diff.nnz else 0.0) <= 1e-12 * scale, l
+
+
+def test_graphs_equal_eager_iterations():
+    """GCR iterations replayed from their CUDA graphs give bit for bit the
+    iterates, counts and residuals of eager launches (no graphs) and of the
+    graphs with kernel timing (event nodes) on.  Restart 4 with a short last
+    cycle: maxit 7 stops inside the second cycle."""
+    import ctypes
+    import os
+
+    grid, h, alpha, dt = (32, 32, 32), 1 / 32, 0.02, 8.19 / 32 ** 2
+    m = inputs.vortex(*grid, seed=0).reshape(-1)
+    b = _t(m / dt)
+    out = {}
+    for maxit in (1000, 7):
+        p = ll.Params(rtol=1e-10, restart=4, maxit=maxit)
+        for mode in ("graphs", "eager", "timed"):
+            if mode == "eager":
+                os.environ["LLMG_NO_GRAPHS"] = "1"
+            try:
+                G = ll.Hierarchy(_t(m), alpha, dt, h, grid, p)
+            finally:
+                os.environ.pop("LLMG_NO_GRAPHS", None)
+            if mode == "timed":
+                ll.load_library().ll_mg_profile(G._h, ctypes.c_uint(0xFFFF))
+            x = torch.zeros_like(b)
+            st, it, rr = G.solve(b, x)
+            out[(maxit, mode)] = (st, it, rr, x)
+        ref = out[(maxit, "graphs")]
+        for mode in ("eager", "timed"):
+            st, it, rr, x = out[(maxit, mode)]
+            assert (st, it, rr) == ref[:3], (maxit, mode)
+            assert torch.equal(x, ref[3]), (maxit, mode)
+    assert out[(1000, "graphs")][0] == ll.LL_OK and out[(1000, "graphs")][1] > 8
+    assert out[(7, "graphs")][0] == ll.LL_NOT_CONVERGED and out[(7, "graphs")][1] == 7
+
+
 def test_iteration_counts_stay_bounded_under_refinement():
     """Mesh independence on the GPU (3-D, dt/h^2 = 8.19, alpha = 0.02):
     32^3 -> 128^3 grows the iteration count by at most 30 %."""
