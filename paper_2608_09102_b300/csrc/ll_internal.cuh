@@ -30,7 +30,7 @@ void count_launch();
   } while (0)
 
 constexpr int kBlock = 256;
-constexpr int kRedBlocks = 592;   // 4 x 148 SMs: fixed grid of reduction kernels
+constexpr int kRedBlocks = 1184;  // 8 x 148 SMs: fixed grid of reduction kernels
 constexpr int kMaxRestart = 64;
 constexpr int kMaxColours = 128;
 constexpr int kMaxLevels = 32;

@@ -1670,6 +1670,7 @@ __global__ void __launch_bounds__(256) kg_multidot(long n, const double* __restr
   double acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0;
+#pragma unroll 2  // two elements in flight per thread
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double vt = v[t];
 #pragma unroll
@@ -1711,6 +1712,7 @@ __global__ void __launch_bounds__(256) kg_multiaxpy_r(long n, double* __restrict
   const bool upd = *rnow != 0.0;
   const double f = *rcoef;
   double acc[1] = {0};
+#pragma unroll 2  // two elements in flight per thread
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double a = v[t];
 #pragma unroll 4
@@ -1729,6 +1731,7 @@ __global__ void __launch_bounds__(256) kg_multiaxpy_r(long n, double* __restrict
 __global__ void __launch_bounds__(256) kg_dot2(long n, const double* __restrict__ c, const double* __restrict__ r,
                                                double* __restrict__ partial) {
   double acc[2] = {0, 0};
+#pragma unroll 2  // two elements in flight per thread
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double ct = c[t];
     acc[0] += ct * ct;
@@ -1742,6 +1745,7 @@ __global__ void __launch_bounds__(256) kg_rupdate(long n, double* __restrict__ r
                                                   const double* __restrict__ coef, double* __restrict__ partial) {
   double f = *coef;
   double acc[1] = {0};
+#pragma unroll 2  // two elements in flight per thread
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     double v = r[t] - f * c[t];
     r[t] = v;
