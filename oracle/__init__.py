@@ -139,6 +139,7 @@ def bind(lib):
         "orc_operator_apply": (None, [i, i, i, d, d, d, _dp, _dp, _dp]),
         "orc_grid_aggregates": (i, [i, i, i, i, u32, _ip]),
         "orc_vertex_hash": (u32, [u32, u32]),
+        "orc_step_guess": (i, [i, i, _dp, _dp, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -283,6 +284,20 @@ def step(m, n_steps, grid, h, alpha, dt, params: Params | None = None, project: 
     st = _load().orc_step(mm, int(n_steps), nx, ny, nz, float(h), float(alpha), float(dt),
                           ctypes.byref(cp), 1 if project else 0, its, rrs)
     return mm, its[:n_steps], rrs[:n_steps], st
+
+
+def step_guess(m, prev):
+    """The initial approximation of a step's solve from m = m^n and the
+    earlier states prev (newest first, at most 6): returns (guess, order)."""
+    mm = np.ascontiguousarray(np.asarray(m, np.float64).reshape(-1))
+    d = len(prev)
+    pp = np.ascontiguousarray(np.stack([np.asarray(p, np.float64).reshape(-1) for p in prev])
+                              if d else np.zeros(1)).reshape(-1)
+    x = np.zeros_like(mm)
+    k = _load().orc_step_guess(mm.size, d, mm, pp, x)
+    if k < 0:
+        raise ValueError("at most 6 earlier states")
+    return x, k
 
 
 def step_vjp(m, x, g, grid, h, alpha, dt, params: Params | None = None):

@@ -1046,29 +1046,66 @@ done:
 
 /* The initial approximation u_0 of each step's solve (Algorithm 1 takes it
  * as an input; the paper does not fix it for the time loop).  Reading: the
- * polynomial extrapolation of the states through m^n and the k earlier ones
- * this call has, k = min(steps so far, 3):
- *   k = 0: m^n;  1: 2 m^n - m^{n-1};  2: 3 m^n - 3 m^{n-1} + m^{n-2};
- *   3: 4 m^n - 6 m^{n-1} + 4 m^{n-2} - m^{n-3},
- * which is O(dt^{k+1}) from the new solution where m^n is O(dt) from it.
- * prev[j] holds m^{n-1-j}. */
-static void step_guess(int n3, int k, const double *m, double *const *prev, double *x) {
-  static const double c[4][4] = {{1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
+ * states m^n, m^{n-1}, ... extrapolated one step ahead with the terms of
+ * Newton's backward-difference series m^n + D m^n + D^2 m^n + ... that keep
+ * shrinking, D^j m^n being the j-th backward difference over the d earlier
+ * states this call has (d <= ORC_STEP_HIST): D m^n whenever d >= 1, then
+ * D^j m^n for j = 2, 3, ... while |D^j m^n| < |D^{j-1} m^n| (Euclidean
+ * norms over all components; the squares are compared).  With the terms up
+ * to D^k the sum is the polynomial extrapolation of degree k through
+ * m^n ... m^{n-k}: sum_{l=0..k} (-1)^l C(k+1, l+1) m^{n-l}, O(dt^{k+1}) from
+ * the new solution while the series converges.  prev[j] holds m^{n-1-j}. */
+#define ORC_STEP_HIST 6
+
+static int step_order(int n3, int d, const double *m, double *const *prev) {
+  if (d == 0) return 0;
+  double s2[ORC_STEP_HIST + 1] = {0};
   for (int i = 0; i < n3; ++i) {
-    double v = c[k][0] * m[i];
-    for (int j = 0; j < k; ++j) v += c[k][j + 1] * prev[j][i];
+    double t[ORC_STEP_HIST + 1];
+    t[0] = m[i];
+    for (int l = 1; l <= d; ++l) t[l] = prev[l - 1][i];
+    for (int j = 1; j <= d; ++j) {  /* t[0] becomes D^j m^n */
+      for (int l = 0; l + j <= d; ++l) t[l] = t[l] - t[l + 1];
+      s2[j] += t[0] * t[0];
+    }
+  }
+  int k = 1;
+  for (int j = 2; j <= d && s2[j] < s2[j - 1]; ++j) k = j;
+  return k;
+}
+
+static void step_guess(int n3, int d, const double *m, double *const *prev, double *x) {
+  int k = step_order(n3, d, m, prev);
+  double c[ORC_STEP_HIST + 1];
+  for (int l = 0; l <= k; ++l) { /* (-1)^l C(k+1, l+1) */
+    double b = 1.0;
+    for (int q = 0; q <= l; ++q) b = b * (double)(k + 1 - q) / (double)(q + 1);
+    c[l] = (l % 2 ? -1.0 : 1.0) * b;
+  }
+  for (int i = 0; i < n3; ++i) {
+    double v = c[0] * m[i];
+    for (int l = 1; l <= k; ++l) v += c[l] * prev[l - 1][i];
     x[i] = v;
   }
 }
 
+/* the initial approximation alone, for the tests: prev holds d states of n3
+ * values each, newest first; returns the order k it used */
+int orc_step_guess(int n3, int d, const double *m, const double *prev, double *x) {
+  double *p[ORC_STEP_HIST];
+  if (d < 0 || d > ORC_STEP_HIST) return -1;
+  for (int j = 0; j < d; ++j) p[j] = (double *)prev + (size_t)j * n3;
+  step_guess(n3, d, m, p, x);
+  return step_order(n3, d, m, p);
+}
+
 /* push m^n onto the history (prev[0] newest); returns the new depth */
-static int step_push(int n3, int k, const double *m, double **prev) {
-  double *t = prev[2];
-  prev[2] = prev[1];
-  prev[1] = prev[0];
+static int step_push(int n3, int d, const double *m, double **prev) {
+  double *t = prev[ORC_STEP_HIST - 1];
+  for (int j = ORC_STEP_HIST - 1; j > 0; --j) prev[j] = prev[j - 1];
   prev[0] = t;
   memcpy(prev[0], m, (size_t)n3 * sizeof(double));
-  return k < 3 ? k + 1 : 3;
+  return d < ORC_STEP_HIST ? d + 1 : ORC_STEP_HIST;
 }
 
 /* n_steps steps of the semi-implicit scheme: m~ = m^n, b = m^n/dt, solve
@@ -1079,8 +1116,8 @@ int orc_step(double *m, int n_steps, int nx, int ny, int nz, double h, double al
   int n = nx * ny * nz, worst = ORC_OK;
   double *b = (double *)xmalloc((size_t)3 * n * sizeof(double));
   double *x = (double *)xmalloc((size_t)3 * n * sizeof(double));
-  double *prev[3];
-  for (int j = 0; j < 3; ++j) prev[j] = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *prev[ORC_STEP_HIST];
+  for (int j = 0; j < ORC_STEP_HIST; ++j) prev[j] = (double *)xmalloc((size_t)3 * n * sizeof(double));
   int depth = 0;
   for (int s = 0; s < n_steps; ++s) {
     orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
@@ -1104,7 +1141,7 @@ int orc_step(double *m, int n_steps, int nx, int ny, int nz, double h, double al
   }
   free(b);
   free(x);
-  for (int j = 0; j < 3; ++j) free(prev[j]);
+  for (int j = 0; j < ORC_STEP_HIST; ++j) free(prev[j]);
   return worst;
 }
 
@@ -1119,8 +1156,8 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
   int n = nx * ny * nz, worst = ORC_OK;
   double *b = (double *)xmalloc((size_t)3 * n * sizeof(double));
   double *x = (double *)xmalloc((size_t)3 * n * sizeof(double));
-  double *prev[3];
-  for (int j = 0; j < 3; ++j) prev[j] = (double *)xmalloc((size_t)3 * n * sizeof(double));
+  double *prev[ORC_STEP_HIST];
+  for (int j = 0; j < ORC_STEP_HIST; ++j) prev[j] = (double *)xmalloc((size_t)3 * n * sizeof(double));
   int depth = 0;
   for (int s = 0; s < n_steps; ++s) {
     orc_hier *H = orc_setup(nx, ny, nz, h, alpha, dt, m, prm);
@@ -1152,7 +1189,7 @@ int orc_step_llg(double *m, int n_steps, int nx, int ny, int nz, double h, doubl
   }
   free(b);
   free(x);
-  for (int j = 0; j < 3; ++j) free(prev[j]);
+  for (int j = 0; j < ORC_STEP_HIST; ++j) free(prev[j]);
   return worst;
 }
 

@@ -563,22 +563,100 @@ def test_random_unit_vectors_limit_of_the_vcycle(alpha):
         assert neg > 0.25
 
 
+def _adaptive_guess(states):
+    """The reading restated: Newton's backward-difference series of
+    states[0] = m^n, states[l] = m^{n-l}, its terms D^j m^n taken while their
+    norms shrink (D m^n always), summed as the polynomial extrapolation of
+    that degree."""
+    from math import comb
+
+    d = len(states) - 1
+    if d == 0:
+        return states[0].copy(), 0
+    t = [s.copy() for s in states]
+    s2 = [0.0] * (d + 1)
+    for j in range(1, d + 1):
+        for l in range(d - j + 1):
+            t[l] = t[l] - t[l + 1]
+        s2[j] = float(np.dot(t[0], t[0]))
+    k = 1
+    for j in range(2, d + 1):
+        if s2[j] < s2[j - 1]:
+            k = j
+        else:
+            break
+    c = [(-1) ** l * comb(k + 1, l + 1) for l in range(k + 1)]
+    return sum(c[l] * states[l] for l in range(k + 1)), k
+
+
+def step_guess_violations():
+    """The closed-form pins of the step guess, as a list of violations (empty
+    when the oracle passes).  States sampled from a vector polynomial of
+    degree q in time, with shrinking terms: the backward differences shrink
+    up to D^q (D^{q+1} is rounding), so the guess is the polynomial's next
+    value; with d < q earlier states the degree-d extrapolation misses it.
+    A series whose differences grow keeps the linear extrapolation."""
+    bad = []
+    rng = np.random.default_rng(3)
+    n3 = 300
+    for q in (1, 2, 3, 4, 5):
+        a = [rng.standard_normal(n3) * 0.05 ** j for j in range(q + 1)]
+
+        def P(t):
+            return sum(a[j] * t ** j for j in range(q + 1))
+
+        states = [P(-float(l)) for l in range(7)]  # m^n at t = 0, earlier at -1, -2, ...
+        nxt = P(1.0)
+        for d in range(7):
+            x, k = oracle.step_guess(states[0], states[1:d + 1])
+            err = np.abs(x - nxt).max()
+            if d == 0 and not (k == 0 and np.array_equal(x, states[0])):
+                bad.append(("m^n", q, d, k))
+            elif d >= q and not (k >= q and err <= 1e-12 * np.abs(nxt).max()):
+                bad.append(("exact", q, d, k, err))
+            elif 0 < d < q and not (k == d and err > 1e-8):
+                bad.append(("degree", q, d, k, err))
+    m = np.ones(n3)
+    prev = [m + (-2.0) ** l * 1e-3 for l in range(1, 4)]
+    x, k = oracle.step_guess(m, prev)
+    if not (k == 1 and np.array_equal(x, 2 * m - prev[0])):
+        bad.append(("growing", k))
+    return bad
+
+
+def test_step_guess_extrapolates_polynomials_in_time_exactly():
+    assert step_guess_violations() == []
+
+
+def test_step_guess_matches_the_restated_rule():
+    rng = np.random.default_rng(5)
+    base = rng.standard_normal(600)
+    drift = rng.standard_normal(600)
+    for d in range(7):
+        states = [base + (1 + 0.3 * l) ** 2 * 1e-2 * drift + 1e-9 * rng.standard_normal(600) for l in range(d + 1)]
+        x, k = oracle.step_guess(states[0], states[1:])
+        xr, kr = _adaptive_guess(states)
+        assert k == kr, (d, k, kr)
+        assert np.array_equal(x, xr), d
+
+
 def test_step_initial_approximation_is_the_extrapolated_state():
     """Reading of the time loop (Algorithm 1 takes u_0 as an input): step k of
-    a call starts from the polynomial extrapolation through m^n and the
-    min(k, 3) states before it.  A five-step call equals five explicit solves
-    with those guesses, and each extrapolated guess starts closer to the
+    a call starts from the extrapolation of m^n and the min(k, 6) states
+    before it, with as many backward-difference terms as keep shrinking.  An
+    eight-step call equals eight explicit solves with those guesses, the order
+    grows past cubic, and each extrapolated guess starts closer to the
     solution than m^n does."""
     n = 16
     grid, h, alpha, dt = (n, n, 1), 1 / n, 0.05, 2e-3
     m0 = inputs.smooth_field(*grid, seed=4).reshape(-1)
     p = oracle.Params(rtol=1e-12)
-    coef = {0: [1.0], 1: [2.0, -1.0], 2: [3.0, -3.0, 1.0], 3: [4.0, -6.0, 4.0, -1.0]}
     ms = [m0]
-    gains = []
-    for k in range(5):
-        order = min(k, 3)
-        guess = sum(c * ms[-1 - j] for j, c in enumerate(coef[order]))
+    gains, orders = [], []
+    for k in range(8):
+        states = ms[::-1][:7]
+        guess, order = _adaptive_guess(states)
+        orders.append(order)
         H = oracle.Hierarchy(grid, h, alpha, dt, ms[-1], p)
         x, st, it, rr = H.solve(ms[-1] / dt, guess.copy())
         assert st == oracle.OK
@@ -586,7 +664,8 @@ def test_step_initial_approximation_is_the_extrapolated_state():
             gains.append(np.linalg.norm(x - guess) / np.linalg.norm(x - ms[-1]))
         v = x.reshape(3, -1)
         ms.append((v / np.linalg.norm(v, axis=0)).reshape(-1))
-    out, its, rrs, st = oracle.step(m0, 5, grid, h, alpha, dt, p)
+    out, its, rrs, st = oracle.step(m0, 8, grid, h, alpha, dt, p)
     assert st == oracle.OK
     assert np.abs(out - ms[-1]).max() <= 1e-13
+    assert max(orders) >= 4, orders
     assert max(gains) < 0.5, gains

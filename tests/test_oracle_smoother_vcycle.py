@@ -161,13 +161,31 @@ KMUTATIONS = {
 }
 
 
+SO = "static int step_order("
+SG = "static void step_guess("
+
+# mistakes in the time loop's initial approximation, caught by its closed-form
+# pins (step_guess_violations in test_oracle_pins.py)
+GMUTATIONS = {
+    # the order stops at cubic
+    "guess_cubic_cap": (SO, "j <= d && s2[j] < s2[j - 1]", "j <= d && j <= 3 && s2[j] < s2[j - 1]"),
+    # every available term is taken, shrinking or not
+    "guess_no_shrink_test": (SO, "j <= d && s2[j] < s2[j - 1]", "j <= d && s2[j] >= 0.0"),
+    # the alternating signs of the extrapolation weights are lost
+    "guess_weight_sign": (SG, "c[l] = (l % 2 ? -1.0 : 1.0) * b;", "c[l] = b;"),
+    # C(k, l + 1) instead of C(k + 1, l + 1)
+    "guess_binomial": (SG, "b = b * (double)(k + 1 - q) / (double)(q + 1);",
+                       "b = b * (double)(k - q) / (double)(q + 1);"),
+}
+
+
 @pytest.fixture(scope="module")
 def mutant_dir(tmp_path_factory):
     return tmp_path_factory.mktemp("oracle_mutants")
 
 
 def _mutant(name, where):
-    head, old, new = {**MUTATIONS, **KMUTATIONS}[name]
+    head, old, new = {**MUTATIONS, **KMUTATIONS, **GMUTATIONS}[name]
     src = open(os.path.join(os.path.dirname(oracle.__file__), "ll_oracle.c")).read()
     c = os.path.join(str(where), name + ".c")
     so = os.path.join(str(where), name + ".so")
@@ -220,3 +238,17 @@ def test_planted_kcycle_mistakes_are_caught(name, mutant_dir):
     # is nearly orthogonal to the first already, so that mistake moves the
     # result by a few 1e-8 only)
     assert min(errs) > 1e-9, errs
+
+
+@pytest.mark.parametrize("name", sorted(GMUTATIONS))
+def test_planted_step_guess_mistakes_are_caught(name, mutant_dir):
+    from tests.test_oracle_pins import step_guess_violations
+
+    lib = _mutant(name, mutant_dir)
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        bad = step_guess_violations()
+    finally:
+        oracle._lib = saved
+    assert bad, name
