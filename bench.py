@@ -493,8 +493,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "grid": list(GRID), "h": H_SPACING, "alpha": ALPHA, "dt": DT,
                    "rtol": RTOL, "precision": args.precision, "kcycle": args.kcycle,
                    "parallelism": "replicas" if world > 1 else "single", "levels": H.levels,
-                   "initial_guess": "polynomial extrapolation through m^n and up to 3 earlier states "
-                                    "(m^n for a fresh integration's first step)",
+                   "initial_guess": "m^n and up to 6 earlier states extrapolated with the backward-difference "
+                                    "terms that keep shrinking (m^n for a fresh integration's first step)",
                    "l2": "inputs larger than L2: the working set per step (~3 GB: GCR bases, operators) exceeds "
                          "the 126 MB L2"},
         "iterations_per_step": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},

@@ -123,11 +123,13 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 /* n_steps time steps of the semi-implicit scheme with projection (Sec. 4):
  * per step m~ = m, rhs = m/dt, solve (Algorithm 1) from the initial
  * approximation u_0, then m <- x/|x| per cell.  u_0 = m for the first step;
- * for step k the polynomial extrapolation through m^n and the min(k, 3)
- * states before it (2 m^n - m^{n-1}; 3 m^n - 3 m^{n-1} + m^{n-2};
- * 4 m^n - 6 m^{n-1} + 4 m^{n-2} - m^{n-3}).  The stopping test
- * ||r|| < rtol ||rhs|| is the same for any u_0.  Aggregates are computed
- * once; each step redoes the numeric setup.
+ * for step k, m^n and the d = min(k, 6) states before it extrapolated one
+ * step ahead with the terms of Newton's backward-difference series
+ * m^n + D m^n + D^2 m^n + ... that keep shrinking: D m^n, then D^j m^n while
+ * ||D^j m^n|| < ||D^{j-1} m^n|| (j <= d); up to D^k the sum is the degree-k
+ * extrapolation sum_l (-1)^l C(k+1, l+1) m^{n-l} (k = 1: 2 m^n - m^{n-1}).
+ * The stopping test ||r|| < rtol ||rhs|| is the same for any u_0.
+ * Aggregates are computed once; each step redoes the numeric setup.
  *   m               device SoA 3*N float64, in/out (cells must be nonzero).
  *   iters_per_step  host, optional, n_steps ints.
  *   relres_per_step host, optional, n_steps doubles.
@@ -138,7 +140,7 @@ int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid g
 /* n_steps time steps on an existing hierarchy (same grid and parameters;
  * alpha and dt are the hierarchy's): per step the numeric setup is redone for
  * m~ = m, then solve and project as ll_step does.  Reuses the aggregates.
- * The hierarchy keeps up to three states before its last output and that
+ * The hierarchy keeps up to six states before its last output and that
  * output: when m is bit for bit that output (a continued integration), the
  * call's first step also starts from the extrapolation.
  *   m device SoA 3*N float64, in/out; iters/relres host, optional, n_steps.

@@ -1895,18 +1895,42 @@ __global__ void k_rhs_llg(long n, const double* __restrict__ m, double alpha, do
 }
 
 // The initial approximation of a time step's solve (the same reading as the
-// oracle's step_guess): the polynomial extrapolation through m and the k
-// earlier states p1 (newest), p2, p3:  k = 1: 2 m - p1;  2: 3 m - 3 p1 + p2;
-// 3: 4 m - 6 p1 + 4 p2 - p3
-__global__ void k_step_guess(long n, int k, const double* __restrict__ m, const double* __restrict__ p1,
-                             const double* __restrict__ p2, const double* __restrict__ p3,
-                             double* __restrict__ x) {
+// oracle's step_guess): m^n and up to kStepHist earlier states s_1 (newest)
+// ... s_d extrapolated one step ahead with the terms of Newton's
+// backward-difference series m + D m + D^2 m + ... that keep shrinking.
+// k_step_diff_norms gives the partial sums of |D^j m|^2, j = 1..d, each
+// difference formed element by element with the oracle's operations
+// (t_l -= t_{l+1}, j times); the host picks the order k and k_step_guess
+// forms sum_{l<=k} c_l s_l, c_l = (-1)^l C(k+1, l+1).
+constexpr int kStepHist = 6;
+struct StepStates {
+  const double* s[kStepHist + 1];  // s[0] = m^n, s[l] = m^{n-l}
+};
+__global__ void __launch_bounds__(256) k_step_diff_norms(long n, int d, StepStates S, double* __restrict__ partial) {
+  double acc[kStepHist];
+#pragma unroll
+  for (int j = 0; j < kStepHist; ++j) acc[j] = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double t[kStepHist + 1];
+#pragma unroll
+    for (int l = 0; l <= kStepHist; ++l) t[l] = l <= d ? S.s[l][i] : 0.0;
+#pragma unroll
+    for (int j = 1; j <= kStepHist; ++j) {
+#pragma unroll
+      for (int l = 0; l + j <= kStepHist; ++l) t[l] = t[l] - t[l + 1];
+      if (j <= d) acc[j - 1] += t[0] * t[0];
+    }
+  }
+  block_reduce_store<kStepHist>(acc, partial, kStepHist);
+}
+struct StepCoef {
+  double c[kStepHist + 1];
+};
+__global__ void k_step_guess(long n, int k, StepStates S, StepCoef C, double* __restrict__ x) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double v;
-  if (k == 1) v = 2.0 * m[i] + -1.0 * p1[i];
-  else if (k == 2) v = 3.0 * m[i] + -3.0 * p1[i] + 1.0 * p2[i];
-  else v = 4.0 * m[i] + -6.0 * p1[i] + 4.0 * p2[i] + -1.0 * p3[i];
+  double v = C.c[0] * S.s[0][i];
+  for (int l = 1; l <= k; ++l) v += C.c[l] * S.s[l][i];
   x[i] = v;
 }
 

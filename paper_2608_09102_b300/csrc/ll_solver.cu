@@ -115,10 +115,10 @@ struct ll_mg_hierarchy {
   DBuf<double> r0tmp64;  // colour-0 residual of the level-0 restriction (float64 path)
   bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
   // time-stepping history for the steps' initial approximations: up to three
-  // states before the last output (step_h[(step_i + j) % 3] holds the j-th
-  // newest, j < step_depth) and the last output itself (step_last), valid
-  // when step_hist is set
-  DBuf<double> step_h[3], step_last;
+  // states before the last output (step_h[(step_i + j) % kStepHist] holds
+  // the j-th newest, j < step_depth) and the last output itself
+  // (step_last), valid when step_hist is set
+  DBuf<double> step_h[kStepHist], step_last, step_norms;
   DBuf<int> step_differ;
   int step_i = 0, step_depth = 0;
   bool step_hist = false;
@@ -335,8 +335,11 @@ constexpr int kGalerkinSortBlocks = 200000;  // float64 Galerkin levels >= 2 wit
 // Coarse-level kernels use small blocks: a colour class of a small level then
 // spreads over many SMs instead of queueing on the float64 units of one.
 constexpr int kCoarseBlock = 64;
-// tail levels with at most this many cells run on one CTA (see k_coarse_tail)
-constexpr int kSoloCells = 200;
+// tail levels with at most this many cells run on one CTA (see k_coarse_tail);
+// float32 ones up to 500 (the 467-cell level 6 of the 128^3 hierarchy: mixed
+// tail -3 %, while float64 phases on one SM's float64 pipe took +8 %)
+template <typename T> constexpr int kSoloCells = 200;
+template <> constexpr int kSoloCells<float> = 500;
 constexpr int kTailCells = 5000;  // levels at or below this size run in the cluster tail
 constexpr int kMaxCoarsestCells = 2048;
 
@@ -545,7 +548,7 @@ void fill_tail(ll_mg_hierarchy* H, DBuf<TailArgs<T, TM>>& dst) {
   A.first = H->tail_first;
   A.last = H->nlev - 1;
   A.solo_first = A.last;  // the coarsest level at least
-  while (A.solo_first > A.first && H->lev[A.solo_first - 1].n <= kSoloCells) --A.solo_first;
+  while (A.solo_first > A.first && H->lev[A.solo_first - 1].n <= kSoloCells<T>) --A.solo_first;
   A.nu_pre = H->prm.nu_pre;
   A.nu_post = H->prm.nu_post;
   A.uni = H->union_mode;
@@ -1719,13 +1722,13 @@ int ll_mg_solve(ll_mg_hierarchy* H, const double* rhs, double* x, double rtol, i
 
 // time steps on an existing hierarchy; fresh = numeric setup already done for
 // m; src = explicit source terms (q, he0, he1, he2) or NULL
-// Time steps of m in place.  The initial approximation of each solve: the
-// polynomial extrapolation through m and the (up to three) states before it
-// that are known -- within a call from its second step, and from the first
-// step when m is bit for bit the last output of the previous call on this
-// hierarchy (a continued integration); else m itself (the oracle's
-// step_guess; not for x_save, the adjoint's forward map, whose solves start
-// from m).
+// Time steps of m in place.  The initial approximation of each solve: m and
+// the (up to kStepHist) states before it that are known -- within a call
+// from its second step, and from the first step when m is bit for bit the
+// last output of the previous call on this hierarchy (a continued
+// integration) -- extrapolated with the backward-difference terms that keep
+// shrinking (the oracle's step_guess; not for x_save, the adjoint's forward
+// map, whose solves start from m).
 static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step,
                  bool fresh, const double* src = nullptr, double* x_save = nullptr) {
   int worst = LL_OK;
@@ -1738,6 +1741,7 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
       if (!H->step_last.p) {
         for (auto& b : H->step_h) b.alloc(n3);
         H->step_last.alloc(n3);
+        H->step_norms.alloc(kStepHist);
         H->step_differ.alloc(1);
       }
       if (H->step_hist && n_steps > 0) {
@@ -1751,7 +1755,7 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
       }
       H->step_hist = false;  // set again when every step of this call has completed
     }
-    auto hist = [&](int j) { return H->step_h[(H->step_i + j) % 3].p; };
+    auto hist = [&](int j) { return H->step_h[(H->step_i + j) % kStepHist].p; };
     for (int k = 0; k < n_steps; ++k) {
       if (k > 0 || !fresh) numeric(H, m);
       if (src)
@@ -1761,15 +1765,33 @@ static int steps(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step
         k_scale<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, m, 1.0 / dt, H->stepb);
       LL_LAUNCHED();
       if (depth > 0) {
-        k_step_guess<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, depth, m, hist(0), hist(1), hist(2), H->stepx);
+        StepStates S = {};
+        S.s[0] = m;
+        for (int l = 1; l <= depth; ++l) S.s[l] = hist(l - 1);
+        k_step_diff_norms<<<kRedBlocks, kBlock, 0, H->s>>>(n3, depth, S, H->partial);
+        LL_LAUNCHED();
+        k_finish<<<kStepHist, kBlock, 0, H->s>>>(H->partial, H->step_norms);
+        LL_LAUNCHED();
+        double nrm[kStepHist];
+        LL_CU(cudaMemcpyAsync(nrm, H->step_norms.p, kStepHist * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+        LL_CU(cudaStreamSynchronize(H->s));
+        int order = 1;  // the terms D^j m while their norms shrink (nrm[j-1] = |D^j m|^2)
+        for (int j = 2; j <= depth && nrm[j - 1] < nrm[j - 2]; ++j) order = j;
+        StepCoef C = {};
+        for (int l = 0; l <= order; ++l) {  // (-1)^l C(order+1, l+1)
+          double b = 1.0;
+          for (int q = 0; q <= l; ++q) b = b * (double)(order + 1 - q) / (double)(q + 1);
+          C.c[l] = (l % 2 ? -1.0 : 1.0) * b;
+        }
+        k_step_guess<<<cdiv(n3, kBlock), kBlock, 0, H->s>>>(n3, order, S, C, H->stepx);
         LL_LAUNCHED();
       } else {
         LL_CU(cudaMemcpyAsync(H->stepx.p, m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
       }
       if (guess) {  // m^n becomes the newest earlier state (the oldest slot is reused)
-        H->step_i = (H->step_i + 2) % 3;
+        H->step_i = (H->step_i + kStepHist - 1) % kStepHist;
         LL_CU(cudaMemcpyAsync(hist(0), m, n3 * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
-        depth = std::min(depth + 1, 3);
+        depth = std::min(depth + 1, kStepHist);
         H->step_depth = depth;
       }
       int it = 0;
