@@ -114,10 +114,11 @@ struct ll_mg_hierarchy {
   DBuf<float> m32;  // m~ per slot: the float32 level-0 kernels form C and D^-1 from it
   DBuf<double> r0tmp64;  // colour-0 residual of the level-0 restriction (float64 path)
   bool sell_ok = false;  // large float64 classes may use the SELL-32 sweeps (not in batches)
-  // time-stepping history for the steps' initial approximations: up to three
-  // states before the last output (step_h[(step_i + j) % kStepHist] holds
-  // the j-th newest, j < step_depth) and the last output itself
-  // (step_last), valid when step_hist is set
+  // time-stepping history for the steps' initial approximations: up to
+  // kStepHist states before the last output (step_h[(step_i + j) % kStepHist]
+  // holds the j-th newest, j < step_depth) and the last output itself
+  // (step_last), valid when step_hist is set; step_norms: the squared norms
+  // of the backward differences
   DBuf<double> step_h[kStepHist], step_last, step_norms;
   DBuf<int> step_differ;
   int step_i = 0, step_depth = 0;
