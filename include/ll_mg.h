@@ -142,7 +142,8 @@ int ll_step(double* m, int n_steps, double alpha, double dt, double h, ll_grid g
  * m~ = m, then solve and project as ll_step does.  Reuses the aggregates.
  * The hierarchy keeps up to six states before its last output and that
  * output: when m is bit for bit that output (a continued integration), the
- * call's first step also starts from the extrapolation.
+ * call's first step also starts from the extrapolation.  ll_mg_update with
+ * another alpha or dt drops them.
  *   m device SoA 3*N float64, in/out; iters/relres host, optional, n_steps.
  * Returns the worst status over the steps (errors stop early). */
 int ll_mg_step(ll_mg_hierarchy* H, double* m, int n_steps, int* iters_per_step, double* relres_per_step);

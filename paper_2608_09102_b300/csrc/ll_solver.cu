@@ -1701,6 +1701,7 @@ int ll_mg_update(ll_mg_hierarchy* H, const double* m_tilde, double alpha, double
   if (!H || !m_tilde || !(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha)) return LL_EINVAL;
   try {
     enter(H);
+    if (alpha != H->alpha || dt != H->dt) H->step_hist = false;  // the kept states belong to the old step
     H->alpha = alpha;
     H->dt = dt;
     numeric(H, m_tilde);

@@ -289,6 +289,14 @@ def test_continued_integration_keeps_the_extrapolation_history():
     Gd = ll.Hierarchy(md, alpha, dt, h, grid, p)
     st, itd, _ = Gd.step(md, 2)
     assert torch.equal(mc, md) and itc == itd
+    # another dt through ll_mg_update: the kept states are dropped, so the
+    # next steps equal those of a fresh hierarchy with the new dt
+    Gd.update(md, alpha, 2 * dt)
+    me = md.clone()
+    st, ite, _ = Gd.step(md, 3)
+    Ge = ll.Hierarchy(me, alpha, 2 * dt, h, grid, p)
+    st, itf, _ = Ge.step(me, 3)
+    assert torch.equal(md, me) and ite == itf
 
 
 def test_fp64_probe_runs():
