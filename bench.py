@@ -557,9 +557,22 @@ def other_workloads(ll, torch, inputs, dev):
     the 64^2 solve against a dense-LU-sized problem, the 256^2 x 128 random
     unit vectors with the mixed configuration (K-cycle on level 1), the
     512-instance ragged batch with the autotuner's stored choices, and the
-    96^3 gradient."""
+    96^3 gradient.  A workload whose call fails is recorded with its error
+    and the others still run."""
     out = {}
-    # configuration 1: 2-D 64^2, alpha 0.1, dt 1e-3, one solve to 1e-10
+    for name, leg in (("config1_64x64", _leg_config1), ("config3_256x256x128_mixed_kcycle1", _leg_config3),
+                      ("config4_batch512_mixed_autotuned", _leg_config4), ("config5_grad96_fp64", _leg_config5)):
+        try:
+            out[name] = leg(ll, torch, inputs, dev)
+        except ll.LLError as e:
+            out[name] = {"error": str(e)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
+
+def _leg_config1(ll, torch, inputs, dev):
+    """2-D 64^2, alpha 0.1, dt 1e-3, one solve to 1e-10."""
     g1 = (64, 64, 1)
     m1 = torch.tensor(inputs.smooth_field(*g1, seed=0).reshape(-1), device=dev)
     H1 = ll.Hierarchy(m1, 0.1, 1e-3, 1 / 64, g1, ll.Params(rtol=1e-10))
@@ -568,9 +581,12 @@ def other_workloads(ll, torch, inputs, dev):
     H1.solve(b1, x1)
     x1.zero_()
     ms, (st, it, rr) = _event_ms(torch, lambda: H1.solve(b1, x1))
-    out["config1_64x64"] = {"ms_per_solve": ms, "iterations": it, "relres": rr, "status": st,
-                            "unknown_solves_per_s": 3 * 64 * 64 / (ms * 1e-3)}
-    # configuration 3: 256 x 256 x 128 random unit vectors, h 1/256, dt 1e-4
+    return {"ms_per_solve": ms, "iterations": it, "relres": rr, "status": st,
+            "unknown_solves_per_s": 3 * 64 * 64 / (ms * 1e-3)}
+
+
+def _leg_config3(ll, torch, inputs, dev):
+    """256 x 256 x 128 random unit vectors, h 1/256, dt 1e-4, three alphas."""
     g3 = (256, 256, 128)
     m3 = torch.tensor(inputs.random_sphere(*g3, seed=0).reshape(-1), device=dev)
     b3 = m3 / 1e-4
@@ -584,10 +600,11 @@ def other_workloads(ll, torch, inputs, dev):
         c3["alpha_%g" % alpha] = {"ms_per_solve": ms, "iterations": it, "relres": rr, "status": st,
                                   "unknown_solves_per_s": 3 * 256 * 256 * 128 / (ms * 1e-3)}
         del H3, x3
-    out["config3_256x256x128_mixed_kcycle1"] = c3
-    del m3, b3
-    torch.cuda.empty_cache()
-    # configuration 4: the ragged batch, stored autotuner choices
+    return c3
+
+
+def _leg_config4(ll, torch, inputs, dev):
+    """The ragged 512-instance batch with the autotuner's stored choices."""
     spec = inputs.batch_instances(BATCH_COUNT, seed=0)
     ms4 = [torch.tensor(inputs.smooth_field(*q["grid"], seed=q["seed"]).reshape(-1), device=dev) for q in spec]
     al, dts = [q["alpha"] for q in spec], [q["dt"] for q in spec]
@@ -612,12 +629,12 @@ def other_workloads(ll, torch, inputs, dev):
     ms, (st, its, rrs, sts) = _event_ms(torch, lambda: [bstep() for _ in range(2)][-1])
     conv = sum(1 for v in sts if v == ll.LL_OK)
     solved = 3 * sum(int(np.prod(q["grid"])) for q, v in zip(spec, sts) if v == ll.LL_OK)
-    out["config4_batch512_mixed_autotuned"] = {"ms_per_step": ms / 2, "converged": conv, "instances": len(spec),
-                                              "classes_tuned_now": tuned, "groups": B.groups,
-                                              "converged_unknown_solves_per_s": solved / (ms / 2 * 1e-3)}
-    del B, ms4, rhs, xs
-    torch.cuda.empty_cache()
-    # configuration 5: the 96^3 gradient (20 steps, checkpoints every 5)
+    return {"ms_per_step": ms / 2, "converged": conv, "instances": len(spec), "classes_tuned_now": tuned,
+            "groups": B.groups, "converged_unknown_solves_per_s": solved / (ms / 2 * 1e-3)}
+
+
+def _leg_config5(ll, torch, inputs, dev):
+    """The 96^3 gradient (20 steps, checkpoints every 5)."""
     g5, n5 = (96, 96, 96), 96 ** 3
     m0 = torch.tensor(inputs.smooth_field(*g5, seed=0).reshape(-1), device=dev)
     mt = torch.tensor(inputs.smooth_field(*g5, seed=1).reshape(-1), device=dev)
@@ -632,9 +649,7 @@ def other_workloads(ll, torch, inputs, dev):
 
     grad()
     ms, loss = _event_ms(torch, grad)
-    out["config5_grad96_fp64"] = {"ms_per_gradient": ms, "loss": loss,
-                                  "unknown_solves_per_s": 60 * 3 * n5 / (ms * 1e-3)}
-    return out
+    return {"ms_per_gradient": ms, "loss": loss, "unknown_solves_per_s": 60 * 3 * n5 / (ms * 1e-3)}
 
 
 # ---------------------------------------------------------------------------

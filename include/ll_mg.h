@@ -178,6 +178,14 @@ void ll_mg_destroy(ll_mg_hierarchy* H);
 /* Human-readable text of a status code (static storage). */
 const char* ll_status_string(int status);
 
+/* The CUDA runtime call behind the calling thread's last LL_ECUDA or
+ * LL_ENOMEM: error name, its text and the library source line, e.g.
+ * "cudaErrorInvalidConfiguration (invalid configuration argument) at
+ * ll_solver.cu:812"; "" if no call of this thread has failed.  Thread-local
+ * storage, valid until the thread's next failing call; no counterpart in the
+ * paper (a diagnostic). */
+const char* ll_last_cuda_error(void);
+
 /* ---- introspection (for tests and benchmarks) ------------------------------ */
 
 /* Number of levels (level 0 = the grid). */

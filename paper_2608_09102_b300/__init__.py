@@ -34,12 +34,18 @@ EXPORTS = (
     "ll_mg_batch_instance_levels", "ll_mg_batch_destroy", "ll_mg_step_save", "ll_mg_batch_subbatches", "ll_mg_adjoint_setup",
     "ll_mg_step_vjp", "ll_mg_step_host", "ll_fp64_fma_probe", "ll_mg_batch_setup_groups", "ll_mg_batch_groups",
     "ll_mg_batch_instance_group", "ll_mg_batch_autotune", "ll_mg_tune_octave", "ll_mg_tune_lookup",
+    "ll_last_cuda_error",
 )
 
 
 class LLError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__("%s failed: %s (status %d)" % (what, status_string(status), status))
+        msg = "%s failed: %s (status %d)" % (what, status_string(status), status)
+        if status in (LL_ECUDA, LL_ENOMEM):
+            detail = last_cuda_error()
+            if detail:
+                msg += ": " + detail
+        super().__init__(msg)
         self.status = status
 
 
@@ -145,6 +151,7 @@ def load_library():
         "ll_mg_batch_autotune": (i, [i, vp, vp, vp, vp, vp, P, ctypes.c_char_p, vp, P, ip]),
         "ll_mg_tune_octave": (i, [d, d]),
         "ll_mg_tune_lookup": (i, [ctypes.c_char_p, _Grid, d, d, P]),
+        "ll_last_cuda_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -156,6 +163,11 @@ def load_library():
 
 def status_string(status: int) -> str:
     return load_library().ll_status_string(int(status)).decode()
+
+
+def last_cuda_error() -> str:
+    """The CUDA call behind this thread's last LL_ECUDA / LL_ENOMEM ("" if none)."""
+    return load_library().ll_last_cuda_error().decode()
 
 
 def default_params() -> Params:

@@ -423,7 +423,10 @@ void batch_values(ll_mg_batch* B) {
     int bad = 0;
     LL_CU(cudaMemcpyAsync(&bad, B->bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     LL_CU(cudaStreamSynchronize(s));
-    if (bad) throw Status{LL_ECUDA};  // a pattern without its transpose: not a Galerkin level
+    if (bad) {  // a pattern without its transpose: not a Galerkin level
+      note_internal_error("union pattern without its transpose", __FILE__, __LINE__);
+      throw Status{LL_ECUDA};
+    }
   }
   LL_CU(cudaStreamSynchronize(s));
 }
@@ -841,10 +844,12 @@ int batch_create_groups(int count, const double* const* m, const double* alpha, 
 
 // run fn(group, its instance indices) for every group, one host thread per
 // group; returns the first failure (negative status) or the worst outcome
+// (a failing group's CUDA error text is passed on to the calling thread)
 template <typename F>
 int for_groups(ll_mg_batch* B, F fn) {
   int ng = (int)B->groups.size();
   std::vector<int> rc(ng, LL_OK);
+  std::vector<std::string> err(ng);
   std::vector<std::thread> th;
   for (int g = 0; g < ng; ++g)
     th.emplace_back([&, g]() {
@@ -855,11 +860,15 @@ int for_groups(ll_mg_batch* B, F fn) {
       } catch (std::bad_alloc&) {
         rc[g] = LL_ENOMEM;
       }
+      if (rc[g] < 0) err[g] = t_cuda_error;
     });
   for (auto& t : th) t.join();
   int worst = LL_OK;
-  for (int r : rc)
-    if (r < 0) return r;
+  for (int g = 0; g < ng; ++g)
+    if (rc[g] < 0) {
+      snprintf(t_cuda_error, sizeof t_cuda_error, "%s", err[g].c_str());
+      return rc[g];
+    }
   for (int r : rc) worst = std::max(worst, r);
   return worst;
 }

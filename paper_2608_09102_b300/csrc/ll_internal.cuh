@@ -16,10 +16,17 @@ namespace llmg {
 struct Status {
   int code;
 };
+// records the failed call (error name, source line) for ll_last_cuda_error
+void note_cuda_error(cudaError_t e, const char* file, int line);
+// the same for a failed consistency check of the library's own results
+void note_internal_error(const char* what, const char* file, int line);
 #define LL_CU(call)                                                   \
   do {                                                                \
     cudaError_t e_ = (call);                                          \
-    if (e_ != cudaSuccess) throw ::llmg::Status{e_ == cudaErrorMemoryAllocation ? LL_ENOMEM : LL_ECUDA}; \
+    if (e_ != cudaSuccess) {                                          \
+      ::llmg::note_cuda_error(e_, __FILE__, __LINE__);                \
+      throw ::llmg::Status{e_ == cudaErrorMemoryAllocation ? LL_ENOMEM : LL_ECUDA}; \
+    }                                                                 \
   } while (0)
 // called after every kernel launch: checks it and counts it
 void count_launch();

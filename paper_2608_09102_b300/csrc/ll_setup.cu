@@ -649,7 +649,10 @@ void colour_classes(int n, const int* colour, int ncol, const int* key, int nkey
   ccnt.zero(s);
   k_tile_counts<<<ntiles, kSortTile, 0, s>>>(n, colour, key, nkeys, ntiles, cnt);
   LL_LAUNCHED();
-  if (exclusive_scan(cnt, off, (int)nb, s) != n) throw Status{LL_ECUDA};
+  if (exclusive_scan(cnt, off, (int)nb, s) != n) {
+    note_internal_error("bucket counts do not sum to the row count", __FILE__, __LINE__);
+    throw Status{LL_ECUDA};
+  }
   k_tile_scatter<<<ntiles, kSortTile, 0, s>>>(n, colour, key, nkeys, ntiles, off, crow);
   LL_LAUNCHED();
   k_colour_counts<<<cdiv(n, kBlock), kBlock, 0, s>>>(n, colour, ccnt);

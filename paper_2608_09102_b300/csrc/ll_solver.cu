@@ -2,6 +2,7 @@
 // aggregation-multigrid solver (see include/ll_mg.h for the contract).
 #include <limits.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -10,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <string>
 #include <type_traits>
 
 #include "ll_internal.cuh"
@@ -31,6 +33,18 @@ static thread_local long long t_launches = 0;
 void count_launch() {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   ++t_launches;
+}
+
+// the calling thread's last failed CUDA call, for ll_last_cuda_error
+static thread_local char t_cuda_error[160] = "";
+void note_cuda_error(cudaError_t e, const char* file, int line) {
+  const char* base = strrchr(file, '/');
+  snprintf(t_cuda_error, sizeof t_cuda_error, "%s (%s) at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e),
+           base ? base + 1 : file, line);
+}
+void note_internal_error(const char* what, const char* file, int line) {
+  const char* base = strrchr(file, '/');
+  snprintf(t_cuda_error, sizeof t_cuda_error, "%s at %s:%d", what, base ? base + 1 : file, line);
 }
 
 struct CLevel {  // an aggregated level l >= 1 (3x3 BSR operator)
@@ -857,6 +871,12 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
       cfg.attrs = &at;
       cfg.numAttrs = 1;
     };
+    // The kernel's dynamic shared-memory limit is one value for the whole
+    // process, set to what the largest case (N = kGjMax on 8 CTAs) needs:
+    // hierarchies of several host threads (the groups of a batch) set it
+    // concurrently, and a per-N value could be lowered by another thread
+    // between its setting and this thread's launch.
+    constexpr int kGjSmemMax = (int)sizeof(double) * ((kGjMax / 8) * kGjMax + 2 * (kGjMax + 1));
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute at;
     if (H->gj_cluster == 0) {
@@ -864,14 +884,14 @@ void numeric_launch(ll_mg_hierarchy* H, const double* m) {
       config(16, cfg, at);
       int nclusters = 0;
       if (cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-          cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)cfg.dynamicSmemBytes) == cudaSuccess &&
+          cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kGjSmemMax) ==
+              cudaSuccess &&
           cudaOccupancyMaxActiveClusters(&nclusters, k_gj_inverse, &cfg) == cudaSuccess && nclusters > 0)
         H->gj_cluster = 16;
       cudaGetLastError();
     }
     config(H->gj_cluster, cfg, at);
-    LL_CU(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes));
+    LL_CU(cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kGjSmemMax));
     LL_CU(cudaLaunchKernelEx(&cfg, k_gj_inverse, N, (const double*)H->lu.p, H->ainv.p, H->lu_status.p));
     LL_LAUNCHED();
   } else {
@@ -1920,6 +1940,8 @@ const char* ll_status_string(int status) {
     default: return "unknown status";
   }
 }
+
+const char* ll_last_cuda_error(void) { return t_cuda_error; }
 
 int ll_mg_levels(const ll_mg_hierarchy* H) { return H ? H->nlev : -1; }
 

@@ -346,3 +346,27 @@ def test_union_tail_matches_per_class_launches(monkeypatch):
         assert abs(its1[k] - its2[k]) <= 1, (k, its1[k], its2[k])
         if sts1[k] == ll.LL_OK:
             assert np.linalg.norm(xs1[k] - xs2[k]) <= 1e-10 * np.linalg.norm(xs2[k]), k
+
+
+def test_groups_with_different_coarsest_sizes_update_repeatedly():
+    """Groups run on host threads of their own, and every instance's numeric
+    setup ends with the coarsest inverse, whose shared memory depends on the
+    coarsest size.  Groups of different coarsest sizes updated many times
+    over must each succeed and leave the solves unchanged."""
+    cases = [{"grid": (16 + 8 * (k % 3), 16, 1), "h": 1 / 16, "alpha": 0.1, "dt": 2e-3, "kind": "smooth"}
+             for k in range(24)]
+    sizes = [8, 24, 48, 84]  # coarsest cells: 24 to 252 unknowns
+    per = [ll.Params(rtol=1e-10, coarsest_cells=sizes[k % 4], nu_pre=1 + (k // 4) % 2) for k in range(len(cases))]
+    ms = [_field("smooth", c["grid"], k) for k, c in enumerate(cases)]
+    mt = [_t(m) for m in ms]
+    al, dts = [c["alpha"] for c in cases], [c["dt"] for c in cases]
+    B = ll.Batch(mt, al, dts, [c["h"] for c in cases], [c["grid"] for c in cases], params=per)
+    assert B.groups == 8
+    st0, its0, _, _, xs0 = _solve(B, ms, cases)
+    assert st0 == ll.LL_OK
+    for _ in range(40):
+        B.update(mt, al, dts)
+    st, its, _, _, xs = _solve(B, ms, cases)
+    assert st == ll.LL_OK and its == its0
+    for a, b in zip(xs, xs0):
+        assert np.array_equal(a, b)
