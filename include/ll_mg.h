@@ -81,6 +81,15 @@ typedef struct ll_mg_params {
                           kernels: lanes per block row, 4 or 8; 0: by
                           the level's size                            (0)    */
   int coarse_block;    /* their threads per block, 32/64/128/256; 0: 64 (0)  */
+  /* stagnation stop (no counterpart in the paper: a safeguard for instances
+   * whose preconditioned GCR makes no progress): at a restart, stop with
+   * LL_NOT_CONVERGED when the true residual norm exceeds stall_ratio times
+   * its value at the latest restart at least stall_window iterations
+   * earlier.  Restarted GCR that cannot reduce the residual in a cycle
+   * rebuilds nearly the same Krylov space in the next, so such an instance
+   * would spend its remaining iterations up to maxit without progress. */
+  int stall_window;    /* iterations; 0: off                         (0)    */
+  double stall_ratio;  /* > 0 when stall_window > 0                  (0.99) */
 } ll_mg_params;
 
 typedef struct ll_mg_hierarchy ll_mg_hierarchy; /* opaque, library-owned */

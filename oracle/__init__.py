@@ -59,6 +59,8 @@ class _Params(ctypes.Structure):
         ("seed", ctypes.c_uint32),
         ("prec", ctypes.c_int),
         ("kcycle", ctypes.c_int),
+        ("stall_window", ctypes.c_int),
+        ("stall_ratio", ctypes.c_double),
     ]
 
 
@@ -69,6 +71,10 @@ class Params:
     prec: 0 = aggregation V-cycle, 1 = none (plain GCR), 2 = exact (dense LU
     of the whole operator, tiny grids only).
     kcycle: coarse levels 1..kcycle are solved by two inner GCR steps (K-cycle).
+    stall_window, stall_ratio: stagnation stop (not in the paper; 0 = off): at
+    a restart, stop as not converged when the true residual norm exceeds
+    stall_ratio times its value at the latest restart at least stall_window
+    iterations earlier.
     """
 
     rtol: float = 1e-8
@@ -82,11 +88,13 @@ class Params:
     seed: int = 0
     prec: int = 0
     kcycle: int = 0
+    stall_window: int = 0
+    stall_ratio: float = 0.99
 
     def _c(self) -> _Params:
         return _Params(self.rtol, self.maxit, self.restart, self.nu_pre, self.nu_post,
                        self.coarsest_cells, self.max_levels, self.rounds, self.seed & 0xFFFFFFFF,
-                       self.prec, self.kcycle)
+                       self.prec, self.kcycle, self.stall_window, self.stall_ratio)
 
 
 _lib = None

@@ -677,6 +677,12 @@ typedef struct {
   uint32_t seed;
   int prec; /* 0 = V-cycle, 1 = none (plain GCR), 2 = exact dense LU of A */
   int kcycle; /* levels 1..kcycle (not the coarsest) are solved by two inner GCR steps */
+  /* stagnation stop (not in the paper; a safeguard, 0 = off): at a restart,
+   * stop as not converged when the true residual norm exceeds stall_ratio
+   * times its value at the latest restart at least stall_window iterations
+   * earlier */
+  int stall_window;
+  double stall_ratio;
 } orc_params;
 
 typedef struct {
@@ -961,6 +967,10 @@ int orc_solve(const orc_hier *H, const double *b, double *x, double rtol, int *i
   double *gam = (double *)xcalloc((size_t)mmax * mmax, sizeof(double));
   double *a = (double *)xcalloc((size_t)mmax, sizeof(double));
   double *y = (double *)xcalloc((size_t)mmax, sizeof(double));
+  /* true residual norms at the restarts so far, for the stagnation stop */
+  int nbound = 0;
+  int *bound_it = (int *)xmalloc((size_t)(H->prm.maxit + 2) * sizeof(int));
+  double *bound_nr = (double *)xmalloc((size_t)(H->prm.maxit + 2) * sizeof(double));
   if (nb == 0.0) {
     memset(x, 0, (size_t)nn * sizeof(double));
     *iters = 0;
@@ -983,6 +993,13 @@ int orc_solve(const orc_hier *H, const double *b, double *x, double rtol, int *i
       break;
     }
     if (total >= H->prm.maxit) break;
+    if (H->prm.stall_window > 0) {
+      int k = nbound - 1;
+      while (k >= 0 && bound_it[k] > total - H->prm.stall_window) --k;
+      if (k >= 0 && nr > H->prm.stall_ratio * bound_nr[k]) break; /* stagnated: not converged */
+    }
+    bound_it[nbound] = total;
+    bound_nr[nbound++] = nr;
     int m = mmax;
     if (m > H->prm.maxit - total) m = H->prm.maxit - total;
     int done_j = 0, broke = 0;
@@ -1031,6 +1048,8 @@ int orc_solve(const orc_hier *H, const double *b, double *x, double rtol, int *i
   for (int i = 0; i < nn; ++i) r[i] = b[i] - r[i];
   *relres = sqrt(dot(nn, r, r)) / nb;
 done:
+  free(bound_it);
+  free(bound_nr);
   free(r);
   free(Z);
   free(C);

@@ -59,7 +59,7 @@ class _Params(ctypes.Structure):
         ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("coarsest_cells", ctypes.c_int),
         ("max_levels", ctypes.c_int), ("rounds", ctypes.c_int), ("seed", ctypes.c_uint),
         ("precision", ctypes.c_int), ("kcycle", ctypes.c_int), ("coarse_lanes", ctypes.c_int),
-        ("coarse_block", ctypes.c_int),
+        ("coarse_block", ctypes.c_int), ("stall_window", ctypes.c_int), ("stall_ratio", ctypes.c_double),
     ]
 
 
@@ -80,16 +80,18 @@ class Params:
     kcycle: int = 0
     coarse_lanes: int = 0
     coarse_block: int = 0
+    stall_window: int = 0
+    stall_ratio: float = 0.99
 
     def _c(self) -> _Params:
         return _Params(self.rtol, self.maxit, self.restart, self.nu_pre, self.nu_post, self.coarsest_cells,
                        self.max_levels, self.rounds, self.seed & 0xFFFFFFFF, self.precision, self.kcycle,
-                       self.coarse_lanes, self.coarse_block)
+                       self.coarse_lanes, self.coarse_block, self.stall_window, self.stall_ratio)
 
     @classmethod
     def _from_c(cls, c: "_Params") -> "Params":
         return cls(c.rtol, c.maxit, c.restart, c.nu_pre, c.nu_post, c.coarsest_cells, c.max_levels, c.rounds,
-                   c.seed, c.precision, c.kcycle, c.coarse_lanes, c.coarse_block)
+                   c.seed, c.precision, c.kcycle, c.coarse_lanes, c.coarse_block, c.stall_window, c.stall_ratio)
 
 
 _lib = None

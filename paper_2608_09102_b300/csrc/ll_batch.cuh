@@ -546,6 +546,7 @@ struct InstState {
   int done = 0;               // 0 running, 1 finished, 2 finished with a zero right-hand side (x = 0)
   double relres = 0;
   bool paused = false;        // stopped at a restart boundary to continue in a smaller sub-batch
+  StallHist stall;            // true residual norms at its restarts (stagnation stop)
 };
 
 // GCR (Algorithm 1) on every instance in lockstep, restarts of prm.restart;
@@ -587,7 +588,7 @@ void batch_gcr(ll_mg_batch* B, double rtol, std::vector<InstState*>& S, bool com
       } else if (sqrt(rn2) < rtol * bnorm[i]) {
         st = LL_OK;
         done = 1;
-      } else if (total >= B->prm.maxit) {
+      } else if (total >= B->prm.maxit || q.stall.stalled(B->prm, total, sqrt(rn2))) {
         done = 1;
       } else {
         act[i] = 1;
@@ -795,7 +796,8 @@ bool same_params(const ll_mg_params& a, const ll_mg_params& b) {
   return a.rtol == b.rtol && a.maxit == b.maxit && a.restart == b.restart && a.nu_pre == b.nu_pre &&
          a.nu_post == b.nu_post && a.coarsest_cells == b.coarsest_cells && a.max_levels == b.max_levels &&
          a.rounds == b.rounds && a.seed == b.seed && a.precision == b.precision && a.kcycle == b.kcycle &&
-         a.coarse_lanes == b.coarse_lanes && a.coarse_block == b.coarse_block;
+         a.coarse_lanes == b.coarse_lanes && a.coarse_block == b.coarse_block &&
+         a.stall_window == b.stall_window && (a.stall_window == 0 || a.stall_ratio == b.stall_ratio);
 }
 
 int batch_create_groups(int count, const double* const* m, const double* alpha, const double* dt, const double* h,

@@ -1531,6 +1531,25 @@ void run_iteration(ll_mg_hierarchy* H, int j) {
   }
 }
 
+// The true residual norms at the restarts of one solve, for the stagnation
+// stop of ll_mg_params (stall_window, stall_ratio).
+struct StallHist {
+  std::vector<std::pair<int, double>> at;  // (iterations so far, norm)
+  // true: stop (the norm rn at `total` iterations exceeds stall_ratio times
+  // the norm at the latest restart at least stall_window iterations
+  // earlier); otherwise the restart is recorded
+  bool stalled(const ll_mg_params& p, int total, double rn) {
+    if (p.stall_window > 0)
+      for (int k = (int)at.size() - 1; k >= 0; --k)
+        if (at[k].first <= total - p.stall_window) {
+          if (rn > p.stall_ratio * at[k].second) return true;
+          break;
+        }
+    at.push_back({total, rn});
+    return false;
+  }
+};
+
 template <typename T, typename TM>
 int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int* iters, double* relres) {
   cudaStream_t s = H->s;
@@ -1545,6 +1564,7 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
   int total = 0, status = LL_NOT_CONVERGED;
   double bnorm = 0;
   bool current = false;  // the loop ended on the true residual of the final x
+  StallHist stall;
   for (;;) {
     true_residual(H);
     double rn2 = H->h_head[0];
@@ -1564,7 +1584,7 @@ int gcr(ll_mg_hierarchy* H, const double* b_nat, double* x_nat, double rtol, int
       current = true;
       break;
     }
-    if (total >= H->prm.maxit) {
+    if (total >= H->prm.maxit || stall.stalled(H->prm, total, sqrt(rn2))) {
       current = true;
       break;
     }
@@ -1629,7 +1649,8 @@ bool valid_params(const ll_mg_params& p) {
          p.kcycle >= 0 && p.kcycle <= kMaxLevels &&
          (p.coarse_lanes == 0 || p.coarse_lanes == kRowLanes || p.coarse_lanes == 8) &&
          (p.coarse_block == 0 || p.coarse_block == 32 || p.coarse_block == 64 || p.coarse_block == 128 ||
-          p.coarse_block == 256);
+          p.coarse_block == 256) &&
+         p.stall_window >= 0 && (p.stall_window == 0 || (p.stall_ratio > 0 && isfinite(p.stall_ratio)));
 }
 
 // standalone = false: an instance of a batch, solved only through the batch's
@@ -1701,6 +1722,8 @@ void ll_mg_default_params(ll_mg_params* p) {
   p->kcycle = 0;
   p->coarse_lanes = 0;
   p->coarse_block = 0;
+  p->stall_window = 0;
+  p->stall_ratio = 0.99;
 }
 
 static bool valid_problem(double alpha, double dt, double h, ll_grid grid) {
@@ -1930,7 +1953,7 @@ void ll_mg_destroy(ll_mg_hierarchy* H) {
 const char* ll_status_string(int status) {
   switch (status) {
     case LL_OK: return "converged";
-    case LL_NOT_CONVERGED: return "not converged within maxit";
+    case LL_NOT_CONVERGED: return "not converged (maxit reached, or stagnated under the stall test)";
     case LL_BREAKDOWN: return "breakdown (non-finite residual or zero GCR norm)";
     case LL_EINVAL: return "invalid argument";
     case LL_ECUDA: return "CUDA runtime error";

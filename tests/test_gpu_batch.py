@@ -370,3 +370,47 @@ def test_groups_with_different_coarsest_sizes_update_repeatedly():
     assert st == ll.LL_OK and its == its0
     for a, b in zip(xs, xs0):
         assert np.array_equal(a, b)
+
+
+def test_stagnation_stop_single_and_batch():
+    """The optional stagnation stop (stall_window 20, stall_ratio 0.99): two
+    2-D instances whose V-cycle-preconditioned GCR makes no progress (large
+    dt/h^2, small alpha) stop at the restart after 20 iterations, as the
+    oracle's solve with the same stop does, in a single solve and in a batch
+    next to converging instances; the converging instances still match the
+    oracle within 1e-10, and their iterations equal those of the same batch
+    without the stop within one."""
+    stag = [{"grid": (64, 64, 1), "h": 1 / 64, "alpha": 0.01, "dt": 300 / 64 ** 2, "kind": "smooth"},
+            {"grid": (48, 48, 1), "h": 1 / 48, "alpha": 0.02, "dt": 200 / 48 ** 2, "kind": "smooth"}]
+    cases = stag + SMALL[:4]
+    stall = dict(stall_window=20, stall_ratio=0.99)
+    ms = [_field(c["kind"], c["grid"], 5 + k) for k, c in enumerate(cases)]
+    oracle_out = [_oracle_solve(c, m, rtol=1e-10, maxit=200, coarsest_cells=CC, **stall) for c, m in zip(cases, ms)]
+    for k in range(2):
+        assert oracle_out[k][1] == oracle.NOT_CONVERGED and oracle_out[k][2] == 20
+    for k in range(2, len(cases)):
+        assert oracle_out[k][1] == oracle.OK
+    # single solve
+    c, m = stag[0], ms[0]
+    H = ll.Hierarchy(_t(m), c["alpha"], c["dt"], c["h"], c["grid"],
+                     ll.Params(rtol=1e-10, maxit=200, coarsest_cells=CC, **stall))
+    x = torch.zeros(3 * int(np.prod(c["grid"])), dtype=torch.float64, device=DEV)
+    st, it, rr = H.solve(_t(m / c["dt"]), x)
+    assert st == ll.LL_NOT_CONVERGED and it == 20
+    assert abs(rr - oracle_out[0][3]) <= 1e-3
+    # batch, with and without the stop
+    args = ([_t(m) for m in ms], [c["alpha"] for c in cases], [c["dt"] for c in cases], [c["h"] for c in cases],
+            [c["grid"] for c in cases])
+    out = {}
+    for key, kw in (("stall", stall), ("plain", {})):
+        B = ll.Batch(*args, ll.Params(rtol=1e-10, maxit=200, coarsest_cells=CC, **kw))
+        out[key] = _solve(B, ms, cases)
+    st, its, rrs, sts, xs = out["stall"]
+    _, its_p, _, sts_p, _ = out["plain"]
+    for k in range(2):
+        assert sts[k] == ll.LL_NOT_CONVERGED and its[k] == 20 and sts_p[k] == ll.LL_NOT_CONVERGED
+        assert its_p[k] == 200 and abs(rrs[k] - oracle_out[k][3]) <= 1e-3
+    for k in range(2, len(cases)):
+        xo, sto, ito, rro = oracle_out[k]
+        assert sts[k] == ll.LL_OK and abs(its[k] - ito) <= 1 and abs(its[k] - its_p[k]) <= 1, (k, its[k], ito)
+        assert np.linalg.norm(xs[k] - xo) <= 1e-10 * np.linalg.norm(xo), k

@@ -669,3 +669,51 @@ def test_step_initial_approximation_is_the_extrapolated_state():
     assert np.abs(out - ms[-1]).max() <= 1e-13
     assert max(orders) >= 4, orders
     assert max(gains) < 0.5, gains
+
+
+def _stall_stop(hist, restart, window, ratio, maxit):
+    """The stagnation stop restated on a residual history of a run without
+    it: the restarts fall every `restart` iterations; at a restart t the
+    solve stops when hist[t] exceeds `ratio` times its value at the latest
+    restart t0 <= t - window.  Returns the iteration it stops at, or None."""
+    for t in range(restart, maxit, restart):
+        earlier = [t0 for t0 in range(0, t, restart) if t0 <= t - window]
+        if earlier and hist[t] > ratio * hist[earlier[-1]]:
+            return t
+    return None
+
+
+@pytest.mark.parametrize("alpha", [0.01, 0.1, 1.0])
+def test_stagnation_stop(alpha):
+    """The optional stagnation stop (stall_window, stall_ratio; not in the
+    paper): on the random-unit-vector field, where the V-cycle-preconditioned
+    GCR stagnates for alpha <= 0.1 and converges for alpha = 1, the stop
+    point follows from the stated rule applied to the residual history of a
+    run without it, and the stopped solve equals a run with maxit set to that
+    point, bit for bit.  Windows that are not multiples of the restart length
+    and a ratio under which the converging solve stops too check which
+    earlier restart the rule compares with and the direction of the test."""
+    grid, h = (16, 16, 8), 1.0 / 16
+    dt = 6.5536 * h * h
+    m = inputs.random_sphere(*grid, seed=0).reshape(-1)
+    b = m / dt
+    maxit = 60
+    _, st0, it0, rr0, hist = oracle.Hierarchy(grid, h, alpha, dt, m,
+                                              oracle.Params(rtol=1e-8, maxit=maxit)).solve(b, history=True)
+    cases = [(20, 0.99), (15, 0.99), (25, 0.99), (10, 0.5), (20, 1e-9)]
+    stops = []
+    for window, ratio in cases:
+        p = oracle.Params(rtol=1e-8, maxit=maxit, stall_window=window, stall_ratio=ratio)
+        x, st, it, rr = oracle.Hierarchy(grid, h, alpha, dt, m, p).solve(b)
+        t = _stall_stop(hist, 10, window, ratio, min(maxit, it0))
+        stops.append(t)
+        if t is None:  # the stop never fires: the run is unchanged
+            assert (st, it, rr) == (st0, it0, rr0)
+            continue
+        assert st == oracle.NOT_CONVERGED and it == t
+        xr, str_, itr, rrr = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-8, maxit=t)).solve(b)
+        assert itr == t and np.array_equal(x, xr) and rr == rrr
+    if alpha < 1:
+        assert stops[:3] == [20, 20, 30]  # a window of 25 compares iteration 30 with 0
+    else:
+        assert stops[:4] == [None] * 4 and stops[4] == 20
