@@ -35,6 +35,13 @@
  * Errors: a return value of 0 (LL_OK) means success.  Positive values are
  * numerical outcomes with the outputs written (best iterate, true residual).
  * Negative values mean failure with the outputs untouched.
+ *
+ * Threads: one hierarchy, batch or adjoint is used by one host thread at a
+ * time.  Different ones may be used concurrently from different threads (a
+ * batch with per-instance parameters does so itself, one thread per group):
+ * the library's process-wide state is a launch counter (atomic), kernel
+ * attributes that every call sets to the same values, and the error text of
+ * ll_last_cuda_error (per thread).  Graph captures are thread-local.
  */
 #ifndef LL_MG_H
 #define LL_MG_H
@@ -45,7 +52,8 @@ extern "C" {
 
 /* ---- status codes ------------------------------------------------------- */
 #define LL_OK 0
-#define LL_NOT_CONVERGED 1    /* maxit reached; x = last iterate */
+#define LL_NOT_CONVERGED 1    /* maxit reached, or the stagnation stop of
+                                 ll_mg_params; x = last iterate */
 #define LL_BREAKDOWN 2        /* non-finite residual or gamma_jj = 0 in GCR */
 #define LL_EINVAL (-1)        /* bad argument (null pointer, dt <= 0, ...) */
 #define LL_ECUDA (-2)         /* a CUDA runtime call failed */
