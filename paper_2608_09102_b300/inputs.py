@@ -95,9 +95,11 @@ def trivial_state(nx: int, ny: int = 1, nz: int = 1):
 
 def c1_state(nx: int, ny: int = 1, nz: int = 1, theta: float = 0.01):
     """C1 state: [cos(g) sin(0.01), sin(g) sin(0.01), cos(0.01)], g the
-    product of cos(pi x), cos(pi y), cos(pi z)."""
+    product of cos(pi x), cos(pi y), cos(pi z) over the grid's dimensions
+    (a direction of one cell has no factor: its cell centre 1/2 would make g
+    vanish, i.e. a constant field)."""
     X, Y, Z = _coords(nx, ny, nz)
-    g = np.cos(np.pi * X) * np.cos(np.pi * Y) * np.cos(np.pi * Z)
+    g = np.cos(np.pi * X) * (np.cos(np.pi * Y) if ny > 1 else 1.0) * (np.cos(np.pi * Z) if nz > 1 else 1.0)
     v = np.stack([np.cos(g) * np.sin(theta), np.sin(g) * np.sin(theta), np.cos(theta) + 0.0 * g])
     return _normalise(v)
 

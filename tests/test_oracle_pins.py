@@ -717,3 +717,44 @@ def test_stagnation_stop(alpha):
         assert stops[:3] == [20, 20, 30]  # a window of 25 compares iteration 30 with 0
     else:
         assert stops[:4] == [None] * 4 and stops[4] == 20
+
+
+# the paper's closed-form initial states (Sec. 4.4) and the symmetries that
+# the exchange-only step must keep: the cell-centred Neumann Laplacian
+# commutes with the grid's mirrors, and the step with proper rotations of
+# every spin, so a state with m(mirror p) = R m(p) keeps it at every step
+_ROT_X = np.array([1.0, -1.0, -1.0])  # rotation by pi about the x axis
+
+
+def _paper_state_symmetries(M, name):
+    """Largest deviation from each symmetry the state has (M: (3, nz, ny, nx))."""
+    R = _ROT_X[:, None, None, None]
+    if name == "s":  # (0,1,0) | (1,0,0) | (0,1,0) across x: mirror symmetric
+        return [np.abs(M[..., ::-1] - M).max()]
+    if name == "c":  # (0,1,0) | (1,0,0) | (0,-1,0): the mirror in x turns m2
+        return [np.abs(R * M[..., ::-1] - M).max()]
+    if name == "flower":  # as C, and the same about the mirror in y
+        return [np.abs(R * M[..., ::-1] - M).max(), np.abs(R * M[:, :, ::-1, :] - M).max()]
+    # c1: g = cos(pi x) cos(pi y) [cos(pi z)] is even under (x, y) -> (1-x, 1-y)
+    return [np.abs(M[:, :, ::-1, ::-1] - M).max()]
+
+
+@pytest.mark.parametrize("grid", [(40, 30, 1), (16, 12, 8)])
+@pytest.mark.parametrize("name", ["c1", "s", "c", "flower"])
+def test_paper_initial_states_keep_their_symmetries(name, grid):
+    """Three steps from each closed-form initial state of Sec. 4.4 (C1, S,
+    C, Flower) converge, leave every spin of unit length, change the field,
+    and keep the state's mirror symmetries to the solve's accuracy (a wrong
+    neighbour at a boundary, or an operator term that does not commute with
+    the mirrors, breaks them)."""
+    nx, ny, nz = grid
+    h = 1.0 / nx
+    dt, alpha = 8 * h * h, 0.05
+    m0 = getattr(inputs, name + "_state")(nx, ny, nz).reshape(-1)
+    M0 = m0.reshape(3, nz, ny, nx)
+    assert max(_paper_state_symmetries(M0, name)) <= 1e-15  # C1: cosines of mirrored points round apart
+    m, its, rrs, st = oracle.step(m0, 3, grid, h, alpha, dt, oracle.Params(rtol=1e-12))
+    assert st == oracle.OK and min(its) > 0
+    assert np.abs(m - m0).max() > 1e-3
+    np.testing.assert_allclose(np.linalg.norm(m.reshape(3, -1), axis=0), 1.0, atol=1e-14)
+    assert max(_paper_state_symmetries(m.reshape(3, nz, ny, nx), name)) <= 1e-9
