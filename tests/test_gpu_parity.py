@@ -542,3 +542,25 @@ def test_random_sphere_full_size_kcycle_converges(c3_field, alpha):
         print("random sphere 256x256x128, alpha %g, K-cycle: iterations to 1e-8 bf16 %d; to 1e-10 fp64 %d, "
               "bf16 %d; error vs fp64 %.2e" % (alpha, it, it64, it2, err))
         assert err <= 1e-8
+
+
+@pytest.mark.parametrize("grid", [(40, 30, 1), (16, 12, 8)])
+@pytest.mark.parametrize("name", ["c1", "s", "c", "flower"])
+def test_paper_initial_states_match_oracle(name, grid):
+    """Three GPU time steps from each closed-form initial state of Sec. 4.4
+    equal the oracle's within 1e-10 (iterations within one) and keep the
+    state's mirror symmetries."""
+    from tests.test_oracle_pins import _paper_state_symmetries
+
+    nx, ny, nz = grid
+    h = 1.0 / nx
+    dt, alpha = 8 * h * h, 0.05
+    m0 = getattr(inputs, name + "_state")(nx, ny, nz).reshape(-1)
+    mo, ito, rro, sto = oracle.step(m0, 3, grid, h, alpha, dt, oracle.Params(rtol=1e-12))
+    mg = _t(m0)
+    st, its, rrs = ll.step(mg, 3, alpha, dt, h, grid, ll.Params(rtol=1e-12))
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert np.all(np.abs(np.array(its) - ito) <= 1), (its, ito)
+    m = _np(mg)
+    assert np.abs(m - mo).max() <= 1e-10
+    assert max(_paper_state_symmetries(m.reshape(3, nz, ny, nx), name)) <= 1e-9
