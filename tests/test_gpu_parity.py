@@ -564,3 +564,55 @@ def test_paper_initial_states_match_oracle(name, grid):
     m = _np(mg)
     assert np.abs(m - mo).max() <= 1e-10
     assert max(_paper_state_symmetries(m.reshape(3, nz, ny, nx), name)) <= 1e-9
+
+
+# degenerate shapes and the undamped scheme: grids one cell wide in x (the
+# red-black slots of level 0 then hold one cell per row, half of them
+# padding), 1-D along y or z, the smallest grid (two cells, one level), and
+# alpha = 0 (C(m) = [m]x only); (grid, alpha, dt/h^2, coarsest_cells)
+DEGENERATE = [((1, 40, 1), 0.1, 4.0, 4), ((1, 1, 48), 0.3, 4.0, 4), ((1, 9, 7), 0.05, 4.0, 4),
+              ((2, 1, 1), 0.1, 4.0, 64), ((24, 20, 1), 0.0, 4.0, 8), ((10, 8, 6), 0.0, 2.0, 8)]
+
+
+@pytest.mark.parametrize("grid,alpha,ratio,cc", DEGENERATE)
+def test_degenerate_shapes_and_undamped(grid, alpha, ratio, cc):
+    """Aggregates and colours bit for bit, the solve within 1e-10 of the
+    oracle's (iterations within one) and one time step within 1e-10."""
+    h = 1.0 / max(grid)
+    dt = ratio * h * h
+    m = inputs.smooth_field(*grid, seed=1).reshape(-1)
+    O = oracle.Hierarchy(grid, h, alpha, dt, m, oracle.Params(rtol=1e-12, coarsest_cells=cc))
+    G = ll.Hierarchy(_t(m), alpha, dt, h, grid, ll.Params(rtol=1e-12, coarsest_cells=cc))
+    assert G.levels == O.nlevels
+    for l in range(O.nlevels):
+        assert G.level_cells(l) == O.cells(l)
+        assert np.array_equal(G.colours(l), O.colours(l)), l
+        if l < O.nlevels - 1:
+            assert np.array_equal(G.aggregates(l), O.agg(l)), l
+    b = m / dt
+    xo, sto, ito, rro = O.solve(b, np.zeros_like(b))
+    x = torch.zeros(b.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(b), x)
+    assert st == ll.LL_OK and sto == oracle.OK
+    assert abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(_np(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+    mo, _, _, _ = oracle.step(m, 1, grid, h, alpha, dt, oracle.Params(rtol=1e-12, coarsest_cells=cc))
+    mg = _t(m)
+    st, its, rrs = ll.step(mg, 1, alpha, dt, h, grid, ll.Params(rtol=1e-12, coarsest_cells=cc))
+    assert st == ll.LL_OK and np.abs(_np(mg) - mo).max() <= 1e-10
+
+
+def test_undamped_3d_stagnation_matches_oracle():
+    """The undamped scheme at dt/h^2 = 4 on a 10 x 8 x 6 grid: the
+    V-cycle-preconditioned GCR stagnates near a relative residual of 1 in
+    the oracle, and the GPU solve ends the same way."""
+    grid, h = (10, 8, 6), 0.1
+    dt = 4 * h * h
+    m = inputs.smooth_field(*grid, seed=1).reshape(-1)
+    p = dict(rtol=1e-12, coarsest_cells=8, maxit=60)
+    xo, sto, ito, rro = oracle.Hierarchy(grid, h, 0.0, dt, m, oracle.Params(**p)).solve(m / dt)
+    G = ll.Hierarchy(_t(m), 0.0, dt, h, grid, ll.Params(**p))
+    x = torch.zeros(m.size, dtype=torch.float64, device=DEV)
+    st, it, rr = G.solve(_t(m / dt), x)
+    assert sto == oracle.NOT_CONVERGED and st == ll.LL_NOT_CONVERGED and it == ito == 60
+    assert rro > 0.5 and rr > 0.5 and abs(rr - rro) <= 0.05
