@@ -55,6 +55,17 @@ def test_status_strings(lib):
     for st in (0, 1, 2, -1, -2, -3, -4, -5):
         assert ll.status_string(st)
     assert ll.status_string(12345) == "unknown status"
+    import threading
+
+    seen = []  # a fresh thread: no CUDA call of it has failed, so no error text
+    t = threading.Thread(target=lambda: seen.append(ll.last_cuda_error()))
+    t.start()
+    t.join()
+    assert seen == [""]
+    d = ll.Params()  # the binding's defaults mirror the library's
+    c = ll._Params()
+    ll.load_library().ll_mg_default_params(ctypes.byref(c))
+    assert (c.stall_window, c.stall_ratio) == (d.stall_window, d.stall_ratio) == (0, 0.99)
 
 
 def test_invalid_arguments_are_rejected_on_the_host(lib):
@@ -72,6 +83,10 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.ll_mg_setup(dummy, 0.1, 1e-3, 0.1, g, ctypes.byref(bad), None, ctypes.byref(out)) == ll.LL_EINVAL
     bad = ll.Params(kcycle=-1)._c()
     assert lib.ll_mg_setup(dummy, 0.1, 1e-3, 0.1, g, ctypes.byref(bad), None, ctypes.byref(out)) == ll.LL_EINVAL
+    for kw in (dict(stall_window=-1), dict(stall_window=20, stall_ratio=0.0),
+               dict(stall_window=20, stall_ratio=float("nan"))):
+        bad = ll.Params(**kw)._c()
+        assert lib.ll_mg_setup(dummy, 0.1, 1e-3, 0.1, g, ctypes.byref(bad), None, ctypes.byref(out)) == ll.LL_EINVAL
     assert lib.ll_mg_solve(None, dummy, dummy, 0.0, None, None) == ll.LL_EINVAL
     assert lib.ll_step(None, 1, 0.1, 1e-3, 0.1, g, None, None, None, None) == ll.LL_EINVAL
     assert lib.ll_mg_levels(None) == -1

@@ -38,3 +38,45 @@ def test_reference_arm_other_ranks_do_nothing():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "0"], capture_output=True, text=True, timeout=120, env=env, cwd=ROOT)
     assert out.returncode == 0 and "{" not in out.stdout
+
+
+def test_other_workloads_record_a_failing_leg(monkeypatch):
+    """A workload of the list whose library call fails is recorded with the
+    error (the status and the failing CUDA call) and the others still run,
+    so that the bench line is printed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2608_09102_b300 as ll
+
+    class _Cuda:
+        @staticmethod
+        def synchronize():
+            pass
+
+        @staticmethod
+        def empty_cache():
+            pass
+
+    class _Torch:
+        cuda = _Cuda
+
+    ran = []
+
+    def ok(name):
+        def leg(ll_, torch, inputs, dev):
+            ran.append(name)
+            return {"ran": name}
+        return leg
+
+    def fails(ll_, torch, inputs, dev):
+        ran.append("config4")
+        raise ll.LLError(ll.LL_ECUDA, "ll_mg_batch_update")
+
+    monkeypatch.setattr(bench, "_leg_config1", ok("config1"))
+    monkeypatch.setattr(bench, "_leg_config3", ok("config3"))
+    monkeypatch.setattr(bench, "_leg_config4", fails)
+    monkeypatch.setattr(bench, "_leg_config5", ok("config5"))
+    out = bench.other_workloads(ll, _Torch, None, None)
+    assert ran == ["config1", "config3", "config4", "config5"]
+    assert "ll_mg_batch_update failed: CUDA runtime error" in out["config4_batch512_mixed_autotuned"]["error"]
+    assert out["config5_grad96_fp64"] == {"ran": "config5"}
