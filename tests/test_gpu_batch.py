@@ -372,14 +372,23 @@ def test_groups_with_different_coarsest_sizes_update_repeatedly():
         assert np.array_equal(a, b)
 
 
-def test_stagnation_stop_single_and_batch():
+@pytest.mark.parametrize("precision", [ll.LL_FP64, ll.LL_MIXED_FP32])
+def test_stagnation_stop_single_and_batch(precision):
     """The optional stagnation stop (stall_window 20, stall_ratio 0.99): two
     2-D instances whose V-cycle-preconditioned GCR makes no progress (large
     dt/h^2, small alpha) stop at the restart after 20 iterations, as the
     oracle's solve with the same stop does, in a single solve and in a batch
     next to converging instances; the converging instances still match the
-    oracle within 1e-10, and their iterations equal those of the same batch
-    without the stop within one."""
+    oracle within 1e-10 (float32 V-cycle: 1e-8, the mixed path's bound), and
+    their iterations equal those of the same batch without the stop within
+    one."""
+    tol = 1e-10 if precision == ll.LL_FP64 else 1e-8
+    # with the float32 V-cycle, GCR on the stagnating instances may also end
+    # in a breakdown (a zero or non-finite image) before the stop's restart
+    bad = (ll.LL_NOT_CONVERGED,) if precision == ll.LL_FP64 else (ll.LL_NOT_CONVERGED, ll.LL_BREAKDOWN)
+
+    def stopped(st, it):
+        return st in bad and it <= 20 and (st != ll.LL_NOT_CONVERGED or it == 20)
     stag = [{"grid": (64, 64, 1), "h": 1 / 64, "alpha": 0.01, "dt": 300 / 64 ** 2, "kind": "smooth"},
             {"grid": (48, 48, 1), "h": 1 / 48, "alpha": 0.02, "dt": 200 / 48 ** 2, "kind": "smooth"}]
     cases = stag + SMALL[:4]
@@ -393,24 +402,30 @@ def test_stagnation_stop_single_and_batch():
     # single solve
     c, m = stag[0], ms[0]
     H = ll.Hierarchy(_t(m), c["alpha"], c["dt"], c["h"], c["grid"],
-                     ll.Params(rtol=1e-10, maxit=200, coarsest_cells=CC, **stall))
+                     ll.Params(rtol=1e-10, maxit=200, coarsest_cells=CC, precision=precision, **stall))
     x = torch.zeros(3 * int(np.prod(c["grid"])), dtype=torch.float64, device=DEV)
     st, it, rr = H.solve(_t(m / c["dt"]), x)
-    assert st == ll.LL_NOT_CONVERGED and it == 20
-    assert abs(rr - oracle_out[0][3]) <= 1e-3
+    assert stopped(st, it), (st, it)
+    if st == ll.LL_NOT_CONVERGED:
+        assert abs(rr - oracle_out[0][3]) <= 1e-3
     # batch, with and without the stop
     args = ([_t(m) for m in ms], [c["alpha"] for c in cases], [c["dt"] for c in cases], [c["h"] for c in cases],
             [c["grid"] for c in cases])
     out = {}
     for key, kw in (("stall", stall), ("plain", {})):
-        B = ll.Batch(*args, ll.Params(rtol=1e-10, maxit=200, coarsest_cells=CC, **kw))
+        B = ll.Batch(*args, ll.Params(rtol=1e-10, maxit=200, coarsest_cells=CC, precision=precision, **kw))
         out[key] = _solve(B, ms, cases)
     st, its, rrs, sts, xs = out["stall"]
     _, its_p, _, sts_p, _ = out["plain"]
     for k in range(2):
-        assert sts[k] == ll.LL_NOT_CONVERGED and its[k] == 20 and sts_p[k] == ll.LL_NOT_CONVERGED
-        assert its_p[k] == 200 and abs(rrs[k] - oracle_out[k][3]) <= 1e-3
+        assert stopped(sts[k], its[k]) and sts_p[k] in bad, (k, sts[k], its[k], sts_p[k])
+        if sts_p[k] == ll.LL_NOT_CONVERGED:
+            assert its_p[k] == 200
+        if sts[k] == ll.LL_NOT_CONVERGED:
+            assert abs(rrs[k] - oracle_out[k][3]) <= 1e-3
     for k in range(2, len(cases)):
         xo, sto, ito, rro = oracle_out[k]
-        assert sts[k] == ll.LL_OK and abs(its[k] - ito) <= 1 and abs(its[k] - its_p[k]) <= 1, (k, its[k], ito)
-        assert np.linalg.norm(xs[k] - xo) <= 1e-10 * np.linalg.norm(xo), k
+        assert sts[k] == ll.LL_OK and abs(its[k] - its_p[k]) <= 1, (k, its[k], its_p[k])
+        if precision == ll.LL_FP64:
+            assert abs(its[k] - ito) <= 1, (k, its[k], ito)
+        assert np.linalg.norm(xs[k] - xo) <= tol * np.linalg.norm(xo), k
